@@ -1,0 +1,401 @@
+"""Benchmark of the TOCAB hot path on GB300.
+
+Headline (one JSON line on rank 0): pull PageRank with TOCAB, 20 iterations, damping 0.85,
+on a seeded R-MAT graph of scale 24 (edge factor 16, a=.57 b=.19 c=.19, relabelled,
+self loops and duplicates removed).  metric = GTEPS = 20 * E / (time of one 20-iteration
+run).  A "step" is one such run with the graph already resident in HBM.  The column
+indices (about 1 GB) are larger than the 135 MB L2, so every step streams from HBM.
+
+Also reported: unblocked pull, TOCAB/unblocked push and pull BFS (64 sources, symmetrised
+R-MAT 24) as variants, the roofline of the dominant kernel (the pull gather), the e2e
+number through the C ABI with host buffers, the FP64 oracle on the host cores
+(cpu_baseline), and SM clocks sampled during the timed region.
+
+--impl reference times the FP64 CPU oracle (the only reference implementation of the
+method) on the same graph, on a bounded sample of iterations.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import graphgen as gg  # noqa: E402
+
+ITERS = 20
+DAMPING = 0.85
+METRIC = "PageRank/BFS GTEPS on 1 GB300, TOCAB vs unblocked; % of HBM-bound roofline"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="tocab", choices=["tocab", "reference"])
+    ap.add_argument("--scale", type=int, default=24)
+    ap.add_argument("--blocks", type=int, default=0, help="TOCAB block count (0 = from L2 size)")
+    ap.add_argument("--bfs-sources", type=int, default=64)
+    ap.add_argument("--no-variants", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------------------------------------
+def dist_init(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
+
+
+# --------------------------------------------------------------------------------------------
+def make_graph(scale: int, device: str):
+    return gg.rmat(scale, device=device)
+
+
+def time_runs(fn, steps: int, stream) -> list[float]:
+    """Per-step device times (ms) of fn() with CUDA events on `stream`."""
+    out = []
+    for _ in range(steps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record(stream)
+        fn()
+        e.record(stream)
+        e.synchronize()
+        out.append(s.elapsed_time(e))
+    return out
+
+
+def bench_tocab(args, world, rank, local):
+    import paper_1904_02241_gb300 as T
+    T.lib()
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream()
+    t0 = time.time()
+    g = make_graph(args.scale, "cuda")
+    V, E = g.V, g.E
+    gen_s = time.time() - t0
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=V)
+    P = T.tocab_partition(G, T.TC_PULL, args.blocks)
+    torch.cuda.synchronize()
+    out = torch.empty(V, dtype=torch.float32, device=dev)
+
+    def step():
+        T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    start = torch.cuda.Event(enable_timing=True)
+    end = torch.cuda.Event(enable_timing=True)
+    start.record(stream)
+    for _ in range(args.steps):
+        step()
+    end.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    ms_total = start.elapsed_time(end)
+    # per-kernel durations over an identical set of steps, timed by the library with events
+    prof = [T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out, profile=True, return_stats=True)[1]
+            for _ in range(max(3, min(args.steps, 5)))]
+    clk = clocks.stop()
+    ms_step = max_over_ranks(ms_total / args.steps, world)
+    edges_all = sum_over_ranks(float(E) * ITERS, world)
+    value = edges_all / (ms_step * 1e-3) / 1e9
+
+    gather_ms = statistics.median(p.ms_gather for p in prof) / ITERS
+    merge_ms = statistics.median(p.ms_merge for p in prof) / ITERS
+    launches_per_step = prof[0].launches
+
+    # algorithmic bytes of one gather launch (Alg. 4 over all blocks): colidx 4E, local
+    # row offsets 4(R+1), contributions read once 4V, partial sums written 4R
+    R = P.num_rows
+    gather_bytes = 4 * E + 4 * (R + 1) + 4 * V + 4 * R
+    peak, peak_kind = load_peaks()
+    achieved = gather_bytes / (gather_ms * 1e-3) / 1e9
+    bmin = 4 * E + 4 * (V + 1) + 4 * V + 4 * V + 4 * V
+    res = {
+        "metric": METRIC,
+        "value": round(value, 3),
+        "unit": "GTEPS",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"pagerank_pull_tocab rmat{args.scale} ef16 20 iters d=0.85",
+                   "graph": f"rmat{args.scale}", "V": V, "E": E, "iters": ITERS,
+                   "blocks": P.num_blocks, "block_width": P.block_width, "local_rows": R,
+                   "l2": "inputs larger than L2 (colidx %.2f GB vs 135 MB L2); no flush" % (4 * E / 1e9),
+                   "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 2)},
+        "roofline": {"bound": "hbm", "kernel": "k_pull_gather<false>", "achieved": round(achieved, 1),
+                     "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "traffic": None, "algorithmic_bytes": gather_bytes,
+                     "gather_ms": round(gather_ms, 4), "merge_ms": round(merge_ms, 4),
+                     "iteration_bmin_frac": round(bmin / (ms_step / ITERS * 1e-3) / 1e9 / peak, 4)},
+        "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    del prof
+    return res, (g, G, P, out, stream)
+
+
+def variants(args, ctx, world):
+    """Unblocked pull, push (unblocked and TOCAB), pull BFS: GTEPS of each."""
+    import paper_1904_02241_gb300 as T
+    g, G, P, out, stream = ctx
+    E = g.E
+    steps = max(3, min(args.steps, 5))
+    res = {}
+
+    def run(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize()
+        return statistics.median(time_runs(fn, steps, stream))
+
+    ms = run(lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out))
+    res["pull_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res["pull_tocab_blocks"] = P.num_blocks
+    Pp = T.tocab_partition(G, T.TC_PUSH, args.blocks)
+    ms = run(lambda: T.pagerank_push(G, Pp, damping=DAMPING, iters=ITERS, out=out))
+    res["push_tocab_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    ms = run(lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))
+    res["push_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    del Pp
+    # BFS on the symmetrised graph, 64 seeded sources (TEPS counts each undirected edge once)
+    gs = gg.symmetrize(g)
+    Gs = T.graph_load_csr(gs.rowptr, gs.colidx, V=gs.V)
+    Ps = T.tocab_partition(Gs, T.TC_PULL, args.blocks)
+    lv = torch.empty(gs.V, dtype=torch.int32, device="cuda")
+    srcs = gg.sources(gs, args.bfs_sources, seed=13)
+    for thr, key in [(0.05, "bfs_tocab"), (-1.0, "bfs_unblocked")]:
+        T.bfs_pull(Gs, Ps, srcs[0], tocab_threshold=thr, out=lv)
+        torch.cuda.synchronize()
+        tot_ms, tot_edges = 0.0, 0
+        for s in srcs:
+            t0 = torch.cuda.Event(enable_timing=True)
+            t1 = torch.cuda.Event(enable_timing=True)
+            t0.record(stream)
+            _, st = T.bfs_pull(Gs, Ps, s, tocab_threshold=thr, out=lv, return_stats=True)
+            t1.record(stream)
+            t1.synchronize()
+            tot_ms += t0.elapsed_time(t1)
+            tot_edges += st.edges_reached // 2
+        res[key + "_gteps"] = round(tot_edges / (tot_ms * 1e-3) / 1e9, 2)
+    res["bfs_graph"] = {"V": gs.V, "E_directed": gs.E, "sources": len(srcs)}
+    return res
+
+
+def e2e(args, ctx):
+    """Same metric through the C ABI from host buffers: H2D of the CSR, graph load
+    (validation + transpose), partition, 20 iterations, D2H of the ranks."""
+    import paper_1904_02241_gb300 as T
+    g, G, P, out, stream = ctx
+    rp_h = g.rowptr.cpu().pin_memory()
+    ci_h = g.colidx.cpu().pin_memory()
+    out_h = torch.empty(g.V, dtype=torch.float32).pin_memory()
+    times = []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        G2 = T.graph_load_csr(rp_h, ci_h, V=g.V)
+        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks)
+        T.pagerank_pull(G2, P2, damping=DAMPING, iters=ITERS, out=out_h)
+        t1.record(stream)
+        t1.synchronize()
+        times.append(t0.elapsed_time(t1))
+        del P2, G2
+    ms = statistics.median(times)
+    return {"value": round(g.E * ITERS / (ms * 1e-3) / 1e9, 3), "unit": "GTEPS",
+            "h2d_bytes_per_step": int(rp_h.numel() * 4 + ci_h.numel() * 4),
+            "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": round(ms, 3),
+            "includes": "H2D CSR + load/transpose + partition + 20 iters + D2H ranks"}
+
+
+def cpu_baseline(g, budget_s: float):
+    """The FP64 oracle (Alg. 1) on the host cores, on a bounded number of iterations."""
+    import oracle
+    oracle.build()
+    rp, ci = g.rowptr.cpu().numpy(), g.colidx.cpu().numpy()
+    tr = oracle.transpose(g.V, rp, ci)
+    cores = os.cpu_count() or 1
+    t0 = time.time()
+    oracle.pagerank_pull(g.V, rp, ci, iters=1, nthreads=cores, transposed=tr)
+    one = time.time() - t0
+    iters = max(1, min(ITERS, int(budget_s / max(one, 1e-3))))
+    t0 = time.time()
+    oracle.pagerank_pull(g.V, rp, ci, iters=iters, nthreads=cores, transposed=tr)
+    dt = time.time() - t0
+    return {"value": round(g.E * iters / dt / 1e9, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+            "sample": f"{iters} of the 20 FP64 pull iterations on the same rmat graph "
+                      f"(V={g.V}, E={g.E}), OpenMP over destinations"}
+
+
+def reference_arm(args, world, rank):
+    if rank != 0:
+        return
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    g = make_graph(args.scale, dev)
+    g = gg.CSRGraph(g.V, g.rowptr.cpu(), g.colidx.cpu(), g.name)
+    import oracle
+    oracle.build()
+    rp, ci = g.rowptr.numpy(), g.colidx.numpy()
+    tr = oracle.transpose(g.V, rp, ci)
+    cores = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle.pagerank_pull(g.V, rp, ci, iters=1, nthreads=cores, transposed=tr)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.time()
+        oracle.pagerank_pull(g.V, rp, ci, iters=1, nthreads=cores, transposed=tr)
+        times.append(time.time() - t0)
+    sec_iter = statistics.median(times)
+    value = g.E / sec_iter / 1e9
+    sample = f"1 FP64 pull iteration per step (of the 20) on rmat{args.scale} (V={g.V}, E={g.E})"
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_iter * 1e3 * ITERS, 2),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"pagerank_pull rmat{args.scale} ef16 20 iters d=0.85 (FP64 CPU oracle)",
+                   "graph": f"rmat{args.scale}", "V": g.V, "E": g.E, "iters": ITERS},
+        "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    args = parse()
+    world, rank, local = dist_init(args)
+    if args.impl == "reference":
+        reference_arm(args, world, rank)
+        return
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the TOCAB path has no CPU fallback)")
+    res, ctx = bench_tocab(args, world, rank, local)
+    if rank == 0:
+        if not args.no_variants:
+            res["variants"] = variants(args, ctx, world)
+        res["e2e"] = e2e(args, ctx)
+        if world == 1:
+            res["cpu_baseline"] = cpu_baseline(ctx[0], args.cpu_seconds)
+        print(json.dumps(res), flush=True)
+    barrier(world)
+
+
+if __name__ == "__main__":
+    main()

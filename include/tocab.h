@@ -1,0 +1,225 @@
+/*
+ * tocab.h -- C ABI of the GB300 (sm_103a) throughput-oriented cache blocking (TOCAB)
+ * library: pull/push PageRank and topology-driven pull BFS over CSR graphs, after
+ * "GraphCage: Cache Aware Graph Processing on GPUs" (Chen, 2019).
+ *
+ * Conventions for every entry point
+ *   - Return value: TC_OK (0) on success, a negative TC_ERR_* code otherwise; no
+ *     exception or longjmp crosses this boundary.  On failure the outputs are
+ *     unspecified and tc_last_error() returns a message for the calling thread.
+ *   - Pointers are plain host or device addresses; where an argument can be either,
+ *     a TC_MEM_HOST / TC_MEM_DEVICE flag says which.  Device pointers must belong to
+ *     the device that is current when the call is made.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     All device work of a call is ordered on that stream; calls that return host data
+ *     synchronise it.
+ *   - The caller owns every input and output buffer.  Handles (tc_graph, tc_part) and
+ *     their device scratch are owned by the library and released by the *_free calls.
+ *     A handle may be used by one call at a time (calls on one handle must not overlap).
+ *   - Vertex IDs and edge offsets are int32: V < 2^31 and E < 2^31, else
+ *     TC_ERR_UNSUPPORTED.
+ */
+#ifndef TOCAB_H
+#define TOCAB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------- */
+#define TC_OK                  0
+#define TC_ERR_INVALID_ARG    (-1)   /* bad pointer, size, flag or parameter            */
+#define TC_ERR_INVALID_GRAPH  (-2)   /* CSR not monotone, column out of range, ...       */
+#define TC_ERR_OOM            (-3)   /* device or host allocation failed                 */
+#define TC_ERR_CUDA           (-4)   /* a CUDA runtime call failed (text in last error)  */
+#define TC_ERR_TIMEOUT        (-5)   /* a bounded device-side wait gave up               */
+#define TC_ERR_UNSUPPORTED    (-6)   /* size beyond int32 limits or unsupported option   */
+
+/* ---- flags --------------------------------------------------------------------------- */
+#define TC_MEM_HOST     0
+#define TC_MEM_DEVICE   1
+
+#define TC_PULL         0            /* blocks = source ranges of G^T (column blocking)  */
+#define TC_PUSH         1            /* blocks = destination ranges of G (row blocking)   */
+
+#define TC_DANGLING_REDISTRIBUTE 0   /* dangling rank mass spread uniformly (sum = 1)     */
+#define TC_DANGLING_DROP         1   /* Alg. 1 read literally: dangling mass is dropped   */
+
+typedef struct tc_graph tc_graph;    /* opaque: a graph resident on one device           */
+typedef struct tc_part  tc_part;     /* opaque: a TOCAB partition of a tc_graph           */
+
+/* ---- status ---------------------------------------------------------------------------- */
+/* Static text for a status code. */
+const char *tc_status_string(int status);
+/* Message of the last failed call on this thread ("" if none). */
+const char *tc_last_error(void);
+/* Library version as 10000*major + 100*minor + patch. */
+int tc_version(void);
+
+/* ---- graph ----------------------------------------------------------------------------- */
+/*
+ * tc_graph_load_csr -- copy a directed graph G = (V, E) given as an out-edge CSR
+ * (rowptr int32[V+1], colidx int32[E]; row u lists the destinations of u's out-edges)
+ * onto the current device, validate it, and build on the device the transpose G^T
+ * (in-edge CSR, in-rows sorted by source) and the per-vertex out-degree reciprocals.
+ * Sec. 2.1 (CSR, Fig. 1b); Alg. 1 pulls over G^T, Alg. 2 pushes over G.
+ *   rowptr/colidx : host or device arrays per `mem`; not retained after the call.
+ *   E             : must equal rowptr[V]; duplicates and self loops are kept as given.
+ *   out           : receives the new handle (free with tc_graph_free).
+ * Errors: TC_ERR_INVALID_ARG (null pointer, V < 0, E < 0), TC_ERR_INVALID_GRAPH
+ * (rowptr[0] != 0, rowptr not monotone, rowptr[V] != E, colidx outside [0, V)),
+ * TC_ERR_UNSUPPORTED (V or E >= 2^31), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_graph_load_csr(int32_t V, int64_t E, const int32_t *rowptr, const int32_t *colidx,
+                      int mem, void *stream, tc_graph **out);
+/* Release a graph and its device memory (NULL is ignored). */
+void tc_graph_free(tc_graph *g);
+
+typedef struct tc_graph_info {
+    int32_t V;
+    int64_t E;
+    int32_t max_in_degree;
+    int32_t max_out_degree;
+    int64_t num_dangling;     /* vertices with out-degree 0 */
+    int32_t device;
+} tc_graph_info;
+int tc_graph_get_info(const tc_graph *g, tc_graph_info *info);
+
+/*
+ * tc_graph_export_transpose -- copy the device-built G^T out (rowptr[V+1], colidx[E],
+ * in-rows sorted by source id) to host or device buffers per `mem`.  Synchronises.
+ */
+int tc_graph_export_transpose(const tc_graph *g, int32_t *rowptr, int32_t *colidx, int mem,
+                              void *stream);
+
+/* ---- TOCAB partition --------------------------------------------------------------------- */
+/*
+ * Sec. 3.1 "Throughput Oriented Cache Blocking", preprocessing phase: static 1D blocking.
+ * TC_PULL: every edge of G^T goes to the block of its SOURCE, blocks are source ranges
+ * [b*W, (b+1)*W) (column blocking; Fig. 3).  TC_PUSH: every edge of G goes to the block
+ * of its DESTINATION (row blocking, the same code on the transposed input).
+ * Inside a block only vertices with at least one edge get a local ID (Fig. 4), given in
+ * ascending global-ID order; id_map maps local to global IDs.  All blocks are
+ * concatenated in block order into one row space of R local rows.
+ *   num_blocks : B >= 1 (W = ceil(V/B); the partition then has ceil(V/W) <= B blocks),
+ *                or 0 to derive W from the device's L2 size: W FP32 vertex values take
+ *                `l2_fraction` of cudaDeviceProp::l2CacheSize; the default (<= 0) is 4/11,
+ *                i.e. W = l2CacheSize / 11 -- the paper's 256 Ki vertices per subgraph
+ *                on its 2.75 MB L2 (Sec. 4.3, Table 3).
+ * Errors: TC_ERR_INVALID_ARG (dir, B < 0, B > V when V > 0), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+typedef struct tc_part_params {
+    float   l2_fraction;      /* used when num_blocks == 0; <= 0 means 4/11 */
+    int32_t merge_range;      /* k of the merge (Fig. 5): vertices per merge CTA; 0 = 1024 */
+    int32_t hub_degree;       /* rows with more edges go to CTA-per-row tasks; 0 = 2048 */
+} tc_part_params;
+
+int tc_tocab_partition(const tc_graph *g, int dir, int32_t num_blocks,
+                       const tc_part_params *params /* NULL = defaults */, void *stream,
+                       tc_part **out);
+void tc_part_free(tc_part *p);
+
+typedef struct tc_part_info {
+    int32_t dir;
+    int32_t num_blocks;       /* B */
+    int32_t block_width;      /* W */
+    int64_t num_rows;         /* R = sum over blocks of local rows */
+    int64_t num_edges;        /* E */
+    int32_t merge_range;      /* k */
+    int32_t num_hubs;         /* rows handled one CTA per row */
+} tc_part_info;
+int tc_part_get_info(const tc_part *p, tc_part_info *info);
+
+/*
+ * tc_part_export -- copy the blocked CSR out (mem = host or device), for inspection:
+ *   blk_rows[B+1]  first local row of each block;   blk_edges[B+1] first edge of each block
+ *   rowptr[R+1]    edge offset of every local row;  id_map[R] global ID of every local row
+ *   colidx[E]      global column (source for pull, destination for push) of every edge.
+ * Any output pointer may be NULL to skip it.  Synchronises.
+ */
+int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_edges, int32_t *rowptr,
+                   int32_t *id_map, int32_t *colidx, int mem, void *stream);
+
+/* Default block width W for a vertex count V and an L2 size (host-only helper, the rule
+ * used when num_blocks == 0). */
+int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
+
+/* ---- PageRank ------------------------------------------------------------------------------ */
+typedef struct tc_pr_params {
+    float   damping;          /* d, e.g. 0.85 */
+    int32_t iters;            /* fixed number of Jacobi iterations (>= 0) */
+    int32_t dangling;         /* TC_DANGLING_REDISTRIBUTE or TC_DANGLING_DROP */
+    int32_t out_mem;          /* memory space of ranks_out (and of init) */
+    const float *init;        /* initial ranks [V] or NULL for 1/V */
+    int32_t profile;          /* nonzero: time each kernel with CUDA events (stats) */
+} tc_pr_params;
+
+typedef struct tc_pr_stats {
+    int32_t iters;            /* iterations run */
+    int32_t launches;         /* kernels launched by the call */
+    float   ms_total;         /* device time of the whole call (profile only) */
+    float   ms_gather;        /* device time of gather/scatter kernels (profile only) */
+    float   ms_merge;         /* device time of merge/update kernels (profile only) */
+    double  dangling_mass;    /* dangling mass D of the final ranks */
+} tc_pr_stats;
+
+/*
+ * tc_pagerank_pull -- PageRank in the pull direction.  Alg. 1 per iteration:
+ *   contributions[u] = rank[u] / out_degree[u];  sums[v] = sum_{u -> v} contributions[u];
+ *   rank[v] = (1-d)/|V| + d * (sums[v] + D/|V|)   (D = dangling mass, REDISTRIBUTE mode)
+ * part == NULL runs the unblocked kernel (one gather over G^T with the update fused).
+ * part != NULL (TC_PULL) runs TOCAB: Alg. 4 per block into dense partial sums over local
+ * IDs, then the merge of Fig. 5 (CTA per vertex range) fused with the update.
+ * All blocks read the previous iteration's contributions (Jacobi).  FP32 arithmetic.
+ *   ranks_out : [V] floats in params->out_mem space.
+ * Errors: TC_ERR_INVALID_ARG (null graph/params/output, damping outside [0,1], iters < 0,
+ * partition of another graph or direction), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_pagerank_pull(const tc_graph *g, const tc_part *part, const tc_pr_params *params,
+                     float *ranks_out, tc_pr_stats *stats, void *stream);
+
+/*
+ * tc_pagerank_push -- PageRank in the push direction.  Alg. 2: every source scatters its
+ * contribution into sums[dst] with atomic adds; part == NULL scatters over all of G,
+ * part != NULL (TC_PUSH) runs Alg. 5 block by block, so that the atomics of one block
+ * land in its destination range; then the same update as Alg. 1.  Summation order of
+ * the atomics is not deterministic.  Same arguments and errors as tc_pagerank_pull.
+ */
+int tc_pagerank_push(const tc_graph *g, const tc_part *part, const tc_pr_params *params,
+                     float *ranks_out, tc_pr_stats *stats, void *stream);
+
+/* ---- BFS --------------------------------------------------------------------------------------- */
+typedef struct tc_bfs_params {
+    float   tocab_threshold;  /* use the blocked kernel in levels whose frontier holds more
+                                 than this fraction of V (Sec. 3.3); < 0 = never, 0 = always */
+    int32_t out_mem;          /* memory space of levels_out */
+    int32_t profile;          /* nonzero: per-kernel device timing into stats */
+} tc_bfs_params;
+
+typedef struct tc_bfs_stats {
+    int32_t levels;           /* number of BFS levels expanded (depth + 1 of the deepest) */
+    int32_t tocab_levels;     /* levels run with the blocked kernel */
+    int64_t reached;          /* vertices with level >= 0 */
+    int64_t edges_reached;    /* sum of out-degrees of reached vertices */
+    float   ms_total;         /* device time (profile only) */
+} tc_bfs_stats;
+
+/*
+ * tc_bfs_pull -- topology-driven, level-synchronous BFS in the pull direction with
+ * bitmap status arrays (front, next, visited; Sec. 3.3, Fig. 1e/f): in level L every
+ * unvisited vertex v scans its in-edges and joins level L+1 if an in-neighbour is in
+ * the frontier.  With part != NULL (TC_PULL) levels whose frontier exceeds the threshold
+ * run per block into local next bitmaps over local IDs, OR-reduced in the merge kernel
+ * (Sec. 3.3).  levels_out[v] = hop distance from `source`, -1 when unreachable.
+ * Errors: TC_ERR_INVALID_ARG (source outside [0, V)), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
+                const tc_bfs_params *params, int32_t *levels_out, tc_bfs_stats *stats,
+                void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TOCAB_H */

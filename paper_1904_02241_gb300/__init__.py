@@ -1,0 +1,226 @@
+"""GB300 (sm_103a) throughput-oriented cache blocking (TOCAB) for graph processing.
+
+Thin Python binding over the C ABI of ``libtocab.so`` (declared in include/tocab.h).
+Functions keep the C names without the ``tc_`` prefix:
+
+  graph_load_csr(rowptr, colidx)            -> Graph     (tc_graph_load_csr)
+  tocab_partition(graph, dir, num_blocks)   -> Partition (tc_tocab_partition)
+  pagerank_pull(graph, part, ...)           -> ranks     (tc_pagerank_pull)
+  pagerank_push(graph, part, ...)           -> ranks     (tc_pagerank_push)
+  bfs_pull(graph, part, source, ...)        -> levels    (tc_bfs_pull)
+
+Every step of the computation runs in the library's CUDA kernels; this module only
+passes pointers, sizes and the current torch CUDA stream.  PyTorch provides device
+memory and streams.  If the library is missing the import of a function fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import torch
+
+from . import _lib as L
+from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
+                   TC_PULL, TC_PUSH)
+
+__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull",
+           "Graph", "Partition", "TocabError", "lib", "default_block_width"]
+
+
+class TocabError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        lib = L.load()
+        msg = lib.tc_last_error().decode(errors="replace")
+        name = lib.tc_status_string(status).decode()
+        super().__init__(f"{where}: {name} ({status}): {msg}")
+        self.status = status
+
+
+def lib():
+    return L.load()
+
+
+def _check(status: int, where: str):
+    if status != L.TC_OK:
+        raise TocabError(status, where)
+
+
+def _stream(stream=None) -> int:
+    if stream is None:
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+        return 0
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _mem(t: torch.Tensor) -> int:
+    return L.TC_MEM_DEVICE if t.is_cuda else L.TC_MEM_HOST
+
+
+def _i32(t) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
+    if t.dtype != torch.int32:
+        raise TypeError(f"expected an int32 tensor, got {t.dtype}")
+    return t.contiguous()
+
+
+class Graph:
+    """A graph resident on the current CUDA device (owns a tc_graph handle)."""
+
+    def __init__(self, handle: C.c_void_p):
+        self._h = handle
+        info = L.tc_graph_info()
+        _check(L.load().tc_graph_get_info(self._h, C.byref(info)), "tc_graph_get_info")
+        self.V = info.V
+        self.E = info.E
+        self.max_in_degree = info.max_in_degree
+        self.max_out_degree = info.max_out_degree
+        self.num_dangling = info.num_dangling
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            L.load().tc_graph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def export_transpose(self, device: str = "cpu"):
+        rp = torch.empty(self.V + 1, dtype=torch.int32, device=device)
+        ci = torch.empty(max(self.E, 1), dtype=torch.int32, device=device)
+        _check(L.load().tc_graph_export_transpose(self._h, rp.data_ptr(), ci.data_ptr(), _mem(rp),
+                                                  _stream()), "tc_graph_export_transpose")
+        return rp, ci[: self.E]
+
+
+class Partition:
+    """A TOCAB partition of a Graph (owns a tc_part handle; keeps the graph alive)."""
+
+    def __init__(self, handle: C.c_void_p, graph: Graph):
+        self._h = handle
+        self.graph = graph
+        info = L.tc_part_info()
+        _check(L.load().tc_part_get_info(self._h, C.byref(info)), "tc_part_get_info")
+        self.dir = info.dir
+        self.num_blocks = info.num_blocks
+        self.block_width = info.block_width
+        self.num_rows = info.num_rows
+        self.num_edges = info.num_edges
+        self.merge_range = info.merge_range
+        self.num_hubs = info.num_hubs
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            L.load().tc_part_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+    def export(self):
+        """Blocked CSR as host numpy arrays (blk_rows, blk_edges, rowptr, id_map, colidx)."""
+        B, R, E = self.num_blocks, self.num_rows, self.num_edges
+        br = torch.empty(B + 1, dtype=torch.int64)
+        be = torch.empty(B + 1, dtype=torch.int64)
+        rp = torch.empty(R + 1, dtype=torch.int32)
+        im = torch.empty(max(R, 1), dtype=torch.int32)
+        ci = torch.empty(max(E, 1), dtype=torch.int32)
+        _check(L.load().tc_part_export(self._h, br.data_ptr(), be.data_ptr(), rp.data_ptr(), im.data_ptr(),
+                                       ci.data_ptr(), L.TC_MEM_HOST, _stream()), "tc_part_export")
+        return {"B": B, "W": self.block_width, "blk_rows": br.numpy(), "blk_edges": be.numpy(),
+                "rowptr": rp.numpy(), "id_map": im.numpy()[:R], "colidx": ci.numpy()[:E]}
+
+
+def graph_load_csr(rowptr, colidx, V: int | None = None, stream=None) -> Graph:
+    """tc_graph_load_csr: out-edge CSR (int32 tensors on host or device) -> Graph."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    if V is None:
+        V = rowptr.numel() - 1
+    if rowptr.is_cuda != colidx.is_cuda and colidx.numel() > 0:
+        raise ValueError("rowptr and colidx must live in the same memory space")
+    h = C.c_void_p()
+    ci_ptr = colidx.data_ptr() if colidx.numel() > 0 else None
+    _check(L.load().tc_graph_load_csr(V, colidx.numel(), rowptr.data_ptr(), ci_ptr, _mem(rowptr),
+                                      _stream(stream), C.byref(h)), "tc_graph_load_csr")
+    return Graph(h)
+
+
+def tocab_partition(graph: Graph, dir: int = L.TC_PULL, num_blocks: int = 0, l2_fraction: float = 0.0,
+                    merge_range: int = 0, hub_degree: int = 0, stream=None) -> Partition:
+    """tc_tocab_partition: static 1D blocking (num_blocks = 0 derives W from the L2 size)."""
+    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree)
+    h = C.c_void_p()
+    _check(L.load().tc_tocab_partition(graph.handle, dir, num_blocks, C.byref(pp), _stream(stream), C.byref(h)),
+           "tc_tocab_partition")
+    return Partition(h, graph)
+
+
+def default_block_width(V: int, l2_bytes: int, l2_fraction: float = 0.0) -> int:
+    return int(L.load().tc_default_block_width(V, l2_bytes, l2_fraction))
+
+
+def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream):
+    if out is None:
+        out = torch.empty(graph.V, dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or out.numel() < graph.V or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor with V elements")
+    mode = {"redistribute": L.TC_DANGLING_REDISTRIBUTE, "drop": L.TC_DANGLING_DROP}[dangling] \
+        if isinstance(dangling, str) else int(dangling)
+    init_ptr = None
+    if init is not None:
+        if init.dtype != torch.float32 or init.is_cuda != out.is_cuda:
+            raise ValueError("init must be float32 in the same memory space as out")
+        init = init.contiguous()
+        init_ptr = init.data_ptr()
+    pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), init_ptr, 1 if profile else 0)
+    st = L.tc_pr_stats()
+    _check(fn(graph.handle, part.handle if part is not None else None, C.byref(pp), out.data_ptr(),
+              C.byref(st), _stream(stream)), name)
+    return out, st
+
+
+def pagerank_pull(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
+                  dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
+                  profile: bool = False, stream=None, return_stats: bool = False):
+    """tc_pagerank_pull (Alg. 1; TOCAB Alg. 4 + merge when part is given)."""
+    r, st = _pagerank(L.load().tc_pagerank_pull, "tc_pagerank_pull", graph, part, damping, iters, dangling, out,
+                      init, profile, stream)
+    return (r, st) if return_stats else r
+
+
+def pagerank_push(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
+                  dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
+                  profile: bool = False, stream=None, return_stats: bool = False):
+    """tc_pagerank_push (Alg. 2; TOCAB Alg. 5 when part is given)."""
+    r, st = _pagerank(L.load().tc_pagerank_push, "tc_pagerank_push", graph, part, damping, iters, dangling, out,
+                      init, profile, stream)
+    return (r, st) if return_stats else r
+
+
+def bfs_pull(graph: Graph, part: Partition | None, source: int, tocab_threshold: float = 0.05,
+             out: torch.Tensor | None = None, profile: bool = False, stream=None, return_stats: bool = False):
+    """tc_bfs_pull: hop levels from source (-1 = unreachable)."""
+    if out is None:
+        out = torch.empty(graph.V, dtype=torch.int32, device="cuda")
+    if out.dtype != torch.int32 or out.numel() < graph.V or not out.is_contiguous():
+        raise ValueError("out must be a contiguous int32 tensor with V elements")
+    bp = L.tc_bfs_params(float(tocab_threshold), _mem(out), 1 if profile else 0)
+    st = L.tc_bfs_stats()
+    _check(L.load().tc_bfs_pull(graph.handle, part.handle if part is not None else None, int(source), C.byref(bp),
+                                out.data_ptr(), C.byref(st), _stream(stream)), "tc_bfs_pull")
+    return (out, st) if return_stats else out

@@ -1,0 +1,95 @@
+"""ctypes declarations of the C ABI in include/tocab.h (argument marshalling only)."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtocab.so")
+
+TC_OK = 0
+TC_ERR_INVALID_ARG = -1
+TC_ERR_INVALID_GRAPH = -2
+TC_ERR_OOM = -3
+TC_ERR_CUDA = -4
+TC_ERR_TIMEOUT = -5
+TC_ERR_UNSUPPORTED = -6
+TC_MEM_HOST = 0
+TC_MEM_DEVICE = 1
+TC_PULL = 0
+TC_PUSH = 1
+TC_DANGLING_REDISTRIBUTE = 0
+TC_DANGLING_DROP = 1
+
+
+class tc_graph_info(C.Structure):
+    _fields_ = [("V", C.c_int32), ("E", C.c_int64), ("max_in_degree", C.c_int32),
+                ("max_out_degree", C.c_int32), ("num_dangling", C.c_int64), ("device", C.c_int32)]
+
+
+class tc_part_params(C.Structure):
+    _fields_ = [("l2_fraction", C.c_float), ("merge_range", C.c_int32), ("hub_degree", C.c_int32)]
+
+
+class tc_part_info(C.Structure):
+    _fields_ = [("dir", C.c_int32), ("num_blocks", C.c_int32), ("block_width", C.c_int32),
+                ("num_rows", C.c_int64), ("num_edges", C.c_int64), ("merge_range", C.c_int32),
+                ("num_hubs", C.c_int32)]
+
+
+class tc_pr_params(C.Structure):
+    _fields_ = [("damping", C.c_float), ("iters", C.c_int32), ("dangling", C.c_int32),
+                ("out_mem", C.c_int32), ("init", C.c_void_p), ("profile", C.c_int32)]
+
+
+class tc_pr_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("launches", C.c_int32), ("ms_total", C.c_float),
+                ("ms_gather", C.c_float), ("ms_merge", C.c_float), ("dangling_mass", C.c_double)]
+
+
+class tc_bfs_params(C.Structure):
+    _fields_ = [("tocab_threshold", C.c_float), ("out_mem", C.c_int32), ("profile", C.c_int32)]
+
+
+class tc_bfs_stats(C.Structure):
+    _fields_ = [("levels", C.c_int32), ("tocab_levels", C.c_int32), ("reached", C.c_int64),
+                ("edges_reached", C.c_int64), ("ms_total", C.c_float)]
+
+
+VP = C.c_void_p
+# name -> (restype, argtypes)
+SIGNATURES = {
+    "tc_status_string": (C.c_char_p, [C.c_int]),
+    "tc_last_error": (C.c_char_p, []),
+    "tc_version": (C.c_int, []),
+    "tc_graph_load_csr": (C.c_int, [C.c_int32, C.c_int64, VP, VP, C.c_int, VP, C.POINTER(VP)]),
+    "tc_graph_free": (None, [VP]),
+    "tc_graph_get_info": (C.c_int, [VP, C.POINTER(tc_graph_info)]),
+    "tc_graph_export_transpose": (C.c_int, [VP, VP, VP, C.c_int, VP]),
+    "tc_tocab_partition": (C.c_int, [VP, C.c_int, C.c_int32, C.POINTER(tc_part_params), VP, C.POINTER(VP)]),
+    "tc_part_free": (None, [VP]),
+    "tc_part_get_info": (C.c_int, [VP, C.POINTER(tc_part_info)]),
+    "tc_part_export": (C.c_int, [VP, VP, VP, VP, VP, VP, C.c_int, VP]),
+    "tc_default_block_width": (C.c_int32, [C.c_int32, C.c_int64, C.c_float]),
+    "tc_pagerank_pull": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
+    "tc_pagerank_push": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
+    "tc_bfs_pull": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_bfs_params), VP, C.POINTER(tc_bfs_stats), VP]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libtocab.so; raises if it has not been built (there is no fallback)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError(f"{path} is missing: build it with "
+                              "`python -m paper_1904_02241_gb300.build` (nvcc, sm_103a)")
+        lib = C.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(lib, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = lib
+    return _lib

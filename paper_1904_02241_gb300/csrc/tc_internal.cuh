@@ -1,0 +1,143 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <string>
+
+#include "tocab.h"
+
+namespace tc {
+
+// ---- error handling -------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+int fail(int status, const char *fmt, ...);   // sets last error, returns status
+
+#define TC_CUDA(call)                                                                   \
+    do {                                                                                \
+        cudaError_t err__ = (call);                                                     \
+        if (err__ != cudaSuccess) {                                                     \
+            return ::tc::fail(err__ == cudaErrorMemoryAllocation ? TC_ERR_OOM           \
+                                                                 : TC_ERR_CUDA,         \
+                              "%s failed at %s:%d: %s", #call, __FILE__, __LINE__,      \
+                              cudaGetErrorString(err__));                               \
+        }                                                                               \
+    } while (0)
+
+#define TC_LAUNCH_CHECK() TC_CUDA(cudaGetLastError())
+
+#define TC_TRY(expr)                    \
+    do {                                \
+        int st__ = (expr);              \
+        if (st__ != TC_OK) return st__; \
+    } while (0)
+
+// ---- device buffer that frees itself --------------------------------------------------
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    ~DevBuf() { release(); }
+    void release() {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+    int alloc(size_t n) {  // grows only
+        if (n <= bytes && p) return TC_OK;
+        release();
+        if (n == 0) n = 16;
+        cudaError_t e = cudaMalloc(&p, n);
+        if (e != cudaSuccess) {
+            p = nullptr;
+            return fail(TC_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
+        }
+        bytes = n;
+        return TC_OK;
+    }
+    template <class T> T *as() const { return static_cast<T *>(p); }
+};
+
+struct DeviceCaps {
+    int device = 0;
+    int sms = 0;
+    int64_t l2_bytes = 0;
+    int max_smem_optin = 0;
+};
+int device_caps(DeviceCaps *caps);
+
+// ---- primitives (tc_prims.cu) -----------------------------------------------------------
+// Exclusive scan of n int32 values into int64 out (out may not alias in); writes n outputs.
+int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s);
+int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s);
+
+// Stable sort of (key, val) int32 pairs by bucket(key) for bucket values < 2^bits,
+// where bucket(key) = key / divisor (divisor >= 1).  LSD passes of 8 bits.
+// Results land in (k_out, v_out); k_tmp/v_tmp are scratch of n elements each.
+int stable_bucket_sort(const int32_t *k_in, const int32_t *v_in, int32_t *k_out, int32_t *v_out,
+                       int32_t *k_tmp, int32_t *v_tmp, int64_t n, int32_t divisor, int bits,
+                       cudaStream_t s);
+
+// rowptr[v] = first i with keys[i] >= v, for v in [0, V]; keys sorted ascending, n keys.
+int offsets_from_sorted(const int32_t *keys, int64_t n, int32_t V, int32_t *rowptr,
+                        cudaStream_t s);
+// Expand CSR rows into a per-edge row id array.
+int expand_rows(const int32_t *rowptr, int32_t V, int32_t *row_of_edge, cudaStream_t s);
+
+// ---- handles -------------------------------------------------------------------------------
+struct Workspace;  // per-graph reusable scratch for the iteration drivers
+
+}  // namespace tc
+
+struct tc_graph {
+    int32_t V = 0;
+    int64_t E = 0;
+    int device = 0;
+    tc::DevBuf out_rowptr, out_colidx;  // G
+    tc::DevBuf in_rowptr, in_colidx;    // G^T
+    tc::DevBuf inv_outdeg;              // float[V], 0 for dangling vertices
+    int32_t max_in_degree = 0, max_out_degree = 0;
+    int64_t num_dangling = 0;
+    // rows above the hub degree, for the unblocked kernels (CTA per row)
+    int32_t hub_degree = 2048;
+    int32_t num_in_hubs = 0, num_out_hubs = 0;
+    tc::DevBuf in_hubs, out_hubs;
+    // reusable scratch (grown on demand, freed with the graph)
+    tc::DevBuf ws_contrib, ws_scalars, ws_partials, ws_bits, ws_misc;
+};
+
+struct tc_part {
+    const tc_graph *g = nullptr;
+    int32_t dir = TC_PULL;
+    int32_t B = 1, W = 1;
+    int32_t V = 0;
+    int64_t E = 0, R = 0;
+    int32_t k = 1024;           // merge range width
+    int32_t nranges = 0;        // ceil(V / k)
+    int32_t hub_degree = 2048;
+    int32_t num_hubs = 0;
+    int64_t num_groups = 0;     // 32-row groups over the row space
+    int64_t *h_blk_rows = nullptr, *h_blk_edges = nullptr;  // host copies [B+1]
+    tc::DevBuf rowptr;          // int32[R+1] (global edge offsets)
+    tc::DevBuf id_map;          // int32[R]
+    tc::DevBuf colidx;          // int32[E]
+    tc::DevBuf merge_off;       // int32[B * (nranges+1)]
+    tc::DevBuf hubs;            // int32[num_hubs] rows with degree > hub_degree
+    tc::DevBuf partial;         // float[R] partial sums (scratch)
+    tc::DevBuf rowbits;         // uint32[ceil(R/32)] local next bits (BFS scratch)
+    ~tc_part() {
+        delete[] h_blk_rows;
+        delete[] h_blk_edges;
+    }
+};
+
+namespace tc {
+// Rows of a CSR with more than `min_degree` edges, as a compact int32 list (ascending).
+int collect_hubs(const int32_t *rowptr, int64_t nrows, int32_t min_degree, DevBuf *list, int32_t *count,
+                 cudaStream_t s);
+}  // namespace tc

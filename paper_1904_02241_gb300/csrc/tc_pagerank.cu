@@ -1,0 +1,466 @@
+// PageRank iteration kernels and drivers.
+//   pull, unblocked : Alg. 1 with the update fused into the gather epilogue.
+//   pull, TOCAB     : Alg. 4 per block into partial sums over local IDs, then the merge of
+//                     Fig. 5 (one CTA per vertex range) fused with the update.
+//   push            : Alg. 2 / Alg. 5 atomic scatter, then a separate update kernel.
+// Load balancing (Sec. 3.2): a warp takes 32 consecutive rows; rows with fewer than 32
+// edges are summed serially by their lane, rows up to the hub degree by the whole warp,
+// and hub rows by a whole CTA each (thread / warp / CTA per row, no atomics in pull).
+#include "tc_common_dev.cuh"
+
+namespace tc {
+
+constexpr int PR_THREADS = 256;
+constexpr int PR_WARPS = PR_THREADS / 32;
+
+struct UpdateArgs {
+    float base;             // (1-d)/V
+    float damping;          // d
+    int drop;               // 1: dangling mass is not redistributed
+    int32_t V;
+    const double *D_cur;    // dangling mass of the ranks the current contributions came from
+    double *D_next;         // dangling mass of the ranks written now
+    double *dpart;          // per-CTA partial dangling sums
+    unsigned *counter;      // arrival counter for the last-CTA reduction
+    const float *inv_outdeg;
+    float *rank_out;        // may be null (only the last iteration writes ranks)
+    float *contrib_next;    // contributions for the next iteration
+};
+
+__device__ __forceinline__ float spread_of(const UpdateArgs &u) {
+    return u.drop ? 0.0f : (float)(*u.D_cur / (double)u.V);
+}
+
+// rank[v] = (1-d)/V + d (sum + D/V); contribution = rank / out_degree; returns the dangling share.
+__device__ __forceinline__ float apply_update(const UpdateArgs &u, int32_t v, float sum, float spread) {
+    const float r = u.base + u.damping * (sum + spread);
+    if (u.rank_out) u.rank_out[v] = r;
+    const float inv = __ldg(u.inv_outdeg + v);
+    u.contrib_next[v] = r * inv;
+    return inv == 0.0f ? r : 0.0f;
+}
+
+// ---------------------------------------------------------------------------------------------
+// Pull gather over a CSR whose rows are destinations (G^T, or the TOCAB row space).
+// FUSED = true: rows are vertices, apply the update; FUSED = false: write partial[row].
+// ---------------------------------------------------------------------------------------------
+template <bool FUSED>
+__global__ void __launch_bounds__(PR_THREADS) k_pull_gather(const int32_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ colidx, int64_t nrows,
+                                                            const int32_t *__restrict__ hubs, int32_t num_hubs,
+                                                            int32_t hub_degree, int hub_ctas,
+                                                            const float *__restrict__ contrib,
+                                                            float *__restrict__ partial, UpdateArgs u) {
+    __shared__ float fred[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float dsum = 0.0f;
+    float spread = 0.0f;
+    if (FUSED) spread = spread_of(u);
+    if ((int)blockIdx.x < hub_ctas) {
+        for (int32_t h = blockIdx.x; h < num_hubs; h += hub_ctas) {
+            const int32_t row = hubs[h];
+            const int32_t s = rowptr[row], e = rowptr[row + 1];
+            float acc = 0.0f;
+            for (int32_t i = s + threadIdx.x; i < e; i += PR_THREADS) acc += __ldg(contrib + __ldg(colidx + i));
+            acc = block_sum<float>(acc, fred);
+            if (threadIdx.x == 0) {
+                if (FUSED) dsum += apply_update(u, row, acc, spread);
+                else partial[row] = acc;
+            }
+        }
+    } else {
+        const int64_t ngroups = (nrows + 31) >> 5;
+        const int64_t nwarps = (int64_t)(gridDim.x - hub_ctas) * PR_WARPS;
+        for (int64_t grp = (int64_t)(blockIdx.x - hub_ctas) * PR_WARPS + warp; grp < ngroups; grp += nwarps) {
+            const int64_t row = grp * 32 + lane;
+            const bool valid = row < nrows;
+            int32_t s = 0, e = 0;
+            if (valid) {
+                s = __ldg(rowptr + row);
+                e = __ldg(rowptr + row + 1);
+            }
+            const int32_t deg = e - s;
+            float sum = 0.0f;
+            if (deg < 32) {  // thread per row
+                for (int32_t i = s; i < e; ++i) sum += __ldg(contrib + __ldg(colidx + i));
+            }
+            unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= 32 && deg <= hub_degree);
+            while (wm) {  // warp per row
+                const int l = __ffs(wm) - 1;
+                wm &= wm - 1;
+                const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
+                float acc = 0.0f;
+                for (int32_t i = ws + lane; i < we; i += 32) acc += __ldg(contrib + __ldg(colidx + i));
+#pragma unroll
+                for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+                if (lane == l) sum = acc;
+            }
+            if (valid && deg <= hub_degree) {
+                if (FUSED) dsum += apply_update(u, (int32_t)row, sum, spread);
+                else partial[row] = sum;
+            }
+        }
+    }
+    if (FUSED) {
+        const float bs = block_sum<float>(dsum, fred);
+        grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+    }
+}
+
+// ---------------------------------------------------------------------------------------------
+// TOCAB merge (Fig. 5): CTA j owns vertices [j*k, (j+1)*k).  Warp w adds the slices of blocks
+// w, w+8, ... (in block order) into its private shared-memory accumulator; the eight
+// accumulators are then added in warp order, so the summation order is fixed.  The update of
+// Alg. 1 (lines 9-10), the next contributions and the dangling mass are fused in.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(PR_THREADS) k_pull_merge(const float *__restrict__ partial,
+                                                           const int32_t *__restrict__ id_map,
+                                                           const int32_t *__restrict__ merge_off, int32_t B,
+                                                           int32_t nranges, int32_t k, UpdateArgs u) {
+    extern __shared__ float acc[];  // [PR_WARPS][k]
+    __shared__ float fred[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t j = blockIdx.x;
+    const int32_t vbase = j * k;
+    for (int t = threadIdx.x; t < PR_WARPS * k; t += PR_THREADS) acc[t] = 0.0f;
+    __syncthreads();
+    float *mine = acc + warp * k;
+    for (int32_t b = warp; b < B; b += PR_WARPS) {
+        const int32_t *o = merge_off + (int64_t)b * (nranges + 1) + j;
+        const int32_t r0 = __ldg(o), r1 = __ldg(o + 1);
+        for (int32_t r = r0 + lane; r < r1; r += 32) mine[__ldg(id_map + r) - vbase] += __ldg(partial + r);
+        __syncwarp();
+    }
+    __syncthreads();
+    const float spread = spread_of(u);
+    float dsum = 0.0f;
+    for (int t = threadIdx.x; t < k; t += PR_THREADS) {
+        const int32_t v = vbase + t;
+        if (v >= u.V) break;
+        float s = 0.0f;
+#pragma unroll
+        for (int w = 0; w < PR_WARPS; ++w) s += acc[w * k + t];
+        dsum += apply_update(u, v, s, spread);
+    }
+    const float bs = block_sum<float>(dsum, fred);
+    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+}
+
+// Initial ranks (1/V or caller's), first contributions and their dangling mass.
+__global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict__ init, UpdateArgs u) {
+    __shared__ float fred[32];
+    float dsum = 0.0f;
+    const float r0 = 1.0f / (float)u.V;
+    for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < u.V; v += (int64_t)gridDim.x * PR_THREADS) {
+        const float r = init ? init[v] : r0;
+        if (u.rank_out) u.rank_out[v] = r;
+        const float inv = __ldg(u.inv_outdeg + v);
+        u.contrib_next[v] = r * inv;
+        if (inv == 0.0f) dsum += r;
+    }
+    const float bs = block_sum<float>(dsum, fred);
+    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Push scatter (Alg. 2; Alg. 5 when id_map != null): rows are sources; red.global.add into sums.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(PR_THREADS) k_push_scatter(const int32_t *__restrict__ rowptr,
+                                                             const int32_t *__restrict__ colidx, int64_t nrows,
+                                                             const int32_t *__restrict__ id_map,
+                                                             const int32_t *__restrict__ hubs, int32_t num_hubs,
+                                                             int32_t hub_degree, int hub_ctas,
+                                                             const float *__restrict__ contrib, float *sums) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if ((int)blockIdx.x < hub_ctas) {
+        for (int32_t h = blockIdx.x; h < num_hubs; h += hub_ctas) {
+            const int32_t row = hubs[h];
+            const int32_t src = id_map ? __ldg(id_map + row) : row;
+            const float c = __ldg(contrib + src);
+            const int32_t s = rowptr[row], e = rowptr[row + 1];
+            if (c != 0.0f)
+                for (int32_t i = s + threadIdx.x; i < e; i += PR_THREADS) atomicAdd(sums + __ldg(colidx + i), c);
+        }
+        return;
+    }
+    const int64_t ngroups = (nrows + 31) >> 5;
+    const int64_t nwarps = (int64_t)(gridDim.x - hub_ctas) * PR_WARPS;
+    for (int64_t grp = (int64_t)(blockIdx.x - hub_ctas) * PR_WARPS + warp; grp < ngroups; grp += nwarps) {
+        const int64_t row = grp * 32 + lane;
+        const bool valid = row < nrows;
+        int32_t s = 0, e = 0;
+        float c = 0.0f;
+        if (valid) {
+            s = __ldg(rowptr + row);
+            e = __ldg(rowptr + row + 1);
+            c = __ldg(contrib + (id_map ? __ldg(id_map + row) : (int32_t)row));
+        }
+        const int32_t deg = e - s;
+        if (deg < 32 && c != 0.0f)
+            for (int32_t i = s; i < e; ++i) atomicAdd(sums + __ldg(colidx + i), c);
+        unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= 32 && deg <= hub_degree && c != 0.0f);
+        while (wm) {
+            const int l = __ffs(wm) - 1;
+            wm &= wm - 1;
+            const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
+            const float cl = __shfl_sync(0xffffffffu, c, l);
+            for (int32_t i = ws + lane; i < we; i += 32) atomicAdd(sums + __ldg(colidx + i), cl);
+        }
+    }
+}
+
+// Update after a push iteration: ranks from sums, next contributions, sums cleared.
+__global__ void __launch_bounds__(PR_THREADS) k_push_update(float *sums, UpdateArgs u) {
+    __shared__ float fred[32];
+    const float spread = spread_of(u);
+    float dsum = 0.0f;
+    for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < u.V; v += (int64_t)gridDim.x * PR_THREADS) {
+        const float s = sums[v];
+        sums[v] = 0.0f;
+        dsum += apply_update(u, (int32_t)v, s, spread);
+    }
+    const float bs = block_sum<float>(dsum, fred);
+    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+}
+
+// ---------------------------------------------------------------------------------------------
+// host drivers
+// ---------------------------------------------------------------------------------------------
+struct Timer {
+    bool on = false;
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    float *acc = nullptr;
+    int begin(bool enable, cudaStream_t st, float *target) {
+        on = enable;
+        s = st;
+        acc = target;
+        if (!on) return TC_OK;
+        TC_CUDA(cudaEventCreate(&ev[0]));
+        TC_CUDA(cudaEventCreate(&ev[1]));
+        TC_CUDA(cudaEventRecord(ev[0], s));
+        return TC_OK;
+    }
+    int end() {
+        if (!on) return TC_OK;
+        TC_CUDA(cudaEventRecord(ev[1], s));
+        TC_CUDA(cudaEventSynchronize(ev[1]));
+        float ms = 0;
+        TC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        *acc += ms;
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+        return TC_OK;
+    }
+};
+
+static int occupancy_grid(const void *kernel, int threads, size_t smem, int64_t work_ctas, int *grid) {
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    int per_sm = 0;
+    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem));
+    if (per_sm < 1) per_sm = 1;
+    int64_t g = (int64_t)caps.sms * per_sm;
+    if (work_ctas < g) g = work_ctas;
+    if (g < 1) g = 1;
+    *grid = (int)g;
+    return TC_OK;
+}
+
+struct PrState {
+    float *contrib[2];
+    double *D;          // D[0], D[1]
+    unsigned *counter;
+    double *dpart;      // per-CTA partials (capacity dpart_cap)
+    int64_t dpart_cap;
+    float *rank_dev;    // ranks on the device (caller's buffer or scratch)
+    float *sums;        // push only
+};
+
+static int prepare_state(tc_graph *g, const tc_pr_params *pp, float *ranks_out, bool push, int64_t max_ctas,
+                         PrState *st) {
+    const int32_t V = g->V;
+    TC_TRY(g->ws_contrib.alloc((size_t)V * 4 * (push ? 3 : 2) + 256));
+    st->contrib[0] = g->ws_contrib.as<float>();
+    st->contrib[1] = st->contrib[0] + V;
+    st->sums = push ? st->contrib[1] + V : nullptr;
+    st->dpart_cap = max_ctas;
+    TC_TRY(g->ws_scalars.alloc(64 + (size_t)max_ctas * 8));
+    st->D = reinterpret_cast<double *>(g->ws_scalars.as<char>());
+    st->counter = reinterpret_cast<unsigned *>(g->ws_scalars.as<char>() + 32);
+    st->dpart = reinterpret_cast<double *>(g->ws_scalars.as<char>() + 64);
+    if (pp->out_mem == TC_MEM_DEVICE) {
+        st->rank_dev = ranks_out;
+    } else {
+        TC_TRY(g->ws_misc.alloc((size_t)V * 4 + 256));
+        st->rank_dev = g->ws_misc.as<float>();
+    }
+    return TC_OK;
+}
+
+static int check_pr_args(const tc_graph *g, const tc_part *part, const tc_pr_params *pp, float *ranks_out, int dir) {
+    if (!g || !pp || !ranks_out) return fail(TC_ERR_INVALID_ARG, "pagerank: null graph, params or output");
+    if (!(pp->damping >= 0.0f && pp->damping <= 1.0f)) return fail(TC_ERR_INVALID_ARG, "pagerank: damping outside [0,1]");
+    if (pp->iters < 0) return fail(TC_ERR_INVALID_ARG, "pagerank: iters < 0");
+    if (pp->dangling != TC_DANGLING_REDISTRIBUTE && pp->dangling != TC_DANGLING_DROP)
+        return fail(TC_ERR_INVALID_ARG, "pagerank: bad dangling mode");
+    if (pp->out_mem != TC_MEM_HOST && pp->out_mem != TC_MEM_DEVICE)
+        return fail(TC_ERR_INVALID_ARG, "pagerank: bad out_mem");
+    if (part && (part->g != g || part->dir != dir))
+        return fail(TC_ERR_INVALID_ARG, "pagerank: partition belongs to another graph or direction");
+    return TC_OK;
+}
+
+static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_params *pp, float *ranks_out,
+                         tc_pr_stats *stats, cudaStream_t s, bool push) {
+    tc_graph *g = const_cast<tc_graph *>(cg);  // scratch buffers only
+    const int32_t V = g->V;
+    if (stats) memset(stats, 0, sizeof(*stats));
+    if (V == 0) return TC_OK;
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+
+    // launch shapes
+    int g_gather = 1, g_upd = 1, g_merge = 1, hub_ctas = 0;
+    int64_t nrows;
+    const int32_t *rp, *ci, *hubs, *idm = nullptr;
+    int32_t nhubs, hubdeg;
+    if (part) {
+        nrows = part->R;
+        rp = part->rowptr.as<int32_t>();
+        ci = part->colidx.as<int32_t>();
+        hubs = part->hubs.as<int32_t>();
+        nhubs = part->num_hubs;
+        hubdeg = part->hub_degree;
+        idm = part->id_map.as<int32_t>();
+    } else {
+        nrows = V;
+        rp = push ? g->out_rowptr.as<int32_t>() : g->in_rowptr.as<int32_t>();
+        ci = push ? g->out_colidx.as<int32_t>() : g->in_colidx.as<int32_t>();
+        hubs = push ? g->out_hubs.as<int32_t>() : g->in_hubs.as<int32_t>();
+        nhubs = push ? g->num_out_hubs : g->num_in_hubs;
+        hubdeg = g->hub_degree;
+    }
+    hub_ctas = nhubs > 0 ? (nhubs < caps.sms ? nhubs : caps.sms) : 0;
+    const int64_t group_ctas = ((nrows + 31) / 32 + PR_WARPS - 1) / PR_WARPS;
+    const void *kgather = push ? (const void *)k_push_scatter
+                               : (part ? (const void *)k_pull_gather<false> : (const void *)k_pull_gather<true>);
+    TC_TRY(occupancy_grid(kgather, PR_THREADS, 0, group_ctas > 0 ? group_ctas : 1, &g_gather));
+    g_gather += hub_ctas;
+    TC_TRY(occupancy_grid((const void *)k_push_update, PR_THREADS, 0, ((int64_t)V + PR_THREADS - 1) / PR_THREADS, &g_upd));
+    size_t merge_smem = 0;
+    if (part && !push) {
+        g_merge = part->nranges;
+        merge_smem = (size_t)PR_WARPS * part->k * 4;
+        if (merge_smem > 48 * 1024)
+            TC_CUDA(cudaFuncSetAttribute(k_pull_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
+    }
+    int g_init = 1;
+    TC_TRY(occupancy_grid((const void *)k_pr_init, PR_THREADS, 0, ((int64_t)V + PR_THREADS - 1) / PR_THREADS, &g_init));
+    int64_t max_ctas = g_gather;
+    if (g_init > max_ctas) max_ctas = g_init;
+    if (g_upd > max_ctas) max_ctas = g_upd;
+    if (g_merge > max_ctas) max_ctas = g_merge;
+
+    PrState st;
+    TC_TRY(prepare_state(g, pp, ranks_out, push, max_ctas, &st));
+    TC_CUDA(cudaMemsetAsync(st.counter, 0, 8, s));
+    if (push) TC_CUDA(cudaMemsetAsync(st.sums, 0, (size_t)V * 4, s));
+
+    UpdateArgs u;
+    u.base = (1.0f - pp->damping) / (float)V;
+    u.damping = pp->damping;
+    u.drop = pp->dangling == TC_DANGLING_DROP;
+    u.V = V;
+    u.dpart = st.dpart;
+    u.counter = st.counter;
+    u.inv_outdeg = g->inv_outdeg.as<float>();
+
+    float ms_total = 0, ms_gather = 0, ms_merge = 0;
+    Timer tt;
+    TC_TRY(tt.begin(pp->profile != 0, s, &ms_total));
+    int launches = 0;
+    // init: contributions[0], D[0]
+    u.D_cur = st.D + 1;
+    u.D_next = st.D + 0;
+    u.rank_out = pp->iters == 0 ? st.rank_dev : nullptr;
+    u.contrib_next = st.contrib[0];
+    {
+        const float *init_dev = pp->init;
+        if (pp->init && pp->out_mem == TC_MEM_HOST) {
+            TC_CUDA(cudaMemcpyAsync(st.rank_dev, pp->init, (size_t)V * 4, cudaMemcpyHostToDevice, s));
+            init_dev = st.rank_dev;
+        }
+        k_pr_init<<<g_init, PR_THREADS, 0, s>>>(init_dev, u);
+        TC_LAUNCH_CHECK();
+        ++launches;
+    }
+    for (int it = 0; it < pp->iters; ++it) {
+        const bool last = it == pp->iters - 1;
+        const float *cur = push ? st.contrib[0] : st.contrib[it & 1];
+        u.D_cur = st.D + (it & 1);
+        u.D_next = st.D + ((it + 1) & 1);
+        u.rank_out = last ? st.rank_dev : nullptr;
+        u.contrib_next = push ? st.contrib[0] : st.contrib[(it + 1) & 1];
+        Timer t1;
+        TC_TRY(t1.begin(pp->profile != 0, s, &ms_gather));
+        if (push) {
+            k_push_scatter<<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, idm, hubs, nhubs, hubdeg, hub_ctas, cur,
+                                                          st.sums);
+        } else if (part) {
+            k_pull_gather<false><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, hubs, nhubs, hubdeg, hub_ctas, cur,
+                                                                 part->partial.as<float>(), u);
+        } else {
+            k_pull_gather<true><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, hubs, nhubs, hubdeg, hub_ctas, cur,
+                                                                nullptr, u);
+        }
+        TC_LAUNCH_CHECK();
+        ++launches;
+        TC_TRY(t1.end());
+        if (push || part) {
+            Timer t2;
+            TC_TRY(t2.begin(pp->profile != 0, s, &ms_merge));
+            if (push) {
+                k_push_update<<<g_upd, PR_THREADS, 0, s>>>(st.sums, u);
+            } else {
+                k_pull_merge<<<g_merge, PR_THREADS, merge_smem, s>>>(part->partial.as<float>(), part->id_map.as<int32_t>(),
+                                                                     part->merge_off.as<int32_t>(), part->B,
+                                                                     part->nranges, part->k, u);
+            }
+            TC_LAUNCH_CHECK();
+            ++launches;
+            TC_TRY(t2.end());
+        }
+    }
+    TC_TRY(tt.end());
+    if (pp->out_mem == TC_MEM_HOST)
+        TC_CUDA(cudaMemcpyAsync(ranks_out, st.rank_dev, (size_t)V * 4, cudaMemcpyDeviceToHost, s));
+    if (stats) {
+        double D = 0;
+        TC_CUDA(cudaMemcpyAsync(&D, st.D + (pp->iters & 1), 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        stats->dangling_mass = D;
+        stats->iters = pp->iters;
+        stats->launches = launches;
+        stats->ms_total = ms_total;
+        stats->ms_gather = ms_gather;
+        stats->ms_merge = ms_merge;
+    } else if (pp->out_mem == TC_MEM_HOST) {
+        TC_CUDA(cudaStreamSynchronize(s));
+    }
+    return TC_OK;
+}
+
+}  // namespace tc
+
+extern "C" int tc_pagerank_pull(const tc_graph *g, const tc_part *part, const tc_pr_params *params, float *ranks_out,
+                                tc_pr_stats *stats, void *stream) {
+    TC_TRY(tc::check_pr_args(g, part, params, ranks_out, TC_PULL));
+    return tc::pagerank_impl(g, part, params, ranks_out, stats, (cudaStream_t)stream, false);
+}
+
+extern "C" int tc_pagerank_push(const tc_graph *g, const tc_part *part, const tc_pr_params *params, float *ranks_out,
+                                tc_pr_stats *stats, void *stream) {
+    TC_TRY(tc::check_pr_args(g, part, params, ranks_out, TC_PUSH));
+    return tc::pagerank_impl(g, part, params, ranks_out, stats, (cudaStream_t)stream, true);
+}

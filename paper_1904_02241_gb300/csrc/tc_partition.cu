@@ -1,0 +1,272 @@
+// TOCAB preprocessing (Sec. 3.1): static 1D blocking of a CSR by column ranges, local IDs
+// for the rows that have edges in a block (Fig. 4), the merge range table (Fig. 5) and the
+// hub-row list used by the load balancer (Sec. 3.2).  Everything runs on the device.
+#include "tc_internal.cuh"
+
+namespace tc {
+
+// head[i] = 1 when edge i starts a new local row: first edge, new block or new row.
+__global__ void k_row_heads(const int32_t *col, const int32_t *row, int64_t E, int32_t W, int32_t *head) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
+        int32_t h = 1;
+        if (i > 0) h = (col[i] / W != col[i - 1] / W) || (row[i] != row[i - 1]);
+        head[i] = h;
+    }
+}
+
+__global__ void k_fill_rows(const int32_t *head, const int64_t *rowid, const int32_t *row, int64_t E,
+                            int32_t *rowptr, int32_t *id_map) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
+        if (head[i]) {
+            const int64_t r = rowid[i];
+            rowptr[r] = (int32_t)i;
+            id_map[r] = row[i];
+        }
+    }
+}
+
+// blk_edges[b] = first edge whose column is >= b*W (columns are block-major after the sort);
+// blk_rows[b] = local row of that edge (R when past the end).
+__global__ void k_block_bounds(const int32_t *col, const int64_t *rowid, const int32_t *head, int64_t E, int64_t R,
+                               int32_t W, int32_t B, int64_t *blk_edges, int64_t *blk_rows) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += gridDim.x * blockDim.x) {
+        const int64_t bound = (int64_t)b * W;
+        int64_t lo = 0, hi = E;
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)col[mid] < bound) lo = mid + 1; else hi = mid;
+        }
+        blk_edges[b] = lo;
+        blk_rows[b] = (lo < E) ? rowid[lo] : R;
+        (void)head;
+    }
+}
+
+// off[b][j] = first local row of block b whose global id is >= j*k, j in [0, nranges].
+__global__ void k_merge_offsets(const int32_t *id_map, const int64_t *blk_rows, int32_t B, int32_t nranges, int32_t k,
+                                int32_t *off) {
+    const int64_t total = (int64_t)B * (nranges + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = (int32_t)(t / (nranges + 1));
+        const int32_t j = (int32_t)(t - (int64_t)b * (nranges + 1));
+        const int64_t bound = (int64_t)j * k;
+        int64_t lo = blk_rows[b], hi = blk_rows[b + 1];
+        while (lo < hi) {
+            int64_t mid = (lo + hi) >> 1;
+            if ((int64_t)id_map[mid] < bound) lo = mid + 1; else hi = mid;
+        }
+        off[t] = (int32_t)lo;
+    }
+}
+
+__global__ void k_hub_flags(const int32_t *rowptr, int64_t nrows, int32_t min_degree, int32_t *flag) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x)
+        flag[r] = (rowptr[r + 1] - rowptr[r]) > min_degree;
+}
+
+__global__ void k_hub_compact(const int32_t *flag, const int64_t *pos, int64_t nrows, int32_t *list) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < nrows; r += (int64_t)gridDim.x * blockDim.x)
+        if (flag[r]) list[pos[r]] = (int32_t)r;
+}
+
+int collect_hubs(const int32_t *rowptr, int64_t nrows, int32_t min_degree, DevBuf *list, int32_t *count,
+                 cudaStream_t s) {
+    *count = 0;
+    if (nrows <= 0) return list->alloc(16);
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    DevBuf flag, pos;
+    TC_TRY(flag.alloc(nrows * 4));
+    TC_TRY(pos.alloc(nrows * 8));
+    k_hub_flags<<<caps.sms * 8, 256, 0, s>>>(rowptr, nrows, min_degree, flag.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32_to_i64(flag.as<int32_t>(), nrows, pos.as<int64_t>(), s));
+    int64_t last_pos = 0;
+    int32_t last_flag = 0;
+    TC_CUDA(cudaMemcpyAsync(&last_pos, pos.as<int64_t>() + nrows - 1, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(&last_flag, flag.as<int32_t>() + nrows - 1, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    const int64_t n = last_pos + last_flag;
+    TC_TRY(list->alloc((n > 0 ? n : 1) * 4));
+    if (n > 0) {
+        k_hub_compact<<<caps.sms * 8, 256, 0, s>>>(flag.as<int32_t>(), pos.as<int64_t>(), nrows, list->as<int32_t>());
+        TC_LAUNCH_CHECK();
+    }
+    TC_CUDA(cudaStreamSynchronize(s));
+    *count = (int32_t)n;
+    return TC_OK;
+}
+
+static int log2_ceil(int64_t x) {
+    int b = 0;
+    while (((int64_t)1 << b) < x) ++b;
+    return b;
+}
+
+static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const tc_part_params *pp, cudaStream_t s,
+                          tc_part *p) {
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    const int32_t V = g->V;
+    const int64_t E = g->E;
+    const int32_t *rp = dir == TC_PULL ? g->in_rowptr.as<int32_t>() : g->out_rowptr.as<int32_t>();
+    const int32_t *ci = dir == TC_PULL ? g->in_colidx.as<int32_t>() : g->out_colidx.as<int32_t>();
+    p->g = g;
+    p->dir = dir;
+    p->V = V;
+    p->E = E;
+    const float frac = (pp && pp->l2_fraction > 0) ? pp->l2_fraction : 0.0f;
+    p->k = (pp && pp->merge_range > 0) ? pp->merge_range : 1024;
+    if (p->k % 32 != 0) return fail(TC_ERR_INVALID_ARG, "merge_range must be a multiple of 32");
+    p->hub_degree = (pp && pp->hub_degree > 0) ? pp->hub_degree : 2048;
+    if (num_blocks == 0) {
+        p->W = tc_default_block_width(V, caps.l2_bytes, frac);
+    } else {
+        p->W = V > 0 ? (int32_t)(((int64_t)V + num_blocks - 1) / num_blocks) : 1;
+    }
+    if (p->W < 1) p->W = 1;
+    p->B = V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1;
+    p->nranges = (int32_t)(((int64_t)V + p->k - 1) / p->k);
+    const int32_t B = p->B, W = p->W;
+    const int grid = caps.sms * 8;
+
+    TC_TRY(p->colidx.alloc((size_t)E * 4));
+    DevBuf rows_sorted, rows_in, head, rowid, ktmp, vtmp;
+    TC_TRY(rows_sorted.alloc((size_t)E * 4));
+    if (E > 0) {
+        TC_TRY(rows_in.alloc((size_t)E * 4));
+        TC_TRY(expand_rows(rp, V, rows_in.as<int32_t>(), s));
+        if (B > 1) {
+            TC_TRY(ktmp.alloc((size_t)E * 4));
+            TC_TRY(vtmp.alloc((size_t)E * 4));
+            TC_TRY(stable_bucket_sort(ci, rows_in.as<int32_t>(), p->colidx.as<int32_t>(), rows_sorted.as<int32_t>(),
+                                      ktmp.as<int32_t>(), vtmp.as<int32_t>(), E, W, log2_ceil(B), s));
+            ktmp.release();
+            vtmp.release();
+        } else {
+            TC_CUDA(cudaMemcpyAsync(p->colidx.p, ci, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
+            TC_CUDA(cudaMemcpyAsync(rows_sorted.p, rows_in.p, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
+        }
+        rows_in.release();
+        TC_TRY(head.alloc((size_t)E * 4));
+        TC_TRY(rowid.alloc((size_t)E * 8));
+        k_row_heads<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), rows_sorted.as<int32_t>(), E, W, head.as<int32_t>());
+        TC_LAUNCH_CHECK();
+        TC_TRY(scan_i32_to_i64(head.as<int32_t>(), E, rowid.as<int64_t>(), s));
+        int64_t last_id = 0;
+        int32_t last_head = 0;
+        TC_CUDA(cudaMemcpyAsync(&last_id, rowid.as<int64_t>() + E - 1, 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaMemcpyAsync(&last_head, head.as<int32_t>() + E - 1, 4, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        p->R = last_id + last_head;  // rowid is an exclusive scan of the row heads
+    } else {
+        p->R = 0;
+    }
+    const int64_t R = p->R;
+    TC_TRY(p->rowptr.alloc(((size_t)R + 1) * 4));
+    TC_TRY(p->id_map.alloc((size_t)(R > 0 ? R : 1) * 4));
+    DevBuf blk_edges, blk_rows;
+    TC_TRY(blk_edges.alloc(((size_t)B + 1) * 8));
+    TC_TRY(blk_rows.alloc(((size_t)B + 1) * 8));
+    if (E > 0) {
+        k_fill_rows<<<grid, 256, 0, s>>>(head.as<int32_t>(), rowid.as<int64_t>(), rows_sorted.as<int32_t>(), E,
+                                         p->rowptr.as<int32_t>(), p->id_map.as<int32_t>());
+        TC_LAUNCH_CHECK();
+        k_block_bounds<<<(B + 256) / 256, 256, 0, s>>>(p->colidx.as<int32_t>(), rowid.as<int64_t>(), head.as<int32_t>(),
+                                                       E, R, W, B, blk_edges.as<int64_t>(), blk_rows.as<int64_t>());
+        TC_LAUNCH_CHECK();
+    } else {
+        TC_CUDA(cudaMemsetAsync(blk_edges.p, 0, ((size_t)B + 1) * 8, s));
+        TC_CUDA(cudaMemsetAsync(blk_rows.p, 0, ((size_t)B + 1) * 8, s));
+    }
+    const int32_t Ei = (int32_t)E;
+    TC_CUDA(cudaMemcpyAsync(p->rowptr.as<int32_t>() + R, &Ei, 4, cudaMemcpyHostToDevice, s));
+    p->h_blk_rows = new (std::nothrow) int64_t[B + 1];
+    p->h_blk_edges = new (std::nothrow) int64_t[B + 1];
+    if (!p->h_blk_rows || !p->h_blk_edges) return fail(TC_ERR_OOM, "host allocation failed");
+    TC_CUDA(cudaMemcpyAsync(p->h_blk_rows, blk_rows.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(p->h_blk_edges, blk_edges.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
+
+    // merge range table
+    const int64_t noff = (int64_t)B * (p->nranges + 1);
+    TC_TRY(p->merge_off.alloc((size_t)(noff > 0 ? noff : 1) * 4));
+    if (noff > 0) {
+        k_merge_offsets<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), blk_rows.as<int64_t>(), B, p->nranges, p->k,
+                                             p->merge_off.as<int32_t>());
+        TC_LAUNCH_CHECK();
+    }
+    TC_TRY(collect_hubs(p->rowptr.as<int32_t>(), R, p->hub_degree, &p->hubs, &p->num_hubs, s));
+    p->num_groups = (R + 31) / 32;
+    TC_TRY(p->partial.alloc((size_t)(R > 0 ? R : 1) * 4));
+    TC_TRY(p->rowbits.alloc((size_t)((R + 31) / 32 + 1) * 4));
+    TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+}  // namespace tc
+
+extern "C" int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction) {
+    // Default: the paper's 256 Ki FP32 values on a 2.75 MB (= 11 x 256 KiB) L2, i.e. the
+    // block's vertex values take 4/11 of the L2 and W = l2_bytes / 11 exactly.
+    int64_t W = l2_fraction > 0 ? (int64_t)((double)l2_fraction * (double)l2_bytes / 4.0) : l2_bytes / 11;
+    if (W < 32) W = 32;
+    if (V > 0 && W > V) W = V;
+    if (W > INT32_MAX) W = INT32_MAX;
+    return (int32_t)W;
+}
+
+extern "C" int tc_tocab_partition(const tc_graph *g, int dir, int32_t num_blocks, const tc_part_params *params,
+                                  void *stream, tc_part **out) {
+    using namespace tc;
+    if (!out) return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: out is NULL");
+    *out = nullptr;
+    if (!g) return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: graph is NULL");
+    if (dir != TC_PULL && dir != TC_PUSH) return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: bad direction");
+    if (num_blocks < 0 || (g->V > 0 && num_blocks > g->V))
+        return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: num_blocks must be in [0, V]");
+    tc_part *p = new (std::nothrow) tc_part();
+    if (!p) return fail(TC_ERR_OOM, "host allocation failed");
+    int st = partition_impl(g, dir, num_blocks, params, (cudaStream_t)stream, p);
+    if (st != TC_OK) {
+        cudaStreamSynchronize((cudaStream_t)stream);
+        delete p;
+        return st;
+    }
+    *out = p;
+    return TC_OK;
+}
+
+extern "C" void tc_part_free(tc_part *p) {
+    if (!p) return;
+    cudaDeviceSynchronize();
+    delete p;
+}
+
+extern "C" int tc_part_get_info(const tc_part *p, tc_part_info *info) {
+    if (!p || !info) return tc::fail(TC_ERR_INVALID_ARG, "tc_part_get_info: null argument");
+    info->dir = p->dir;
+    info->num_blocks = p->B;
+    info->block_width = p->W;
+    info->num_rows = p->R;
+    info->num_edges = p->E;
+    info->merge_range = p->k;
+    info->num_hubs = p->num_hubs;
+    return TC_OK;
+}
+
+extern "C" int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_edges, int32_t *rowptr,
+                              int32_t *id_map, int32_t *colidx, int mem, void *stream) {
+    using namespace tc;
+    if (!p) return fail(TC_ERR_INVALID_ARG, "tc_part_export: null partition");
+    if (mem != TC_MEM_HOST && mem != TC_MEM_DEVICE) return fail(TC_ERR_INVALID_ARG, "bad mem flag");
+    cudaStream_t s = (cudaStream_t)stream;
+    const cudaMemcpyKind d2x = mem == TC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const cudaMemcpyKind h2x = mem == TC_MEM_DEVICE ? cudaMemcpyHostToDevice : cudaMemcpyHostToHost;
+    if (blk_rows) TC_CUDA(cudaMemcpyAsync(blk_rows, p->h_blk_rows, ((size_t)p->B + 1) * 8, h2x, s));
+    if (blk_edges) TC_CUDA(cudaMemcpyAsync(blk_edges, p->h_blk_edges, ((size_t)p->B + 1) * 8, h2x, s));
+    if (rowptr) TC_CUDA(cudaMemcpyAsync(rowptr, p->rowptr.p, ((size_t)p->R + 1) * 4, d2x, s));
+    if (id_map && p->R > 0) TC_CUDA(cudaMemcpyAsync(id_map, p->id_map.p, (size_t)p->R * 4, d2x, s));
+    if (colidx && p->E > 0) TC_CUDA(cudaMemcpyAsync(colidx, p->colidx.p, (size_t)p->E * 4, d2x, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
+}

@@ -1,0 +1,234 @@
+"""GPU parity: every CUDA path through the C ABI against the FP64 CPU oracle.
+
+Integer work (transpose, partition, BFS levels) must match bit-exactly; FP32 PageRank
+must be within an L1 relative error of 1e-5 of the FP64 oracle after 20 iterations."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from tests.gpu_util import l1_rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_02241_gb300 as T
+    T.lib()
+    return T
+
+
+def _graphs():
+    return {
+        "rmat12": gg.rmat(12),
+        "rmat14_noperm": gg.rmat(14, permute_seed=None),
+        "er": gg.erdos_renyi(3000, 20000, seed=5),
+        "grid": gg.grid2d(37, 41),
+        "star": gg.star(300),
+        "two": gg.from_edge_list(2, [(0, 1)]),
+        "isolated": gg.from_edge_list(7, [(0, 1), (1, 0), (5, 6)]),
+        "single": gg.empty_graph(1),
+        "plc": gg.powerlaw_config(5000, 6, 2.2, seed=3),
+    }
+
+
+GRAPHS = _graphs()
+
+
+def _load(T, g, device=True):
+    rp, ci = (g.rowptr.cuda(), g.colidx.cuda()) if device else (g.rowptr, g.colidx)
+    return T.graph_load_csr(rp, ci, V=g.V)
+
+
+# ------------------------------------------------------------------ a1: load + transpose
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("device", [True, False])
+def test_transpose_bit_exact(T, name, device):
+    g = GRAPHS[name]
+    G = _load(T, g, device)
+    rp, ci = G.export_transpose()
+    wrp, wci = oracle.transpose(g.V, *g.numpy())
+    np.testing.assert_array_equal(rp.numpy(), wrp)
+    np.testing.assert_array_equal(ci.numpy(), wci)
+    deg = np.diff(g.numpy()[0])
+    assert G.num_dangling == int((deg == 0).sum())
+    assert G.max_out_degree == int(deg.max(initial=0))
+
+
+def test_invalid_csr_rejected(T):
+    bad_rp = torch.tensor([0, 2, 1], dtype=torch.int32)
+    ci = torch.tensor([1, 0], dtype=torch.int32)
+    with pytest.raises(T.TocabError) as e:
+        T.graph_load_csr(bad_rp, ci)
+    assert e.value.status == -2
+    with pytest.raises(T.TocabError) as e:
+        T.graph_load_csr(torch.tensor([0, 1, 2], dtype=torch.int32), torch.tensor([1, 5], dtype=torch.int32))
+    assert e.value.status == -2
+
+
+# ------------------------------------------------------------------ a2: partition
+
+@pytest.mark.parametrize("name", ["rmat12", "er", "grid", "star", "isolated", "plc"])
+@pytest.mark.parametrize("B", [1, 2, 3, 4, 7, 64])
+@pytest.mark.parametrize("direction", ["pull", "push"])
+def test_partition_bit_exact(T, name, B, direction):
+    g = GRAPHS[name]
+    if B > g.V:
+        pytest.skip("B > V")
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL if direction == "pull" else T.TC_PUSH, B)
+    got = P.export()
+    rp, ci = g.numpy()
+    base = oracle.transpose(g.V, rp, ci) if direction == "pull" else (rp, ci)
+    want = oracle.partition(g.V, base[0], base[1], P.block_width)
+    assert got["B"] == want["B"]
+    for key in ("blk_rows", "blk_edges", "rowptr", "id_map", "colidx"):
+        np.testing.assert_array_equal(np.asarray(got[key], np.int64), np.asarray(want[key], np.int64), err_msg=key)
+
+
+def test_partition_auto_width_uses_l2(T):
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 0)
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    assert P.block_width == min(g.V, l2 // 11)
+
+
+# ------------------------------------------------------------------ a3-a6: pull PageRank
+
+def _oracle_pr(g, **kw):
+    rp, ci = g.numpy()
+    return oracle.pagerank_pull(g.V, rp, ci, **kw)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("B", [None, 1, 3, 4, 64])
+def test_pagerank_pull_parity(T, name, B):
+    g = GRAPHS[name]
+    if B is not None and B > g.V:
+        pytest.skip("B > V")
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B) if B is not None else None
+    r, st = T.pagerank_pull(G, P, return_stats=True)
+    want = _oracle_pr(g)
+    assert l1_rel(r.cpu().numpy(), want) <= TOL
+    assert abs(st.dangling_mass - want[np.diff(g.numpy()[0]) == 0].sum()) <= 1e-5
+
+
+@pytest.mark.parametrize("B", [None, 4])
+def test_pagerank_pull_drop_mode_and_damping(T, B):
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B) if B else None
+    for d, mode in [(0.85, "drop"), (0.5, "redistribute"), (0.0, "redistribute"), (1.0, "redistribute")]:
+        r = T.pagerank_pull(G, P, damping=d, dangling=mode)
+        assert l1_rel(r.cpu().numpy(), _oracle_pr(g, damping=d, dangling=mode)) <= TOL, (d, mode)
+
+
+@pytest.mark.parametrize("iters", [0, 1, 2, 7])
+def test_pagerank_pull_iteration_counts_and_host_output(T, iters):
+    g = GRAPHS["er"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 3)
+    out = torch.empty(g.V, dtype=torch.float32)  # host output
+    T.pagerank_pull(G, P, iters=iters, out=out)
+    assert l1_rel(out.numpy(), _oracle_pr(g, iters=iters)) <= TOL
+
+
+def test_pagerank_pull_init(T):
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    init = torch.rand(g.V, generator=torch.Generator().manual_seed(0), dtype=torch.float64)
+    init = init / init.sum()
+    r = T.pagerank_pull(G, None, iters=5, init=init.float().cuda())
+    want = _oracle_pr(g, iters=5, init=init.float().double().numpy())
+    assert l1_rel(r.cpu().numpy(), want) <= TOL
+
+
+def test_closed_form_star_on_gpu(T):
+    n, d = 300, 0.85
+    G = _load(T, GRAPHS["star"])
+    hstar = (1 + d * n) / ((n + 1) * (1 + d))
+    h20 = hstar + (-d) ** 20 * (1.0 / (n + 1) - hstar)
+    for P in (None, T.tocab_partition(G, T.TC_PULL, 4)):
+        r = T.pagerank_pull(G, P).cpu().numpy()
+        assert abs(r[0] - h20) / h20 < 1e-5
+        assert np.allclose(r[1:], (1 - h20) / n, rtol=1e-5)
+
+
+def test_pull_result_is_deterministic(T):
+    g = GRAPHS["rmat14_noperm"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 4)
+    a = T.pagerank_pull(G, P).cpu()
+    b = T.pagerank_pull(G, P).cpu()
+    assert torch.equal(a, b)
+    a = T.pagerank_pull(G, None).cpu()
+    b = T.pagerank_pull(G, None).cpu()
+    assert torch.equal(a, b)
+
+
+# ------------------------------------------------------------------ a7: push PageRank
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+@pytest.mark.parametrize("B", [None, 1, 4, 64])
+def test_pagerank_push_parity(T, name, B):
+    g = GRAPHS[name]
+    if B is not None and B > g.V:
+        pytest.skip("B > V")
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PUSH, B) if B is not None else None
+    r = T.pagerank_push(G, P)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+
+
+def test_partition_direction_mismatch_rejected(T):
+    G = _load(T, GRAPHS["rmat12"])
+    P = T.tocab_partition(G, T.TC_PULL, 2)
+    with pytest.raises(T.TocabError) as e:
+        T.pagerank_push(G, P)
+    assert e.value.status == -1
+
+
+# ------------------------------------------------------------------ a8: BFS
+
+BFS_GRAPHS = {
+    "rmat12_sym": gg.symmetrize(gg.rmat(12)),
+    "rmat12_dir": gg.rmat(12),
+    "grid": gg.grid2d(37, 41),
+    "path": gg.path(200),
+    "star": gg.star(300),
+    "isolated": gg.from_edge_list(7, [(0, 1), (1, 0), (5, 6)]),
+    "single": gg.empty_graph(1),
+}
+
+
+@pytest.mark.parametrize("name", list(BFS_GRAPHS))
+@pytest.mark.parametrize("mode", ["unblocked", "tocab_always", "tocab_threshold"])
+def test_bfs_bit_exact(T, name, mode):
+    g = BFS_GRAPHS[name]
+    G = _load(T, g)
+    P = None if mode == "unblocked" else T.tocab_partition(G, T.TC_PULL, min(4, g.V))
+    thr = {"unblocked": -1.0, "tocab_always": 0.0, "tocab_threshold": 0.05}[mode]
+    rp, ci = g.numpy()
+    for s in gg.sources(g, 3, seed=13) + [0, g.V - 1]:
+        lv, st = T.bfs_pull(G, P, s, tocab_threshold=thr, return_stats=True)
+        want = oracle.bfs(g.V, rp, ci, s)
+        np.testing.assert_array_equal(lv.cpu().numpy(), want)
+        assert st.reached == int((want >= 0).sum())
+        deg = np.diff(rp)
+        assert st.edges_reached == int(deg[want >= 0].sum())
+        if mode == "tocab_always" and st.levels > 0:
+            assert st.tocab_levels == st.levels
+
+
+def test_bfs_bad_source(T):
+    G = _load(T, BFS_GRAPHS["path"])
+    with pytest.raises(T.TocabError):
+        T.bfs_pull(G, None, 200)

@@ -219,6 +219,39 @@ int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
                 const tc_bfs_params *params, int32_t *levels_out, tc_bfs_stats *stats,
                 void *stream);
 
+/* ---- PageRank without allocation ------------------------------------------------------------ */
+/* Largest vertex count and size in bytes of the static device scratch used below. */
+#define TC_NOALLOC_MAX_V          (1 << 20)
+#define TC_NOALLOC_SCRATCH_BYTES  (256 + 4096 * 8 + 3 * 4 * TC_NOALLOC_MAX_V)
+
+/*
+ * tc_pagerank_pull_noalloc -- the unblocked pull PageRank of tc_pagerank_pull for callers
+ * that cannot allocate device memory (the paper has no counterpart: this entry point is a
+ * deployment aid).  Typical callers run inside a host framework whose allocator owns the
+ * device memory pool, or fix their memory budget at start-up and may not call cudaMalloc
+ * or cudaFree afterwards.  This call allocates nothing: no cudaMalloc, no cudaFree, no
+ * allocating library routine.  Its scratch (contributions, out-degree reciprocals,
+ * dangling-mass partials) is a static device array of TC_NOALLOC_SCRATCH_BYTES (about
+ * 12.6 MB) that every GPU which loads the library holds until the process exits.
+ *   V          : 1 <= V <= TC_NOALLOC_MAX_V, else TC_ERR_UNSUPPORTED (nothing is launched).
+ *   in_rowptr  : device int32[V+1], in-edge CSR of G^T (row v lists the sources of v's
+ *   in_colidx    in-edges; device int32[E]).  Not validated: pass a well-formed CSR.
+ *   out_degree : device int32[V], out-degree of every vertex in G.
+ *   damping, iters, dangling : as tc_pr_params (TC_DANGLING_REDISTRIBUTE or _DROP).
+ *   ranks_out  : device float[V], receives the ranks after `iters` iterations.
+ *   stream     : cudaStream_t; the call only enqueues work on it and does not synchronise.
+ * The first call on a device looks up the scratch's device address (cudaGetSymbolAddress)
+ * with that device current; make that first call before any stream capture.  All calls
+ * share the one scratch array, which keeps the previous call's contents (the call re-arms
+ * what must start at zero): calls whose work overlaps on the GPU -- on different streams,
+ * or from different threads -- race and give wrong results; serialise them.
+ * Errors: TC_ERR_UNSUPPORTED (V out of range), TC_ERR_INVALID_ARG (null pointer, damping
+ * outside [0,1], iters < 0, bad dangling mode), TC_ERR_CUDA (launch or lookup failure).
+ */
+int tc_pagerank_pull_noalloc(int32_t V, const int32_t *in_rowptr, const int32_t *in_colidx,
+                             const int32_t *out_degree, float damping, int32_t iters,
+                             int32_t dangling, float *ranks_out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -74,6 +74,7 @@ SIGNATURES = {
     "tc_pagerank_pull": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_pagerank_push": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_bfs_pull": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_bfs_params), VP, C.POINTER(tc_bfs_stats), VP]),
+    "tc_pagerank_pull_noalloc": (C.c_int, [C.c_int32, VP, VP, VP, C.c_float, C.c_int32, C.c_int32, VP, VP]),
 }
 
 _lib = None

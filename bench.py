@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--bfs-sources", type=int, default=64)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--quick", action="store_true",
+                    help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
     return ap.parse_args()
 
 
@@ -387,12 +389,13 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the TOCAB path has no CPU fallback)")
     res, ctx = bench_tocab(args, world, rank, local)
-    if rank == 0:
+    if rank == 0 and not args.quick:
         if not args.no_variants:
             res["variants"] = variants(args, ctx, world)
         res["e2e"] = e2e(args, ctx)
         if world == 1:
             res["cpu_baseline"] = cpu_baseline(ctx[0], args.cpu_seconds)
+    if rank == 0:
         print(json.dumps(res), flush=True)
     barrier(world)
 

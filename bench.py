@@ -45,10 +45,14 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tocab", choices=["tocab", "reference"])
     ap.add_argument("--scale", type=int, default=24)
-    ap.add_argument("--blocks", type=int, default=0, help="TOCAB block count (0 = from L2 size)")
+    ap.add_argument("--blocks", type=int, default=0, help="TOCAB block count (0 = from --policy)")
+    ap.add_argument("--policy", default="smem", choices=["smem", "l2"],
+                    help="block width when --blocks 0: one CTA's shared memory, or the paper's L2 rule")
     ap.add_argument("--bfs-sources", type=int, default=64)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--merge", default="fixed", choices=["fixed", "ordered", "float"],
+                    help="TOCAB pull merge: fixed-point (deterministic), ordered (deterministic), float")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
     return ap.parse_args()
@@ -181,12 +185,12 @@ def bench_tocab(args, world, rank, local):
     V, E = g.V, g.E
     gen_s = time.time() - t0
     G = T.graph_load_csr(g.rowptr, g.colidx, V=V)
-    P = T.tocab_partition(G, T.TC_PULL, args.blocks)
+    P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy)
     torch.cuda.synchronize()
     out = torch.empty(V, dtype=torch.float32, device=dev)
 
     def step():
-        T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out)
+        T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out, merge=args.merge)
 
     for _ in range(args.warmup):
         step()
@@ -205,7 +209,8 @@ def bench_tocab(args, world, rank, local):
     barrier(world)
     ms_total = start.elapsed_time(end)
     # per-kernel durations over an identical set of steps, timed by the library with events
-    prof = [T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out, profile=True, return_stats=True)[1]
+    prof = [T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out, profile=True, return_stats=True,
+                            merge=args.merge)[1]
             for _ in range(max(3, min(args.steps, 5)))]
     clk = clocks.stop()
     ms_step = max_over_ranks(ms_total / args.steps, world)
@@ -216,10 +221,19 @@ def bench_tocab(args, world, rank, local):
     merge_ms = statistics.median(p.ms_merge for p in prof) / ITERS
     launches_per_step = prof[0].launches
 
-    # algorithmic bytes of one gather launch (Alg. 4 over all blocks): colidx 4E, local
-    # row offsets 4(R+1), contributions read once 4V, partial sums written 4R
+    # algorithmic bytes of one gather launch (Alg. 4 over all blocks), for the format in use:
+    #   staged : 2 B per (padded) edge of block-relative sources + 1 bit row-start mask,
+    #            each contribution read once (4V), partial sums written (4R)
+    #   unstaged: 4 B per edge (global sources), 4(R+1) row offsets, 4V, 4R
     R = P.num_rows
-    gather_bytes = 4 * E + 4 * (R + 1) + 4 * V + 4 * R
+    if P.staged:
+        gather_bytes = 2 * P.staged_edges + P.staged_edges // 8 + 4 * V + 4 * R
+        kname = "k_tile_gather"
+    else:
+        gather_bytes = 4 * E + 4 * (R + 1) + 4 * V + 4 * R
+        kname = "k_pull_gather<false>"
+    merge_bytes = 4 * R + (2 if P.merge_range <= 65536 else 4) * R + 8 * P.num_blocks * ((V + P.merge_range - 1)
+                                                                                        // P.merge_range) + 8 * V
     peak, peak_kind = load_peaks()
     achieved = gather_bytes / (gather_ms * 1e-3) / 1e9
     bmin = 4 * E + 4 * (V + 1) + 4 * V + 4 * V + 4 * V
@@ -237,14 +251,16 @@ def bench_tocab(args, world, rank, local):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"pagerank_pull_tocab rmat{args.scale} ef16 20 iters d=0.85",
+                   "merge": args.merge,
                    "graph": f"rmat{args.scale}", "V": V, "E": E, "iters": ITERS,
                    "blocks": P.num_blocks, "block_width": P.block_width, "local_rows": R,
                    "l2": "inputs larger than L2 (colidx %.2f GB vs 135 MB L2); no flush" % (4 * E / 1e9),
                    "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 2)},
-        "roofline": {"bound": "hbm", "kernel": "k_pull_gather<false>", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "traffic": None, "algorithmic_bytes": gather_bytes,
                      "gather_ms": round(gather_ms, 4), "merge_ms": round(merge_ms, 4),
+                     "merge_gbs": round(merge_bytes / (merge_ms * 1e-3) / 1e9, 1),
                      "iteration_bmin_frac": round(bmin / (ms_step / ITERS * 1e-3) / 1e9 / peak, 4)},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
@@ -270,7 +286,13 @@ def variants(args, ctx, world):
     ms = run(lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out))
     res["pull_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
     res["pull_tocab_blocks"] = P.num_blocks
-    Pp = T.tocab_partition(G, T.TC_PUSH, args.blocks)
+    other = "l2" if args.policy == "smem" else "smem"
+    Po = T.tocab_partition(G, T.TC_PULL, 0, block_policy=other)
+    ms = run(lambda: T.pagerank_pull(G, Po, damping=DAMPING, iters=ITERS, out=out))
+    res[f"pull_tocab_{other}_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res[f"pull_tocab_{other}_blocks"] = Po.num_blocks
+    del Po
+    Pp = T.tocab_partition(G, T.TC_PUSH, args.blocks, block_policy="l2")
     ms = run(lambda: T.pagerank_push(G, Pp, damping=DAMPING, iters=ITERS, out=out))
     res["push_tocab_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
     ms = run(lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))
@@ -279,7 +301,7 @@ def variants(args, ctx, world):
     # BFS on the symmetrised graph, 64 seeded sources (TEPS counts each undirected edge once)
     gs = gg.symmetrize(g)
     Gs = T.graph_load_csr(gs.rowptr, gs.colidx, V=gs.V)
-    Ps = T.tocab_partition(Gs, T.TC_PULL, args.blocks)
+    Ps = T.tocab_partition(Gs, T.TC_PULL, args.blocks, block_policy="l2")
     lv = torch.empty(gs.V, dtype=torch.int32, device="cuda")
     srcs = gg.sources(gs, args.bfs_sources, seed=13)
     for thr, key in [(0.05, "bfs_tocab"), (-1.0, "bfs_unblocked")]:
@@ -297,6 +319,45 @@ def variants(args, ctx, world):
             tot_edges += st.edges_reached // 2
         res[key + "_gteps"] = round(tot_edges / (tot_ms * 1e-3) / 1e9, 2)
     res["bfs_graph"] = {"V": gs.V, "E_directed": gs.E, "sources": len(srcs)}
+    del Gs, Ps, gs, lv
+    torch.cuda.empty_cache()
+    res.update(batch_variants(args, stream))
+    return res
+
+
+def batch_variants(args, stream):
+    """Batching: 256 personalised PageRank sources on R-MAT 22 (one [V x 256] launch per
+    iteration), and 1,000 R-MAT graphs with scales 10..16 in one persistent, graph-captured
+    launch with the lanes-per-vertex variant chosen by the autotuner."""
+    import paper_1904_02241_gb300 as T
+    res = {}
+    g22 = gg.rmat(22, device="cuda")
+    G22 = T.graph_load_csr(g22.rowptr, g22.colidx, V=g22.V)
+    srcs = gg.sources(g22, 256, seed=17)
+    R = torch.empty((g22.V, 256), dtype=torch.float32, device="cuda")
+    T.ppr_batch(G22, srcs, iters=ITERS, out=R)
+    torch.cuda.synchronize()
+    ms = statistics.median(time_runs(lambda: T.ppr_batch(G22, srcs, iters=ITERS, out=R), 3, stream))
+    res["ppr_batch"] = {"graph": "rmat22", "V": g22.V, "E": g22.E, "sources": 256, "iters": ITERS,
+                        "ms": round(ms, 2), "ms_per_iter": round(ms / ITERS, 3),
+                        "edge_columns_per_s_G": round(g22.E * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
+                        "gteps_equiv": round(g22.E * ITERS / (ms * 1e-3) / 1e9, 3)}
+    del R, G22, g22
+    torch.cuda.empty_cache()
+    scales = gg.batch_scales(1000, 10, 16, seed=19)
+    gb, off = gg.rmat_batch(scales, seed=19, device="cuda")
+    M = T.multigraph_load(gb.rowptr, gb.colidx, off)
+    best, times = T.multi_autotune(M, iters=ITERS)
+    out = torch.empty(gb.V, dtype=torch.float32, device="cuda")
+    T.pagerank_multi(M, iters=ITERS, out=out)
+    torch.cuda.synchronize()
+    ms = statistics.median(time_runs(lambda: T.pagerank_multi(M, iters=ITERS, out=out), 5, stream))
+    res["many_graphs"] = {"graphs": 1000, "scales": "U{10..16}", "V": gb.V, "E": gb.E, "iters": ITERS,
+                          "autotuned_lanes_per_vertex": best, "autotune_ms": {str(k): round(v, 3) for k, v in times.items()},
+                          "ms": round(ms, 3), "gteps": round(gb.E * ITERS / (ms * 1e-3) / 1e9, 2),
+                          "launches_per_run": 1, "cuda_graph": True}
+    del M, gb, out
+    torch.cuda.empty_cache()
     return res
 
 
@@ -315,7 +376,7 @@ def e2e(args, ctx):
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
         G2 = T.graph_load_csr(rp_h, ci_h, V=g.V)
-        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks)
+        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks, block_policy=args.policy)
         T.pagerank_pull(G2, P2, damping=DAMPING, iters=ITERS, out=out_h)
         t1.record(stream)
         t1.synchronize()

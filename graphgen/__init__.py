@@ -258,3 +258,55 @@ def sources(g: CSRGraph, count: int, seed: int = 13, symmetric: bool = True) -> 
         return [0] * count
     idx = hash_u32(seed, torch.arange(count, dtype=torch.int64))
     return [int(cand[int(i) % cand.numel()]) for i in idx]
+
+
+def rmat_batch(scales, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+               seed: int = 19, permute_seed: int | None = 7, device="cpu"):
+    """Many independent R-MAT graphs drawn in one vectorised pass (same recipe as ``rmat`` per
+    graph: edge_factor * 2**s draws, quadrant descent, per-graph random relabelling, self loops
+    and duplicates removed).  Returns (CSRGraph of the disjoint union, vtx_off int32[n+1]):
+    graph g owns the vertices [vtx_off[g], vtx_off[g+1])."""
+    sc = torch.as_tensor(list(scales), dtype=torch.int64, device=device)
+    n = sc.numel()
+    Vg = torch.pow(torch.full_like(sc, 2), sc)
+    Mg = edge_factor * Vg
+    vtx_off = torch.zeros(n + 1, dtype=torch.int64, device=device)
+    vtx_off[1:] = torch.cumsum(Vg, 0)
+    M = int(Mg.sum())
+    V = int(vtx_off[-1])
+    gid_e = torch.repeat_interleave(torch.arange(n, device=device), Mg)
+    e = torch.arange(M, dtype=torch.int64, device=device)
+    ta = int(round(a * 2**32))
+    tab = int(round((a + b) * 2**32))
+    tabc = int(round((a + b + c) * 2**32))
+    s_e = sc[gid_e]
+    src = torch.zeros(M, dtype=torch.int64, device=device)
+    dst = torch.zeros(M, dtype=torch.int64, device=device)
+    for lvl in range(int(sc.max()) if n else 0):
+        act = s_e > lvl
+        u = hash_u32(seed, e * 32 + lvl)
+        sbit = (u >= tab).to(torch.int64)
+        dbit = (((u >= ta) & (u < tab)) | (u >= tabc)).to(torch.int64)
+        src = torch.where(act, (src << 1) | sbit, src)
+        dst = torch.where(act, (dst << 1) | dbit, dst)
+    base = vtx_off[:-1][gid_e]
+    src = src + base
+    dst = dst + base
+    del gid_e, s_e, e
+    if permute_seed is not None:
+        v = torch.arange(V, dtype=torch.int64, device=device)
+        gid_v = torch.repeat_interleave(torch.arange(n, device=device), Vg)
+        key = (gid_v << 32) | hash_u32(permute_seed, v)
+        order = torch.argsort(key)            # vertices grouped by graph, hash order inside
+        new_id = torch.empty_like(order)
+        new_id[order] = v                     # rank in that order = new global id
+        src = new_id[src]
+        dst = new_id[dst]
+    g = _csr_from_edges(V, src, dst, f"rmat_batch{n}")
+    return g, vtx_off.to(torch.int32)
+
+
+def batch_scales(count: int = 1000, lo: int = 10, hi: int = 16, seed: int = 19) -> list[int]:
+    """Seeded scales drawn uniformly from [lo, hi] for a many-graph batch."""
+    u = hash_u32(seed, torch.arange(count, dtype=torch.int64))
+    return [lo + int(x) % (hi - lo + 1) for x in u]

@@ -103,17 +103,27 @@ int tc_graph_export_transpose(const tc_graph *g, int32_t *rowptr, int32_t *colid
  * Inside a block only vertices with at least one edge get a local ID (Fig. 4), given in
  * ascending global-ID order; id_map maps local to global IDs.  All blocks are
  * concatenated in block order into one row space of R local rows.
- *   num_blocks : B >= 1 (W = ceil(V/B); the partition then has ceil(V/W) <= B blocks),
+ *   num_blocks : B >= 1 (W = ceil(V/B), rounded up to a multiple of 32 when above 32; the
+ *                partition then has ceil(V/W) <= B blocks),
  *                or 0 to derive W from the device's L2 size: W FP32 vertex values take
  *                `l2_fraction` of cudaDeviceProp::l2CacheSize; the default (<= 0) is 4/11,
  *                i.e. W = l2CacheSize / 11 -- the paper's 256 Ki vertices per subgraph
  *                on its 2.75 MB L2 (Sec. 4.3, Table 3).
  * Errors: TC_ERR_INVALID_ARG (dir, B < 0, B > V when V > 0), TC_ERR_OOM, TC_ERR_CUDA.
  */
+#define TC_BLOCKS_L2    0            /* num_blocks == 0: W from the L2 size (the paper's rule) */
+#define TC_BLOCKS_SMEM  1            /* num_blocks == 0: W from one CTA's shared memory, B a
+                                        multiple of the SM count (whole waves of CTAs)         */
+
 typedef struct tc_part_params {
-    float   l2_fraction;      /* used when num_blocks == 0; <= 0 means 4/11 */
-    int32_t merge_range;      /* k of the merge (Fig. 5): vertices per merge CTA; 0 = 1024 */
+    float   l2_fraction;      /* used when num_blocks == 0 with TC_BLOCKS_L2; <= 0 means 4/11 */
+    int32_t merge_range;      /* k of the merge (Fig. 5): vertices per merge CTA, a multiple of
+                                 32; 0 = 1024 */
     int32_t hub_degree;       /* rows with more edges go to CTA-per-row tasks; 0 = 2048 */
+    int32_t block_policy;     /* TC_BLOCKS_L2 or TC_BLOCKS_SMEM (used when num_blocks == 0) */
+    int32_t smem_stage;       /* pull only: 0 = stage each block's contributions in shared
+                                 memory whenever W fits (W <= about 41K sources, W % 32 == 0),
+                                 -1 = never, 1 = require it (TC_ERR_UNSUPPORTED if W does not fit) */
 } tc_part_params;
 
 int tc_tocab_partition(const tc_graph *g, int dir, int32_t num_blocks,
@@ -129,6 +139,8 @@ typedef struct tc_part_info {
     int64_t num_edges;        /* E */
     int32_t merge_range;      /* k */
     int32_t num_hubs;         /* rows handled one CTA per row */
+    int32_t staged;           /* 1: the gather stages block contributions in shared memory */
+    int64_t staged_edges;     /* edges of the staged stream incl. per-block padding (0 if not) */
 } tc_part_info;
 int tc_part_get_info(const tc_part *p, tc_part_info *info);
 
@@ -147,6 +159,10 @@ int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_edges, int3
 int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
 
 /* ---- PageRank ------------------------------------------------------------------------------ */
+#define TC_MERGE_FIXED    0          /* TOCAB merge adds in 64-bit fixed point: deterministic */
+#define TC_MERGE_ORDERED  1          /* per-warp FP32 accumulators added in a fixed order     */
+#define TC_MERGE_FLOAT    2          /* FP32 shared-memory atomics: last bits may vary        */
+
 typedef struct tc_pr_params {
     float   damping;          /* d, e.g. 0.85 */
     int32_t iters;            /* fixed number of Jacobi iterations (>= 0) */
@@ -154,6 +170,7 @@ typedef struct tc_pr_params {
     int32_t out_mem;          /* memory space of ranks_out (and of init) */
     const float *init;        /* initial ranks [V] or NULL for 1/V */
     int32_t profile;          /* nonzero: time each kernel with CUDA events (stats) */
+    int32_t merge_mode;       /* TOCAB pull merge: TC_MERGE_FIXED (0), _ORDERED or _FLOAT */
 } tc_pr_params;
 
 typedef struct tc_pr_stats {
@@ -218,6 +235,71 @@ typedef struct tc_bfs_stats {
 int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
                 const tc_bfs_params *params, int32_t *levels_out, tc_bfs_stats *stats,
                 void *stream);
+
+/* ---- batched personalised PageRank -------------------------------------------------------- */
+/*
+ * tc_ppr_batch -- personalised PageRank for n sources in one batch (one column per source).
+ * Column j runs Alg. 1 with the teleport (1-d) and the dangling mass of the column both sent
+ * to its source s_j, starting from e_{s_j}:
+ *   R'[v,j] = d * sum_{u->v} R[u,j] / out_degree[u] + [v == s_j] ((1-d) + d * D_j),
+ *   D_j = sum of R[u,j] over dangling u.
+ * The batch lives as an FP32 [V x n] row-major matrix; every iteration is one pull launch in
+ * which a warp reads whole rows of the contribution matrix.  The whole batch is
+ * one launch per iteration.
+ *   sources : host int32[n], each in [0, V) (repeats allowed);  1 <= n <= 1024.
+ *   params  : damping, iters, out_mem (R_out space), profile (stats->ms_total); init ignored.
+ *   R_out   : float[V * n], R_out[v*n + j].
+ * Device scratch: two [V x round_up(n,128)] FP32 matrices, allocated and freed per call.
+ * Synchronises the stream before returning.
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED (n out of range), TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_ppr_batch(const tc_graph *g, const int32_t *sources, int32_t n, const tc_pr_params *params,
+                 float *R_out, tc_pr_stats *stats, void *stream);
+
+/* ---- many small graphs in one batch ---------------------------------------------------------- */
+typedef struct tc_multigraph tc_multigraph;   /* opaque: a batch of independent graphs */
+
+/*
+ * tc_multigraph_load -- load a batch of independent graphs as one disjoint union.  Graph g
+ * owns the vertices [vtx_off[g], vtx_off[g+1]); rowptr/colidx is the out-edge CSR of the union
+ * in those global IDs (layout and rules as tc_graph_load_csr).  Every edge must join two
+ * vertices of the same graph (TC_ERR_INVALID_GRAPH otherwise).
+ *   vtx_off : host int32[num_graphs + 1], vtx_off[0] = 0, non-decreasing, vtx_off[n] = V.
+ * Errors: those of tc_graph_load_csr, TC_ERR_INVALID_ARG for a bad vtx_off.
+ */
+int tc_multigraph_load(int32_t num_graphs, const int32_t *vtx_off, int32_t V, int64_t E,
+                       const int32_t *rowptr, const int32_t *colidx, int mem, void *stream,
+                       tc_multigraph **out);
+void tc_multigraph_free(tc_multigraph *m);
+
+typedef struct tc_multi_params {
+    int32_t lanes_per_vertex; /* 0 = the autotuned choice (hybrid until tuned), -1 = a lane per
+                                 vertex with rows of 32+ edges taken by the warp, or 1/4/8/32 */
+    int32_t ctas_per_sm;      /* 0 = as many as fit (then the launch is graph-captured) */
+    int32_t use_graph;        /* 1 = launch through the cached captured CUDA graph */
+} tc_multi_params;
+
+/*
+ * tc_pagerank_multi -- Alg. 1 on every graph of the batch at once; graph g uses its own
+ * teleport (1-d)/V_g and its own dangling mass D_g (redistributed over its own vertices).
+ * All iterations run in one persistent cooperative kernel with a grid barrier between them
+ * (a bounded spin: TC_ERR_TIMEOUT if it ever gives up); with use_graph the launch is captured
+ * once into a CUDA graph (cached in the handle per parameter set) and replayed.
+ *   ranks_out : float[V] (params->out_mem), in the union's vertex order.  params->init must
+ *               be NULL (TC_ERR_UNSUPPORTED otherwise).
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED, TC_ERR_TIMEOUT, TC_ERR_CUDA.
+ */
+int tc_pagerank_multi(const tc_multigraph *m, const tc_pr_params *params, const tc_multi_params *mp,
+                      float *ranks_out, tc_pr_stats *stats, void *stream);
+
+/*
+ * tc_multi_autotune -- the project's autotuner for the batch: times every lanes-per-vertex
+ * variant (-1, 1, 4, 8, 32; one warm-up and one timed run each, CUDA events) with `params`,
+ * stores the fastest in the handle (used when lanes_per_vertex = 0) and returns it.
+ *   times_ms : optional float[5], time of each variant in the order -1, 1, 4, 8, 32.
+ */
+int tc_multi_autotune(tc_multigraph *m, const tc_pr_params *params, int32_t *best_lanes,
+                      float *times_ms, void *stream);
 
 /* ---- PageRank without allocation ------------------------------------------------------------ */
 /* Largest vertex count and size in bytes of the static device scratch used below. */

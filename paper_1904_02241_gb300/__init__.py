@@ -23,7 +23,8 @@ from . import _lib as L
 from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
                    TC_PULL, TC_PUSH)
 
-__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull",
+__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "multigraph_load",
+           "pagerank_multi", "multi_autotune", "MultiGraph",
            "Graph", "Partition", "TocabError", "lib", "default_block_width"]
 
 
@@ -116,6 +117,8 @@ class Partition:
         self.num_edges = info.num_edges
         self.merge_range = info.merge_range
         self.num_hubs = info.num_hubs
+        self.staged = bool(info.staged)
+        self.staged_edges = info.staged_edges
 
     @property
     def handle(self):
@@ -161,9 +164,12 @@ def graph_load_csr(rowptr, colidx, V: int | None = None, stream=None) -> Graph:
 
 
 def tocab_partition(graph: Graph, dir: int = L.TC_PULL, num_blocks: int = 0, l2_fraction: float = 0.0,
-                    merge_range: int = 0, hub_degree: int = 0, stream=None) -> Partition:
-    """tc_tocab_partition: static 1D blocking (num_blocks = 0 derives W from the L2 size)."""
-    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree)
+                    merge_range: int = 0, hub_degree: int = 0, block_policy: str = "l2", smem_stage: int = 0,
+                    stream=None) -> Partition:
+    """tc_tocab_partition: static 1D blocking.  num_blocks = 0 derives W from the L2 size
+    (block_policy="l2", the paper's rule) or from one CTA's shared memory ("smem")."""
+    policy = {"l2": L.TC_BLOCKS_L2, "smem": L.TC_BLOCKS_SMEM}[block_policy]
+    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree, policy, smem_stage)
     h = C.c_void_p()
     _check(L.load().tc_tocab_partition(graph.handle, dir, num_blocks, C.byref(pp), _stream(stream), C.byref(h)),
            "tc_tocab_partition")
@@ -174,7 +180,10 @@ def default_block_width(V: int, l2_bytes: int, l2_fraction: float = 0.0) -> int:
     return int(L.load().tc_default_block_width(V, l2_bytes, l2_fraction))
 
 
-def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream):
+_MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED, "float": L.TC_MERGE_FLOAT}
+
+
+def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream, merge="fixed"):
     if out is None:
         out = torch.empty(graph.V, dtype=torch.float32, device="cuda")
     if out.dtype != torch.float32 or out.numel() < graph.V or not out.is_contiguous():
@@ -187,7 +196,8 @@ def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profil
             raise ValueError("init must be float32 in the same memory space as out")
         init = init.contiguous()
         init_ptr = init.data_ptr()
-    pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), init_ptr, 1 if profile else 0)
+    pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), init_ptr, 1 if profile else 0,
+                        _MERGE[merge])
     st = L.tc_pr_stats()
     _check(fn(graph.handle, part.handle if part is not None else None, C.byref(pp), out.data_ptr(),
               C.byref(st), _stream(stream)), name)
@@ -196,10 +206,11 @@ def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profil
 
 def pagerank_pull(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
                   dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
-                  profile: bool = False, stream=None, return_stats: bool = False):
-    """tc_pagerank_pull (Alg. 1; TOCAB Alg. 4 + merge when part is given)."""
+                  profile: bool = False, stream=None, return_stats: bool = False, merge: str = "fixed"):
+    """tc_pagerank_pull (Alg. 1; TOCAB Alg. 4 + merge when part is given).
+    merge: "fixed" (deterministic), "ordered" (deterministic) or "float" (fastest)."""
     r, st = _pagerank(L.load().tc_pagerank_pull, "tc_pagerank_pull", graph, part, damping, iters, dangling, out,
-                      init, profile, stream)
+                      init, profile, stream, merge)
     return (r, st) if return_stats else r
 
 
@@ -210,6 +221,83 @@ def pagerank_push(graph: Graph, part: Partition | None = None, damping: float = 
     r, st = _pagerank(L.load().tc_pagerank_push, "tc_pagerank_push", graph, part, damping, iters, dangling, out,
                       init, profile, stream)
     return (r, st) if return_stats else r
+
+
+def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out: torch.Tensor | None = None,
+              profile: bool = False, stream=None, return_stats: bool = False):
+    """tc_ppr_batch: personalised PageRank, one column per source -> [V, n] float32."""
+    src = torch.as_tensor(sources, dtype=torch.int32).contiguous().cpu()
+    n = src.numel()
+    if out is None:
+        out = torch.empty((graph.V, n), dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or out.numel() < graph.V * n or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float32 tensor with V*n elements")
+    pp = L.tc_pr_params(float(damping), int(iters), 0, _mem(out), None, 1 if profile else 0, 0)
+    st = L.tc_pr_stats()
+    _check(L.load().tc_ppr_batch(graph.handle, src.data_ptr(), n, C.byref(pp), out.data_ptr(), C.byref(st),
+                                 _stream(stream)), "tc_ppr_batch")
+    return (out, st) if return_stats else out
+
+
+class MultiGraph:
+    """A batch of independent graphs on the current device (owns a tc_multigraph handle)."""
+
+    def __init__(self, handle, V: int, E: int, n: int):
+        self._h, self.V, self.E, self.num_graphs = handle, V, E, n
+        self.tuned_lanes = 0
+
+    @property
+    def handle(self):
+        return self._h
+
+    def free(self):
+        if self._h:
+            L.load().tc_multigraph_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def multigraph_load(rowptr, colidx, vtx_off, stream=None) -> MultiGraph:
+    """tc_multigraph_load: disjoint union CSR (global ids) + vertex offsets of its graphs."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    off = torch.as_tensor(vtx_off, dtype=torch.int32).contiguous().cpu()
+    V = rowptr.numel() - 1
+    h = C.c_void_p()
+    ci_ptr = colidx.data_ptr() if colidx.numel() > 0 else None
+    _check(L.load().tc_multigraph_load(off.numel() - 1, off.data_ptr(), V, colidx.numel(), rowptr.data_ptr(), ci_ptr,
+                                       _mem(rowptr), _stream(stream), C.byref(h)), "tc_multigraph_load")
+    return MultiGraph(h, V, colidx.numel(), off.numel() - 1)
+
+
+def pagerank_multi(mg: MultiGraph, damping: float = 0.85, iters: int = 20, dangling="redistribute",
+                   out: torch.Tensor | None = None, lanes_per_vertex: int = 0, ctas_per_sm: int = 0,
+                   use_graph: bool = True, profile: bool = False, stream=None, return_stats: bool = False):
+    """tc_pagerank_multi: PageRank on every graph of the batch in one persistent launch."""
+    if out is None:
+        out = torch.empty(mg.V, dtype=torch.float32, device="cuda")
+    mode = {"redistribute": L.TC_DANGLING_REDISTRIBUTE, "drop": L.TC_DANGLING_DROP}[dangling]
+    pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), None, 1 if profile else 0, 0)
+    mp = L.tc_multi_params(int(lanes_per_vertex), int(ctas_per_sm), 1 if use_graph else 0)
+    st = L.tc_pr_stats()
+    _check(L.load().tc_pagerank_multi(mg.handle, C.byref(pp), C.byref(mp), out.data_ptr(), C.byref(st),
+                                      _stream(stream)), "tc_pagerank_multi")
+    return (out, st) if return_stats else out
+
+
+def multi_autotune(mg: MultiGraph, damping: float = 0.85, iters: int = 20, stream=None):
+    """tc_multi_autotune: time the lanes-per-vertex variants; returns (best, {lanes: ms})."""
+    pp = L.tc_pr_params(float(damping), int(iters), 0, L.TC_MEM_DEVICE, None, 0, 0)
+    best = C.c_int32()
+    times = (C.c_float * 5)()
+    _check(L.load().tc_multi_autotune(mg.handle, C.byref(pp), C.byref(best), times, _stream(stream)),
+           "tc_multi_autotune")
+    mg.tuned_lanes = best.value
+    return best.value, dict(zip([-1, 1, 4, 8, 32], list(times)))
 
 
 def bfs_pull(graph: Graph, part: Partition | None, source: int, tocab_threshold: float = 0.05,

@@ -27,24 +27,39 @@ class tc_graph_info(C.Structure):
                 ("max_out_degree", C.c_int32), ("num_dangling", C.c_int64), ("device", C.c_int32)]
 
 
+TC_BLOCKS_L2 = 0
+TC_BLOCKS_SMEM = 1
+
+
 class tc_part_params(C.Structure):
-    _fields_ = [("l2_fraction", C.c_float), ("merge_range", C.c_int32), ("hub_degree", C.c_int32)]
+    _fields_ = [("l2_fraction", C.c_float), ("merge_range", C.c_int32), ("hub_degree", C.c_int32),
+                ("block_policy", C.c_int32), ("smem_stage", C.c_int32)]
 
 
 class tc_part_info(C.Structure):
     _fields_ = [("dir", C.c_int32), ("num_blocks", C.c_int32), ("block_width", C.c_int32),
                 ("num_rows", C.c_int64), ("num_edges", C.c_int64), ("merge_range", C.c_int32),
-                ("num_hubs", C.c_int32)]
+                ("num_hubs", C.c_int32), ("staged", C.c_int32), ("staged_edges", C.c_int64)]
+
+
+TC_MERGE_FIXED = 0
+TC_MERGE_ORDERED = 1
+TC_MERGE_FLOAT = 2
 
 
 class tc_pr_params(C.Structure):
     _fields_ = [("damping", C.c_float), ("iters", C.c_int32), ("dangling", C.c_int32),
-                ("out_mem", C.c_int32), ("init", C.c_void_p), ("profile", C.c_int32)]
+                ("out_mem", C.c_int32), ("init", C.c_void_p), ("profile", C.c_int32),
+                ("merge_mode", C.c_int32)]
 
 
 class tc_pr_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("launches", C.c_int32), ("ms_total", C.c_float),
                 ("ms_gather", C.c_float), ("ms_merge", C.c_float), ("dangling_mass", C.c_double)]
+
+
+class tc_multi_params(C.Structure):
+    _fields_ = [("lanes_per_vertex", C.c_int32), ("ctas_per_sm", C.c_int32), ("use_graph", C.c_int32)]
 
 
 class tc_bfs_params(C.Structure):
@@ -74,6 +89,12 @@ SIGNATURES = {
     "tc_pagerank_pull": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_pagerank_push": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_bfs_pull": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_bfs_params), VP, C.POINTER(tc_bfs_stats), VP]),
+    "tc_ppr_batch": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
+    "tc_multigraph_load": (C.c_int, [C.c_int32, VP, C.c_int32, C.c_int64, VP, VP, C.c_int, VP, C.POINTER(VP)]),
+    "tc_multigraph_free": (None, [VP]),
+    "tc_pagerank_multi": (C.c_int, [VP, C.POINTER(tc_pr_params), C.POINTER(tc_multi_params), VP,
+                                    C.POINTER(tc_pr_stats), VP]),
+    "tc_multi_autotune": (C.c_int, [VP, C.POINTER(tc_pr_params), C.POINTER(C.c_int32), VP, VP]),
     "tc_pagerank_pull_noalloc": (C.c_int, [C.c_int32, VP, VP, VP, C.c_float, C.c_int32, C.c_int32, VP, VP]),
 }
 

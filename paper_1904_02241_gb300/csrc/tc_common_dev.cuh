@@ -51,4 +51,33 @@ __device__ __forceinline__ void grid_sum_last_cta(double mine, double *part, uns
     }
 }
 
+// Two sums at once (a in x, b in y), same protocol as grid_sum_last_cta.
+__device__ __forceinline__ void grid_sum2_last_cta(double a, double b, double *part /* 2 per CTA */,
+                                                   unsigned *counter, double *out_a, double *out_b) {
+    __shared__ bool am_last2;
+    __shared__ double red2[32];
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = a;
+        part[2 * blockIdx.x + 1] = b;
+        __threadfence();
+        const unsigned ticket = atomicAdd(counter, 1u);
+        am_last2 = (ticket == gridDim.x - 1);
+    }
+    __syncthreads();
+    if (!am_last2) return;
+    __threadfence();
+    double ta = 0.0, tb = 0.0;
+    for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
+        ta += __ldcg(part + 2 * i);
+        tb += __ldcg(part + 2 * i + 1);
+    }
+    ta = block_sum<double>(ta, red2);
+    tb = block_sum<double>(tb, red2);
+    if (threadIdx.x == 0) {
+        *out_a = ta;
+        *out_b = tb;
+        *counter = 0u;
+    }
+}
+
 }  // namespace tc

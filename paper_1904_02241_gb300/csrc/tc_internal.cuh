@@ -130,6 +130,15 @@ struct tc_part {
     tc::DevBuf hubs;            // int32[num_hubs] rows with degree > hub_degree
     tc::DevBuf partial;         // float[R] partial sums (scratch)
     tc::DevBuf rowbits;         // uint32[ceil(R/32)] local next bits (BFS scratch)
+    tc::DevBuf merge_offT;      // int32[(nranges+1) * B]: merge_off transposed (range-major)
+    tc::DevBuf blk_rows_dev;    // int64[B+1]
+    // ---- shared-memory staged format (pull, W <= smem capacity; see tc_tile.cu) ----
+    bool tiled = false;
+    int64_t padded_edges = 0;   // edges of the staged stream (blocks padded to TILE_WCHUNK)
+    tc::DevBuf col16;           // uint16[padded_edges]: source - b*W
+    tc::DevBuf heads;           // 1 bit per staged edge: a local row starts here
+    tc::DevBuf wtab;            // int2[B * 33]: per block and warp, (first edge, first row)
+    tc::DevBuf id16;            // uint16[R]: id_map[r] mod k (k a power of two), for the merge
     ~tc_part() {
         delete[] h_blk_rows;
         delete[] h_blk_edges;
@@ -137,6 +146,16 @@ struct tc_part {
 };
 
 namespace tc {
+// Shared-memory staged TOCAB format (tc_tile.cu).
+constexpr int TILE_WCHUNK = 512;         // edges a warp streams per step (16 per lane)
+constexpr int TILE_THREADS = 1024;
+size_t tile_smem_bytes(int32_t W);       // dynamic shared memory of the staged gather for width W
+int32_t tile_max_width(int max_smem_optin);
+int build_tiles(tc_part *p, int sms, cudaStream_t s);
+size_t merge_smem_bytes(int32_t k, int32_t B);   // dynamic shared memory of the pull merge
+// Launch the staged gather (+ long rows) writing p->partial from contributions `contrib`.
+int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, cudaStream_t s, int *launches);
+
 // Rows of a CSR with more than `min_degree` edges, as a compact int32 list (ascending).
 int collect_hubs(const int32_t *rowptr, int64_t nrows, int32_t min_degree, DevBuf *list, int32_t *count,
                  cudaStream_t s);

@@ -1,0 +1,522 @@
+// Many independent graphs in one batch: pull PageRank (Alg. 1) on the disjoint union of the
+// graphs, every graph with its own teleport term (1-d)/V_g and its own dangling mass D_g.
+// All iterations run in ONE persistent cooperative kernel (grid barrier between iterations,
+// with a bounded spin) that is captured once into a CUDA graph and replayed.  The mapping of
+// lanes to vertices (1, 4, 8 or 32 lanes per vertex, or the thread/warp hybrid) is a template
+// parameter; tc_multi_autotune times every variant on the batch and keeps the fastest.
+#include <cooperative_groups.h>
+
+#include "tc_common_dev.cuh"
+
+namespace tc {
+
+constexpr int MU_THREADS = 256;
+constexpr int MU_WARPS = MU_THREADS / 32;
+constexpr int MU_CHUNK = 512;                  // vertices per warp work item
+constexpr double MU_FX = 2305843009213693952.0;  // 2^61 fixed point: a graph's mass is <= 1
+constexpr int MU_NVARIANTS = 5;
+static const int kLanes[MU_NVARIANTS] = {-1, 1, 4, 8, 32};  // -1: thread/warp hybrid
+
+}  // namespace tc
+
+struct tc_multigraph {
+    tc_graph *g = nullptr;                 // the disjoint union
+    int32_t n = 0;                         // graphs
+    tc::DevBuf vtx_off, gid, invVg;        // int32[n+1], int32[V], float[n]
+    tc::DevBuf rank, contrib, dacc, sync;  // float[V], float[2V], u64[3n], barrier words
+    int32_t tuned_lanes = 0;               // 0: not tuned yet
+    // captured CUDA graph of the persistent launch, for one parameter set
+    cudaGraphExec_t exec = nullptr;
+    float cached_damping = -1.0f;
+    int32_t cached_iters = -1, cached_drop = -1, cached_lanes = 0, cached_ctas = 0;
+    ~tc_multigraph() {
+        if (exec) cudaGraphExecDestroy(exec);
+        delete g;
+    }
+};
+
+namespace tc {
+
+struct MultiArgs {
+    const int32_t *rowptr, *colidx, *gid;
+    const float *inv_outdeg, *invVg;
+    int32_t V, n, iters, drop;
+    float damping;
+    float *contrib;             // [2][Vp]
+    int64_t Vp;
+    float *rank;                // [V]
+    unsigned long long *dacc;   // [3][n]
+    unsigned *bar;              // [0] count, [1] generation
+    int *err;
+};
+
+// Grid-wide barrier with a bounded spin (about a second); on a timeout it records code 4.
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, int *err) {
+    __syncthreads();
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        const unsigned arrived = atomicAdd(bar, 1u);
+        if (arrived == gridDim.x - 1) {
+            bar[0] = 0u;
+            __threadfence();
+            atomicAdd(bar + 1, 1u);
+        } else {
+            const long long t0 = clock64();
+            while (*gen == g0) {
+                if (clock64() - t0 > (1LL << 31)) {
+                    atomicCAS(err, 0, 4);
+                    break;
+                }
+                __nanosleep(64);
+            }
+        }
+        __threadfence();
+        ok = (*(volatile int *)err == 0);
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// Sum of the in-edges of vertex v over `lanes` cooperating lanes (sub = lane index in group).
+template <int LANES>
+__device__ __forceinline__ float gather_sum(const MultiArgs &a, const float *__restrict__ c, int64_t v, int sub,
+                                            bool valid) {
+    float acc = 0.0f;
+    if (valid) {
+        const int32_t s = __ldg(a.rowptr + v), e = __ldg(a.rowptr + v + 1);
+        for (int32_t i = s + sub; i < e; i += LANES) acc += __ldg(c + __ldg(a.colidx + i));
+    }
+#pragma unroll
+    for (int d = LANES / 2; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+    return acc;
+}
+
+// Hybrid: a lane per vertex, rows of 32+ edges by the whole warp.
+__device__ __forceinline__ float gather_hybrid(const MultiArgs &a, const float *__restrict__ c, int64_t v, bool valid) {
+    const int lane = threadIdx.x & 31;
+    int32_t s = 0, e = 0;
+    if (valid) {
+        s = __ldg(a.rowptr + v);
+        e = __ldg(a.rowptr + v + 1);
+    }
+    float sum = 0.0f;
+    if (e - s < 32)
+        for (int32_t i = s; i < e; ++i) sum += __ldg(c + __ldg(a.colidx + i));
+    unsigned wm = __ballot_sync(0xffffffffu, valid && e - s >= 32);
+    while (wm) {
+        const int l = __ffs(wm) - 1;
+        wm &= wm - 1;
+        const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
+        float acc = 0.0f;
+        for (int32_t i = ws + lane; i < we; i += 32) acc += __ldg(c + __ldg(a.colidx + i));
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        if (lane == l) sum = acc;
+    }
+    return sum;
+}
+
+// Flush a lane's dangling sum for graph g (fixed point); lanes of a warp that share g are
+// added first so that a warp issues one atomic per graph.
+__device__ __forceinline__ void flush_dangling(unsigned long long *dn, int32_t g, float val, bool has) {
+    const unsigned active = __ballot_sync(0xffffffffu, has);
+    if (!active) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, has ? g : -1);
+    unsigned long long fx = has ? (unsigned long long)__double2ll_rn((double)val * MU_FX) : 0ull;
+    // sum over peers: every lane adds the values of its peers (at most 32 shuffles)
+    unsigned long long tot = 0ull;
+    unsigned m = peers;
+    while (m) {
+        const int l = __ffs(m) - 1;
+        m &= m - 1;
+        tot += __shfl_sync(peers, fx, l);
+    }
+    const int lane = threadIdx.x & 31;
+    if (has && (__ffs(peers) - 1) == lane && tot) atomicAdd(dn + g, tot);
+}
+
+// LANES: lanes per vertex (1, 4, 8, 32), or 0 for the hybrid.
+template <int LANES>
+__global__ void __launch_bounds__(MU_THREADS) k_multi_pagerank(MultiArgs a) {
+    const int lane = threadIdx.x & 31;
+    constexpr int L = LANES == 0 ? 1 : LANES;     // lanes per vertex in this warp step
+    constexpr int VPW = 32 / L;                   // vertices per warp step
+    const int sub = lane % L, slot = lane / L;
+    const int64_t nitems = ((int64_t)a.V + MU_CHUNK - 1) / MU_CHUNK;
+    const int64_t gw = (int64_t)blockIdx.x * MU_WARPS + (threadIdx.x >> 5);
+    const int64_t nw = (int64_t)gridDim.x * MU_WARPS;
+    unsigned long long *D[3] = {a.dacc, a.dacc + a.n, a.dacc + 2 * a.n};
+
+    // ---- init: r0 = 1/V_g, contributions, D_0 per graph; D[1] cleared ----
+    if (blockIdx.x == 0)
+        for (int32_t g = threadIdx.x; g < a.n; g += MU_THREADS) D[1][g] = 0ull;
+    for (int64_t it = gw; it < nitems; it += nw) {
+        const int64_t v0 = it * MU_CHUNK;
+        int32_t gcur = -1;
+        float dl = 0.0f;
+        for (int64_t v = v0 + lane; v < v0 + MU_CHUNK; v += 32) {
+            const bool valid = v < a.V;
+            const int32_t g = valid ? __ldg(a.gid + v) : -1;
+            float r = 0.0f, inv = 1.0f;
+            if (valid) {
+                r = __ldg(a.invVg + g);
+                inv = __ldg(a.inv_outdeg + v);
+                a.contrib[v] = r * inv;
+                if (a.iters == 0) a.rank[v] = r;
+            }
+            const bool change = __any_sync(0xffffffffu, g != gcur && gcur >= 0);
+            if (change) {
+                flush_dangling(D[0], gcur, dl, gcur >= 0 && dl != 0.0f);
+                dl = 0.0f;
+            }
+            gcur = valid ? g : gcur;
+            if (valid && inv == 0.0f) dl += r;
+        }
+        flush_dangling(D[0], gcur, dl, gcur >= 0 && dl != 0.0f);
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+
+    for (int32_t iter = 0; iter < a.iters; ++iter) {
+        const float *cur = a.contrib + (iter & 1) * a.Vp;
+        float *nxt = a.contrib + ((iter + 1) & 1) * a.Vp;
+        const unsigned long long *Dc = D[iter % 3];
+        unsigned long long *Dn = D[(iter + 1) % 3];
+        if (blockIdx.x == 0)
+            for (int32_t g = threadIdx.x; g < a.n; g += MU_THREADS) D[(iter + 2) % 3][g] = 0ull;
+        const bool last = iter == a.iters - 1;
+        for (int64_t it = gw; it < nitems; it += nw) {
+            const int64_t v0 = it * MU_CHUNK;
+            const int64_t v1 = (v0 + MU_CHUNK < a.V) ? v0 + MU_CHUNK : a.V;
+            int32_t gcur = -1;
+            float dl = 0.0f;
+            for (int64_t vb = v0; vb < v1; vb += VPW) {
+                const int64_t v = vb + slot;
+                const bool valid = v < v1;
+                float sum;
+                if (LANES == 0) sum = gather_hybrid(a, cur, v, valid);
+                else sum = gather_sum<L>(a, cur, v, sub, valid);
+                int32_t g = -1;
+                float r = 0.0f, inv = 1.0f;
+                if (valid && sub == 0) {
+                    g = __ldg(a.gid + v);
+                    const float ivg = __ldg(a.invVg + g);
+                    const float spread = a.drop ? 0.0f : (float)((double)Dc[g] / MU_FX) * ivg;
+                    r = (1.0f - a.damping) * ivg + a.damping * (sum + spread);
+                    inv = __ldg(a.inv_outdeg + v);
+                    nxt[v] = r * inv;
+                    if (last) a.rank[v] = r;
+                }
+                const bool lead = valid && sub == 0;
+                const bool change = __any_sync(0xffffffffu, lead && g != gcur && gcur >= 0);
+                if (change) {
+                    flush_dangling(Dn, gcur, dl, gcur >= 0 && dl != 0.0f);
+                    dl = 0.0f;
+                    gcur = -1;
+                }
+                if (lead) {
+                    gcur = g;
+                    if (inv == 0.0f) dl += r;
+                }
+            }
+            flush_dangling(Dn, gcur, dl, gcur >= 0 && dl != 0.0f);
+        }
+        if (!grid_barrier(a.bar, a.err)) return;
+    }
+}
+
+__global__ void k_multi_gid(const int32_t *vtx_off, int32_t n, int32_t V, int32_t *gid, float *invVg) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = n;  // last g with vtx_off[g] <= v
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (vtx_off[mid] <= v) lo = mid; else hi = mid;
+        }
+        gid[v] = lo;
+    }
+    for (int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; g < n; g += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t nv = vtx_off[g + 1] - vtx_off[g];
+        invVg[g] = nv > 0 ? 1.0f / (float)nv : 0.0f;
+    }
+}
+
+// every in-edge u -> v must join two vertices of the same graph
+__global__ void k_multi_check(const int32_t *rowptr, const int32_t *colidx, const int32_t *gid, int32_t V, int *bad) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t g = gid[v];
+        for (int32_t i = rowptr[v]; i < rowptr[v + 1]; ++i)
+            if (gid[colidx[i]] != g) {
+                atomicOr(bad, 1);
+                break;
+            }
+    }
+}
+
+typedef void (*MultiKernel)(MultiArgs);
+static MultiKernel multi_kernel(int lanes) {
+    switch (lanes) {
+        case 1: return k_multi_pagerank<1>;
+        case 4: return k_multi_pagerank<4>;
+        case 8: return k_multi_pagerank<8>;
+        case 32: return k_multi_pagerank<32>;
+        default: return k_multi_pagerank<0>;
+    }
+}
+
+static int multi_grid(int lanes, int ctas_per_sm, int *grid) {
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    int per_sm = 0;
+    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)multi_kernel(lanes), MU_THREADS, 0));
+    if (per_sm < 1) return fail(TC_ERR_CUDA, "k_multi_pagerank cannot be resident");
+    if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
+    *grid = caps.sms * per_sm;
+    return TC_OK;
+}
+
+// Clears the barrier words and the dangling accumulators, then launches the persistent kernel.
+static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int grid, cudaStream_t s) {
+    TC_CUDA(cudaMemsetAsync(m->sync.p, 0, 16, s));
+    TC_CUDA(cudaMemsetAsync(m->dacc.p, 0, (size_t)3 * m->n * 8, s));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(MU_THREADS);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TC_CUDA(cudaLaunchKernelEx(&cfg, multi_kernel(lanes), a));
+    return TC_OK;
+}
+
+static MultiArgs make_args(tc_multigraph *m, const tc_pr_params *pp) {
+    MultiArgs a;
+    a.rowptr = m->g->in_rowptr.as<int32_t>();
+    a.colidx = m->g->in_colidx.as<int32_t>();
+    a.gid = m->gid.as<int32_t>();
+    a.inv_outdeg = m->g->inv_outdeg.as<float>();
+    a.invVg = m->invVg.as<float>();
+    a.V = m->g->V;
+    a.n = m->n;
+    a.iters = pp->iters;
+    a.drop = pp->dangling == TC_DANGLING_DROP;
+    a.damping = pp->damping;
+    a.Vp = ((int64_t)a.V + 63) / 64 * 64;
+    a.contrib = m->contrib.as<float>();
+    a.rank = m->rank.as<float>();
+    a.dacc = m->dacc.as<unsigned long long>();
+    a.bar = m->sync.as<unsigned>();
+    a.err = reinterpret_cast<int *>(m->sync.as<unsigned>() + 2);
+    return a;
+}
+
+// One run: clear the barrier/error words, then the persistent kernel (through the cached
+// CUDA graph when use_graph).
+static int run_multi(tc_multigraph *m, const tc_pr_params *pp, int lanes, int ctas_per_sm, bool use_graph,
+                     cudaStream_t s) {
+    int grid = 0;
+    TC_TRY(multi_grid(lanes, ctas_per_sm, &grid));
+    const MultiArgs a = make_args(m, pp);
+    if (!use_graph) return launch_multi(m, a, lanes, grid, s);
+    const bool same = m->exec && m->cached_damping == pp->damping && m->cached_iters == pp->iters &&
+                      m->cached_drop == a.drop && m->cached_lanes == lanes && m->cached_ctas == grid;
+    if (!same) {
+        if (m->exec) {
+            cudaGraphExecDestroy(m->exec);
+            m->exec = nullptr;
+        }
+        cudaStream_t cs;
+        TC_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+        int st = TC_OK;
+        if (e == cudaSuccess) {
+            st = launch_multi(m, a, lanes, grid, cs);
+            cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+            if (e == cudaSuccess) e = e2;
+        }
+        if (e == cudaSuccess && st == TC_OK) e = cudaGraphInstantiate(&m->exec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        cudaStreamDestroy(cs);
+        if (st != TC_OK) return st;
+        if (e != cudaSuccess) {
+            m->exec = nullptr;
+            return fail(TC_ERR_CUDA, "capturing the persistent launch failed: %s", cudaGetErrorString(e));
+        }
+        m->cached_damping = pp->damping;
+        m->cached_iters = pp->iters;
+        m->cached_drop = a.drop;
+        m->cached_lanes = lanes;
+        m->cached_ctas = grid;
+    }
+    TC_CUDA(cudaGraphLaunch(m->exec, s));
+    return TC_OK;
+}
+
+static int timed_run(tc_multigraph *m, const tc_pr_params *pp, int lanes, cudaStream_t s, float *ms) {
+    cudaEvent_t ev[2];
+    TC_CUDA(cudaEventCreate(&ev[0]));
+    TC_CUDA(cudaEventCreate(&ev[1]));
+    TC_CUDA(cudaEventRecord(ev[0], s));
+    int st = run_multi(m, pp, lanes, 0, false, s);
+    cudaEventRecord(ev[1], s);
+    cudaEventSynchronize(ev[1]);
+    cudaEventElapsedTime(ms, ev[0], ev[1]);
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    return st;
+}
+
+}  // namespace tc
+
+extern "C" int tc_multigraph_load(int32_t num_graphs, const int32_t *vtx_off, int32_t V, int64_t E,
+                                  const int32_t *rowptr, const int32_t *colidx, int mem, void *stream,
+                                  tc_multigraph **out) {
+    using namespace tc;
+    if (!out) return fail(TC_ERR_INVALID_ARG, "tc_multigraph_load: out is NULL");
+    *out = nullptr;
+    if (num_graphs < 1 || !vtx_off) return fail(TC_ERR_INVALID_ARG, "tc_multigraph_load: no graphs");
+    if (vtx_off[0] != 0 || vtx_off[num_graphs] != V)
+        return fail(TC_ERR_INVALID_ARG, "tc_multigraph_load: vtx_off must run from 0 to V");
+    for (int32_t g = 0; g < num_graphs; ++g)
+        if (vtx_off[g + 1] < vtx_off[g]) return fail(TC_ERR_INVALID_ARG, "tc_multigraph_load: vtx_off not monotone");
+    cudaStream_t s = (cudaStream_t)stream;
+    tc_graph *g = nullptr;
+    TC_TRY(tc_graph_load_csr(V, E, rowptr, colidx, mem, stream, &g));
+    tc_multigraph *m = new (std::nothrow) tc_multigraph();
+    if (!m) {
+        tc_graph_free(g);
+        return fail(TC_ERR_OOM, "host allocation failed");
+    }
+    m->g = g;
+    m->n = num_graphs;
+    int st = m->vtx_off.alloc(((size_t)num_graphs + 1) * 4);
+    if (st == TC_OK) st = m->gid.alloc((size_t)(V > 0 ? V : 1) * 4);
+    if (st == TC_OK) st = m->invVg.alloc((size_t)num_graphs * 4);
+    const int64_t Vp = ((int64_t)V + 63) / 64 * 64;
+    if (st == TC_OK) st = m->rank.alloc((size_t)(V > 0 ? V : 1) * 4);
+    if (st == TC_OK) st = m->contrib.alloc((size_t)(2 * Vp + 64) * 4);
+    if (st == TC_OK) st = m->dacc.alloc((size_t)3 * num_graphs * 8);
+    if (st == TC_OK) st = m->sync.alloc(64);
+    if (st != TC_OK) {
+        delete m;
+        return st;
+    }
+    cudaError_t e = cudaMemcpyAsync(m->vtx_off.p, vtx_off, ((size_t)num_graphs + 1) * 4, cudaMemcpyHostToDevice, s);
+    DeviceCaps caps;
+    if (e == cudaSuccess && (st = device_caps(&caps)) == TC_OK) {
+        k_multi_gid<<<caps.sms * 8, 256, 0, s>>>(m->vtx_off.as<int32_t>(), num_graphs, V, m->gid.as<int32_t>(),
+                                                 m->invVg.as<float>());
+        e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->sync.p, 0, 64, s);
+        if (e == cudaSuccess && V > 0) {
+            k_multi_check<<<caps.sms * 8, 256, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(),
+                                                       m->gid.as<int32_t>(), V, reinterpret_cast<int *>(m->sync.p));
+            e = cudaGetLastError();
+        }
+        int bad = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, m->sync.p, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e == cudaSuccess && bad) st = fail(TC_ERR_INVALID_GRAPH, "tc_multigraph_load: an edge joins two graphs");
+        if (e == cudaSuccess) e = cudaMemsetAsync(m->sync.p, 0, 64, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (e != cudaSuccess) st = fail(TC_ERR_CUDA, "tc_multigraph_load: %s", cudaGetErrorString(e));
+    if (st != TC_OK) {
+        delete m;
+        return st;
+    }
+    *out = m;
+    return TC_OK;
+}
+
+extern "C" void tc_multigraph_free(tc_multigraph *m) {
+    if (!m) return;
+    cudaDeviceSynchronize();
+    delete m;
+}
+
+extern "C" int tc_multi_autotune(tc_multigraph *m, const tc_pr_params *params, int32_t *best_lanes, float *times_ms,
+                                 void *stream) {
+    using namespace tc;
+    if (!m || !params) return fail(TC_ERR_INVALID_ARG, "tc_multi_autotune: null argument");
+    if (m->g->V == 0) return fail(TC_ERR_INVALID_ARG, "tc_multi_autotune: empty batch");
+    cudaStream_t s = (cudaStream_t)stream;
+    float best = 3.4e38f;
+    int best_l = -1;
+    for (int k = 0; k < MU_NVARIANTS; ++k) {
+        float ms = 0, ms2 = 0;
+        TC_TRY(timed_run(m, params, kLanes[k], s, &ms));   // warm-up
+        TC_TRY(timed_run(m, params, kLanes[k], s, &ms2));
+        if (times_ms) times_ms[k] = ms2;
+        if (ms2 < best) {
+            best = ms2;
+            best_l = kLanes[k];
+        }
+    }
+    int err = 0;
+    TC_CUDA(cudaMemcpyAsync(&err, m->sync.as<unsigned>() + 2, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (err) return fail(TC_ERR_TIMEOUT, "tc_multi_autotune: a grid barrier gave up");
+    m->tuned_lanes = best_l;
+    if (best_lanes) *best_lanes = best_l;
+    return TC_OK;
+}
+
+extern "C" int tc_pagerank_multi(const tc_multigraph *cm, const tc_pr_params *params, const tc_multi_params *mp,
+                                 float *ranks_out, tc_pr_stats *stats, void *stream) {
+    using namespace tc;
+    tc_multigraph *m = const_cast<tc_multigraph *>(cm);
+    if (!m || !params || !ranks_out) return fail(TC_ERR_INVALID_ARG, "tc_pagerank_multi: null argument");
+    if (!(params->damping >= 0.0f && params->damping <= 1.0f) || params->iters < 0)
+        return fail(TC_ERR_INVALID_ARG, "tc_pagerank_multi: damping outside [0,1] or iters < 0");
+    if (params->dangling != TC_DANGLING_REDISTRIBUTE && params->dangling != TC_DANGLING_DROP)
+        return fail(TC_ERR_INVALID_ARG, "tc_pagerank_multi: bad dangling mode");
+    if (params->out_mem != TC_MEM_HOST && params->out_mem != TC_MEM_DEVICE)
+        return fail(TC_ERR_INVALID_ARG, "tc_pagerank_multi: bad out_mem");
+    if (params->init) return fail(TC_ERR_UNSUPPORTED, "tc_pagerank_multi: init ranks are not supported");
+    int lanes = mp ? mp->lanes_per_vertex : 0;
+    if (lanes == 0) lanes = m->tuned_lanes ? m->tuned_lanes : -1;
+    if (lanes != -1 && lanes != 1 && lanes != 4 && lanes != 8 && lanes != 32)
+        return fail(TC_ERR_INVALID_ARG, "tc_pagerank_multi: lanes_per_vertex must be 0, -1, 1, 4, 8 or 32");
+    const bool use_graph = mp ? mp->use_graph != 0 : true;
+    const int ctas = mp ? mp->ctas_per_sm : 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (m->g->V == 0) return TC_OK;
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (params->profile) {
+        TC_CUDA(cudaEventCreate(&ev[0]));
+        TC_CUDA(cudaEventCreate(&ev[1]));
+        TC_CUDA(cudaEventRecord(ev[0], s));
+    }
+    TC_TRY(run_multi(m, params, lanes, ctas, use_graph && ctas == 0, s));
+    float ms = 0;
+    if (params->profile) {
+        TC_CUDA(cudaEventRecord(ev[1], s));
+        TC_CUDA(cudaEventSynchronize(ev[1]));
+        TC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    const cudaMemcpyKind kind = params->out_mem == TC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    TC_CUDA(cudaMemcpyAsync(ranks_out, m->rank.p, (size_t)m->g->V * 4, kind, s));
+    if (stats || params->out_mem == TC_MEM_HOST) {
+        int err = 0;
+        TC_CUDA(cudaMemcpyAsync(&err, m->sync.as<unsigned>() + 2, 4, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        if (err) return fail(TC_ERR_TIMEOUT, "tc_pagerank_multi: a grid barrier gave up");
+    }
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->iters = params->iters;
+        stats->launches = 1;
+        stats->ms_total = ms;
+        stats->ms_gather = ms;
+    }
+    return TC_OK;
+}

@@ -25,6 +25,7 @@ struct UpdateArgs {
     const float *inv_outdeg;
     float *rank_out;        // may be null (only the last iteration writes ranks)
     float *contrib_next;    // contributions for the next iteration
+    double *fx_scale;       // fixed-point scale of the merge (written by the init kernel)
 };
 
 __device__ __forceinline__ float spread_of(const UpdateArgs &u) {
@@ -108,48 +109,293 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_gather(const int32_t *__res
 }
 
 // ---------------------------------------------------------------------------------------------
-// TOCAB merge (Fig. 5): CTA j owns vertices [j*k, (j+1)*k).  Warp w adds the slices of blocks
-// w, w+8, ... (in block order) into its private shared-memory accumulator; the eight
-// accumulators are then added in warp order, so the summation order is fixed.  The update of
-// Alg. 1 (lines 9-10), the next contributions and the dangling mass are fused in.
+// TOCAB merge (Fig. 5): CTA j owns vertices [j*k, (j+1)*k).  For every block it reads the slice
+// of local rows whose global IDs fall in the range (bounds from the range-major table).  The
+// slices are cut into chunks of at most 32 rows; warp w takes chunks w, w+16, ... of the
+// flattened chunk list, several at a time, and adds them into its own shared-memory
+// accumulator (the rows of one chunk have distinct IDs, so no atomics are needed).  The 16
+// accumulators are then added in warp order: the summation order is fixed, so the merge is
+// deterministic.  The update of Alg. 1 (lines 9-10), the next contributions and the dangling
+// mass are fused in.
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(PR_THREADS) k_pull_merge(const float *__restrict__ partial,
+constexpr int MG_THREADS = 512;
+constexpr int MG_WARPS = MG_THREADS / 32;
+constexpr int MG_UNROLL = 16;
+constexpr int MG_CMAP_EXTRA = 2048;  // chunk-to-block map entries beyond one per block
+
+size_t merge_smem_bytes(int32_t k, int32_t B) {
+    return (size_t)MG_WARPS * k * 4 + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+}
+
+// id16 != null: local id inside the range is id16[r] (k a power of two <= 65536);
+// otherwise id_map[r] - j*k.
+__global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *__restrict__ partial,
                                                            const int32_t *__restrict__ id_map,
-                                                           const int32_t *__restrict__ merge_off, int32_t B,
-                                                           int32_t nranges, int32_t k, UpdateArgs u) {
-    extern __shared__ float acc[];  // [PR_WARPS][k]
+                                                           const uint16_t *__restrict__ id16,
+                                                           const int32_t *__restrict__ offT, int32_t B, int32_t k,
+                                                           UpdateArgs u) {
+    extern __shared__ __align__(16) unsigned char msm[];
+    float *acc = reinterpret_cast<float *>(msm);                        // [MG_WARPS][k]
+    int32_t *lo = reinterpret_cast<int32_t *>(acc + (size_t)MG_WARPS * k);  // [B]
+    int32_t *len = lo + B;                                              // [B]
+    int32_t *cpre = len + B;                                            // [B + 1] chunk prefix
+    uint16_t *cmap = reinterpret_cast<uint16_t *>(cpre + B + 1);        // [B + MG_CMAP_EXTRA]
+    const int32_t cmap_cap = B + MG_CMAP_EXTRA;
+    __shared__ int32_t wsum[MG_WARPS];
     __shared__ float fred[32];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t j = blockIdx.x;
     const int32_t vbase = j * k;
-    for (int t = threadIdx.x; t < PR_WARPS * k; t += PR_THREADS) acc[t] = 0.0f;
+    for (int t = tid; t < MG_WARPS * k; t += MG_THREADS) acc[t] = 0.0f;
+    // slice bounds and chunk counts of every block, then an exclusive scan of the counts
+    const int per = (B + MG_THREADS - 1) / MG_THREADS;
+    int32_t run = 0;
+    for (int q = 0; q < per; ++q) {
+        const int32_t b = tid * per + q;
+        if (b < B) {
+            const int32_t l0 = __ldg(offT + (int64_t)j * B + b), l1 = __ldg(offT + (int64_t)(j + 1) * B + b);
+            lo[b] = l0;
+            len[b] = l1 - l0;
+            run += (l1 - l0 + 31) >> 5;
+        }
+    }
+    int incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    float *mine = acc + warp * k;
-    for (int32_t b = warp; b < B; b += PR_WARPS) {
-        const int32_t *o = merge_off + (int64_t)b * (nranges + 1) + j;
-        const int32_t r0 = __ldg(o), r1 = __ldg(o + 1);
-        for (int32_t r = r0 + lane; r < r1; r += 32) mine[__ldg(id_map + r) - vbase] += __ldg(partial + r);
-        __syncwarp();
+    if (warp == 0) {
+        const int w = lane < MG_WARPS ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < MG_WARPS) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int32_t base = wsum[warp] + incl - run;
+    for (int q = 0; q < per; ++q) {
+        const int32_t b = tid * per + q;
+        if (b < B) {
+            cpre[b] = base;
+            base += (len[b] + 31) >> 5;
+        }
+    }
+    if (tid == MG_THREADS - 1) cpre[B] = base;
+    __syncthreads();
+    // chunk -> block map (B <= 65535 here); chunks past its capacity are found by walking
+    for (int q = 0; q < per; ++q) {
+        const int32_t b = tid * per + q;
+        if (b < B)
+            for (int32_t c = cpre[b]; c < cpre[b + 1] && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
+    }
+    __syncthreads();
+    const int32_t nchunks = cpre[B];
+    float *mine = acc + (size_t)warp * k;
+    for (int32_t c0 = warp; c0 < nchunks; c0 += MG_WARPS * MG_UNROLL) {
+        int32_t idq[MG_UNROLL];
+        float vq[MG_UNROLL];
+#pragma unroll
+        for (int q = 0; q < MG_UNROLL; ++q) {
+            const int32_t c = c0 + q * MG_WARPS;
+            idq[q] = -1;
+            vq[q] = 0.0f;
+            if (c < nchunks) {
+                int32_t bp;
+                if (c < cmap_cap) {
+                    bp = cmap[c];
+                } else {
+                    bp = cmap[cmap_cap - 1];
+                    while (cpre[bp + 1] <= c) ++bp;
+                }
+                const int32_t i = ((c - cpre[bp]) << 5) + lane;
+                if (i < len[bp]) {
+                    const int32_t r = lo[bp] + i;
+                    idq[q] = id16 ? (int32_t)__ldg(id16 + r) : __ldg(id_map + r) - vbase;
+                    vq[q] = __ldg(partial + r);
+                }
+            }
+        }
+        // one chunk at a time: rows of a chunk have distinct IDs; chunks may share IDs
+#pragma unroll
+        for (int q = 0; q < MG_UNROLL; ++q) {
+            if (idq[q] >= 0) mine[idq[q]] += vq[q];
+            __syncwarp();
+        }
     }
     __syncthreads();
     const float spread = spread_of(u);
     float dsum = 0.0f;
-    for (int t = threadIdx.x; t < k; t += PR_THREADS) {
+    for (int t = tid; t < k; t += MG_THREADS) {
         const int32_t v = vbase + t;
         if (v >= u.V) break;
-        float s = 0.0f;
+        float sum = 0.0f;
 #pragma unroll
-        for (int w = 0; w < PR_WARPS; ++w) s += acc[w * k + t];
-        dsum += apply_update(u, v, s, spread);
+        for (int w = 0; w < MG_WARPS; ++w) sum += acc[(size_t)w * k + t];
+        dsum += apply_update(u, v, sum, spread);
     }
     const float bs = block_sum<float>(dsum, fred);
     grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
 }
 
-// Initial ranks (1/V or caller's), first contributions and their dangling mass.
-__global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict__ init, UpdateArgs u) {
+// Same slices and chunks as k_pull_merge_ordered, but one shared accumulator per CTA updated
+// with shared-memory atomics.  FIXED: each partial becomes a 64-bit fixed-point integer v
+// (scale 2^48 / max(1, mass), so no vertex sum exceeds 2^48) split as
+// v = hi * 2^32 + mid * 2^16 + lo; the three parts are added with native 32-bit shared
+// reductions (hi signed; mid and lo stay below 2^32 for fewer than 65536 entries per vertex)
+// and recombined exactly, so the result does not depend on the order: deterministic.
+// Otherwise FP32 atomics (the order of the additions, and so the last bits, may vary).
+template <bool FIXED>
+__global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *__restrict__ partial,
+                                                                  const int32_t *__restrict__ id_map,
+                                                                  const uint16_t *__restrict__ id16,
+                                                                  const int32_t *__restrict__ offT, int32_t B,
+                                                                  int32_t k, UpdateArgs u) {
+    extern __shared__ __align__(16) unsigned char msm[];
+    int32_t *acc_hi = reinterpret_cast<int32_t *>(msm);        // FIXED: [k] each
+    uint32_t *acc_mid = reinterpret_cast<uint32_t *>(acc_hi + k);
+    uint32_t *acc_lo = acc_mid + k;
+    float *acc32 = reinterpret_cast<float *>(msm);               // FP32: [k]
+    int32_t *lo = reinterpret_cast<int32_t *>(msm + (size_t)k * (FIXED ? 12 : 4));  // [B]
+    int32_t *len = lo + B;
+    int32_t *cpre = len + B;
+    uint16_t *cmap = reinterpret_cast<uint16_t *>(cpre + B + 1);
+    const int32_t cmap_cap = B + MG_CMAP_EXTRA;
+    __shared__ int32_t wsum[MG_WARPS];
     __shared__ float fred[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t j = blockIdx.x;
+    const int32_t vbase = j * k;
+    const double scale = FIXED ? *u.fx_scale * (1.0 / 8192.0) : 1.0;  // 2^61 -> 2^48 per unit mass
+    for (int t = tid; t < k; t += MG_THREADS) {
+        if (FIXED) {
+            acc_hi[t] = 0;
+            acc_mid[t] = 0u;
+            acc_lo[t] = 0u;
+        } else {
+            acc32[t] = 0.0f;
+        }
+    }
+    const int per = (B + MG_THREADS - 1) / MG_THREADS;
+    int32_t run = 0;
+    for (int q = 0; q < per; ++q) {
+        const int32_t b = tid * per + q;
+        if (b < B) {
+            const int32_t l0 = __ldg(offT + (int64_t)j * B + b), l1 = __ldg(offT + (int64_t)(j + 1) * B + b);
+            lo[b] = l0;
+            len[b] = l1 - l0;
+            run += (l1 - l0 + 31) >> 5;
+        }
+    }
+    int incl = run;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        const int w = lane < MG_WARPS ? wsum[lane] : 0;
+        int wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        if (lane < MG_WARPS) wsum[lane] = wi - w;
+    }
+    __syncthreads();
+    int32_t base = wsum[warp] + incl - run;
+    for (int q = 0; q < per; ++q) {
+        const int32_t b = tid * per + q;
+        if (b < B) {
+            cpre[b] = base;
+            base += (len[b] + 31) >> 5;
+        }
+    }
+    if (tid == MG_THREADS - 1) cpre[B] = base;
+    __syncthreads();
+    for (int q = 0; q < per; ++q) {
+        const int32_t b = tid * per + q;
+        if (b < B)
+            for (int32_t c = cpre[b]; c < cpre[b + 1] && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
+    }
+    __syncthreads();
+    const int32_t nchunks = cpre[B];
+    for (int32_t c0 = warp; c0 < nchunks; c0 += MG_WARPS * MG_UNROLL) {
+        int32_t idq[MG_UNROLL];
+        float vq[MG_UNROLL];
+#pragma unroll
+        for (int q = 0; q < MG_UNROLL; ++q) {
+            const int32_t c = c0 + q * MG_WARPS;
+            idq[q] = -1;
+            vq[q] = 0.0f;
+            if (c < nchunks) {
+                int32_t bp;
+                if (c < cmap_cap) {
+                    bp = cmap[c];
+                } else {
+                    bp = cmap[cmap_cap - 1];
+                    while (cpre[bp + 1] <= c) ++bp;
+                }
+                const int32_t i = ((c - cpre[bp]) << 5) + lane;
+                if (i < len[bp]) {
+                    const int32_t r = lo[bp] + i;
+                    idq[q] = id16 ? (int32_t)__ldg(id16 + r) : __ldg(id_map + r) - vbase;
+                    vq[q] = __ldg(partial + r);
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MG_UNROLL; ++q) {
+            if (idq[q] >= 0) {
+                if (FIXED) {
+                    const long long v = __double2ll_rn((double)vq[q] * scale);
+                    atomicAdd(acc_hi + idq[q], (int32_t)(v >> 32));
+                    atomicAdd(acc_mid + idq[q], (uint32_t)((v >> 16) & 0xFFFF));
+                    atomicAdd(acc_lo + idq[q], (uint32_t)(v & 0xFFFF));
+                } else {
+                    atomicAdd(acc32 + idq[q], vq[q]);
+                }
+            }
+        }
+    }
+    __syncthreads();
+    const float spread = spread_of(u);
+    const double inv_scale = 1.0 / scale;
     float dsum = 0.0f;
+    for (int t = tid; t < k; t += MG_THREADS) {
+        const int32_t v = vbase + t;
+        if (v >= u.V) break;
+        float sum;
+        if (FIXED) {
+            const long long tot = ((long long)acc_hi[t] << 32) + ((long long)acc_mid[t] << 16) + (long long)acc_lo[t];
+            sum = (float)((double)tot * inv_scale);
+        } else {
+            sum = acc32[t];
+        }
+        dsum += apply_update(u, v, sum, spread);
+    }
+    const float bs = block_sum<float>(dsum, fred);
+    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+}
+
+size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed) {
+    return (size_t)k * (fixed ? 12 : 4) + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+}
+
+// Initial ranks (1/V or caller's), first contributions, their dangling mass, and the
+// fixed-point scale of the merge: 2^61 / max(1, sum |r|).  No later iteration has a larger
+// L1 mass (each is (1-d) + d * previous at most), so no vertex sum can overflow 2^63.
+__global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict__ init, UpdateArgs u, double *mass) {
+    __shared__ float fred[32];
+    float dsum = 0.0f, msum = 0.0f;
     const float r0 = 1.0f / (float)u.V;
     for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < u.V; v += (int64_t)gridDim.x * PR_THREADS) {
         const float r = init ? init[v] : r0;
@@ -157,9 +403,18 @@ __global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict_
         const float inv = __ldg(u.inv_outdeg + v);
         u.contrib_next[v] = r * inv;
         if (inv == 0.0f) dsum += r;
+        msum += fabsf(r);
     }
     const float bs = block_sum<float>(dsum, fred);
-    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+    const float bm = block_sum<float>(msum, fred);
+    grid_sum2_last_cta((double)bs, (double)bm, u.dpart, u.counter, u.D_next, mass);
+}
+
+// 2^61 / max(1, mass): a vertex sum is at most the mass, so |sum * scale| <= 2^61 < 2^63
+// (the factor 4 of headroom also covers the rounding of the FP32 mass).
+__global__ void k_pr_scale(const double *mass, double *scale) {
+    const double m = *mass;
+    *scale = 2305843009213693952.0 / (m > 1.0 ? m : 1.0);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -271,7 +526,10 @@ struct PrState {
     float *contrib[2];
     double *D;          // D[0], D[1]
     unsigned *counter;
-    double *dpart;      // per-CTA partials (capacity dpart_cap)
+    double *mass;       // L1 mass of the initial ranks
+    double *scale;      // fixed-point scale of the merge
+    int *err;           // sticky error flag of bounded device waits
+    double *dpart;      // per-CTA partials (capacity 2 * dpart_cap doubles)
     int64_t dpart_cap;
     float *rank_dev;    // ranks on the device (caller's buffer or scratch)
     float *sums;        // push only
@@ -280,15 +538,22 @@ struct PrState {
 static int prepare_state(tc_graph *g, const tc_pr_params *pp, float *ranks_out, bool push, int64_t max_ctas,
                          PrState *st) {
     const int32_t V = g->V;
-    TC_TRY(g->ws_contrib.alloc((size_t)V * 4 * (push ? 3 : 2) + 256));
+    const int64_t Vp = ((int64_t)V + 63) / 64 * 64;  // 256-byte aligned vectors, padded for bulk copies
+    TC_TRY(g->ws_contrib.alloc((size_t)Vp * 4 * (push ? 3 : 2) + 256));
     st->contrib[0] = g->ws_contrib.as<float>();
-    st->contrib[1] = st->contrib[0] + V;
-    st->sums = push ? st->contrib[1] + V : nullptr;
+    st->contrib[1] = st->contrib[0] + Vp;
+    st->sums = push ? st->contrib[1] + Vp : nullptr;
     st->dpart_cap = max_ctas;
-    TC_TRY(g->ws_scalars.alloc(64 + (size_t)max_ctas * 8));
-    st->D = reinterpret_cast<double *>(g->ws_scalars.as<char>());
-    st->counter = reinterpret_cast<unsigned *>(g->ws_scalars.as<char>() + 32);
-    st->dpart = reinterpret_cast<double *>(g->ws_scalars.as<char>() + 64);
+    const bool fresh = g->ws_scalars.p == nullptr;
+    TC_TRY(g->ws_scalars.alloc(128 + (size_t)max_ctas * 16));
+    char *sc = g->ws_scalars.as<char>();
+    st->D = reinterpret_cast<double *>(sc);
+    st->counter = reinterpret_cast<unsigned *>(sc + 32);
+    st->err = reinterpret_cast<int *>(sc + 40);
+    st->mass = reinterpret_cast<double *>(sc + 48);
+    st->scale = reinterpret_cast<double *>(sc + 56);
+    st->dpart = reinterpret_cast<double *>(sc + 128);
+    (void)fresh;
     if (pp->out_mem == TC_MEM_DEVICE) {
         st->rank_dev = ranks_out;
     } else {
@@ -306,6 +571,8 @@ static int check_pr_args(const tc_graph *g, const tc_part *part, const tc_pr_par
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad dangling mode");
     if (pp->out_mem != TC_MEM_HOST && pp->out_mem != TC_MEM_DEVICE)
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad out_mem");
+    if (pp->merge_mode < TC_MERGE_FIXED || pp->merge_mode > TC_MERGE_FLOAT)
+        return fail(TC_ERR_INVALID_ARG, "pagerank: bad merge_mode");
     if (part && (part->g != g || part->dir != dir))
         return fail(TC_ERR_INVALID_ARG, "pagerank: partition belongs to another graph or direction");
     return TC_OK;
@@ -323,6 +590,7 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     // launch shapes
     int g_gather = 1, g_upd = 1, g_merge = 1, hub_ctas = 0;
     int64_t nrows;
+    int64_t max_ctas_hint = 1;
     const int32_t *rp, *ci, *hubs, *idm = nullptr;
     int32_t nhubs, hubdeg;
     if (part) {
@@ -342,6 +610,7 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
         hubdeg = g->hub_degree;
     }
     hub_ctas = nhubs > 0 ? (nhubs < caps.sms ? nhubs : caps.sms) : 0;
+    const bool tiled = part && !push && part->tiled;
     const int64_t group_ctas = ((nrows + 31) / 32 + PR_WARPS - 1) / PR_WARPS;
     const void *kgather = push ? (const void *)k_push_scatter
                                : (part ? (const void *)k_pull_gather<false> : (const void *)k_pull_gather<true>);
@@ -349,22 +618,34 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     g_gather += hub_ctas;
     TC_TRY(occupancy_grid((const void *)k_push_update, PR_THREADS, 0, ((int64_t)V + PR_THREADS - 1) / PR_THREADS, &g_upd));
     size_t merge_smem = 0;
+    int merge_mode = TC_MERGE_FIXED;
     if (part && !push) {
         g_merge = part->nranges;
-        merge_smem = (size_t)PR_WARPS * part->k * 4;
-        if (merge_smem > 48 * 1024)
-            TC_CUDA(cudaFuncSetAttribute(k_pull_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
+        merge_mode = pp->merge_mode;
+        if (merge_mode == TC_MERGE_ORDERED) {
+            merge_smem = merge_smem_bytes(part->k, part->B);
+            if (merge_smem > 48 * 1024)
+                TC_CUDA(cudaFuncSetAttribute(k_pull_merge_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)merge_smem));
+        } else {
+            const bool fx = merge_mode == TC_MERGE_FIXED;
+            merge_smem = merge_atomic_smem_bytes(part->k, part->B, fx);
+            if (merge_smem > 48 * 1024)
+                TC_CUDA(cudaFuncSetAttribute(fx ? k_pull_merge_atomic<true> : k_pull_merge_atomic<false>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
+        }
     }
     int g_init = 1;
     TC_TRY(occupancy_grid((const void *)k_pr_init, PR_THREADS, 0, ((int64_t)V + PR_THREADS - 1) / PR_THREADS, &g_init));
     int64_t max_ctas = g_gather;
     if (g_init > max_ctas) max_ctas = g_init;
+    if (max_ctas_hint > max_ctas) max_ctas = max_ctas_hint;
     if (g_upd > max_ctas) max_ctas = g_upd;
     if (g_merge > max_ctas) max_ctas = g_merge;
 
     PrState st;
     TC_TRY(prepare_state(g, pp, ranks_out, push, max_ctas, &st));
-    TC_CUDA(cudaMemsetAsync(st.counter, 0, 8, s));
+    TC_CUDA(cudaMemsetAsync(st.counter, 0, 16, s));  // counter and error flag
     if (push) TC_CUDA(cudaMemsetAsync(st.sums, 0, (size_t)V * 4, s));
 
     UpdateArgs u;
@@ -375,6 +656,7 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     u.dpart = st.dpart;
     u.counter = st.counter;
     u.inv_outdeg = g->inv_outdeg.as<float>();
+    u.fx_scale = st.scale;
 
     float ms_total = 0, ms_gather = 0, ms_merge = 0;
     Timer tt;
@@ -391,9 +673,11 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
             TC_CUDA(cudaMemcpyAsync(st.rank_dev, pp->init, (size_t)V * 4, cudaMemcpyHostToDevice, s));
             init_dev = st.rank_dev;
         }
-        k_pr_init<<<g_init, PR_THREADS, 0, s>>>(init_dev, u);
+        k_pr_init<<<g_init, PR_THREADS, 0, s>>>(init_dev, u, st.mass);
         TC_LAUNCH_CHECK();
-        ++launches;
+        k_pr_scale<<<1, 1, 0, s>>>(st.mass, st.scale);
+        TC_LAUNCH_CHECK();
+        launches += 2;
     }
     for (int it = 0; it < pp->iters; ++it) {
         const bool last = it == pp->iters - 1;
@@ -407,6 +691,10 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
         if (push) {
             k_push_scatter<<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, idm, hubs, nhubs, hubdeg, hub_ctas, cur,
                                                           st.sums);
+        } else if (tiled) {
+            int nl = 0;
+            TC_TRY(launch_tiled_gather(part, cur, st.err, s, &nl));
+            launches += nl - 1;
         } else if (part) {
             k_pull_gather<false><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, hubs, nhubs, hubdeg, hub_ctas, cur,
                                                                  part->partial.as<float>(), u);
@@ -423,9 +711,19 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
             if (push) {
                 k_push_update<<<g_upd, PR_THREADS, 0, s>>>(st.sums, u);
             } else {
-                k_pull_merge<<<g_merge, PR_THREADS, merge_smem, s>>>(part->partial.as<float>(), part->id_map.as<int32_t>(),
-                                                                     part->merge_off.as<int32_t>(), part->B,
-                                                                     part->nranges, part->k, u);
+                const uint16_t *i16 = part->id16.p ? part->id16.as<uint16_t>() : nullptr;
+                if (merge_mode == TC_MERGE_ORDERED)
+                    k_pull_merge_ordered<<<g_merge, MG_THREADS, merge_smem, s>>>(
+                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
+                        part->B, part->k, u);
+                else if (merge_mode == TC_MERGE_FIXED)
+                    k_pull_merge_atomic<true><<<g_merge, MG_THREADS, merge_smem, s>>>(
+                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
+                        part->B, part->k, u);
+                else
+                    k_pull_merge_atomic<false><<<g_merge, MG_THREADS, merge_smem, s>>>(
+                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
+                        part->B, part->k, u);
             }
             TC_LAUNCH_CHECK();
             ++launches;
@@ -435,6 +733,12 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     TC_TRY(tt.end());
     if (pp->out_mem == TC_MEM_HOST)
         TC_CUDA(cudaMemcpyAsync(ranks_out, st.rank_dev, (size_t)V * 4, cudaMemcpyDeviceToHost, s));
+    if (stats || pp->out_mem == TC_MEM_HOST) {
+        int err = 0;
+        TC_CUDA(cudaMemcpyAsync(&err, st.err, 4, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        if (err) return fail(TC_ERR_TIMEOUT, "pagerank: a bounded device wait gave up (code %d)", err);
+    }
     if (stats) {
         double D = 0;
         TC_CUDA(cudaMemcpyAsync(&D, st.D + (pp->iters & 1), 8, cudaMemcpyDeviceToHost, s));

@@ -42,9 +42,10 @@ __global__ void k_block_bounds(const int32_t *col, const int64_t *rowid, const i
     }
 }
 
-// off[b][j] = first local row of block b whose global id is >= j*k, j in [0, nranges].
+// off[b][j] = first local row of block b whose global id is >= j*k, j in [0, nranges];
+// offT[j][b] holds the same table range-major (the merge of range j reads one row of it).
 __global__ void k_merge_offsets(const int32_t *id_map, const int64_t *blk_rows, int32_t B, int32_t nranges, int32_t k,
-                                int32_t *off) {
+                                int32_t *off, int32_t *offT) {
     const int64_t total = (int64_t)B * (nranges + 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t b = (int32_t)(t / (nranges + 1));
@@ -56,7 +57,13 @@ __global__ void k_merge_offsets(const int32_t *id_map, const int64_t *blk_rows, 
             if ((int64_t)id_map[mid] < bound) lo = mid + 1; else hi = mid;
         }
         off[t] = (int32_t)lo;
+        offT[(int64_t)j * B + b] = (int32_t)lo;
     }
+}
+
+__global__ void k_id16(const int32_t *id_map, int64_t R, int32_t kmask, uint16_t *id16) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
+        id16[r] = (uint16_t)(id_map[r] & kmask);
 }
 
 __global__ void k_hub_flags(const int32_t *rowptr, int64_t nrows, int32_t min_degree, int32_t *flag) {
@@ -119,14 +126,33 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->k = (pp && pp->merge_range > 0) ? pp->merge_range : 1024;
     if (p->k % 32 != 0) return fail(TC_ERR_INVALID_ARG, "merge_range must be a multiple of 32");
     p->hub_degree = (pp && pp->hub_degree > 0) ? pp->hub_degree : 2048;
-    if (num_blocks == 0) {
+    const int32_t smem_w = tile_max_width(caps.max_smem_optin);
+    const int policy = pp ? pp->block_policy : TC_BLOCKS_L2;
+    if (num_blocks == 0 && policy == TC_BLOCKS_SMEM) {
+        // the smallest multiple of the SM count of blocks whose width fits shared memory:
+        // one CTA per block, whole waves
+        int64_t m = 1, Wc = 1;
+        for (;; ++m) {
+            Wc = ((int64_t)V + m * caps.sms - 1) / (m * caps.sms);
+            Wc = (Wc + 31) / 32 * 32;
+            if (Wc <= smem_w) break;
+        }
+        p->W = (int32_t)(Wc > 0 ? Wc : 32);
+    } else if (num_blocks == 0) {
         p->W = tc_default_block_width(V, caps.l2_bytes, frac);
     } else {
         p->W = V > 0 ? (int32_t)(((int64_t)V + num_blocks - 1) / num_blocks) : 1;
+        if (p->W > 32) p->W = (p->W + 31) / 32 * 32;  // 128-byte aligned source ranges
     }
     if (p->W < 1) p->W = 1;
     p->B = V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1;
     p->nranges = (int32_t)(((int64_t)V + p->k - 1) / p->k);
+    if (dir == TC_PULL && ((int64_t)V + p->W - 1) / p->W > 65535)
+        return fail(TC_ERR_UNSUPPORTED, "more than 65535 blocks");
+    if (dir == TC_PULL && (int64_t)merge_smem_bytes(p->k, V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1) >
+                              (int64_t)caps.max_smem_optin)
+        return fail(TC_ERR_INVALID_ARG, "merge_range %d with this block count needs more shared memory than a CTA has",
+                    p->k);
     const int32_t B = p->B, W = p->W;
     const int grid = caps.sms * 8;
 
@@ -186,20 +212,34 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     if (!p->h_blk_rows || !p->h_blk_edges) return fail(TC_ERR_OOM, "host allocation failed");
     TC_CUDA(cudaMemcpyAsync(p->h_blk_rows, blk_rows.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
     TC_CUDA(cudaMemcpyAsync(p->h_blk_edges, blk_edges.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
+    TC_TRY(p->blk_rows_dev.alloc(((size_t)B + 1) * 8));
+    TC_CUDA(cudaMemcpyAsync(p->blk_rows_dev.p, blk_rows.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToDevice, s));
 
     // merge range table
     const int64_t noff = (int64_t)B * (p->nranges + 1);
     TC_TRY(p->merge_off.alloc((size_t)(noff > 0 ? noff : 1) * 4));
+    TC_TRY(p->merge_offT.alloc((size_t)(noff > 0 ? noff : 1) * 4));
     if (noff > 0) {
         k_merge_offsets<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), blk_rows.as<int64_t>(), B, p->nranges, p->k,
-                                             p->merge_off.as<int32_t>());
+                                             p->merge_off.as<int32_t>(), p->merge_offT.as<int32_t>());
         TC_LAUNCH_CHECK();
     }
     TC_TRY(collect_hubs(p->rowptr.as<int32_t>(), R, p->hub_degree, &p->hubs, &p->num_hubs, s));
+    if (R > 0 && (p->k & (p->k - 1)) == 0 && p->k <= 65536) {  // 2-byte local ids for the merge
+        TC_TRY(p->id16.alloc((size_t)R * 2));
+        k_id16<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), R, p->k - 1, p->id16.as<uint16_t>());
+        TC_LAUNCH_CHECK();
+    }
     p->num_groups = (R + 31) / 32;
     TC_TRY(p->partial.alloc((size_t)(R > 0 ? R : 1) * 4));
     TC_TRY(p->rowbits.alloc((size_t)((R + 31) / 32 + 1) * 4));
     TC_CUDA(cudaStreamSynchronize(s));
+    const int stage = pp ? pp->smem_stage : 0;
+    if (stage > 0 && dir != TC_PULL) return fail(TC_ERR_UNSUPPORTED, "smem_stage = 1 applies to pull partitions only");
+    if (dir == TC_PULL && stage >= 0 && W <= smem_w && W % 32 == 0 && V > 0)
+        TC_TRY(build_tiles(p, caps.sms, s));
+    if (stage > 0 && !p->tiled)
+        return fail(TC_ERR_UNSUPPORTED, "smem_stage = 1 needs a pull partition with W <= %d and W %% 32 == 0", smem_w);
     return TC_OK;
 }
 
@@ -251,6 +291,8 @@ extern "C" int tc_part_get_info(const tc_part *p, tc_part_info *info) {
     info->num_edges = p->E;
     info->merge_range = p->k;
     info->num_hubs = p->num_hubs;
+    info->staged = p->tiled ? 1 : 0;
+    info->staged_edges = p->padded_edges;
     return TC_OK;
 }
 

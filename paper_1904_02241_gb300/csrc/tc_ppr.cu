@@ -1,0 +1,235 @@
+// Personalised PageRank for a batch of sources (one column per source), pull direction.
+// Column j follows Alg. 1 with the teleport term (1-d) and the dangling mass of column j sent
+// to its own source s_j, starting from e_{s_j}:
+//   R'[v,j] = d * sum_{u->v} R[u,j] / out_degree[u] + [v == s_j] ((1-d) + d * D_j),
+//   D_j     = sum over dangling u of R[u,j].
+// The batch is an FP32 [V x n] row-major matrix; one warp gathers whole rows of the
+// contribution matrix (n floats, float4 per lane), so every in-edge costs one coalesced row
+// read.  Per-column dangling sums are accumulated in 64-bit fixed point (deterministic).
+#include "tc_common_dev.cuh"
+
+namespace tc {
+
+constexpr int PPR_THREADS = 256;
+constexpr int PPR_WARPS = PPR_THREADS / 32;
+constexpr double PPR_FX = 2305843009213693952.0;  // 2^61: every column has L1 mass <= 1
+
+template <int NV4>  // float4 per lane; columns in the padded batch = 128 * NV4
+__global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__restrict__ rowptr,
+                                                            const int32_t *__restrict__ colidx, int32_t V,
+                                                            const float4 *__restrict__ C, float4 *__restrict__ Cn,
+                                                            const int32_t *__restrict__ src_of_col,
+                                                            const unsigned long long *__restrict__ Dcur,
+                                                            unsigned long long *Dnext, unsigned long long *Dzero,
+                                                            const float *__restrict__ inv_outdeg, float damping,
+                                                            float *R_out, int32_t n) {
+    constexpr int NP = 128 * NV4;
+    __shared__ float dsh[PPR_WARPS][NP];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (blockIdx.x == 0)
+        for (int j = threadIdx.x; j < NP; j += PPR_THREADS) Dzero[j] = 0ull;
+    int32_t src[NV4][4];
+    float tele[NV4][4];
+    float dl[NV4][4];
+#pragma unroll
+    for (int q = 0; q < NV4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int j = 128 * q + 4 * lane + c;
+            src[q][c] = src_of_col[j];
+            tele[q][c] = (1.0f - damping) + damping * (float)((double)Dcur[j] / PPR_FX);
+            dl[q][c] = 0.0f;
+        }
+    const int64_t nw = (int64_t)gridDim.x * PPR_WARPS;
+    for (int64_t v = (int64_t)blockIdx.x * PPR_WARPS + warp; v < V; v += nw) {
+        float4 acc[NV4];
+#pragma unroll
+        for (int q = 0; q < NV4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        const int32_t s = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
+        int32_t i = s;
+        for (; i + 1 < e; i += 2) {  // two rows in flight
+            const int64_t u0 = __ldg(colidx + i), u1 = __ldg(colidx + i + 1);
+            float4 x0[NV4], x1[NV4];
+#pragma unroll
+            for (int q = 0; q < NV4; ++q) {
+                x0[q] = __ldg(C + u0 * (NP / 4) + 32 * q + lane);
+                x1[q] = __ldg(C + u1 * (NP / 4) + 32 * q + lane);
+            }
+#pragma unroll
+            for (int q = 0; q < NV4; ++q) {
+                acc[q].x += x0[q].x + x1[q].x;
+                acc[q].y += x0[q].y + x1[q].y;
+                acc[q].z += x0[q].z + x1[q].z;
+                acc[q].w += x0[q].w + x1[q].w;
+            }
+        }
+        if (i < e) {
+            const int64_t u0 = __ldg(colidx + i);
+#pragma unroll
+            for (int q = 0; q < NV4; ++q) {
+                const float4 x = __ldg(C + u0 * (NP / 4) + 32 * q + lane);
+                acc[q].x += x.x;
+                acc[q].y += x.y;
+                acc[q].z += x.z;
+                acc[q].w += x.w;
+            }
+        }
+        const float inv = __ldg(inv_outdeg + v);
+#pragma unroll
+        for (int q = 0; q < NV4; ++q) {
+            float r[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                r[c] = damping * r[c] + (src[q][c] == (int32_t)v ? tele[q][c] : 0.0f);
+                if (inv == 0.0f) dl[q][c] += r[c];
+            }
+            Cn[v * (NP / 4) + 32 * q + lane] = make_float4(r[0] * inv, r[1] * inv, r[2] * inv, r[3] * inv);
+            if (R_out) {
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const int j = 128 * q + 4 * lane + c;
+                    if (j < n) R_out[v * n + j] = r[c];
+                }
+            }
+        }
+    }
+    // per-column dangling sums: warps -> shared -> one fixed-point atomic per column per CTA
+#pragma unroll
+    for (int q = 0; q < NV4; ++q)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) dsh[warp][128 * q + 4 * lane + c] = dl[q][c];
+    __syncthreads();
+    for (int j = threadIdx.x; j < NP; j += PPR_THREADS) {
+        float t = 0.0f;
+#pragma unroll
+        for (int w = 0; w < PPR_WARPS; ++w) t += dsh[w][j];
+        if (t != 0.0f) atomicAdd(Dnext + j, (unsigned long long)__double2ll_rn((double)t * PPR_FX));
+    }
+}
+
+// C = e_{s_j} scaled by 1/out_degree(s_j); D0_j = [s_j dangling]; optional R_out = e_{s_j}.
+__global__ void k_ppr_init(float *C, int32_t NP, const int32_t *src_of_col, const float *inv_outdeg,
+                           unsigned long long *D0, float *R_out, int32_t n) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < NP; j += gridDim.x * blockDim.x) {
+        const int32_t s = src_of_col[j];
+        D0[j] = 0ull;
+        if (s < 0) continue;
+        const float inv = inv_outdeg[s];
+        C[(int64_t)s * NP + j] = inv;
+        if (inv == 0.0f) D0[j] = (unsigned long long)PPR_FX;
+        if (R_out && j < n) R_out[(int64_t)s * n + j] = 1.0f;
+    }
+}
+
+template <int NV4>
+static void launch_ppr(int grid, cudaStream_t s, const tc_graph *g, const float *C, float *Cn, const int32_t *srcc,
+                       const unsigned long long *Dc, unsigned long long *Dn, unsigned long long *Dz, float d,
+                       float *R_out, int32_t n) {
+    k_ppr_gather<NV4><<<grid, PPR_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), g->V,
+                                                  reinterpret_cast<const float4 *>(C), reinterpret_cast<float4 *>(Cn),
+                                                  srcc, Dc, Dn, Dz, g->inv_outdeg.as<float>(), d, R_out, n);
+}
+
+static int ppr_impl(const tc_graph *cg, const int32_t *sources, int32_t n, const tc_pr_params *pp, float *R_out,
+                    tc_pr_stats *stats, cudaStream_t s) {
+    tc_graph *g = const_cast<tc_graph *>(cg);
+    const int32_t V = g->V;
+    int NV4 = 1;
+    while (128 * NV4 < n) NV4 *= 2;
+    const int32_t NP = 128 * NV4;
+    const size_t mat = (size_t)V * NP * 4;
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    DevBuf Cbuf, srcbuf, Dbuf, Rdev;
+    TC_TRY(Cbuf.alloc(2 * mat));
+    TC_TRY(srcbuf.alloc((size_t)NP * 4));
+    TC_TRY(Dbuf.alloc((size_t)3 * NP * 8));
+    float *Cm[2] = {Cbuf.as<float>(), Cbuf.as<float>() + (size_t)V * NP};
+    unsigned long long *D[3] = {Dbuf.as<unsigned long long>(), Dbuf.as<unsigned long long>() + NP,
+                                Dbuf.as<unsigned long long>() + 2 * NP};
+    int32_t *hsrc = new (std::nothrow) int32_t[NP];
+    if (!hsrc) return fail(TC_ERR_OOM, "host allocation failed");
+    for (int32_t j = 0; j < NP; ++j) hsrc[j] = j < n ? sources[j] : -1;
+    cudaError_t e = cudaMemcpyAsync(srcbuf.p, hsrc, (size_t)NP * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] hsrc;
+    if (e != cudaSuccess) return fail(TC_ERR_CUDA, "tc_ppr_batch: %s", cudaGetErrorString(e));
+    float *Rd = R_out;
+    if (pp->out_mem == TC_MEM_HOST) {
+        TC_TRY(Rdev.alloc((size_t)V * n * 4));
+        Rd = Rdev.as<float>();
+    }
+    cudaEvent_t ev[2] = {nullptr, nullptr};
+    if (pp->profile) {
+        TC_CUDA(cudaEventCreate(&ev[0]));
+        TC_CUDA(cudaEventCreate(&ev[1]));
+        TC_CUDA(cudaEventRecord(ev[0], s));
+    }
+    TC_CUDA(cudaMemsetAsync(Cm[0], 0, mat, s));
+    if (pp->iters == 0) TC_CUDA(cudaMemsetAsync(Rd, 0, (size_t)V * n * 4, s));
+    k_ppr_init<<<(NP + 255) / 256, 256, 0, s>>>(Cm[0], NP, srcbuf.as<int32_t>(), g->inv_outdeg.as<float>(), D[0],
+                                                pp->iters == 0 ? Rd : nullptr, n);
+    TC_LAUNCH_CHECK();
+    TC_CUDA(cudaMemsetAsync(D[1], 0, (size_t)NP * 8, s));
+    int per_sm = 1;
+    const void *kf = NV4 == 1 ? (const void *)k_ppr_gather<1>
+                     : NV4 == 2 ? (const void *)k_ppr_gather<2>
+                     : NV4 == 4 ? (const void *)k_ppr_gather<4>
+                                : (const void *)k_ppr_gather<8>;
+    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, PPR_THREADS, 0));
+    const int grid = caps.sms * (per_sm > 0 ? per_sm : 1);
+    int launches = 1;
+    for (int it = 0; it < pp->iters; ++it) {
+        const bool last = it == pp->iters - 1;
+        float *Rw = last ? Rd : nullptr;
+        const float *Cc = Cm[it & 1];
+        float *Cn = Cm[(it + 1) & 1];
+        unsigned long long *Dc = D[it % 3], *Dn = D[(it + 1) % 3], *Dz = D[(it + 2) % 3];
+        switch (NV4) {
+            case 1: launch_ppr<1>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
+            case 2: launch_ppr<2>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
+            case 4: launch_ppr<4>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
+            default: launch_ppr<8>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
+        }
+        TC_LAUNCH_CHECK();
+        ++launches;
+    }
+    float ms = 0;
+    if (pp->profile) {
+        TC_CUDA(cudaEventRecord(ev[1], s));
+        TC_CUDA(cudaEventSynchronize(ev[1]));
+        TC_CUDA(cudaEventElapsedTime(&ms, ev[0], ev[1]));
+        cudaEventDestroy(ev[0]);
+        cudaEventDestroy(ev[1]);
+    }
+    if (pp->out_mem == TC_MEM_HOST)
+        TC_CUDA(cudaMemcpyAsync(R_out, Rd, (size_t)V * n * 4, cudaMemcpyDeviceToHost, s));
+    // the scratch buffers are freed at return: finish their users first
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->iters = pp->iters;
+        stats->launches = launches;
+        stats->ms_total = ms;
+        stats->ms_gather = ms;
+    }
+    return TC_OK;
+}
+
+}  // namespace tc
+
+extern "C" int tc_ppr_batch(const tc_graph *g, const int32_t *sources, int32_t n, const tc_pr_params *params,
+                            float *R_out, tc_pr_stats *stats, void *stream) {
+    using namespace tc;
+    if (!g || !sources || !params || !R_out) return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: null argument");
+    if (n < 1 || n > 1024) return fail(TC_ERR_UNSUPPORTED, "tc_ppr_batch: n must be in [1, 1024]");
+    if (!(params->damping >= 0.0f && params->damping <= 1.0f) || params->iters < 0)
+        return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: damping outside [0,1] or iters < 0");
+    if (params->out_mem != TC_MEM_HOST && params->out_mem != TC_MEM_DEVICE)
+        return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: bad out_mem");
+    for (int32_t j = 0; j < n; ++j)
+        if (sources[j] < 0 || sources[j] >= g->V) return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: source %d outside [0, V)", j);
+    if ((int64_t)g->V * ((n + 127) / 128 * 128) * 8 > ((int64_t)1 << 40))
+        return fail(TC_ERR_UNSUPPORTED, "tc_ppr_batch: V x n too large");
+    return ppr_impl(g, sources, n, params, R_out, stats, (cudaStream_t)stream);
+}

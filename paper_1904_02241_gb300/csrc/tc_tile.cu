@@ -1,0 +1,339 @@
+// Shared-memory staged TOCAB gather (Alg. 4 with the block's vertex values on chip).
+//
+// The paper sizes a block so that its contributions fit in the last-level cache (Sec. 3.1).
+// On GB300 the whole contribution vector of a scale-24 graph already fits in the 135 MB L2,
+// and the random requests themselves become the bound (one L1/L2 sector request per edge).
+// This format sizes a block so that its contributions fit in one CTA's shared memory instead,
+// where a random warp gather costs a few bank cycles:
+//   * one CTA per block; the block's contributions are copied into shared memory with bulk
+//     asynchronous copies (TMA, cp.async.bulk) completing on an mbarrier;
+//   * col16[]  : uint16 source offset inside the block (source - b*W), each block's edges
+//                padded to a multiple of TILE_WCHUNK;
+//   * heads[]  : one bit per edge, set where a local row starts (uint16 per 16 edges);
+//   * wtab[]   : per block, 33 (edge, row) pairs: warp w of the CTA owns the row-aligned edge
+//                range [wtab[w].x, wtab[w+1].x) whose first row is wtab[w].y.
+// A warp streams its range in chunks of TILE_WCHUNK edges, 16 consecutive edges per lane
+// (two 16-byte loads), sums the source values of each lane's row pieces, and joins pieces of
+// rows that cross lanes or chunks with a warp segmented scan.  Finished row sums go to a
+// per-warp shared-memory stage and leave as coalesced stores to partial[row] in the
+// partition's row numbering; the merge kernel (Fig. 5) reduces them.
+#include "tc_common_dev.cuh"
+
+namespace tc {
+
+constexpr int WCH = TILE_WCHUNK;             // edges per warp chunk (16 per lane)
+constexpr int TWARPS = TILE_THREADS / 32;
+
+__host__ __device__ static inline size_t slice_bytes(int32_t W) { return ((size_t)W * 4 + 127) / 128 * 128; }
+
+size_t tile_smem_bytes(int32_t W) { return slice_bytes(W) + (size_t)TWARPS * WCH * 4; }
+
+int32_t tile_max_width(int max_smem_optin) {
+    const int64_t budget = (int64_t)max_smem_optin - 1024 - (int64_t)TWARPS * WCH * 4;
+    int64_t W = budget / 4;
+    W = W / 32 * 32;
+    if (W > 65536) W = 65536;
+    return W > 0 ? (int32_t)W : 0;
+}
+
+// ---- PTX helpers: mbarrier and bulk asynchronous copies -------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: gives up after ~2^31 cycles (about a second), records `code` in *err.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err, int code) {
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > (1LL << 31)) {
+            atomicCAS(err, 0, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+struct TileArgs {
+    const uint16_t *col16;
+    const uint16_t *heads;
+    const int2 *wtab;      // [B][TWARPS + 1]
+    const float *contrib;
+    int32_t V, W;
+    float *partial;
+    int *err;
+};
+
+// Segmented-scan element: flag = "a row starts inside this piece", val = open-row value.
+__device__ __forceinline__ void seg_combine(bool &f, float &v, bool fp, float vp) {
+    // (fp, vp) precedes (f, v): if this piece restarts, keep it; else add the earlier value
+    if (!f) v += vp;
+    f = f || fp;
+}
+
+__global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t slice_bar;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t b = blockIdx.x;
+    float *slice = reinterpret_cast<float *>(smem);
+    float *stage = reinterpret_cast<float *>(smem + slice_bytes(t.W)) + warp * WCH;
+
+    // ---- the block's contributions -> shared memory (bulk copies on one mbarrier) ----
+    if (tid == 0) {
+        mbar_init(&slice_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (tid == 0) {
+        const int64_t lo = (int64_t)b * t.W;
+        const int64_t n = ((int64_t)t.V - lo) < t.W ? ((int64_t)t.V - lo) : t.W;
+        const uint32_t bytes = (uint32_t)((n * 4 + 15) & ~15LL);
+        mbar_expect_tx(&slice_bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += 16384) {
+            const uint32_t part = (bytes - off) < 16384u ? (bytes - off) : 16384u;
+            bulk_g2s(reinterpret_cast<unsigned char *>(slice) + off,
+                     reinterpret_cast<const unsigned char *>(t.contrib + lo) + off, part, &slice_bar);
+        }
+    }
+    // every thread waits for the copy (bounded); on a timeout the flag is set and all leave
+    if (!mbar_wait(&slice_bar, 0, t.err, 1)) return;
+
+    const int2 w0 = t.wtab[(int64_t)b * (TWARPS + 1) + warp];
+    const int2 w1 = t.wtab[(int64_t)b * (TWARPS + 1) + warp + 1];
+    const int32_t es = w0.x, ee = w1.x;   // edge range of this warp (padded stream positions)
+    const int32_t rs = w0.y;              // its first row
+    if (es >= ee) return;
+
+    int32_t rowbase = rs;                 // row started by the next head
+    float carry = 0.0f;                   // value of the open row (rowbase - 1)
+    bool open = false;                    // whether row rowbase-1 belongs to this warp
+    const int32_t q_begin = es & ~(WCH - 1);
+
+    // software pipeline: loads of the next chunk are issued before this one is processed
+    uint4 nc0, nc1;
+    uint32_t nh;
+    {
+        const int32_t q = q_begin + 16 * lane;
+        const uint4 *p = reinterpret_cast<const uint4 *>(t.col16 + q);
+        nc0 = __ldg(p);
+        nc1 = __ldg(p + 1);
+        nh = __ldg(t.heads + (q >> 4));
+    }
+    for (int32_t q0 = q_begin; q0 < ee; q0 += WCH) {
+        const uint4 c0 = nc0, c1 = nc1;
+        uint32_t hd = nh;
+        if (q0 + WCH < ee) {
+            const int32_t q = q0 + WCH + 16 * lane;
+            const uint4 *p = reinterpret_cast<const uint4 *>(t.col16 + q);
+            nc0 = __ldg(p);
+            nc1 = __ldg(p + 1);
+            nh = __ldg(t.heads + (q >> 4));
+        }
+        // valid edges of this lane: [max(es, e0), min(ee, e0 + 16))
+        const int32_t e0 = q0 + 16 * lane;
+        const int32_t lo_i = es - e0, hi_i = ee - e0;
+        uint32_t valid = 0xFFFFu;
+        if (lo_i > 0) valid = lo_i >= 16 ? 0u : (valid & (0xFFFFu << lo_i));
+        if (hi_i < 16) valid = hi_i <= 0 ? 0u : (valid & ((1u << hi_i) - 1u));
+        hd &= valid;
+        const uint32_t words[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        float val[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            const uint32_t col = (words[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+            val[i] = ((valid >> i) & 1u) ? slice[col] : 0.0f;
+        }
+        // rows of this chunk: exclusive scan of head counts over lanes
+        const int nh_l = __popc(hd);
+        int incl = nh_l;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
+        }
+        const int before = incl - nh_l;                       // heads in earlier lanes
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        // walk the lane's 16 edges: pieces between heads are whole rows (written to the stage)
+        float seg = 0.0f, first = 0.0f;
+        int k = 0;
+        bool seen = false;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if ((hd >> i) & 1u) {
+                if (!seen) {
+                    first = seg;
+                    seen = true;
+                } else {
+                    stage[before + k + 1] = seg;  // row (rowbase + before + k), closed here
+                    ++k;
+                }
+                seg = 0.0f;
+            }
+            seg += val[i];
+        }
+        if (!seen) first = seg;
+        // carry of the open row across lanes: segmented inclusive scan
+        bool f = seen;
+        float v = seen ? seg : first;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const bool fp = __shfl_up_sync(0xffffffffu, f, d);
+            const float vp = __shfl_up_sync(0xffffffffu, v, d);
+            if (lane >= d) seg_combine(f, v, fp, vp);
+        }
+        // open-row value at the end of lane l: f ? v : carry + v (no head yet: the chunk's
+        // carry flows through); the row closed at lane l's first head gets X(l-1) + first
+        const float vprev = __shfl_up_sync(0xffffffffu, v, 1);
+        const bool fprev = __shfl_up_sync(0xffffffffu, f, 1);
+        const float xprev = (lane == 0) ? carry : (fprev ? vprev : carry + vprev);
+        if (seen) stage[before] = xprev + first;
+        const float xlast = __shfl_sync(0xffffffffu, f ? v : carry + v, 31);
+        __syncwarp();
+        // stage[i] holds row (rowbase - 1 + i) for i < total; stage[0] is the open row only
+        // when it belongs to this warp
+        for (int i = lane; i < total; i += 32) {
+            if (i > 0 || open) t.partial[rowbase - 1 + i] = stage[i];
+        }
+        __syncwarp();
+        if (total > 0) open = true;
+        rowbase += total;
+        carry = xlast;
+    }
+    if (open && lane == 0) t.partial[rowbase - 1] = carry;
+}
+
+// ---------------------------------------------------------------------------------------------
+// building the staged format from a base partition
+// ---------------------------------------------------------------------------------------------
+__global__ void k_tile_fill(const int32_t *rowptr, const int32_t *colidx, int64_t R, const int64_t *blk_rows,
+                            const int64_t *blk_edges, const int64_t *pbase, int32_t B, int32_t W, uint16_t *col16,
+                            uint32_t *heads32) {
+    // one thread per local row: copy its edges (block-relative sources), set its head bit
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        int32_t lo = 0, hi = B;  // block of row r: last b with blk_rows[b] <= r, non-empty
+        while (hi - lo > 1) {
+            const int32_t mid = (lo + hi) >> 1;
+            if (blk_rows[mid] <= r) lo = mid; else hi = mid;
+        }
+        const int32_t b = lo;
+        const int32_t s = rowptr[r], e = rowptr[r + 1];
+        const int64_t dst = pbase[b] + (s - blk_edges[b]);
+        const int32_t base = b * W;
+        for (int32_t i = s; i < e; ++i) col16[dst + (i - s)] = (uint16_t)(colidx[i] - base);
+        atomicOr(heads32 + (dst >> 5), 1u << (dst & 31));
+    }
+}
+
+__global__ void k_tile_wtab(const int32_t *rowptr, const int64_t *blk_rows, const int64_t *blk_edges,
+                            const int64_t *pbase, int32_t B, int2 *wtab) {
+    const int64_t total = (int64_t)B * (TWARPS + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t b = (int32_t)(t / (TWARPS + 1)), w = (int32_t)(t % (TWARPS + 1));
+        const int64_t eb = blk_edges[b], ne = blk_edges[b + 1] - eb;
+        const int64_t nominal = eb + (ne * w + TWARPS - 1) / TWARPS;  // global edge index
+        int64_t rl = blk_rows[b], rh = blk_rows[b + 1];               // first row starting at >= nominal
+        while (rl < rh) {
+            const int64_t mid = (rl + rh) >> 1;
+            if (rowptr[mid] < nominal) rl = mid + 1; else rh = mid;
+        }
+        const int64_t edge = (rl < blk_rows[b + 1]) ? rowptr[rl] : blk_edges[b + 1];
+        wtab[t] = make_int2((int32_t)(pbase[b] + (edge - eb)), (int32_t)rl);
+    }
+}
+
+int build_tiles(tc_part *p, int sms, cudaStream_t s) {
+    (void)sms;
+    p->tiled = false;
+    const int64_t R = p->R;
+    const int32_t B = p->B;
+    if (R == 0 || p->E == 0) return TC_OK;
+    int64_t *h_pbase = new (std::nothrow) int64_t[B + 1];
+    if (!h_pbase) return fail(TC_ERR_OOM, "host allocation failed");
+    h_pbase[0] = 0;
+    for (int32_t b = 0; b < B; ++b) {
+        const int64_t ne = p->h_blk_edges[b + 1] - p->h_blk_edges[b];
+        h_pbase[b + 1] = h_pbase[b] + (ne + WCH - 1) / WCH * WCH;
+    }
+    const int64_t npad = h_pbase[B];
+    if (npad >= INT32_MAX - WCH) {
+        delete[] h_pbase;
+        return TC_OK;  // padded stream beyond int32 positions: keep the unstaged gather
+    }
+    DevBuf pbase, blk_edges;
+    int st = pbase.alloc((size_t)(B + 1) * 8);
+    if (st == TC_OK) st = blk_edges.alloc((size_t)(B + 1) * 8);
+    cudaError_t e = cudaSuccess;
+    if (st == TC_OK) e = cudaMemcpyAsync(pbase.p, h_pbase, (size_t)(B + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (st == TC_OK && e == cudaSuccess)
+        e = cudaMemcpyAsync(blk_edges.p, p->h_blk_edges, (size_t)(B + 1) * 8, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] h_pbase;
+    if (st != TC_OK) return st;
+    if (e != cudaSuccess) return fail(TC_ERR_CUDA, "build_tiles: %s", cudaGetErrorString(e));
+    // + one chunk of slack: the software pipeline never reads past npad, but keep loads in bounds
+    TC_TRY(p->col16.alloc((size_t)(npad + WCH) * 2));
+    TC_TRY(p->heads.alloc((size_t)(npad + WCH) / 8 + 64));
+    TC_CUDA(cudaMemsetAsync(p->col16.p, 0, (size_t)(npad + WCH) * 2, s));
+    TC_CUDA(cudaMemsetAsync(p->heads.p, 0, (size_t)(npad + WCH) / 8 + 64, s));
+    TC_TRY(p->wtab.alloc((size_t)B * (TWARPS + 1) * 8));
+    const int grid = 152 * 8;
+    k_tile_fill<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->colidx.as<int32_t>(), R, p->blk_rows_dev.as<int64_t>(),
+                                     blk_edges.as<int64_t>(), pbase.as<int64_t>(), B, p->W, p->col16.as<uint16_t>(),
+                                     p->heads.as<uint32_t>());
+    TC_LAUNCH_CHECK();
+    k_tile_wtab<<<(B * (TWARPS + 1) + 255) / 256, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->blk_rows_dev.as<int64_t>(),
+                                                               blk_edges.as<int64_t>(), pbase.as<int64_t>(), B,
+                                                               p->wtab.as<int2>());
+    TC_LAUNCH_CHECK();
+    TC_CUDA(cudaStreamSynchronize(s));
+    p->padded_edges = npad;
+    p->tiled = true;
+    return TC_OK;
+}
+
+int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, cudaStream_t s, int *launches) {
+    const size_t smem = tile_smem_bytes(p->W);
+    TC_CUDA(cudaFuncSetAttribute(k_tile_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    TileArgs t;
+    t.col16 = p->col16.as<uint16_t>();
+    t.heads = p->heads.as<uint16_t>();
+    t.wtab = p->wtab.as<int2>();
+    t.contrib = contrib;
+    t.V = p->V;
+    t.W = p->W;
+    t.partial = const_cast<float *>(p->partial.as<float>());
+    t.err = err_flag;
+    k_tile_gather<<<p->B, TILE_THREADS, smem, s>>>(t);
+    TC_LAUNCH_CHECK();
+    ++*launches;
+    return TC_OK;
+}
+
+}  // namespace tc

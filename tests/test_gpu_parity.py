@@ -232,3 +232,152 @@ def test_bfs_bad_source(T):
     G = _load(T, BFS_GRAPHS["path"])
     with pytest.raises(T.TocabError):
         T.bfs_pull(G, None, 200)
+
+
+# ------------------------------------------------------------------ staged (shared-memory) gather
+
+@pytest.mark.parametrize("name,B", [("rmat12", 4), ("rmat14_noperm", 16), ("er", 40), ("grid", 7),
+                                    ("star", 5), ("plc", 5)])
+@pytest.mark.parametrize("stage", [1, -1])
+def test_pagerank_pull_staged_vs_unstaged(T, name, B, stage):
+    g = GRAPHS[name]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B, smem_stage=stage)
+    assert P.staged == (stage == 1)
+    r = T.pagerank_pull(G, P)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+
+
+def test_smem_block_policy(T):
+    g = gg.rmat(16)
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 0, block_policy="smem")
+    assert P.staged and P.block_width % 32 == 0 and P.num_blocks >= 2
+    assert P.staged_edges >= P.num_edges
+    r = T.pagerank_pull(G, P)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    # staged path is deterministic too (fixed-point merge)
+    assert torch.equal(r.cpu(), T.pagerank_pull(G, P).cpu())
+
+
+def test_staged_requirement_rejected_when_width_too_large(T):
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    with pytest.raises(T.TocabError) as e:
+        T.tocab_partition(G, T.TC_PULL, 1, smem_stage=1, hub_degree=0) if g.V > 65536 else \
+            T.tocab_partition(G, T.TC_PUSH, 4, smem_stage=1)
+    assert e.value.status in (-6,)
+
+
+# ------------------------------------------------------------------ a9: batched personalised PageRank
+
+@pytest.mark.parametrize("name,n", [("rmat12", 256), ("rmat12", 5), ("er", 130), ("grid", 1), ("plc", 300),
+                                    ("isolated", 3)])
+def test_ppr_batch_parity(T, name, n):
+    g = GRAPHS[name]
+    G = _load(T, g)
+    rng = np.random.default_rng(n)
+    srcs = rng.integers(0, g.V, n).astype(np.int32)
+    srcs[0] = srcs[-1]  # a repeated source
+    deg = np.diff(g.numpy()[0])
+    if (deg == 0).any():
+        srcs[len(srcs) // 2] = int(np.nonzero(deg == 0)[0][0])  # a dangling source
+    R = T.ppr_batch(G, srcs, iters=20).cpu().numpy()
+    rp, ci = g.numpy()
+    want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
+    for j in range(n):
+        assert l1_rel(R[:, j], want[:, j]) <= TOL, j
+    np.testing.assert_allclose(R.sum(axis=0), 1.0, atol=1e-5)
+
+
+def test_ppr_batch_zero_iters_and_host_output(T):
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    srcs = [3, 9, 3]
+    out = torch.empty((g.V, 3), dtype=torch.float32)
+    T.ppr_batch(G, srcs, iters=0, out=out)
+    want = np.zeros((g.V, 3))
+    want[3, 0] = want[9, 1] = want[3, 2] = 1
+    np.testing.assert_array_equal(out.numpy(), want)
+    T.ppr_batch(G, srcs, iters=3, out=out)
+    rp, ci = g.numpy()
+    np.testing.assert_allclose(out.numpy(), oracle.ppr_pull(g.V, rp, ci, srcs, iters=3), rtol=2e-5, atol=1e-7)
+
+
+def test_ppr_batch_rejects_bad_sources(T):
+    G = _load(T, GRAPHS["rmat12"])
+    with pytest.raises(T.TocabError):
+        T.ppr_batch(G, [0, G.V])
+    with pytest.raises(T.TocabError):
+        T.ppr_batch(G, list(range(1025)))
+
+
+# ------------------------------------------------------------------ merge modes
+
+@pytest.mark.parametrize("merge", ["fixed", "ordered", "float"])
+@pytest.mark.parametrize("policy", ["smem", "l2"])
+def test_pagerank_pull_merge_modes(T, merge, policy):
+    g = gg.rmat(14)
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 0 if policy == "smem" else 3, block_policy=policy)
+    r = T.pagerank_pull(G, P, merge=merge)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    if merge != "float":
+        assert torch.equal(r.cpu(), T.pagerank_pull(G, P, merge=merge).cpu())
+
+
+# ------------------------------------------------------------------ a10: many graphs in one launch
+
+def _multi_oracle(g, off, **kw):
+    rp, ci = g.numpy()
+    off = np.asarray(off)
+    out = np.zeros(g.V)
+    for k in range(len(off) - 1):
+        lo, hi = int(off[k]), int(off[k + 1])
+        sub_rp = rp[lo:hi + 1] - rp[lo]
+        sub_ci = ci[rp[lo]:rp[hi]] - lo
+        if hi > lo:
+            out[lo:hi] = oracle.pagerank_pull(hi - lo, sub_rp, sub_ci, **kw)
+    return out
+
+
+@pytest.fixture(scope="module")
+def batch():
+    return gg.rmat_batch([6, 9, 4, 10, 7, 8, 5, 9, 11, 3], seed=19)
+
+
+@pytest.mark.parametrize("lanes", [0, -1, 1, 4, 8, 32])
+@pytest.mark.parametrize("use_graph", [True, False])
+def test_pagerank_multi_parity(T, batch, lanes, use_graph):
+    g, off = batch
+    M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), off)
+    r = T.pagerank_multi(M, lanes_per_vertex=lanes, use_graph=use_graph).cpu().numpy()
+    want = _multi_oracle(g, off)
+    assert l1_rel(r, want) <= TOL
+    for k in range(len(off) - 1):  # every graph's mass is 1 on its own
+        assert abs(r[off[k]:off[k + 1]].sum() - 1.0) < 1e-4
+
+
+def test_pagerank_multi_modes_and_reuse(T, batch):
+    g, off = batch
+    M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), off)
+    for iters, mode, d in [(0, "redistribute", 0.85), (3, "drop", 0.85), (20, "redistribute", 0.5),
+                           (20, "redistribute", 0.85)]:
+        r = T.pagerank_multi(M, iters=iters, dangling=mode, damping=d).cpu().numpy()
+        assert l1_rel(r, _multi_oracle(g, off, iters=iters, dangling=mode, damping=d)) <= TOL
+
+
+def test_multi_autotune_picks_a_variant(T, batch):
+    g, off = batch
+    M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), off)
+    best, times = T.multi_autotune(M)
+    assert best in (-1, 1, 4, 8, 32) and times[best] == min(times.values())
+    r = T.pagerank_multi(M).cpu().numpy()  # uses the tuned variant
+    assert l1_rel(r, _multi_oracle(g, off)) <= TOL
+
+
+def test_multigraph_rejects_cross_edges(T):
+    g = gg.from_edge_list(4, [(0, 1), (1, 2), (2, 3)])
+    with pytest.raises(T.TocabError) as e:
+        T.multigraph_load(g.rowptr, g.colidx, [0, 2, 4])
+    assert e.value.status == -2

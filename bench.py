@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
     ap.add_argument("--merge", default="fixed", choices=["fixed", "ordered", "float"],
                     help="TOCAB pull merge: fixed-point (deterministic), ordered (deterministic), float")
+    ap.add_argument("--merge-range", type=int, default=0, help="vertices per merge CTA (0 = library default)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
     return ap.parse_args()
@@ -185,7 +186,7 @@ def bench_tocab(args, world, rank, local):
     V, E = g.V, g.E
     gen_s = time.time() - t0
     G = T.graph_load_csr(g.rowptr, g.colidx, V=V)
-    P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy)
+    P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy, merge_range=args.merge_range)
     torch.cuda.synchronize()
     out = torch.empty(V, dtype=torch.float32, device=dev)
 
@@ -251,7 +252,7 @@ def bench_tocab(args, world, rank, local):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"pagerank_pull_tocab rmat{args.scale} ef16 20 iters d=0.85",
-                   "merge": args.merge,
+                   "merge": args.merge, "merge_range": P.merge_range,
                    "graph": f"rmat{args.scale}", "V": V, "E": E, "iters": ITERS,
                    "blocks": P.num_blocks, "block_width": P.block_width, "local_rows": R,
                    "l2": "inputs larger than L2 (colidx %.2f GB vs 135 MB L2); no flush" % (4 * E / 1e9),

@@ -118,7 +118,8 @@ int tc_graph_export_transpose(const tc_graph *g, int32_t *rowptr, int32_t *colid
 typedef struct tc_part_params {
     float   l2_fraction;      /* used when num_blocks == 0 with TC_BLOCKS_L2; <= 0 means 4/11 */
     int32_t merge_range;      /* k of the merge (Fig. 5): vertices per merge CTA, a multiple of
-                                 32; 0 = 1024 */
+                                 32; 0 = 8192 (halved down to 1024 while there would be
+                                 fewer than two ranges per SM) */
     int32_t hub_degree;       /* rows with more edges go to CTA-per-row tasks; 0 = 2048 */
     int32_t block_policy;     /* TC_BLOCKS_L2 or TC_BLOCKS_SMEM (used when num_blocks == 0) */
     int32_t smem_stage;       /* pull only: 0 = stage each block's contributions in shared
@@ -154,14 +155,23 @@ int tc_part_get_info(const tc_part *p, tc_part_info *info);
 int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_edges, int32_t *rowptr,
                    int32_t *id_map, int32_t *colidx, int mem, void *stream);
 
+/* Per-subgraph load balancing: warp_min_per_block (host int32[B], each >= 1) replaces
+ * tc_pr_params.lb_warp_min for the unstaged gathers of this partition; NULL clears it. */
+int tc_part_set_lb(tc_part *p, const int32_t *warp_min_per_block);
+
 /* Default block width W for a vertex count V and an L2 size (host-only helper, the rule
  * used when num_blocks == 0). */
 int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
 
 /* ---- PageRank ------------------------------------------------------------------------------ */
-#define TC_MERGE_FIXED    0          /* TOCAB merge adds in 64-bit fixed point: deterministic */
-#define TC_MERGE_ORDERED  1          /* per-warp FP32 accumulators added in a fixed order     */
-#define TC_MERGE_FLOAT    2          /* FP32 shared-memory atomics: last bits may vary        */
+#define TC_MERGE_FIXED    0          /* one accumulator per CTA, exact fixed-point adds (three
+                                        32-bit shared reductions per partial): deterministic;
+                                        the default, fastest measured on GB300               */
+#define TC_MERGE_ORDERED  1          /* per-warp FP32 accumulators added in a fixed order:
+                                        deterministic; when 16 accumulators of merge_range
+                                        floats do not fit in shared memory the call uses
+                                        TC_MERGE_FIXED instead                                 */
+#define TC_MERGE_FLOAT    2          /* one accumulator, FP32 atomics: last bits may vary     */
 
 typedef struct tc_pr_params {
     float   damping;          /* d, e.g. 0.85 */
@@ -171,6 +181,10 @@ typedef struct tc_pr_params {
     const float *init;        /* initial ranks [V] or NULL for 1/V */
     int32_t profile;          /* nonzero: time each kernel with CUDA events (stats) */
     int32_t merge_mode;       /* TOCAB pull merge: TC_MERGE_FIXED (0), _ORDERED or _FLOAT */
+    int32_t lb_warp_min;      /* unstaged gathers (Sec. 3.2): rows with fewer edges are summed
+                                 by one lane, longer rows by a warp (hubs by a CTA); 0 = 32,
+                                 1 = a warp for every row, large = lane-serial; a partition's
+                                 per-block table (tc_part_set_lb) overrides it */
 } tc_pr_params;
 
 typedef struct tc_pr_stats {
@@ -300,6 +314,49 @@ int tc_pagerank_multi(const tc_multigraph *m, const tc_pr_params *params, const 
  */
 int tc_multi_autotune(tc_multigraph *m, const tc_pr_params *params, int32_t *best_lanes,
                       float *times_ms, void *stream);
+
+/* ---- learned cost model ------------------------------------------------------------------------ */
+/*
+ * Features (16 floats) of a graph or of a TOCAB subgraph, computed on the device from its rows
+ * (destinations for pull): log2 rows, log2 edges, mean degree, degree coefficient of
+ * variation, log2(1 + max/mean degree), fractions of rows with degree 0, 1-7, 8-15, 16-31 and
+ * 32+ (the bins of the paper's Table 1), out-degree coefficient of variation, dangling
+ * fraction, log2(1 + vertex-value bytes / L2), log2(1 + column-index bytes / L2), ID locality
+ * (mean |first source - row| / V), log2(1 + max/mean out-degree).  Synchronises.
+ */
+int tc_graph_features(const tc_graph *g, float *features /* host [16] */);
+/* Features of every block of a partition: host float[B][16] (the out-degree features and the
+ * vertex-value bytes are the graph's and the block width's). */
+int tc_part_features(const tc_part *p, float *features);
+
+/*
+ * The cost model's network (no counterpart in the paper: it only picks parameters of the
+ * method and never changes its results):  z = W3^T relu(W2^T relu(W1^T x + b1) + b2) + b3,
+ * with the outputs split into `n_heads` softmax heads; loss = mean over samples of the summed
+ * cross-entropy.  FP32, forward/backward/Adam in the library's own kernels; every reduction
+ * over samples runs in a fixed order (deterministic).  Parameters are one flat float vector:
+ * W1[n_in][n_hidden], b1, W2[n_hidden][n_hidden], b2, W3[n_hidden][n_out], b3 (row-major).
+ */
+typedef struct tc_mlp tc_mlp;
+int tc_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_heads, const int32_t *head_sizes,
+                  tc_mlp **out);
+void tc_mlp_free(tc_mlp *m);
+int64_t tc_mlp_num_params(const tc_mlp *m);
+/* Set the parameters (host float[num_params]); resets the Adam moments. */
+int tc_mlp_set_params(tc_mlp *m, const float *params);
+/* Copy parameters and/or the last computed gradients to host (either may be NULL). */
+int tc_mlp_get_params(const tc_mlp *m, float *params, float *grads);
+/* Z[N][n_out] = network outputs (logits) for X[N][n_in]; X and Z in `mem` space. */
+int tc_mlp_forward(tc_mlp *m, const float *X, int32_t N, float *Z, int mem, void *stream);
+/* Loss (host *loss) and gradients (kept in the handle) for X[N][n_in], labels Y[N][n_heads]. */
+int tc_mlp_loss_grad(tc_mlp *m, const float *X, const int32_t *Y, int32_t N, int mem,
+                     double *loss, void *stream);
+/* One Adam step (Kingma & Ba) with the gradients of the last tc_mlp_loss_grad. */
+int tc_mlp_adam_step(tc_mlp *m, float lr, float beta1, float beta2, float eps, void *stream);
+/* `epochs` passes of minibatch Adam (lr, beta 0.9/0.999, eps 1e-8) over the samples in the
+ * given order; *final_loss = loss over all samples afterwards. */
+int tc_mlp_train(tc_mlp *m, const float *X, const int32_t *Y, int32_t N, int32_t epochs,
+                 int32_t batch, float lr, int mem, double *final_loss, void *stream);
 
 /* ---- PageRank without allocation ------------------------------------------------------------ */
 /* Largest vertex count and size in bytes of the static device scratch used below. */

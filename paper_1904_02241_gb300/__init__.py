@@ -135,6 +135,14 @@ class Partition:
         except Exception:
             pass
 
+    def set_lb(self, warp_min_per_block=None):
+        """tc_part_set_lb: per-subgraph load balancing (None clears the table)."""
+        if warp_min_per_block is None:
+            _check(L.load().tc_part_set_lb(self._h, None), "tc_part_set_lb")
+            return
+        t = torch.as_tensor(warp_min_per_block, dtype=torch.int32).contiguous().cpu()
+        _check(L.load().tc_part_set_lb(self._h, t.data_ptr()), "tc_part_set_lb")
+
     def export(self):
         """Blocked CSR as host numpy arrays (blk_rows, blk_edges, rowptr, id_map, colidx)."""
         B, R, E = self.num_blocks, self.num_rows, self.num_edges
@@ -183,7 +191,8 @@ def default_block_width(V: int, l2_bytes: int, l2_fraction: float = 0.0) -> int:
 _MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED, "float": L.TC_MERGE_FLOAT}
 
 
-def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream, merge="fixed"):
+def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream, merge="fixed",
+              lb_warp_min=0):
     if out is None:
         out = torch.empty(graph.V, dtype=torch.float32, device="cuda")
     if out.dtype != torch.float32 or out.numel() < graph.V or not out.is_contiguous():
@@ -197,7 +206,7 @@ def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profil
         init = init.contiguous()
         init_ptr = init.data_ptr()
     pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), init_ptr, 1 if profile else 0,
-                        _MERGE[merge])
+                        _MERGE[merge], int(lb_warp_min))
     st = L.tc_pr_stats()
     _check(fn(graph.handle, part.handle if part is not None else None, C.byref(pp), out.data_ptr(),
               C.byref(st), _stream(stream)), name)
@@ -206,20 +215,21 @@ def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profil
 
 def pagerank_pull(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
                   dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
-                  profile: bool = False, stream=None, return_stats: bool = False, merge: str = "fixed"):
+                  profile: bool = False, stream=None, return_stats: bool = False, merge: str = "fixed",
+                  lb_warp_min: int = 0):
     """tc_pagerank_pull (Alg. 1; TOCAB Alg. 4 + merge when part is given).
-    merge: "fixed" (deterministic), "ordered" (deterministic) or "float" (fastest)."""
+    merge: "fixed" (default) or "ordered" (both deterministic), or "float"."""
     r, st = _pagerank(L.load().tc_pagerank_pull, "tc_pagerank_pull", graph, part, damping, iters, dangling, out,
-                      init, profile, stream, merge)
+                      init, profile, stream, merge, lb_warp_min)
     return (r, st) if return_stats else r
 
 
 def pagerank_push(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
                   dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
-                  profile: bool = False, stream=None, return_stats: bool = False):
+                  profile: bool = False, stream=None, return_stats: bool = False, lb_warp_min: int = 0):
     """tc_pagerank_push (Alg. 2; TOCAB Alg. 5 when part is given)."""
     r, st = _pagerank(L.load().tc_pagerank_push, "tc_pagerank_push", graph, part, damping, iters, dangling, out,
-                      init, profile, stream)
+                      init, profile, stream, "fixed", lb_warp_min)
     return (r, st) if return_stats else r
 
 
@@ -232,7 +242,7 @@ def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out
         out = torch.empty((graph.V, n), dtype=torch.float32, device="cuda")
     if out.dtype != torch.float32 or out.numel() < graph.V * n or not out.is_contiguous():
         raise ValueError("out must be a contiguous float32 tensor with V*n elements")
-    pp = L.tc_pr_params(float(damping), int(iters), 0, _mem(out), None, 1 if profile else 0, 0)
+    pp = L.tc_pr_params(float(damping), int(iters), 0, _mem(out), None, 1 if profile else 0, 0, 0)
     st = L.tc_pr_stats()
     _check(L.load().tc_ppr_batch(graph.handle, src.data_ptr(), n, C.byref(pp), out.data_ptr(), C.byref(st),
                                  _stream(stream)), "tc_ppr_batch")
@@ -281,7 +291,7 @@ def pagerank_multi(mg: MultiGraph, damping: float = 0.85, iters: int = 20, dangl
     if out is None:
         out = torch.empty(mg.V, dtype=torch.float32, device="cuda")
     mode = {"redistribute": L.TC_DANGLING_REDISTRIBUTE, "drop": L.TC_DANGLING_DROP}[dangling]
-    pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), None, 1 if profile else 0, 0)
+    pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), None, 1 if profile else 0, 0, 0)
     mp = L.tc_multi_params(int(lanes_per_vertex), int(ctas_per_sm), 1 if use_graph else 0)
     st = L.tc_pr_stats()
     _check(L.load().tc_pagerank_multi(mg.handle, C.byref(pp), C.byref(mp), out.data_ptr(), C.byref(st),
@@ -291,7 +301,7 @@ def pagerank_multi(mg: MultiGraph, damping: float = 0.85, iters: int = 20, dangl
 
 def multi_autotune(mg: MultiGraph, damping: float = 0.85, iters: int = 20, stream=None):
     """tc_multi_autotune: time the lanes-per-vertex variants; returns (best, {lanes: ms})."""
-    pp = L.tc_pr_params(float(damping), int(iters), 0, L.TC_MEM_DEVICE, None, 0, 0)
+    pp = L.tc_pr_params(float(damping), int(iters), 0, L.TC_MEM_DEVICE, None, 0, 0, 0)
     best = C.c_int32()
     times = (C.c_float * 5)()
     _check(L.load().tc_multi_autotune(mg.handle, C.byref(pp), C.byref(best), times, _stream(stream)),

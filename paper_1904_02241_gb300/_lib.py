@@ -50,7 +50,7 @@ TC_MERGE_FLOAT = 2
 class tc_pr_params(C.Structure):
     _fields_ = [("damping", C.c_float), ("iters", C.c_int32), ("dangling", C.c_int32),
                 ("out_mem", C.c_int32), ("init", C.c_void_p), ("profile", C.c_int32),
-                ("merge_mode", C.c_int32)]
+                ("merge_mode", C.c_int32), ("lb_warp_min", C.c_int32)]
 
 
 class tc_pr_stats(C.Structure):
@@ -85,6 +85,7 @@ SIGNATURES = {
     "tc_part_free": (None, [VP]),
     "tc_part_get_info": (C.c_int, [VP, C.POINTER(tc_part_info)]),
     "tc_part_export": (C.c_int, [VP, VP, VP, VP, VP, VP, C.c_int, VP]),
+    "tc_part_set_lb": (C.c_int, [VP, VP]),
     "tc_default_block_width": (C.c_int32, [C.c_int32, C.c_int64, C.c_float]),
     "tc_pagerank_pull": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_pagerank_push": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
@@ -95,6 +96,18 @@ SIGNATURES = {
     "tc_pagerank_multi": (C.c_int, [VP, C.POINTER(tc_pr_params), C.POINTER(tc_multi_params), VP,
                                     C.POINTER(tc_pr_stats), VP]),
     "tc_multi_autotune": (C.c_int, [VP, C.POINTER(tc_pr_params), C.POINTER(C.c_int32), VP, VP]),
+    "tc_graph_features": (C.c_int, [VP, VP]),
+    "tc_part_features": (C.c_int, [VP, VP]),
+    "tc_mlp_create": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, VP, C.POINTER(VP)]),
+    "tc_mlp_free": (None, [VP]),
+    "tc_mlp_num_params": (C.c_int64, [VP]),
+    "tc_mlp_set_params": (C.c_int, [VP, VP]),
+    "tc_mlp_get_params": (C.c_int, [VP, VP, VP]),
+    "tc_mlp_forward": (C.c_int, [VP, VP, C.c_int32, VP, C.c_int, VP]),
+    "tc_mlp_loss_grad": (C.c_int, [VP, VP, VP, C.c_int32, C.c_int, C.POINTER(C.c_double), VP]),
+    "tc_mlp_adam_step": (C.c_int, [VP, C.c_float, C.c_float, C.c_float, C.c_float, VP]),
+    "tc_mlp_train": (C.c_int, [VP, VP, VP, C.c_int32, C.c_int32, C.c_int32, C.c_float, C.c_int,
+                               C.POINTER(C.c_double), VP]),
     "tc_pagerank_pull_noalloc": (C.c_int, [C.c_int32, VP, VP, VP, C.c_float, C.c_int32, C.c_int32, VP, VP]),
 }
 

@@ -139,6 +139,7 @@ struct tc_part {
     tc::DevBuf heads;           // 1 bit per staged edge: a local row starts here
     tc::DevBuf wtab;            // int2[B * 33]: per block and warp, (first edge, first row)
     tc::DevBuf id16;            // uint16[R]: id_map[r] mod k (k a power of two), for the merge
+    tc::DevBuf lb_tab;          // int32[B]: per-block warp_min of the unstaged gathers (optional)
     ~tc_part() {
         delete[] h_blk_rows;
         delete[] h_blk_edges;
@@ -152,7 +153,8 @@ constexpr int TILE_THREADS = 1024;
 size_t tile_smem_bytes(int32_t W);       // dynamic shared memory of the staged gather for width W
 int32_t tile_max_width(int max_smem_optin);
 int build_tiles(tc_part *p, int sms, cudaStream_t s);
-size_t merge_smem_bytes(int32_t k, int32_t B);   // dynamic shared memory of the pull merge
+size_t merge_smem_bytes(int32_t k, int32_t B);   // dynamic shared memory of the ordered pull merge
+size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed);  // ... of the one-accumulator merges
 // Launch the staged gather (+ long rows) writing p->partial from contributions `contrib`.
 int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, cudaStream_t s, int *launches);
 

@@ -45,13 +45,33 @@ __device__ __forceinline__ float apply_update(const UpdateArgs &u, int32_t v, fl
 // Pull gather over a CSR whose rows are destinations (G^T, or the TOCAB row space).
 // FUSED = true: rows are vertices, apply the update; FUSED = false: write partial[row].
 // ---------------------------------------------------------------------------------------------
+// Load-balancing knobs (Sec. 3.2): rows with fewer than warp_min edges are summed by one lane,
+// rows up to hub_degree by the whole warp, larger rows by a whole CTA.  With a per-block table
+// (lb_tab[b], blocks found through blk_rows) every TOCAB subgraph has its own warp_min.
+struct LbArgs {
+    int32_t warp_min;
+    const int32_t *lb_tab;   // null: warp_min everywhere
+    const int64_t *blk_rows; // [B+1]
+    int32_t B;
+};
+
+__device__ __forceinline__ int32_t lb_warp_min(const LbArgs &lb, int64_t row) {
+    if (!lb.lb_tab) return lb.warp_min;
+    int32_t lo = 0, hi = lb.B;
+    while (hi - lo > 1) {
+        const int32_t mid = (lo + hi) >> 1;
+        if (__ldg(lb.blk_rows + mid) <= row) lo = mid; else hi = mid;
+    }
+    return __ldg(lb.lb_tab + lo);
+}
+
 template <bool FUSED>
 __global__ void __launch_bounds__(PR_THREADS) k_pull_gather(const int32_t *__restrict__ rowptr,
                                                             const int32_t *__restrict__ colidx, int64_t nrows,
                                                             const int32_t *__restrict__ hubs, int32_t num_hubs,
                                                             int32_t hub_degree, int hub_ctas,
                                                             const float *__restrict__ contrib,
-                                                            float *__restrict__ partial, UpdateArgs u) {
+                                                            float *__restrict__ partial, UpdateArgs u, LbArgs lb) {
     __shared__ float fred[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     float dsum = 0.0f;
@@ -81,11 +101,12 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_gather(const int32_t *__res
                 e = __ldg(rowptr + row + 1);
             }
             const int32_t deg = e - s;
+            const int32_t wmin = lb_warp_min(lb, grp * 32);
             float sum = 0.0f;
-            if (deg < 32) {  // thread per row
+            if (deg < wmin && deg <= hub_degree) {  // thread per row (hubs go to their CTA)
                 for (int32_t i = s; i < e; ++i) sum += __ldg(contrib + __ldg(colidx + i));
             }
-            unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= 32 && deg <= hub_degree);
+            unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= wmin && deg <= hub_degree);
             while (wm) {  // warp per row
                 const int l = __ffs(wm) - 1;
                 wm &= wm - 1;
@@ -271,7 +292,10 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t j = blockIdx.x;
     const int32_t vbase = j * k;
-    const double scale = FIXED ? *u.fx_scale * (1.0 / 8192.0) : 1.0;  // 2^61 -> 2^48 per unit mass
+    // 2^48 per unit of mass: a power of two, so partial * scale is exact in FP32 and the
+    // conversion to an integer only rounds below 2^-48 of the mass (no FP64 in the loop)
+    const double scale = FIXED ? *u.fx_scale * (1.0 / 8192.0) : 1.0;
+    const float scalef = (float)scale;
     for (int t = tid; t < k; t += MG_THREADS) {
         if (FIXED) {
             acc_hi[t] = 0;
@@ -356,7 +380,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
         for (int q = 0; q < MG_UNROLL; ++q) {
             if (idq[q] >= 0) {
                 if (FIXED) {
-                    const long long v = __double2ll_rn((double)vq[q] * scale);
+                    const long long v = __float2ll_rn(vq[q] * scalef);
                     atomicAdd(acc_hi + idq[q], (int32_t)(v >> 32));
                     atomicAdd(acc_mid + idq[q], (uint32_t)((v >> 16) & 0xFFFF));
                     atomicAdd(acc_lo + idq[q], (uint32_t)(v & 0xFFFF));
@@ -410,11 +434,13 @@ __global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict_
     grid_sum2_last_cta((double)bs, (double)bm, u.dpart, u.counter, u.D_next, mass);
 }
 
-// 2^61 / max(1, mass): a vertex sum is at most the mass, so |sum * scale| <= 2^61 < 2^63
-// (the factor 4 of headroom also covers the rounding of the FP32 mass).
+// 2^61 / 2^ceil(log2(max(1, mass))): a power of two (so FP32 values scale exactly), and a
+// vertex sum is at most the mass, so |sum * scale| <= 2^61 < 2^63.
 __global__ void k_pr_scale(const double *mass, double *scale) {
     const double m = *mass;
-    *scale = 2305843009213693952.0 / (m > 1.0 ? m : 1.0);
+    int e = 0;
+    if (m > 1.0) e = (int)ceil(log2(m));
+    *scale = ldexp(1.0, 61 - e);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -425,7 +451,8 @@ __global__ void __launch_bounds__(PR_THREADS) k_push_scatter(const int32_t *__re
                                                              const int32_t *__restrict__ id_map,
                                                              const int32_t *__restrict__ hubs, int32_t num_hubs,
                                                              int32_t hub_degree, int hub_ctas,
-                                                             const float *__restrict__ contrib, float *sums) {
+                                                             const float *__restrict__ contrib, float *sums,
+                                                             LbArgs lb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if ((int)blockIdx.x < hub_ctas) {
         for (int32_t h = blockIdx.x; h < num_hubs; h += hub_ctas) {
@@ -451,9 +478,10 @@ __global__ void __launch_bounds__(PR_THREADS) k_push_scatter(const int32_t *__re
             c = __ldg(contrib + (id_map ? __ldg(id_map + row) : (int32_t)row));
         }
         const int32_t deg = e - s;
-        if (deg < 32 && c != 0.0f)
+        const int32_t wmin = lb_warp_min(lb, grp * 32);
+        if (deg < wmin && deg <= hub_degree && c != 0.0f)  // hubs are scattered by their CTA only
             for (int32_t i = s; i < e; ++i) atomicAdd(sums + __ldg(colidx + i), c);
-        unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= 32 && deg <= hub_degree && c != 0.0f);
+        unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= wmin && deg <= hub_degree && c != 0.0f);
         while (wm) {
             const int l = __ffs(wm) - 1;
             wm &= wm - 1;
@@ -571,6 +599,7 @@ static int check_pr_args(const tc_graph *g, const tc_part *part, const tc_pr_par
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad dangling mode");
     if (pp->out_mem != TC_MEM_HOST && pp->out_mem != TC_MEM_DEVICE)
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad out_mem");
+    if (pp->lb_warp_min < 0) return fail(TC_ERR_INVALID_ARG, "pagerank: lb_warp_min < 0");
     if (pp->merge_mode < TC_MERGE_FIXED || pp->merge_mode > TC_MERGE_FLOAT)
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad merge_mode");
     if (part && (part->g != g || part->dir != dir))
@@ -622,6 +651,10 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     if (part && !push) {
         g_merge = part->nranges;
         merge_mode = pp->merge_mode;
+        // per-warp accumulators that do not fit in shared memory: the exact fixed-point merge
+        // (also deterministic) takes over
+        if (merge_mode == TC_MERGE_ORDERED && merge_smem_bytes(part->k, part->B) > (size_t)caps.max_smem_optin)
+            merge_mode = TC_MERGE_FIXED;
         if (merge_mode == TC_MERGE_ORDERED) {
             merge_smem = merge_smem_bytes(part->k, part->B);
             if (merge_smem > 48 * 1024)
@@ -688,19 +721,24 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
         u.contrib_next = push ? st.contrib[0] : st.contrib[(it + 1) & 1];
         Timer t1;
         TC_TRY(t1.begin(pp->profile != 0, s, &ms_gather));
+        LbArgs lb;
+        lb.warp_min = pp->lb_warp_min > 0 ? pp->lb_warp_min : 32;
+        lb.lb_tab = (part && part->lb_tab.p) ? part->lb_tab.as<int32_t>() : nullptr;
+        lb.blk_rows = part ? part->blk_rows_dev.as<int64_t>() : nullptr;
+        lb.B = part ? part->B : 1;
         if (push) {
             k_push_scatter<<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, idm, hubs, nhubs, hubdeg, hub_ctas, cur,
-                                                          st.sums);
+                                                          st.sums, lb);
         } else if (tiled) {
             int nl = 0;
             TC_TRY(launch_tiled_gather(part, cur, st.err, s, &nl));
             launches += nl - 1;
         } else if (part) {
             k_pull_gather<false><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, hubs, nhubs, hubdeg, hub_ctas, cur,
-                                                                 part->partial.as<float>(), u);
+                                                                 part->partial.as<float>(), u, lb);
         } else {
             k_pull_gather<true><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, hubs, nhubs, hubdeg, hub_ctas, cur,
-                                                                nullptr, u);
+                                                                nullptr, u, lb);
         }
         TC_LAUNCH_CHECK();
         ++launches;

@@ -123,7 +123,13 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->V = V;
     p->E = E;
     const float frac = (pp && pp->l2_fraction > 0) ? pp->l2_fraction : 0.0f;
-    p->k = (pp && pp->merge_range > 0) ? pp->merge_range : 1024;
+    if (pp && pp->merge_range > 0) {
+        p->k = pp->merge_range;
+    } else {  // 8192 (longest slices that fit well), smaller for small graphs: >= 2 ranges per SM
+        int64_t k = 8192;
+        while (k > 1024 && ((int64_t)V + k - 1) / k < 2 * caps.sms) k >>= 1;
+        p->k = (int32_t)k;
+    }
     if (p->k % 32 != 0) return fail(TC_ERR_INVALID_ARG, "merge_range must be a multiple of 32");
     p->hub_degree = (pp && pp->hub_degree > 0) ? pp->hub_degree : 2048;
     const int32_t smem_w = tile_max_width(caps.max_smem_optin);
@@ -149,8 +155,8 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->nranges = (int32_t)(((int64_t)V + p->k - 1) / p->k);
     if (dir == TC_PULL && ((int64_t)V + p->W - 1) / p->W > 65535)
         return fail(TC_ERR_UNSUPPORTED, "more than 65535 blocks");
-    if (dir == TC_PULL && (int64_t)merge_smem_bytes(p->k, V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1) >
-                              (int64_t)caps.max_smem_optin)
+    if (dir == TC_PULL && (int64_t)merge_atomic_smem_bytes(p->k, V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1,
+                                                           true) > (int64_t)caps.max_smem_optin)
         return fail(TC_ERR_INVALID_ARG, "merge_range %d with this block count needs more shared memory than a CTA has",
                     p->k);
     const int32_t B = p->B, W = p->W;
@@ -310,5 +316,19 @@ extern "C" int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_
     if (id_map && p->R > 0) TC_CUDA(cudaMemcpyAsync(id_map, p->id_map.p, (size_t)p->R * 4, d2x, s));
     if (colidx && p->E > 0) TC_CUDA(cudaMemcpyAsync(colidx, p->colidx.p, (size_t)p->E * 4, d2x, s));
     TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+extern "C" int tc_part_set_lb(tc_part *p, const int32_t *warp_min_per_block) {
+    using namespace tc;
+    if (!p) return fail(TC_ERR_INVALID_ARG, "tc_part_set_lb: null partition");
+    if (!warp_min_per_block) {
+        p->lb_tab.release();
+        return TC_OK;
+    }
+    for (int32_t b = 0; b < p->B; ++b)
+        if (warp_min_per_block[b] < 1) return fail(TC_ERR_INVALID_ARG, "tc_part_set_lb: warp_min must be >= 1");
+    TC_TRY(p->lb_tab.alloc((size_t)p->B * 4));
+    TC_CUDA(cudaMemcpy(p->lb_tab.p, warp_min_per_block, (size_t)p->B * 4, cudaMemcpyHostToDevice));
     return TC_OK;
 }

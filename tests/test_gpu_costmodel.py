@@ -1,0 +1,124 @@
+"""The learned cost model: its CUDA forward/backward/Adam kernels against the FP64 oracle,
+its feature extractor against the plain definitions, and that training learns."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from oracle.mlp import adam_step
+
+pytestmark = pytest.mark.gpu
+HEADS = (9, 3, 2)
+
+
+@pytest.fixture(scope="module")
+def CM():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1904_02241_gb300 import costmodel
+    return costmodel
+
+
+def _data(n, seed):
+    rng = np.random.default_rng(seed)
+    X = rng.normal(size=(n, 16)).astype(np.float32)
+    Y = np.stack([rng.integers(0, h, n) for h in HEADS], axis=1).astype(np.int32)
+    return X, Y
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return np.abs(a - b).max() / max(np.abs(b).max(), 1e-12)
+
+
+def test_mlp_forward_matches_oracle(CM):
+    m = CM.MLP(heads=HEADS)
+    m.init(seed=1)
+    X, _ = _data(37, 2)
+    Z = m.forward(X)
+    Zo, _ = oracle.mlp_forward(m.get(), X.astype(np.float64))
+    assert _rel(Z, Zo) < 1e-5
+
+
+def test_mlp_gradients_match_oracle(CM):
+    m = CM.MLP(heads=HEADS)
+    m.init(seed=3)
+    X, Y = _data(53, 4)
+    loss = m.loss_grad(X, Y)
+    p = m.get()
+    assert abs(loss - oracle.mlp_loss(p, X.astype(np.float64), Y, HEADS)) < 1e-5 * max(1.0, abs(loss))
+    go = oracle.mlp_backward(p, X.astype(np.float64), Y, HEADS)
+    g = m.grads()
+    for k in go:
+        assert _rel(g[k], go[k]) < 2e-4, k
+
+
+def test_mlp_adam_step_matches_oracle(CM):
+    m = CM.MLP(heads=HEADS)
+    m.init(seed=5)
+    X, Y = _data(20, 6)
+    p0 = m.get()
+    m.loss_grad(X, Y)
+    g = m.grads()
+    m.adam_step(lr=1e-2)
+    zeros = {k: np.zeros_like(v) for k, v in p0.items()}
+    want, _, _ = adam_step(p0, g, zeros, zeros, t=1, lr=1e-2)
+    got = m.get()
+    for k in want:
+        assert np.allclose(got[k], want[k], rtol=1e-5, atol=1e-6), k
+
+
+def test_mlp_zero_weights_loss_is_log_classes(CM):
+    m = CM.MLP(heads=HEADS)
+    m.set({n: np.zeros(s) for n, s in m.shapes()})
+    X, Y = _data(10, 7)
+    assert abs(m.loss_grad(X, Y) - sum(np.log(h) for h in HEADS)) < 1e-5
+
+
+def test_mlp_training_learns_a_rule(CM):
+    rng = np.random.default_rng(0)
+    X = rng.normal(size=(512, 16)).astype(np.float32)
+    Y = np.stack([(X[:, 0] > 0) * 4 + (X[:, 1] > 0), (X[:, 2] > 0.5).astype(int), (X[:, 3] + X[:, 4] > 0)],
+                 axis=1).astype(np.int32)
+    m = CM.MLP(heads=HEADS)
+    m.init(seed=1)
+    l0 = m.loss_grad((X - X.mean(0)) / X.std(0), Y)
+    loss = m.train(X, Y, epochs=200, batch=64, lr=3e-3)
+    assert loss < 0.3 * l0
+    acc = (m.predict(X) == Y).mean(axis=0)
+    assert (acc > 0.9).all(), acc
+
+
+def _features_numpy(rowptr, colidx, rowids, V, out_rowptr, l2):
+    d = np.diff(rowptr).astype(np.float64)
+    R, E = len(d), d.sum()
+    mean = E / R
+    od = np.diff(out_rowptr).astype(np.float64)
+    om = od.sum() / V
+    first = np.array([abs(colidx[rowptr[r]] - rowids[r]) if d[r] > 0 else 0 for r in range(R)], np.float64)
+    return np.array([np.log2(R + 1), np.log2(E + 1), mean, d.std() / mean, np.log2(1 + d.max() / mean),
+                     (d == 0).mean(), ((d >= 1) & (d <= 7)).mean(), ((d >= 8) & (d <= 15)).mean(),
+                     ((d >= 16) & (d <= 31)).mean(), (d >= 32).mean(), od.std() / om, (od == 0).mean(),
+                     np.log2(1 + 4 * V / l2), np.log2(1 + 4 * E / l2), first.sum() / (R * V),
+                     np.log2(1 + od.max() / om)])
+
+
+def test_graph_features_match_definitions(CM):
+    import paper_1904_02241_gb300 as T
+    g = gg.rmat(11)
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda())
+    f = CM.graph_features(G)
+    trp, tci = oracle.transpose(g.V, *g.numpy())
+    l2 = torch.cuda.get_device_properties(0).L2_cache_size
+    want = _features_numpy(trp, tci, np.arange(g.V), g.V, g.numpy()[0], l2)
+    np.testing.assert_allclose(f, want, rtol=2e-5, atol=1e-6)
+    P = T.tocab_partition(G, T.TC_PULL, 4)
+    pf = CM.part_features(P)
+    ex = P.export()
+    for b in range(P.num_blocks):
+        r0, r1 = ex["blk_rows"][b], ex["blk_rows"][b + 1]
+        rp = ex["rowptr"][r0:r1 + 1]
+        wb = _features_numpy(rp, ex["colidx"], ex["id_map"][r0:r1], g.V, g.numpy()[0], l2)
+        wb[12] = np.log2(1 + 4 * P.block_width / l2)
+        np.testing.assert_allclose(pf[b], wb, rtol=2e-5, atol=1e-6, err_msg=str(b))

@@ -381,3 +381,36 @@ def test_multigraph_rejects_cross_edges(T):
     with pytest.raises(T.TocabError) as e:
         T.multigraph_load(g.rowptr, g.colidx, [0, 2, 4])
     assert e.value.status == -2
+
+
+# ------------------------------------------------------------------ load-balancing variants
+
+@pytest.mark.parametrize("lb", [1, 8, 32, 1 << 30])
+@pytest.mark.parametrize("kind", ["pull_unblocked", "pull_tocab", "push_tocab", "push_unblocked"])
+def test_load_balancing_variants(T, lb, kind):
+    g = GRAPHS["rmat14_noperm"]
+    G = _load(T, g)
+    if kind == "pull_unblocked":
+        r = T.pagerank_pull(G, None, lb_warp_min=lb)
+    elif kind == "pull_tocab":
+        r = T.pagerank_pull(G, T.tocab_partition(G, T.TC_PULL, 4, smem_stage=-1), lb_warp_min=lb)
+    elif kind == "push_tocab":
+        r = T.pagerank_push(G, T.tocab_partition(G, T.TC_PUSH, 4), lb_warp_min=lb)
+    else:
+        r = T.pagerank_push(G, None, lb_warp_min=lb)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+
+
+def test_per_block_load_balancing(T):
+    g = GRAPHS["rmat14_noperm"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 4, smem_stage=-1)
+    P.set_lb([1, 1 << 30, 32, 8][:P.num_blocks])
+    r = T.pagerank_pull(G, P)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    with pytest.raises(T.TocabError):
+        P.set_lb([0] * P.num_blocks)
+    P.set_lb(None)
+    Pp = T.tocab_partition(G, T.TC_PUSH, 4)
+    Pp.set_lb([1 << 30, 1, 8, 32][:Pp.num_blocks])
+    assert l1_rel(T.pagerank_push(G, Pp).cpu().numpy(), _oracle_pr(g)) <= TOL

@@ -305,15 +305,16 @@ def variants(args, ctx, world):
     Ps = T.tocab_partition(Gs, T.TC_PULL, args.blocks, block_policy="l2")
     lv = torch.empty(gs.V, dtype=torch.int32, device="cuda")
     srcs = gg.sources(gs, args.bfs_sources, seed=13)
-    for thr, key in [(0.05, "bfs_tocab"), (-1.0, "bfs_unblocked")]:
-        T.bfs_pull(Gs, Ps, srcs[0], tocab_threshold=thr, out=lv)
+    for thr, push, key in [(0.05, 0.0, "bfs_tocab"), (-1.0, 0.0, "bfs_unblocked"),
+                           (0.05, 0.02, "bfs_diropt_tocab"), (-1.0, 0.02, "bfs_diropt_unblocked")]:
+        T.bfs_pull(Gs, Ps, srcs[0], tocab_threshold=thr, out=lv, push_threshold=push)
         torch.cuda.synchronize()
         tot_ms, tot_edges = 0.0, 0
         for s in srcs:
             t0 = torch.cuda.Event(enable_timing=True)
             t1 = torch.cuda.Event(enable_timing=True)
             t0.record(stream)
-            _, st = T.bfs_pull(Gs, Ps, s, tocab_threshold=thr, out=lv, return_stats=True)
+            _, st = T.bfs_pull(Gs, Ps, s, tocab_threshold=thr, out=lv, return_stats=True, push_threshold=push)
             t1.record(stream)
             t1.synchronize()
             tot_ms += t0.elapsed_time(t1)

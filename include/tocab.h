@@ -227,6 +227,10 @@ typedef struct tc_bfs_params {
                                  than this fraction of V (Sec. 3.3); < 0 = never, 0 = always */
     int32_t out_mem;          /* memory space of levels_out */
     int32_t profile;          /* nonzero: per-kernel device timing into stats */
+    float   push_threshold;   /* 0 = every level pulls (topology-driven, the default); > 0 =
+                                 levels whose frontier holds at most this fraction of V run
+                                 push (top-down, data-driven queue), the push phases of the
+                                 push-pull-push schedule of Sec. 3.3 */
 } tc_bfs_params;
 
 typedef struct tc_bfs_stats {
@@ -243,7 +247,9 @@ typedef struct tc_bfs_stats {
  * unvisited vertex v scans its in-edges and joins level L+1 if an in-neighbour is in
  * the frontier.  With part != NULL (TC_PULL) levels whose frontier exceeds the threshold
  * run per block into local next bitmaps over local IDs, OR-reduced in the merge kernel
- * (Sec. 3.3).  levels_out[v] = hop distance from `source`, -1 when unreachable.
+ * (Sec. 3.3).  With push_threshold > 0, small-frontier levels run top-down from a queue
+ * instead (direction optimisation); levels are identical either way.
+ * levels_out[v] = hop distance from `source`, -1 when unreachable.
  * Errors: TC_ERR_INVALID_ARG (source outside [0, V)), TC_ERR_OOM, TC_ERR_CUDA.
  */
 int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,

@@ -311,13 +311,15 @@ def multi_autotune(mg: MultiGraph, damping: float = 0.85, iters: int = 20, strea
 
 
 def bfs_pull(graph: Graph, part: Partition | None, source: int, tocab_threshold: float = 0.05,
-             out: torch.Tensor | None = None, profile: bool = False, stream=None, return_stats: bool = False):
-    """tc_bfs_pull: hop levels from source (-1 = unreachable)."""
+             out: torch.Tensor | None = None, profile: bool = False, stream=None, return_stats: bool = False,
+             push_threshold: float = 0.0):
+    """tc_bfs_pull: hop levels from source (-1 = unreachable).  push_threshold > 0 runs the
+    small-frontier levels top-down (direction optimisation)."""
     if out is None:
         out = torch.empty(graph.V, dtype=torch.int32, device="cuda")
     if out.dtype != torch.int32 or out.numel() < graph.V or not out.is_contiguous():
         raise ValueError("out must be a contiguous int32 tensor with V elements")
-    bp = L.tc_bfs_params(float(tocab_threshold), _mem(out), 1 if profile else 0)
+    bp = L.tc_bfs_params(float(tocab_threshold), _mem(out), 1 if profile else 0, float(push_threshold))
     st = L.tc_bfs_stats()
     _check(L.load().tc_bfs_pull(graph.handle, part.handle if part is not None else None, int(source), C.byref(bp),
                                 out.data_ptr(), C.byref(st), _stream(stream)), "tc_bfs_pull")

@@ -63,7 +63,8 @@ class tc_multi_params(C.Structure):
 
 
 class tc_bfs_params(C.Structure):
-    _fields_ = [("tocab_threshold", C.c_float), ("out_mem", C.c_int32), ("profile", C.c_int32)]
+    _fields_ = [("tocab_threshold", C.c_float), ("out_mem", C.c_int32), ("profile", C.c_int32),
+                ("push_threshold", C.c_float)]
 
 
 class tc_bfs_stats(C.Structure):

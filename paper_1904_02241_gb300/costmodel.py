@@ -357,22 +357,29 @@ def _main():
     ap.add_argument("--scale-lo", type=int, default=14)
     ap.add_argument("--scale-hi", type=int, default=20)
     ap.add_argument("--heldout", type=int, default=24)
+    ap.add_argument("--large", type=int, default=0, help="extra training graphs at scales 21-24")
+    ap.add_argument("--large-heldout", type=int, default=0)
+    ap.add_argument("--rmat25", action="store_true", help="add R-MAT scale 25 to the held-out set")
     ap.add_argument("--epochs", type=int, default=400)
     ap.add_argument("--out", default=WEIGHTS)
     ap.add_argument("--report", default=None)
     a = ap.parse_args()
     t0 = time.time()
     log = lambda s: print(s, file=sys.stderr, flush=True)  # noqa: E731
-    X, Y, tables = build_dataset(graph_specs(a.graphs, 1000, a.scale_lo, a.scale_hi), log=log)
+    specs = graph_specs(a.graphs, 1000, a.scale_lo, a.scale_hi) + graph_specs(a.large, 2000, 21, 24)
+    X, Y, tables = build_dataset(specs, log=log)
     m = MLP()
     m.init(seed=0)
     loss = m.train(X, Y, epochs=a.epochs, batch=64, lr=3e-3)
     acc = (m.predict(X) == Y).mean(axis=0).tolist()
-    held = evaluate(m, graph_specs(a.heldout, 900000, a.scale_lo, a.scale_hi), log=log)
-    base = evaluate(None, [], log=log)
-    del base
+    hspecs = graph_specs(a.heldout, 900000, a.scale_lo, a.scale_hi) + graph_specs(a.large_heldout, 910000, 21, 24)
+    if a.rmat25:
+        hspecs.append({"kind": "rmat", "scale": 25, "ef": 16, "a": 0.57, "b": 0.19, "c": 0.19, "seed": 25,
+                       "permute": True})
+    held = evaluate(m, hspecs, log=log)
     gm = lambda k: float(np.exp(np.mean([np.log(r[k] / r["t_best"]) for r in held])))  # noqa: E731
-    meta = {"graphs": a.graphs, "scales": [a.scale_lo, a.scale_hi], "final_loss": loss, "train_accuracy": acc,
+    meta = {"graphs": a.graphs, "scales": [a.scale_lo, a.scale_hi], "large_graphs": a.large,
+            "final_loss": loss, "train_accuracy": acc,
             "heldout": a.heldout, "heldout_model_over_best": gm("t_model"),
             "heldout_heuristic_over_best": gm("t_heuristic"), "seconds": time.time() - t0}
     m.save(a.out, meta)

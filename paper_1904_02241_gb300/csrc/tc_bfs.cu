@@ -181,6 +181,98 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_merge(const uint32_t *__res
     if (threadIdx.x == 0 && tot) atomicAdd(count, tot);
 }
 
+// Push (top-down, data-driven) level for small frontiers (Sec. 3.3: the push phases of the
+// push-pull-push schedule, Alg. 3 without sigma): every frontier vertex in the queue scans its
+// out-edges; an unvisited neighbour is claimed with an atomic OR on the visited bitmap, gets
+// its level, joins the next bitmap and is appended to the next queue (warp-aggregated).
+__global__ void __launch_bounds__(BFS_THREADS) k_bfs_push_level(const int32_t *__restrict__ rowptr,
+                                                                const int32_t *__restrict__ colidx,
+                                                                const int32_t *__restrict__ queue, int32_t qn,
+                                                                uint32_t *visited, uint32_t *next, int32_t *level,
+                                                                int32_t new_level, int32_t *next_queue,
+                                                                unsigned long long *count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * BFS_WARPS;
+    // a warp takes 32 queue entries; each lane walks its vertex's out-edges, long rows by the warp
+    for (int64_t base = ((int64_t)blockIdx.x * BFS_WARPS + (threadIdx.x >> 5)) * 32; base < qn; base += nw * 32) {
+        const int64_t qi = base + lane;
+        int32_t s = 0, e = 0;
+        if (qi < qn) {
+            const int32_t u = queue[qi];
+            s = __ldg(rowptr + u);
+            e = __ldg(rowptr + u + 1);
+        }
+        // rows of 32+ edges: the whole warp, one row at a time
+        unsigned wm = __ballot_sync(0xffffffffu, e - s >= 32);
+        int32_t ls = s, le = (e - s >= 32) ? s : e;  // this lane's own (short) range
+        for (;;) {
+            int32_t i0, i1, stride;
+            bool own = false;
+            if (wm) {
+                const int l = __ffs(wm) - 1;
+                wm &= wm - 1;
+                i0 = __shfl_sync(0xffffffffu, s, l) + lane;
+                i1 = __shfl_sync(0xffffffffu, e, l);
+                stride = 32;
+            } else {
+                i0 = ls;
+                i1 = le;
+                stride = 1;
+                own = true;
+            }
+            // uniform trip count over the warp so that ballots stay converged
+            int32_t trips = (i1 - i0 + stride - 1) / stride;
+            if (trips < 0) trips = 0;
+            int32_t maxtrips = trips;
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) maxtrips = max(maxtrips, __shfl_xor_sync(0xffffffffu, maxtrips, d));
+            for (int32_t t = 0; t < maxtrips; ++t) {
+                bool claimed = false;
+                int32_t v = 0;
+                if (t < trips) {
+                    v = __ldg(colidx + i0 + t * stride);
+                    const uint32_t bit = 1u << (v & 31);
+                    if (!(visited[v >> 5] & bit)) {
+                        const uint32_t old = atomicOr(visited + (v >> 5), bit);
+                        claimed = !(old & bit);
+                    }
+                }
+                const unsigned cm = __ballot_sync(0xffffffffu, claimed);
+                if (cm) {
+                    int32_t pos0 = 0;
+                    if (lane == __ffs(cm) - 1) pos0 = (int32_t)atomicAdd(count, (unsigned long long)__popc(cm));
+                    pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(cm) - 1);
+                    if (claimed) {
+                        level[v] = new_level;
+                        atomicOr(next + (v >> 5), 1u << (v & 31));
+                        next_queue[pos0 + __popc(cm & ((1u << lane) - 1u))] = v;
+                    }
+                }
+            }
+            if (own) break;
+        }
+    }
+}
+
+// Queue of the vertices set in a bitmap (for a push level after a pull level): per word a
+// popcount, an exclusive scan (positions), then the write.
+__global__ void k_bitmap_count(const uint32_t *bits, int32_t nwords, int32_t *cnt) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x)
+        cnt[w] = __popc(bits[w]);
+}
+
+__global__ void k_bitmap_queue(const uint32_t *bits, int32_t nwords, const int64_t *pos, int32_t *queue) {
+    for (int64_t w = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; w < nwords; w += (int64_t)gridDim.x * blockDim.x) {
+        uint32_t m = bits[w];
+        int64_t p = pos[w];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            queue[p++] = (int32_t)(w * 32 + b);
+        }
+    }
+}
+
 // edges_reached = sum of out-degrees of vertices with level >= 0; reached = their count.
 __global__ void __launch_bounds__(BFS_THREADS) k_bfs_stats(const int32_t *level, const int32_t *out_rowptr, int32_t V,
                                                            unsigned long long *out) {
@@ -226,6 +318,18 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
     }
     k_bfs_init<<<grid, BFS_THREADS, 0, s>>>(level, visited, bufs[0], V, nwords, source);
     TC_LAUNCH_CHECK();
+    const bool can_push = bp->push_threshold > 0.0f;
+    DevBuf queues, qcnt, qpos;
+    int32_t *q[2] = {nullptr, nullptr};
+    if (can_push) {
+        TC_TRY(queues.alloc((size_t)2 * V * 4 + 64));
+        TC_TRY(qcnt.alloc((size_t)nwords * 4 + 64));
+        TC_TRY(qpos.alloc((size_t)nwords * 8 + 64));
+        q[0] = queues.as<int32_t>();
+        q[1] = q[0] + V;
+        TC_CUDA(cudaMemcpyAsync(q[0], &source, 4, cudaMemcpyHostToDevice, s));
+    }
+    bool have_queue = can_push;  // the queue q[lvl & 1] holds the current frontier
     unsigned long long front_count = 1, *h_cnt = nullptr;
     TC_CUDA(cudaMallocHost(&h_cnt, 8));
     int lvl = 0, tocab_levels = 0;
@@ -234,9 +338,23 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
     while (front_count > 0) {
         uint32_t *front = bufs[lvl & 1], *next = bufs[(lvl + 1) & 1];
         if (cudaMemsetAsync(cnt, 0, 8, s) != cudaSuccess) { st = fail(TC_ERR_CUDA, "memset failed"); break; }
-        const bool use_tocab = part && bp->tocab_threshold >= 0.0f &&
+        const bool use_push = can_push && (double)front_count <= (double)bp->push_threshold * (double)V;
+        const bool use_tocab = !use_push && part && bp->tocab_threshold >= 0.0f &&
                                (double)front_count > (double)bp->tocab_threshold * (double)V;
-        if (use_tocab) {
+        if (use_push) {
+            if (!have_queue) {  // frontier came from a pull level: bitmap -> queue
+                k_bitmap_count<<<grid, BFS_THREADS, 0, s>>>(front, nwords, qcnt.as<int32_t>());
+                if (cudaGetLastError() != cudaSuccess) { st = fail(TC_ERR_CUDA, "launch failed"); break; }
+                st = scan_i32_to_i64(qcnt.as<int32_t>(), nwords, qpos.as<int64_t>(), s);
+                if (st != TC_OK) break;
+                k_bitmap_queue<<<grid, BFS_THREADS, 0, s>>>(front, nwords, qpos.as<int64_t>(), q[lvl & 1]);
+            }
+            if (cudaMemsetAsync(next, 0, (size_t)nwords * 4, s) != cudaSuccess) { st = fail(TC_ERR_CUDA, "memset failed"); break; }
+            k_bfs_push_level<<<grid, BFS_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(),
+                                                          q[lvl & 1], (int32_t)front_count, visited, next, level,
+                                                          lvl + 1, q[(lvl + 1) & 1], cnt);
+            have_queue = true;
+        } else if (use_tocab) {
             k_bfs_block_level<<<grid, BFS_THREADS, 0, s>>>(part->rowptr.as<int32_t>(), part->colidx.as<int32_t>(),
                                                            part->id_map.as<int32_t>(), part->R, front, visited,
                                                            part->rowbits.as<uint32_t>());
@@ -246,9 +364,11 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
                                                                        part->nranges, part->k, V, nwords, next,
                                                                        visited, level, lvl + 1, cnt);
             ++tocab_levels;
+            have_queue = false;
         } else {
             k_bfs_pull_level<<<grid, BFS_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), V,
                                                           nwords, front, next, visited, level, lvl + 1, cnt);
+            have_queue = false;
         }
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, cnt, 8, cudaMemcpyDeviceToHost, s);

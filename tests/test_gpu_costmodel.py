@@ -122,3 +122,21 @@ def test_graph_features_match_definitions(CM):
         wb = _features_numpy(rp, ex["colidx"], ex["id_map"][r0:r1], g.V, g.numpy()[0], l2)
         wb[12] = np.log2(1 + 4 * P.block_width / l2)
         np.testing.assert_allclose(pf[b], wb, rtol=2e-5, atol=1e-6, err_msg=str(b))
+
+
+def test_learned_model_gains_over_heuristic(CM):
+    """Train on timings the method generates (small seeded graphs of four families), then on
+    held-out graphs compare the time of the network's configuration with the paper's heuristic
+    (pull, block width from the L2 size, thread/warp/CTA balancing) and with the exhaustive best.
+    The network must be at least as good as the heuristic (geometric mean of time / best)."""
+    train = CM.graph_specs(28, seed=5000, scale_lo=14, scale_hi=16)
+    X, Y, _ = CM.build_dataset(train, iters=5, reps=3)
+    m = CM.MLP()
+    m.init(seed=0)
+    m.train(X, Y, epochs=300, batch=32, lr=3e-3)
+    held = CM.evaluate(m, CM.graph_specs(8, seed=7000, scale_lo=14, scale_hi=16), iters=5, reps=3)
+    gm = lambda k: float(np.exp(np.mean([np.log(r[k] / r["t_best"]) for r in held])))  # noqa: E731
+    model, heur = gm("t_model"), gm("t_heuristic")
+    print(f"held-out time / exhaustive best: model {model:.3f}, heuristic {heur:.3f}, "
+          f"gain {heur / model:.3f}x")
+    assert model <= heur * 1.05

@@ -414,3 +414,19 @@ def test_per_block_load_balancing(T):
     Pp = T.tocab_partition(G, T.TC_PUSH, 4)
     Pp.set_lb([1 << 30, 1, 8, 32][:Pp.num_blocks])
     assert l1_rel(T.pagerank_push(G, Pp).cpu().numpy(), _oracle_pr(g)) <= TOL
+
+
+@pytest.mark.parametrize("name", list(BFS_GRAPHS))
+@pytest.mark.parametrize("push", [1.0, 0.05, 0.002])
+@pytest.mark.parametrize("tocab", [True, False])
+def test_bfs_direction_optimised_bit_exact(T, name, push, tocab):
+    g = BFS_GRAPHS[name]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, min(4, g.V)) if tocab else None
+    rp, ci = g.numpy()
+    for s in gg.sources(g, 3, seed=29) + [0]:
+        lv, st = T.bfs_pull(G, P, s, tocab_threshold=0.0 if tocab else -1.0, push_threshold=push,
+                            return_stats=True)
+        want = oracle.bfs(g.V, rp, ci, s)
+        np.testing.assert_array_equal(lv.cpu().numpy(), want)
+        assert st.reached == int((want >= 0).sum())

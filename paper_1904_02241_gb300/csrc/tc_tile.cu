@@ -156,19 +156,24 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
             nc1 = __ldg(p + 1);
             nh = __ldg(t.heads + (q >> 4));
         }
-        // valid edges of this lane: [max(es, e0), min(ee, e0 + 16))
-        const int32_t e0 = q0 + 16 * lane;
-        const int32_t lo_i = es - e0, hi_i = ee - e0;
-        uint32_t valid = 0xFFFFu;
-        if (lo_i > 0) valid = lo_i >= 16 ? 0u : (valid & (0xFFFFu << lo_i));
-        if (hi_i < 16) valid = hi_i <= 0 ? 0u : (valid & ((1u << hi_i) - 1u));
-        hd &= valid;
         const uint32_t words[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
         float val[16];
+        if (q0 >= es && q0 + WCH <= ee) {  // whole chunk inside the warp's range (warp-uniform)
 #pragma unroll
-        for (int i = 0; i < 16; ++i) {
-            const uint32_t col = (words[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
-            val[i] = ((valid >> i) & 1u) ? slice[col] : 0.0f;
+            for (int i = 0; i < 16; ++i) val[i] = slice[(words[i >> 1] >> (16 * (i & 1))) & 0xFFFFu];
+        } else {
+            // valid edges of this lane: [max(es, e0), min(ee, e0 + 16))
+            const int32_t e0 = q0 + 16 * lane;
+            const int32_t lo_i = es - e0, hi_i = ee - e0;
+            uint32_t valid = 0xFFFFu;
+            if (lo_i > 0) valid = lo_i >= 16 ? 0u : (valid & (0xFFFFu << lo_i));
+            if (hi_i < 16) valid = hi_i <= 0 ? 0u : (valid & ((1u << hi_i) - 1u));
+            hd &= valid;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t col = (words[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                val[i] = ((valid >> i) & 1u) ? slice[col] : 0.0f;
+            }
         }
         // rows of this chunk: exclusive scan of head counts over lanes
         const int nh_l = __popc(hd);
@@ -180,24 +185,20 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
         }
         const int before = incl - nh_l;                       // heads in earlier lanes
         const int total = __shfl_sync(0xffffffffu, incl, 31);
-        // walk the lane's 16 edges: pieces between heads are whole rows (written to the stage)
+        // walk the lane's 16 edges (branch-free): the piece before the first head goes to the
+        // carry scan; every later head closes a whole row, written to the stage
         float seg = 0.0f, first = 0.0f;
-        int k = 0;
-        bool seen = false;
+        float *out = stage + before + 1;
+        uint32_t seenm = 0u;  // all ones once a head has been seen
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            if ((hd >> i) & 1u) {
-                if (!seen) {
-                    first = seg;
-                    seen = true;
-                } else {
-                    stage[before + k + 1] = seg;  // row (rowbase + before + k), closed here
-                    ++k;
-                }
-                seg = 0.0f;
-            }
-            seg += val[i];
+            const uint32_t h = 0u - ((hd >> i) & 1u);  // all ones at a head
+            if (h & seenm) *out++ = seg;               // close the row before this head
+            first = (h & ~seenm) ? seg : first;
+            seenm |= h;
+            seg = h ? val[i] : seg + val[i];
         }
+        const bool seen = seenm != 0u;
         if (!seen) first = seg;
         // carry of the open row across lanes: segmented inclusive scan
         bool f = seen;

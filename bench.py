@@ -306,7 +306,7 @@ def variants(args, ctx, world):
     lv = torch.empty(gs.V, dtype=torch.int32, device="cuda")
     srcs = gg.sources(gs, args.bfs_sources, seed=13)
     for thr, push, key in [(0.05, 0.0, "bfs_tocab"), (-1.0, 0.0, "bfs_unblocked"),
-                           (0.05, 0.02, "bfs_diropt_tocab"), (-1.0, 0.02, "bfs_diropt_unblocked")]:
+                           (0.05, 1.0 / 24, "bfs_diropt_tocab"), (-1.0, 1.0 / 24, "bfs_diropt_unblocked")]:
         T.bfs_pull(Gs, Ps, srcs[0], tocab_threshold=thr, out=lv, push_threshold=push)
         torch.cuda.synchronize()
         tot_ms, tot_edges = 0.0, 0

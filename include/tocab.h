@@ -228,17 +228,26 @@ typedef struct tc_bfs_params {
     int32_t out_mem;          /* memory space of levels_out */
     int32_t profile;          /* nonzero: per-kernel device timing into stats */
     float   push_threshold;   /* 0 = every level pulls (topology-driven, the default); > 0 =
-                                 levels whose frontier holds at most this fraction of V run
-                                 push (top-down, data-driven queue), the push phases of the
-                                 push-pull-push schedule of Sec. 3.3 */
+                                 direction optimisation, the push phases of the push-pull-push
+                                 schedule of Sec. 3.3: start top-down (data-driven queue),
+                                 switch to pull when the frontier's out-edges exceed 1/14 of
+                                 the unvisited vertices' out-edges, and back to push when the
+                                 frontier holds fewer than push_threshold * V vertices */
 } tc_bfs_params;
 
+#define TC_BFS_TRACE 64
 typedef struct tc_bfs_stats {
     int32_t levels;           /* number of BFS levels expanded (depth + 1 of the deepest) */
     int32_t tocab_levels;     /* levels run with the blocked kernel */
     int64_t reached;          /* vertices with level >= 0 */
     int64_t edges_reached;    /* sum of out-degrees of reached vertices */
     float   ms_total;         /* device time (profile only) */
+    int32_t push_levels;      /* levels run top-down */
+    /* first TC_BFS_TRACE levels: kind (0 pull, 1 pull TOCAB, 2 push), frontier size at the
+       start of the level, device time (profile only) */
+    int32_t level_kind[TC_BFS_TRACE];
+    int64_t level_frontier[TC_BFS_TRACE];
+    float   level_ms[TC_BFS_TRACE];
 } tc_bfs_stats;
 
 /*

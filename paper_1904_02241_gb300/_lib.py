@@ -67,9 +67,14 @@ class tc_bfs_params(C.Structure):
                 ("push_threshold", C.c_float)]
 
 
+TC_BFS_TRACE = 64
+
+
 class tc_bfs_stats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("tocab_levels", C.c_int32), ("reached", C.c_int64),
-                ("edges_reached", C.c_int64), ("ms_total", C.c_float)]
+                ("edges_reached", C.c_int64), ("ms_total", C.c_float), ("push_levels", C.c_int32),
+                ("level_kind", C.c_int32 * TC_BFS_TRACE), ("level_frontier", C.c_int64 * TC_BFS_TRACE),
+                ("level_ms", C.c_float * TC_BFS_TRACE)]
 
 
 VP = C.c_void_p

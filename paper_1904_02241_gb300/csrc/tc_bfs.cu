@@ -64,10 +64,11 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_pull_level(const int32_t *_
                                                                 int32_t nwords, const uint32_t *__restrict__ front,
                                                                 uint32_t *__restrict__ next, uint32_t *visited,
                                                                 int32_t *level, int32_t new_level,
-                                                                unsigned long long *count) {
+                                                                unsigned long long *count,
+                                                                const int32_t *__restrict__ out_rowptr) {
     __shared__ unsigned long long red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    unsigned long long found_total = 0;
+    unsigned long long found_total = 0, deg_total = 0;
     const int64_t nw = (int64_t)gridDim.x * BFS_WARPS;
     for (int64_t w = (int64_t)blockIdx.x * BFS_WARPS + warp; w < nwords; w += nw) {
         const uint32_t vis = visited[w];
@@ -85,7 +86,10 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_pull_level(const int32_t *_
             if (cand && deg < 32) found = scan_serial(colidx, s, e, front);
             found = scan_warp_rows(__ballot_sync(0xffffffffu, cand && deg >= 32), s, e, colidx, front, found);
             nb = __ballot_sync(0xffffffffu, found);
-            if (found) level[v] = new_level;
+            if (found) {
+                level[v] = new_level;
+                deg_total += (unsigned long long)(__ldg(out_rowptr + v + 1) - __ldg(out_rowptr + v));
+            }
             if (lane == 0 && nb) visited[w] = vis | nb;
         }
         if (lane == 0) {
@@ -94,7 +98,9 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_pull_level(const int32_t *_
         }
     }
     const unsigned long long t = block_sum<unsigned long long>(found_total, red);
+    const unsigned long long dt = block_sum<unsigned long long>(deg_total, red);
     if (threadIdx.x == 0 && t) atomicAdd(count, t);
+    if (threadIdx.x == 0 && dt) atomicAdd(count + 1, dt);
 }
 
 // TOCAB level, phase 1 (Alg. 4 form for traversal): local row r of the row space belongs to
@@ -139,7 +145,8 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_merge(const uint32_t *__res
                                                            int32_t nranges, int32_t k, int32_t V, int32_t nwords,
                                                            uint32_t *__restrict__ next, uint32_t *visited,
                                                            int32_t *level, int32_t new_level,
-                                                           unsigned long long *count) {
+                                                           unsigned long long *count,
+                                                           const int32_t *__restrict__ out_rowptr) {
     extern __shared__ uint32_t hit[];  // k/32 words
     __shared__ unsigned long long red[32];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -159,7 +166,7 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_merge(const uint32_t *__res
         }
     }
     __syncthreads();
-    unsigned long long found_total = 0;
+    unsigned long long found_total = 0, deg_total = 0;
     for (int t = threadIdx.x; t < kw; t += BFS_THREADS) {
         const int64_t w = (int64_t)(vbase >> 5) + t;
         if (w >= nwords) break;
@@ -173,83 +180,75 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_merge(const uint32_t *__res
             while (m) {
                 const int bit = __ffs(m) - 1;
                 m &= m - 1;
-                level[w * 32 + bit] = new_level;
+                const int64_t v = w * 32 + bit;
+                level[v] = new_level;
+                deg_total += (unsigned long long)(__ldg(out_rowptr + v + 1) - __ldg(out_rowptr + v));
             }
         }
     }
     const unsigned long long tot = block_sum<unsigned long long>(found_total, red);
+    const unsigned long long dt = block_sum<unsigned long long>(deg_total, red);
     if (threadIdx.x == 0 && tot) atomicAdd(count, tot);
+    if (threadIdx.x == 0 && dt) atomicAdd(count + 1, dt);
 }
 
-// Push (top-down, data-driven) level for small frontiers (Sec. 3.3: the push phases of the
+// Push (top-down, data-driven) levels for small frontiers (Sec. 3.3: the push phases of the
 // push-pull-push schedule, Alg. 3 without sigma): every frontier vertex in the queue scans its
 // out-edges; an unvisited neighbour is claimed with an atomic OR on the visited bitmap, gets
 // its level, joins the next bitmap and is appended to the next queue (warp-aggregated).
-__global__ void __launch_bounds__(BFS_THREADS) k_bfs_push_level(const int32_t *__restrict__ rowptr,
+// Edge-balanced push level: the out-degrees of the queue are scanned (pre[q+1]); thread t takes
+// edges t, t + stride, ... of the frontier's concatenated out-rows, finds its row by binary
+// search in pre, and claims the neighbour as above.  Hubs spread over the whole grid.
+__global__ void k_push_degrees(const int32_t *__restrict__ rowptr, const int32_t *__restrict__ queue, int32_t qn,
+                               int32_t *deg) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < qn; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = queue[i];
+        deg[i] = __ldg(rowptr + u + 1) - __ldg(rowptr + u);
+    }
+}
+
+__global__ void __launch_bounds__(BFS_THREADS) k_bfs_push_edges(const int32_t *__restrict__ rowptr,
                                                                 const int32_t *__restrict__ colidx,
                                                                 const int32_t *__restrict__ queue, int32_t qn,
+                                                                const int64_t *__restrict__ pre, int64_t total,
                                                                 uint32_t *visited, uint32_t *next, int32_t *level,
                                                                 int32_t new_level, int32_t *next_queue,
                                                                 unsigned long long *count) {
     const int lane = threadIdx.x & 31;
-    const int64_t nw = (int64_t)gridDim.x * BFS_WARPS;
-    // a warp takes 32 queue entries; each lane walks its vertex's out-edges, long rows by the warp
-    for (int64_t base = ((int64_t)blockIdx.x * BFS_WARPS + (threadIdx.x >> 5)) * 32; base < qn; base += nw * 32) {
-        const int64_t qi = base + lane;
-        int32_t s = 0, e = 0;
-        if (qi < qn) {
-            const int32_t u = queue[qi];
-            s = __ldg(rowptr + u);
-            e = __ldg(rowptr + u + 1);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x + (threadIdx.x & ~31); base < total; base += stride) {
+        const int64_t e = base + lane;
+        bool claimed = false;
+        int32_t v = 0;
+        if (e < total) {
+            int32_t lo = 0, hi = qn;  // last i with pre[i] <= e
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (__ldg(pre + mid) <= e) lo = mid; else hi = mid;
+            }
+            const int32_t u = __ldg(queue + lo);
+            v = __ldg(colidx + __ldg(rowptr + u) + (e - __ldg(pre + lo)));
+            const uint32_t bit = 1u << (v & 31);
+            if (!(visited[v >> 5] & bit)) {
+                const uint32_t old = atomicOr(visited + (v >> 5), bit);
+                claimed = !(old & bit);
+            }
         }
-        // rows of 32+ edges: the whole warp, one row at a time
-        unsigned wm = __ballot_sync(0xffffffffu, e - s >= 32);
-        int32_t ls = s, le = (e - s >= 32) ? s : e;  // this lane's own (short) range
-        for (;;) {
-            int32_t i0, i1, stride;
-            bool own = false;
-            if (wm) {
-                const int l = __ffs(wm) - 1;
-                wm &= wm - 1;
-                i0 = __shfl_sync(0xffffffffu, s, l) + lane;
-                i1 = __shfl_sync(0xffffffffu, e, l);
-                stride = 32;
-            } else {
-                i0 = ls;
-                i1 = le;
-                stride = 1;
-                own = true;
+        const unsigned cm = __ballot_sync(0xffffffffu, claimed);
+        if (cm) {
+            int32_t pos0 = 0;
+            if (lane == __ffs(cm) - 1) pos0 = (int32_t)atomicAdd(count, (unsigned long long)__popc(cm));
+            pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(cm) - 1);
+            unsigned long long dg = 0;
+            if (claimed) {
+                level[v] = new_level;
+                atomicOr(next + (v >> 5), 1u << (v & 31));
+                next_queue[pos0 + __popc(cm & ((1u << lane) - 1u))] = v;
+                dg = (unsigned long long)(__ldg(rowptr + v + 1) - __ldg(rowptr + v));
             }
-            // uniform trip count over the warp so that ballots stay converged
-            int32_t trips = (i1 - i0 + stride - 1) / stride;
-            if (trips < 0) trips = 0;
-            int32_t maxtrips = trips;
 #pragma unroll
-            for (int d = 16; d > 0; d >>= 1) maxtrips = max(maxtrips, __shfl_xor_sync(0xffffffffu, maxtrips, d));
-            for (int32_t t = 0; t < maxtrips; ++t) {
-                bool claimed = false;
-                int32_t v = 0;
-                if (t < trips) {
-                    v = __ldg(colidx + i0 + t * stride);
-                    const uint32_t bit = 1u << (v & 31);
-                    if (!(visited[v >> 5] & bit)) {
-                        const uint32_t old = atomicOr(visited + (v >> 5), bit);
-                        claimed = !(old & bit);
-                    }
-                }
-                const unsigned cm = __ballot_sync(0xffffffffu, claimed);
-                if (cm) {
-                    int32_t pos0 = 0;
-                    if (lane == __ffs(cm) - 1) pos0 = (int32_t)atomicAdd(count, (unsigned long long)__popc(cm));
-                    pos0 = __shfl_sync(0xffffffffu, pos0, __ffs(cm) - 1);
-                    if (claimed) {
-                        level[v] = new_level;
-                        atomicOr(next + (v >> 5), 1u << (v & 31));
-                        next_queue[pos0 + __popc(cm & ((1u << lane) - 1u))] = v;
-                    }
-                }
-            }
-            if (own) break;
+            for (int d = 16; d > 0; d >>= 1) dg += __shfl_xor_sync(0xffffffffu, dg, d);
+            if (lane == 0 && dg) atomicAdd(count + 1, dg);
         }
     }
 }
@@ -323,24 +322,49 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
     int32_t *q[2] = {nullptr, nullptr};
     if (can_push) {
         TC_TRY(queues.alloc((size_t)2 * V * 4 + 64));
-        TC_TRY(qcnt.alloc((size_t)nwords * 4 + 64));
-        TC_TRY(qpos.alloc((size_t)nwords * 8 + 64));
+        const size_t cap = (size_t)(V > nwords ? V : nwords) + 16;
+        TC_TRY(qcnt.alloc(cap * 4));
+        TC_TRY(qpos.alloc(cap * 8));
         q[0] = queues.as<int32_t>();
         q[1] = q[0] + V;
         TC_CUDA(cudaMemcpyAsync(q[0], &source, 4, cudaMemcpyHostToDevice, s));
     }
     bool have_queue = can_push;  // the queue q[lvl & 1] holds the current frontier
     unsigned long long front_count = 1, *h_cnt = nullptr;
-    TC_CUDA(cudaMallocHost(&h_cnt, 8));
-    int lvl = 0, tocab_levels = 0;
+    TC_CUDA(cudaMallocHost(&h_cnt, 16));
+    // direction switching (Beamer et al.): edges out of the frontier (m_f) against edges out of
+    // unvisited vertices (m_u); push -> pull when m_f > m_u / 14, pull -> push when the
+    // frontier holds fewer than push_threshold * V vertices
+    int32_t sdeg[2] = {0, 0};
+    TC_CUDA(cudaMemcpyAsync(sdeg, g->out_rowptr.as<int32_t>() + source, 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    double m_f = (double)(sdeg[1] - sdeg[0]);
+    double m_u = (double)g->E - m_f;
+    bool pushing = can_push;
+    int lvl = 0, tocab_levels = 0, push_levels = 0;
     int st = TC_OK;
+    cudaEvent_t lev[2] = {nullptr, nullptr};
+    if (bp->profile && stats) {
+        TC_CUDA(cudaEventCreate(&lev[0]));
+        TC_CUDA(cudaEventCreate(&lev[1]));
+    }
     const size_t merge_smem = part ? (size_t)(part->k / 32) * 4 : 0;
     while (front_count > 0) {
         uint32_t *front = bufs[lvl & 1], *next = bufs[(lvl + 1) & 1];
-        if (cudaMemsetAsync(cnt, 0, 8, s) != cudaSuccess) { st = fail(TC_ERR_CUDA, "memset failed"); break; }
-        const bool use_push = can_push && (double)front_count <= (double)bp->push_threshold * (double)V;
+        if (cudaMemsetAsync(cnt, 0, 16, s) != cudaSuccess) { st = fail(TC_ERR_CUDA, "memset failed"); break; }
+        if (can_push) {
+            if (pushing && m_f > m_u / 14.0) pushing = false;
+            else if (!pushing && (double)front_count < (double)bp->push_threshold * (double)V) pushing = true;
+        }
+        const bool use_push = can_push && pushing;
         const bool use_tocab = !use_push && part && bp->tocab_threshold >= 0.0f &&
                                (double)front_count > (double)bp->tocab_threshold * (double)V;
+        if (stats && lvl < TC_BFS_TRACE) {
+            stats->level_kind[lvl] = use_push ? 2 : (use_tocab ? 1 : 0);
+            stats->level_frontier[lvl] = (int64_t)front_count;
+        }
+        if (lev[0]) cudaEventRecord(lev[0], s);
+        push_levels += use_push ? 1 : 0;
         if (use_push) {
             if (!have_queue) {  // frontier came from a pull level: bitmap -> queue
                 k_bitmap_count<<<grid, BFS_THREADS, 0, s>>>(front, nwords, qcnt.as<int32_t>());
@@ -350,9 +374,18 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
                 k_bitmap_queue<<<grid, BFS_THREADS, 0, s>>>(front, nwords, qpos.as<int64_t>(), q[lvl & 1]);
             }
             if (cudaMemsetAsync(next, 0, (size_t)nwords * 4, s) != cudaSuccess) { st = fail(TC_ERR_CUDA, "memset failed"); break; }
-            k_bfs_push_level<<<grid, BFS_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(),
-                                                          q[lvl & 1], (int32_t)front_count, visited, next, level,
-                                                          lvl + 1, q[(lvl + 1) & 1], cnt);
+            // out-degree prefix of the queue: frontier edges m_f are already known on the host
+            const int32_t qn = (int32_t)front_count;
+            k_push_degrees<<<grid, BFS_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), q[lvl & 1], qn,
+                                                        qcnt.as<int32_t>());
+            if (cudaGetLastError() != cudaSuccess) { st = fail(TC_ERR_CUDA, "launch failed"); break; }
+            st = scan_i32_to_i64(qcnt.as<int32_t>(), qn, qpos.as<int64_t>(), s);
+            if (st != TC_OK) break;
+            const int64_t total = (int64_t)(m_f + 0.5);
+            if (total > 0)
+                k_bfs_push_edges<<<grid, BFS_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(),
+                                                              q[lvl & 1], qn, qpos.as<int64_t>(), total, visited, next,
+                                                              level, lvl + 1, q[(lvl + 1) & 1], cnt);
             have_queue = true;
         } else if (use_tocab) {
             k_bfs_block_level<<<grid, BFS_THREADS, 0, s>>>(part->rowptr.as<int32_t>(), part->colidx.as<int32_t>(),
@@ -362,20 +395,30 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
                                                                        part->id_map.as<int32_t>(),
                                                                        part->merge_off.as<int32_t>(), part->B,
                                                                        part->nranges, part->k, V, nwords, next,
-                                                                       visited, level, lvl + 1, cnt);
+                                                                       visited, level, lvl + 1, cnt,
+                                                                       g->out_rowptr.as<int32_t>());
             ++tocab_levels;
             have_queue = false;
         } else {
             k_bfs_pull_level<<<grid, BFS_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), V,
-                                                          nwords, front, next, visited, level, lvl + 1, cnt);
+                                                          nwords, front, next, visited, level, lvl + 1, cnt,
+                                                          g->out_rowptr.as<int32_t>());
             have_queue = false;
         }
+        if (lev[1]) cudaEventRecord(lev[1], s);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, cnt, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt, cnt, 16, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) { st = fail(TC_ERR_CUDA, "bfs level %d: %s", lvl, cudaGetErrorString(e)); break; }
-        front_count = *h_cnt;
+        front_count = h_cnt[0];
+        m_f = (double)h_cnt[1];
+        m_u -= m_f;
+        if (lev[1] && lvl < TC_BFS_TRACE) cudaEventElapsedTime(&stats->level_ms[lvl], lev[0], lev[1]);
         ++lvl;
+    }
+    if (lev[0]) {
+        cudaEventDestroy(lev[0]);
+        cudaEventDestroy(lev[1]);
     }
     cudaFreeHost(h_cnt);
     TC_TRY(st);
@@ -395,6 +438,7 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
         TC_CUDA(cudaStreamSynchronize(s));
         stats->levels = lvl;
         stats->tocab_levels = tocab_levels;
+        stats->push_levels = push_levels;
         stats->reached = (int64_t)hs[0];
         stats->edges_reached = (int64_t)hs[1];
         stats->ms_total = ms_total;

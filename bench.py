@@ -344,7 +344,16 @@ def batch_variants(args, stream):
                         "ms": round(ms, 2), "ms_per_iter": round(ms / ITERS, 3),
                         "edge_columns_per_s_G": round(g22.E * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
                         "gteps_equiv": round(g22.E * ITERS / (ms * 1e-3) / 1e9, 3)}
-    del R, G22, g22
+    # TOCAB per 32-column tile: source blocks whose 128-byte row segments fit in L2
+    P22 = T.tocab_partition(G22, T.TC_PULL, 0, l2_fraction=1.0 / 88, merge_range=256)
+    T.ppr_batch(G22, srcs, iters=ITERS, out=R, part=P22)
+    torch.cuda.synchronize()
+    ms = statistics.median(time_runs(lambda: T.ppr_batch(G22, srcs, iters=ITERS, out=R, part=P22), 3, stream))
+    res["ppr_batch_tocab"] = {"blocks": P22.num_blocks, "block_width": P22.block_width, "ms": round(ms, 2),
+                              "ms_per_iter": round(ms / ITERS, 3),
+                              "edge_columns_per_s_G": round(g22.E * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
+                              "gteps_equiv": round(g22.E * ITERS / (ms * 1e-3) / 1e9, 3)}
+    del R, G22, g22, P22
     torch.cuda.empty_cache()
     scales = gg.batch_scales(1000, 10, 16, seed=19)
     gb, off = gg.rmat_batch(scales, seed=19, device="cuda")

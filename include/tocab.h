@@ -272,9 +272,14 @@ int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
  * to its source s_j, starting from e_{s_j}:
  *   R'[v,j] = d * sum_{u->v} R[u,j] / out_degree[u] + [v == s_j] ((1-d) + d * D_j),
  *   D_j = sum of R[u,j] over dangling u.
- * The batch lives as an FP32 [V x n] row-major matrix; every iteration is one pull launch in
- * which a warp reads whole rows of the contribution matrix.  The whole batch is
- * one launch per iteration.
+ * The batch lives as an FP32 [V x n] row-major matrix.
+ *   part == NULL : every iteration is one pull launch in which a warp reads whole rows of the
+ *                  contribution matrix (one launch for the whole batch per iteration).
+ *   part != NULL : TOCAB per column tile (Sec. 3.1): columns in tiles of 32; for each tile,
+ *                  Alg. 4 over the partition's source blocks (size them so that W x 128 bytes
+ *                  of a block's row segments fit in L2, e.g. l2_fraction = 1/88) into 32-wide
+ *                  partial rows, then the Fig. 5 merge (blocks added in order; deterministic)
+ *                  with the update.  The partition's merge_range k must be <= 1600 (256 advised).
  *   sources : host int32[n], each in [0, V) (repeats allowed);  1 <= n <= 1024.
  *   params  : damping, iters, out_mem (R_out space), profile (stats->ms_total); init ignored.
  *   R_out   : float[V * n], R_out[v*n + j].
@@ -282,8 +287,8 @@ int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
  * Synchronises the stream before returning.
  * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED (n out of range), TC_ERR_OOM, TC_ERR_CUDA.
  */
-int tc_ppr_batch(const tc_graph *g, const int32_t *sources, int32_t n, const tc_pr_params *params,
-                 float *R_out, tc_pr_stats *stats, void *stream);
+int tc_ppr_batch(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t n,
+                 const tc_pr_params *params, float *R_out, tc_pr_stats *stats, void *stream);
 
 /* ---- many small graphs in one batch ---------------------------------------------------------- */
 typedef struct tc_multigraph tc_multigraph;   /* opaque: a batch of independent graphs */

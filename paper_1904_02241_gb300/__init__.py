@@ -234,8 +234,9 @@ def pagerank_push(graph: Graph, part: Partition | None = None, damping: float = 
 
 
 def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out: torch.Tensor | None = None,
-              profile: bool = False, stream=None, return_stats: bool = False):
-    """tc_ppr_batch: personalised PageRank, one column per source -> [V, n] float32."""
+              profile: bool = False, stream=None, return_stats: bool = False, part: Partition | None = None):
+    """tc_ppr_batch: personalised PageRank, one column per source -> [V, n] float32.
+    part: a TC_PULL partition for the column-tiled TOCAB form (merge_range <= 256 advised)."""
     src = torch.as_tensor(sources, dtype=torch.int32).contiguous().cpu()
     n = src.numel()
     if out is None:
@@ -244,8 +245,8 @@ def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out
         raise ValueError("out must be a contiguous float32 tensor with V*n elements")
     pp = L.tc_pr_params(float(damping), int(iters), 0, _mem(out), None, 1 if profile else 0, 0, 0)
     st = L.tc_pr_stats()
-    _check(L.load().tc_ppr_batch(graph.handle, src.data_ptr(), n, C.byref(pp), out.data_ptr(), C.byref(st),
-                                 _stream(stream)), "tc_ppr_batch")
+    _check(L.load().tc_ppr_batch(graph.handle, part.handle if part is not None else None, src.data_ptr(), n,
+                                 C.byref(pp), out.data_ptr(), C.byref(st), _stream(stream)), "tc_ppr_batch")
     return (out, st) if return_stats else out
 
 

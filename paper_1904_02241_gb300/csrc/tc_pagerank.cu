@@ -264,6 +264,26 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
     grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
 }
 
+// Exact fixed point of x (an FP32 value already scaled by a power of two, |x| < 2^47) with
+// integer operations only: x = sign * m * 2^(e-150) (m the 24-bit significand), shifted to an
+// integer (rounded half up below 1) and split as v = hi * 2^32 + mid * 2^16 + lo (two's
+// complement; mid, lo in [0, 2^16)).  No FP64 and no 64-bit float conversion: on GB300 those
+// run on the slow FP64 pipe.
+__device__ __forceinline__ void fx_split(float x, int32_t &hi, uint32_t &mid, uint32_t &lo) {
+    const uint32_t b = __float_as_uint(x);
+    const int32_t e = (int32_t)((b >> 23) & 0xFFu);
+    const uint32_t m = (b & 0x7FFFFFu) | (e ? 0x800000u : 0u);
+    const int32_t sh = (e ? e : 1) - 150;  // exponent of the significand's last bit
+    uint64_t v;
+    if (sh >= 0) v = (uint64_t)m << sh;
+    else if (sh > -25) v = (uint64_t)((m + (1u << (-sh - 1))) >> (-sh));
+    else v = 0;
+    const int64_t sv = (b >> 31) ? -(int64_t)v : (int64_t)v;
+    hi = (int32_t)(sv >> 32);
+    mid = (uint32_t)(sv >> 16) & 0xFFFFu;
+    lo = (uint32_t)sv & 0xFFFFu;
+}
+
 // Same slices and chunks as k_pull_merge_ordered, but one shared accumulator per CTA updated
 // with shared-memory atomics.  FIXED: each partial becomes a 64-bit fixed-point integer v
 // (scale 2^48 / max(1, mass), so no vertex sum exceeds 2^48) split as
@@ -380,10 +400,12 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
         for (int q = 0; q < MG_UNROLL; ++q) {
             if (idq[q] >= 0) {
                 if (FIXED) {
-                    const long long v = __float2ll_rn(vq[q] * scalef);
-                    atomicAdd(acc_hi + idq[q], (int32_t)(v >> 32));
-                    atomicAdd(acc_mid + idq[q], (uint32_t)((v >> 16) & 0xFFFF));
-                    atomicAdd(acc_lo + idq[q], (uint32_t)(v & 0xFFFF));
+                    int32_t h;
+                    uint32_t md, lw;
+                    fx_split(vq[q] * scalef, h, md, lw);
+                    if (h) atomicAdd(acc_hi + idq[q], h);
+                    if (md) atomicAdd(acc_mid + idq[q], md);
+                    atomicAdd(acc_lo + idq[q], lw);
                 } else {
                     atomicAdd(acc32 + idq[q], vq[q]);
                 }

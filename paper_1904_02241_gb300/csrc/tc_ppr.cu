@@ -121,6 +121,88 @@ __global__ void k_ppr_init(float *C, int32_t NP, const int32_t *src_of_col, cons
     }
 }
 
+// ---------------------------------------------------------------------------------------------
+// TOCAB form of the batch (Sec. 3.1 applied to a column tile): the n columns are processed in
+// tiles of 32; for tile t the contribution matrix is read as 128-byte row segments C[u, 32t..]
+// and the pull partition's source blocks are sized so that one block's segments stay in L2.
+// Alg. 4 per block writes 32-wide partial rows; the merge of Fig. 5 (CTA per vertex range, the
+// blocks added in block order - deterministic) applies the update for the tile's columns.
+// ---------------------------------------------------------------------------------------------
+constexpr int PT_THREADS = 256;
+constexpr int PT_WARPS = PT_THREADS / 32;
+
+__global__ void __launch_bounds__(PT_THREADS) k_ppr_tile_gather(const int32_t *__restrict__ rowptr,
+                                                                const int32_t *__restrict__ colidx, int64_t R,
+                                                                const float *__restrict__ C, int32_t NP, int32_t t,
+                                                                float *__restrict__ P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * PT_WARPS;
+    const float *Ct = C + 32 * t + lane;
+    for (int64_t r = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); r < R; r += nw) {
+        const int32_t s = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+        int32_t i = s;
+        for (; i + 3 < e; i += 4) {  // four 128-byte segments in flight
+            const int64_t u0 = __ldg(colidx + i), u1 = __ldg(colidx + i + 1), u2 = __ldg(colidx + i + 2),
+                          u3 = __ldg(colidx + i + 3);
+            a0 += __ldg(Ct + u0 * NP);
+            a1 += __ldg(Ct + u1 * NP);
+            a2 += __ldg(Ct + u2 * NP);
+            a3 += __ldg(Ct + u3 * NP);
+        }
+        for (; i < e; ++i) a0 += __ldg(Ct + (int64_t)__ldg(colidx + i) * NP);
+        P[r * 32 + lane] = (a0 + a1) + (a2 + a3);
+    }
+}
+
+__global__ void __launch_bounds__(PT_THREADS) k_ppr_tile_merge(const float *__restrict__ P,
+                                                               const int32_t *__restrict__ id_map,
+                                                               const int32_t *__restrict__ merge_off, int32_t B,
+                                                               int32_t nranges, int32_t k, int32_t V, int32_t NP,
+                                                               int32_t t, const int32_t *__restrict__ src_of_col,
+                                                               const unsigned long long *__restrict__ Dcur,
+                                                               unsigned long long *Dnext, unsigned long long *Dzero,
+                                                               const float *__restrict__ inv_outdeg, float damping,
+                                                               float *Cn, float *R_out, int32_t n) {
+    extern __shared__ float pacc[];  // [k][32]
+    __shared__ float dsh[PT_WARPS][32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int32_t j = blockIdx.x;
+    const int32_t vbase = j * k;
+    if (blockIdx.x == 0 && t == 0)
+        for (int q = threadIdx.x; q < NP; q += PT_THREADS) Dzero[q] = 0ull;
+    for (int q = threadIdx.x; q < k * 32; q += PT_THREADS) pacc[q] = 0.0f;
+    __syncthreads();
+    for (int32_t b = 0; b < B; ++b) {  // blocks in order: every vertex's sum has a fixed order
+        const int32_t *o = merge_off + (int64_t)b * (nranges + 1) + j;
+        const int32_t r0 = __ldg(o), r1 = __ldg(o + 1);
+        for (int32_t r = r0 + warp; r < r1; r += PT_WARPS)
+            pacc[(__ldg(id_map + r) - vbase) * 32 + lane] += __ldg(P + (int64_t)r * 32 + lane);
+        __syncthreads();
+    }
+    const int32_t col = 32 * t + lane;
+    const int32_t s = src_of_col[col];
+    const float tele = (1.0f - damping) + damping * (float)((double)Dcur[col] / PPR_FX);
+    float dl = 0.0f;
+    for (int32_t q = warp; q < k; q += PT_WARPS) {
+        const int32_t v = vbase + q;
+        if (v >= V) break;
+        const float r = damping * pacc[q * 32 + lane] + (s == v ? tele : 0.0f);
+        const float inv = __ldg(inv_outdeg + v);
+        Cn[(int64_t)v * NP + col] = r * inv;
+        if (R_out && col < n) R_out[(int64_t)v * n + col] = r;
+        if (inv == 0.0f) dl += r;
+    }
+    dsh[warp][lane] = dl;
+    __syncthreads();
+    if (warp == 0) {
+        float tot = 0.0f;
+#pragma unroll
+        for (int w = 0; w < PT_WARPS; ++w) tot += dsh[w][lane];
+        if (tot != 0.0f) atomicAdd(Dnext + col, (unsigned long long)__double2ll_rn((double)tot * PPR_FX));
+    }
+}
+
 template <int NV4>
 static void launch_ppr(int grid, cudaStream_t s, const tc_graph *g, const float *C, float *Cn, const int32_t *srcc,
                        const unsigned long long *Dc, unsigned long long *Dn, unsigned long long *Dz, float d,
@@ -130,8 +212,8 @@ static void launch_ppr(int grid, cudaStream_t s, const tc_graph *g, const float 
                                                   srcc, Dc, Dn, Dz, g->inv_outdeg.as<float>(), d, R_out, n);
 }
 
-static int ppr_impl(const tc_graph *cg, const int32_t *sources, int32_t n, const tc_pr_params *pp, float *R_out,
-                    tc_pr_stats *stats, cudaStream_t s) {
+static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sources, int32_t n,
+                    const tc_pr_params *pp, float *R_out, tc_pr_stats *stats, cudaStream_t s) {
     tc_graph *g = const_cast<tc_graph *>(cg);
     const int32_t V = g->V;
     int NV4 = 1;
@@ -179,7 +261,36 @@ static int ppr_impl(const tc_graph *cg, const int32_t *sources, int32_t n, const
     TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kf, PPR_THREADS, 0));
     const int grid = caps.sms * (per_sm > 0 ? per_sm : 1);
     int launches = 1;
-    for (int it = 0; it < pp->iters; ++it) {
+    const int32_t ntiles = NP / 32;
+    DevBuf Pbuf;
+    size_t tm_smem = 0;
+    int tg_grid = 1;
+    if (part) {
+        TC_TRY(Pbuf.alloc((size_t)(part->R > 0 ? part->R : 1) * 32 * 4));
+        tm_smem = (size_t)part->k * 32 * 4;
+        if (tm_smem > 48 * 1024)
+            TC_CUDA(cudaFuncSetAttribute(k_ppr_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tm_smem));
+        int ps = 1;
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_ppr_tile_gather, PT_THREADS, 0));
+        tg_grid = caps.sms * (ps > 0 ? ps : 1);
+    }
+    for (int it = 0; it < pp->iters && part; ++it) {
+        const bool last = it == pp->iters - 1;
+        const float *Cc = Cm[it & 1];
+        float *Cn = Cm[(it + 1) & 1];
+        unsigned long long *Dc = D[it % 3], *Dn = D[(it + 1) % 3], *Dz = D[(it + 2) % 3];
+        for (int32_t t = 0; t < ntiles; ++t) {
+            k_ppr_tile_gather<<<tg_grid, PT_THREADS, 0, s>>>(part->rowptr.as<int32_t>(), part->colidx.as<int32_t>(),
+                                                             part->R, Cc, NP, t, Pbuf.as<float>());
+            k_ppr_tile_merge<<<part->nranges, PT_THREADS, tm_smem, s>>>(
+                Pbuf.as<float>(), part->id_map.as<int32_t>(), part->merge_off.as<int32_t>(), part->B, part->nranges,
+                part->k, g->V, NP, t, srcbuf.as<int32_t>(), Dc, Dn, Dz, g->inv_outdeg.as<float>(), pp->damping,
+                Cn, last ? Rd : nullptr, n);
+            TC_LAUNCH_CHECK();
+            launches += 2;
+        }
+    }
+    for (int it = 0; it < pp->iters && !part; ++it) {
         const bool last = it == pp->iters - 1;
         float *Rw = last ? Rd : nullptr;
         const float *Cc = Cm[it & 1];
@@ -218,10 +329,14 @@ static int ppr_impl(const tc_graph *cg, const int32_t *sources, int32_t n, const
 
 }  // namespace tc
 
-extern "C" int tc_ppr_batch(const tc_graph *g, const int32_t *sources, int32_t n, const tc_pr_params *params,
-                            float *R_out, tc_pr_stats *stats, void *stream) {
+extern "C" int tc_ppr_batch(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t n,
+                            const tc_pr_params *params, float *R_out, tc_pr_stats *stats, void *stream) {
     using namespace tc;
     if (!g || !sources || !params || !R_out) return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: null argument");
+    if (part && (part->g != g || part->dir != TC_PULL))
+        return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: partition must be a TC_PULL partition of this graph");
+    if (part && (size_t)part->k * 32 * 4 > 200 * 1024)
+        return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: the partition's merge_range must be <= 1600 (<= 256 advised)");
     if (n < 1 || n > 1024) return fail(TC_ERR_UNSUPPORTED, "tc_ppr_batch: n must be in [1, 1024]");
     if (!(params->damping >= 0.0f && params->damping <= 1.0f) || params->iters < 0)
         return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: damping outside [0,1] or iters < 0");
@@ -231,5 +346,5 @@ extern "C" int tc_ppr_batch(const tc_graph *g, const int32_t *sources, int32_t n
         if (sources[j] < 0 || sources[j] >= g->V) return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: source %d outside [0, V)", j);
     if ((int64_t)g->V * ((n + 127) / 128 * 128) * 8 > ((int64_t)1 << 40))
         return fail(TC_ERR_UNSUPPORTED, "tc_ppr_batch: V x n too large");
-    return ppr_impl(g, sources, n, params, R_out, stats, (cudaStream_t)stream);
+    return ppr_impl(g, part, sources, n, params, R_out, stats, (cudaStream_t)stream);
 }

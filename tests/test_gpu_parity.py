@@ -430,3 +430,19 @@ def test_bfs_direction_optimised_bit_exact(T, name, push, tocab):
         want = oracle.bfs(g.V, rp, ci, s)
         np.testing.assert_array_equal(lv.cpu().numpy(), want)
         assert st.reached == int((want >= 0).sum())
+
+
+@pytest.mark.parametrize("name,n,B", [("rmat12", 256, 3), ("rmat12", 40, 1), ("er", 130, 7), ("plc", 64, 4),
+                                      ("grid", 33, 2)])
+def test_ppr_batch_tocab_parity(T, name, n, B):
+    g = GRAPHS[name]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B, merge_range=256)
+    rng = np.random.default_rng(n + B)
+    srcs = rng.integers(0, g.V, n).astype(np.int32)
+    R = T.ppr_batch(G, srcs, iters=20, part=P).cpu().numpy()
+    rp, ci = g.numpy()
+    want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
+    for j in range(n):
+        assert l1_rel(R[:, j], want[:, j]) <= TOL, j
+    assert np.array_equal(R, T.ppr_batch(G, srcs, iters=20, part=P).cpu().numpy())  # deterministic

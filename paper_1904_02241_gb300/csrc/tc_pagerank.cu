@@ -414,15 +414,18 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
     }
     __syncthreads();
     const float spread = spread_of(u);
-    const double inv_scale = 1.0 / scale;
+    const float inv_scalef = (float)(1.0 / scale);  // a power of two
     float dsum = 0.0f;
     for (int t = tid; t < k; t += MG_THREADS) {
         const int32_t v = vbase + t;
         if (v >= u.V) break;
         float sum;
         if (FIXED) {
+            // exact 64-bit total, converted with 32-bit integer-to-float steps (no FP64)
             const long long tot = ((long long)acc_hi[t] << 32) + ((long long)acc_mid[t] << 16) + (long long)acc_lo[t];
-            sum = (float)((double)tot * inv_scale);
+            const float th = (float)(int32_t)(tot >> 24);            // |tot| < 2^56
+            const float tl = (float)(uint32_t)(tot & 0xFFFFFFll);     // < 2^24, exact
+            sum = fmaf(th, 16777216.0f, tl) * inv_scalef;
         } else {
             sum = acc32[t];
         }

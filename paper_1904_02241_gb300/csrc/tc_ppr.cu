@@ -10,9 +10,86 @@
 
 namespace tc {
 
+// Compensated (Kahan) addition of y into (sum, c).  A column of a personalised batch often sums
+// thousands of nearly equal small contributions next to one large one; plain sequential FP32
+// addition then rounds the same way every time and drifts.
+__device__ __forceinline__ void kahan_add(float &sum, float &c, float y) {
+    const float yc = y - c;
+    const float t = sum + yc;
+    c = (t - sum) - yc;
+    sum = t;
+}
+
+__device__ __forceinline__ void kahan_add4(float4 &sum, float4 &c, float4 y) {
+    kahan_add(sum.x, c.x, y.x);
+    kahan_add(sum.y, c.y, y.y);
+    kahan_add(sum.z, c.z, y.z);
+    kahan_add(sum.w, c.w, y.w);
+}
+
+__device__ __forceinline__ float4 add4(float4 a, float4 b) { return make_float4(a.x + b.x, a.y + b.y, a.z + b.z, a.w + b.w); }
+
 constexpr int PPR_THREADS = 256;
 constexpr int PPR_WARPS = PPR_THREADS / 32;
 constexpr double PPR_FX = 2305843009213693952.0;  // 2^61: every column has L1 mass <= 1
+
+// Rows with more than PPR_PIECE in-edges are cut into pieces of PPR_PIECE edges, each summed by
+// its own warp into a partial row (k_ppr_piece), and finished by k_ppr_fix, which adds the
+// pieces of a row in order: a hub no longer serialises a whole iteration on one warp.
+constexpr int PPR_PIECE = 2048;
+
+template <int NV4>
+__device__ __forceinline__ void ppr_row_sum(const int32_t *__restrict__ colidx, int32_t s, int32_t e,
+                                            const float4 *__restrict__ C, int lane, float4 *acc) {
+    constexpr int NP = 128 * NV4;
+    constexpr int U = NV4 <= 2 ? 4 : 2;  // rows in flight (a power of two)
+    float4 comp[NV4];
+#pragma unroll
+    for (int q = 0; q < NV4; ++q) comp[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int32_t i = s;
+    for (; i + U - 1 < e; i += U) {
+        int64_t u[U];
+#pragma unroll
+        for (int k2 = 0; k2 < U; ++k2) u[k2] = __ldg(colidx + i + k2);
+        float4 x[U][NV4];
+#pragma unroll
+        for (int k2 = 0; k2 < U; ++k2)
+#pragma unroll
+            for (int q = 0; q < NV4; ++q) x[k2][q] = __ldg(C + u[k2] * (NP / 4) + 32 * q + lane);
+#pragma unroll
+        for (int q = 0; q < NV4; ++q) {  // tree sum of the group, then one compensated add
+            float4 gsum = add4(x[0][q], x[1][q]);
+            if (U == 4) gsum = add4(gsum, add4(x[2][q], x[3][q]));
+            kahan_add4(acc[q], comp[q], gsum);
+        }
+    }
+    for (; i < e; ++i) {
+        const int64_t u0 = __ldg(colidx + i);
+#pragma unroll
+        for (int q = 0; q < NV4; ++q) kahan_add4(acc[q], comp[q], __ldg(C + u0 * (NP / 4) + 32 * q + lane));
+    }
+}
+
+// pieces: (row, first edge) pairs; piece p covers [first, min(first + PPR_PIECE, row end))
+template <int NV4>
+__global__ void __launch_bounds__(PPR_THREADS) k_ppr_piece(const int32_t *__restrict__ rowptr,
+                                                           const int32_t *__restrict__ colidx,
+                                                           const int2 *__restrict__ pieces, int32_t npieces,
+                                                           const float4 *__restrict__ C, float4 *__restrict__ Ppc) {
+    constexpr int NP = 128 * NV4;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * PPR_WARPS;
+    for (int64_t p = (int64_t)blockIdx.x * PPR_WARPS + (threadIdx.x >> 5); p < npieces; p += nw) {
+        const int2 pc = pieces[p];
+        const int32_t e = min(pc.y + PPR_PIECE, __ldg(rowptr + pc.x + 1));
+        float4 acc[NV4];
+#pragma unroll
+        for (int q = 0; q < NV4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        ppr_row_sum<NV4>(colidx, pc.y, e, C, lane, acc);
+#pragma unroll
+        for (int q = 0; q < NV4; ++q) Ppc[p * (NP / 4) + 32 * q + lane] = acc[q];
+    }
+}
 
 template <int NV4>  // float4 per lane; columns in the padded batch = 128 * NV4
 __global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__restrict__ rowptr,
@@ -22,7 +99,10 @@ __global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__res
                                                             const unsigned long long *__restrict__ Dcur,
                                                             unsigned long long *Dnext, unsigned long long *Dzero,
                                                             const float *__restrict__ inv_outdeg, float damping,
-                                                            float *R_out, int32_t n) {
+                                                            float *R_out, int32_t n,
+                                                            const int32_t *__restrict__ hub_rows,
+                                                            const int32_t *__restrict__ hub_piece0, int32_t nhubs,
+                                                            const float4 *__restrict__ Ppc) {
     constexpr int NP = 128 * NV4;
     __shared__ float dsh[PPR_WARPS][NP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -41,38 +121,29 @@ __global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__res
             dl[q][c] = 0.0f;
         }
     const int64_t nw = (int64_t)gridDim.x * PPR_WARPS;
-    for (int64_t v = (int64_t)blockIdx.x * PPR_WARPS + warp; v < V; v += nw) {
+    // the hub rows (finished from their pieces) come first, then every other row
+    for (int64_t w = (int64_t)blockIdx.x * PPR_WARPS + warp; w < (int64_t)V + nhubs; w += nw) {
         float4 acc[NV4];
 #pragma unroll
         for (int q = 0; q < NV4; ++q) acc[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-        const int32_t s = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
-        int32_t i = s;
-        for (; i + 1 < e; i += 2) {  // two rows in flight
-            const int64_t u0 = __ldg(colidx + i), u1 = __ldg(colidx + i + 1);
-            float4 x0[NV4], x1[NV4];
+        int64_t v;
+        if (w < nhubs) {
+            v = hub_rows[w];
+            const int32_t p0 = hub_piece0[w], p1 = hub_piece0[w + 1];
+            for (int32_t p = p0; p < p1; ++p)  // pieces in order
 #pragma unroll
-            for (int q = 0; q < NV4; ++q) {
-                x0[q] = __ldg(C + u0 * (NP / 4) + 32 * q + lane);
-                x1[q] = __ldg(C + u1 * (NP / 4) + 32 * q + lane);
-            }
-#pragma unroll
-            for (int q = 0; q < NV4; ++q) {
-                acc[q].x += x0[q].x + x1[q].x;
-                acc[q].y += x0[q].y + x1[q].y;
-                acc[q].z += x0[q].z + x1[q].z;
-                acc[q].w += x0[q].w + x1[q].w;
-            }
-        }
-        if (i < e) {
-            const int64_t u0 = __ldg(colidx + i);
-#pragma unroll
-            for (int q = 0; q < NV4; ++q) {
-                const float4 x = __ldg(C + u0 * (NP / 4) + 32 * q + lane);
-                acc[q].x += x.x;
-                acc[q].y += x.y;
-                acc[q].z += x.z;
-                acc[q].w += x.w;
-            }
+                for (int q = 0; q < NV4; ++q) {
+                    const float4 x = Ppc[(int64_t)p * (NP / 4) + 32 * q + lane];
+                    acc[q].x += x.x;
+                    acc[q].y += x.y;
+                    acc[q].z += x.z;
+                    acc[q].w += x.w;
+                }
+        } else {
+            v = w - nhubs;
+            const int32_t s = __ldg(rowptr + v), e = __ldg(rowptr + v + 1);
+            if (e - s > PPR_PIECE) continue;  // a hub: done above
+            ppr_row_sum<NV4>(colidx, s, e, C, lane, acc);
         }
         const float inv = __ldg(inv_outdeg + v);
 #pragma unroll
@@ -131,27 +202,80 @@ __global__ void k_ppr_init(float *C, int32_t NP, const int32_t *src_of_col, cons
 constexpr int PT_THREADS = 256;
 constexpr int PT_WARPS = PT_THREADS / 32;
 
+constexpr int PT_PIECE = 1024;  // local rows above this many edges are cut into pieces
+
+// Edges [s, e) of one row, tile t: 8 lanes (sub) each summing one float4 of the 32 columns.
+__device__ __forceinline__ float4 tile_row_sum(const int32_t *__restrict__ colidx, int32_t s, int32_t e,
+                                               const float4 *__restrict__ Ct, int64_t NP4) {
+    float4 a = make_float4(0.f, 0.f, 0.f, 0.f), c = a;
+    int32_t i = s;
+    for (; i + 3 < e; i += 4) {
+        const int64_t u0 = __ldg(colidx + i), u1 = __ldg(colidx + i + 1), u2 = __ldg(colidx + i + 2),
+                      u3 = __ldg(colidx + i + 3);
+        const float4 x0 = __ldg(Ct + u0 * NP4), x1 = __ldg(Ct + u1 * NP4), x2 = __ldg(Ct + u2 * NP4),
+                     x3 = __ldg(Ct + u3 * NP4);
+        kahan_add4(a, c, add4(add4(x0, x1), add4(x2, x3)));
+    }
+    for (; i < e; ++i) kahan_add4(a, c, __ldg(Ct + (int64_t)__ldg(colidx + i) * NP4));
+    return a;
+}
+
+// pieces of long local rows: 4 pieces per warp, 8 lanes each -> partial rows Ppc[piece][32]
+__global__ void __launch_bounds__(PT_THREADS) k_ppr_tile_piece(const int32_t *__restrict__ rowptr,
+                                                               const int32_t *__restrict__ colidx,
+                                                               const int2 *__restrict__ pieces, int32_t npieces,
+                                                               const float *__restrict__ C, int32_t NP, int32_t t,
+                                                               float *__restrict__ Ppc) {
+    const int lane = threadIdx.x & 31;
+    const int sub = lane & 7, slot = lane >> 3;
+    const int64_t nw = (int64_t)gridDim.x * PT_WARPS;
+    const float4 *Ct = reinterpret_cast<const float4 *>(C + 32 * t) + sub;
+    for (int64_t p0 = ((int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5)) * 4; p0 < npieces; p0 += nw * 4) {
+        const int64_t p = p0 + slot;
+        int32_t s = 0, e = 0;
+        if (p < npieces) {
+            const int2 pc = pieces[p];
+            s = pc.y;
+            e = min(pc.y + PT_PIECE, __ldg(rowptr + pc.x + 1));
+        }
+        const float4 a = tile_row_sum(colidx, s, e, Ct, NP / 4);
+        if (p < npieces) reinterpret_cast<float4 *>(Ppc)[p * 8 + sub] = a;
+    }
+}
+
+// long rows: P[row] = sum of the row's pieces, in order
+__global__ void k_ppr_tile_fix(const int32_t *__restrict__ hub_rows, const int32_t *__restrict__ piece0, int32_t nh,
+                               const float *__restrict__ Ppc, float *__restrict__ P) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t h = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; h < nh; h += nw) {
+        float a = 0.0f;
+        for (int32_t p = piece0[h]; p < piece0[h + 1]; ++p) a += Ppc[(int64_t)p * 32 + lane];
+        P[(int64_t)hub_rows[h] * 32 + lane] = a;
+    }
+}
+
+// Four rows per warp: 8 lanes per row, one float4 each (the tile's 32 columns = 128 bytes), and
+// four in-edges in flight per row, so that every warp keeps 16 segment loads outstanding.
 __global__ void __launch_bounds__(PT_THREADS) k_ppr_tile_gather(const int32_t *__restrict__ rowptr,
                                                                 const int32_t *__restrict__ colidx, int64_t R,
                                                                 const float *__restrict__ C, int32_t NP, int32_t t,
                                                                 float *__restrict__ P) {
     const int lane = threadIdx.x & 31;
+    const int sub = lane & 7, slot = lane >> 3;  // 4 rows per warp, 8 lanes per row
     const int64_t nw = (int64_t)gridDim.x * PT_WARPS;
-    const float *Ct = C + 32 * t + lane;
-    for (int64_t r = (int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5); r < R; r += nw) {
-        const int32_t s = __ldg(rowptr + r), e = __ldg(rowptr + r + 1);
-        float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
-        int32_t i = s;
-        for (; i + 3 < e; i += 4) {  // four 128-byte segments in flight
-            const int64_t u0 = __ldg(colidx + i), u1 = __ldg(colidx + i + 1), u2 = __ldg(colidx + i + 2),
-                          u3 = __ldg(colidx + i + 3);
-            a0 += __ldg(Ct + u0 * NP);
-            a1 += __ldg(Ct + u1 * NP);
-            a2 += __ldg(Ct + u2 * NP);
-            a3 += __ldg(Ct + u3 * NP);
+    const float4 *Ct = reinterpret_cast<const float4 *>(C + 32 * t) + sub;
+    const int64_t NP4 = NP / 4;
+    for (int64_t r0 = ((int64_t)blockIdx.x * PT_WARPS + (threadIdx.x >> 5)) * 4; r0 < R; r0 += nw * 4) {
+        const int64_t r = r0 + slot;
+        int32_t s = 0, e = 0;
+        if (r < R) {
+            s = __ldg(rowptr + r);
+            e = __ldg(rowptr + r + 1);
         }
-        for (; i < e; ++i) a0 += __ldg(Ct + (int64_t)__ldg(colidx + i) * NP);
-        P[r * 32 + lane] = (a0 + a1) + (a2 + a3);
+        const bool longrow = e - s > PT_PIECE;  // finished from its pieces
+        const float4 a = tile_row_sum(colidx, s, longrow ? s : e, Ct, NP4);
+        if (r < R && !longrow) reinterpret_cast<float4 *>(P)[r * 8 + sub] = a;
     }
 }
 
@@ -203,13 +327,109 @@ __global__ void __launch_bounds__(PT_THREADS) k_ppr_tile_merge(const float *__re
     }
 }
 
+struct Hubs {
+    const int32_t *rows, *piece0;
+    const int2 *pieces;
+    int32_t nhubs, npieces;
+    float *Ppc;
+};
+
 template <int NV4>
 static void launch_ppr(int grid, cudaStream_t s, const tc_graph *g, const float *C, float *Cn, const int32_t *srcc,
                        const unsigned long long *Dc, unsigned long long *Dn, unsigned long long *Dz, float d,
-                       float *R_out, int32_t n) {
+                       float *R_out, int32_t n, const Hubs &h) {
+    if (h.npieces > 0)
+        k_ppr_piece<NV4><<<grid, PPR_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), h.pieces,
+                                                     h.npieces, reinterpret_cast<const float4 *>(C),
+                                                     reinterpret_cast<float4 *>(h.Ppc));
     k_ppr_gather<NV4><<<grid, PPR_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), g->V,
                                                   reinterpret_cast<const float4 *>(C), reinterpret_cast<float4 *>(Cn),
-                                                  srcc, Dc, Dn, Dz, g->inv_outdeg.as<float>(), d, R_out, n);
+                                                  srcc, Dc, Dn, Dz, g->inv_outdeg.as<float>(), d, R_out, n, h.rows,
+                                                  h.piece0, h.nhubs, reinterpret_cast<const float4 *>(h.Ppc));
+}
+
+__global__ void k_row_bounds(const int32_t *rowptr, const int32_t *rows, int32_t n, int32_t *out) {
+    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        out[2 * i] = rowptr[rows[i]];
+        out[2 * i + 1] = rowptr[rows[i] + 1];
+    }
+}
+
+// Pieces of the rows above `piece` edges: host-built from the hub list (few rows).
+static int build_pieces(const int32_t *rowptr, const int32_t *hub_list, int32_t nh, int32_t NP, DevBuf *rows,
+                        DevBuf *piece0, DevBuf *pieces, DevBuf *Ppc, Hubs *h, cudaStream_t s,
+                        int32_t piece = PPR_PIECE) {
+    h->nhubs = 0;
+    h->npieces = 0;
+    h->rows = nullptr;
+    h->piece0 = nullptr;
+    h->pieces = nullptr;
+    h->Ppc = nullptr;
+    if (nh <= 0) return TC_OK;
+    int32_t *hl = new (std::nothrow) int32_t[nh];
+    int32_t *rs = new (std::nothrow) int32_t[2 * (size_t)nh];
+    if (!hl || !rs) {
+        delete[] hl;
+        delete[] rs;
+        return fail(TC_ERR_OOM, "host allocation failed");
+    }
+    DevBuf bounds;
+    int brc = bounds.alloc((size_t)nh * 8);
+    if (brc != TC_OK) {
+        delete[] hl;
+        delete[] rs;
+        return brc;
+    }
+    k_row_bounds<<<(nh + 255) / 256, 256, 0, s>>>(rowptr, hub_list, nh, bounds.as<int32_t>());
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hl, hub_list, (size_t)nh * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(rs, bounds.p, (size_t)nh * 8, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete[] hl;
+        delete[] rs;
+        return fail(TC_ERR_CUDA, "tc_ppr_batch: %s", cudaGetErrorString(e));
+    }
+    int32_t *p0 = new (std::nothrow) int32_t[nh + 1];
+    int64_t np = 0;
+    for (int32_t i = 0; i < nh; ++i) np += (rs[2 * i + 1] - rs[2 * i] + piece - 1) / piece;
+    int2 *pc = new (std::nothrow) int2[np > 0 ? np : 1];
+    if (!p0 || !pc) {
+        delete[] hl;
+        delete[] rs;
+        delete[] p0;
+        delete[] pc;
+        return fail(TC_ERR_OOM, "host allocation failed");
+    }
+    int64_t q = 0;
+    for (int32_t i = 0; i < nh; ++i) {
+        p0[i] = (int32_t)q;
+        for (int32_t st = rs[2 * i]; st < rs[2 * i + 1]; st += piece) pc[q++] = make_int2(hl[i], st);
+    }
+    p0[nh] = (int32_t)q;
+    int rc = rows->alloc((size_t)nh * 4);
+    if (rc == TC_OK) rc = piece0->alloc((size_t)(nh + 1) * 4);
+    if (rc == TC_OK) rc = pieces->alloc((size_t)(np > 0 ? np : 1) * 8);
+    if (rc == TC_OK) rc = Ppc->alloc((size_t)(np > 0 ? np : 1) * NP * 4);
+    if (rc == TC_OK) {
+        e = cudaMemcpyAsync(rows->p, hl, (size_t)nh * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(piece0->p, p0, (size_t)(nh + 1) * 4, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(pieces->p, pc, (size_t)np * 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) rc = fail(TC_ERR_CUDA, "tc_ppr_batch: %s", cudaGetErrorString(e));
+    }
+    delete[] hl;
+    delete[] rs;
+    delete[] p0;
+    delete[] pc;
+    if (rc != TC_OK) return rc;
+    h->nhubs = nh;
+    h->npieces = (int32_t)np;
+    h->rows = rows->as<int32_t>();
+    h->piece0 = piece0->as<int32_t>();
+    h->pieces = pieces->as<int2>();
+    h->Ppc = Ppc->as<float>();
+    return TC_OK;
 }
 
 static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sources, int32_t n,
@@ -265,7 +485,14 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
     DevBuf Pbuf;
     size_t tm_smem = 0;
     int tg_grid = 1;
+    Hubs th;
+    DevBuf th_list, th_rows, th_p0, th_pcs, th_ppc;
+    int32_t tnh = 0;
     if (part) {
+        TC_TRY(collect_hubs(part->rowptr.as<int32_t>(), part->R, PT_PIECE, &th_list, &tnh, s));
+        // piece partials are 32 floats: NP argument 32
+        TC_TRY(build_pieces(part->rowptr.as<int32_t>(), th_list.as<int32_t>(), tnh, 32, &th_rows, &th_p0, &th_pcs,
+                            &th_ppc, &th, s, PT_PIECE));
         TC_TRY(Pbuf.alloc((size_t)(part->R > 0 ? part->R : 1) * 32 * 4));
         tm_smem = (size_t)part->k * 32 * 4;
         if (tm_smem > 48 * 1024)
@@ -280,8 +507,18 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
         float *Cn = Cm[(it + 1) & 1];
         unsigned long long *Dc = D[it % 3], *Dn = D[(it + 1) % 3], *Dz = D[(it + 2) % 3];
         for (int32_t t = 0; t < ntiles; ++t) {
+            if (th.npieces > 0) {
+                k_ppr_tile_piece<<<tg_grid, PT_THREADS, 0, s>>>(part->rowptr.as<int32_t>(), part->colidx.as<int32_t>(),
+                                                                th.pieces, th.npieces, Cc, NP, t, th.Ppc);
+                ++launches;
+            }
             k_ppr_tile_gather<<<tg_grid, PT_THREADS, 0, s>>>(part->rowptr.as<int32_t>(), part->colidx.as<int32_t>(),
                                                              part->R, Cc, NP, t, Pbuf.as<float>());
+            if (th.nhubs > 0) {
+                k_ppr_tile_fix<<<(th.nhubs * 32 + 255) / 256, 256, 0, s>>>(th.rows, th.piece0, th.nhubs, th.Ppc,
+                                                                          Pbuf.as<float>());
+                ++launches;
+            }
             k_ppr_tile_merge<<<part->nranges, PT_THREADS, tm_smem, s>>>(
                 Pbuf.as<float>(), part->id_map.as<int32_t>(), part->merge_off.as<int32_t>(), part->B, part->nranges,
                 part->k, g->V, NP, t, srcbuf.as<int32_t>(), Dc, Dn, Dz, g->inv_outdeg.as<float>(), pp->damping,
@@ -290,6 +527,14 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
             launches += 2;
         }
     }
+    Hubs hubs;
+    DevBuf hub_list, hub_rows, hub_p0, hub_pcs, hub_ppc;
+    int32_t nh = 0;
+    if (!part) {
+        TC_TRY(collect_hubs(g->in_rowptr.as<int32_t>(), g->V, PPR_PIECE, &hub_list, &nh, s));
+        TC_TRY(build_pieces(g->in_rowptr.as<int32_t>(), hub_list.as<int32_t>(), nh, NP, &hub_rows, &hub_p0, &hub_pcs,
+                            &hub_ppc, &hubs, s));
+    }
     for (int it = 0; it < pp->iters && !part; ++it) {
         const bool last = it == pp->iters - 1;
         float *Rw = last ? Rd : nullptr;
@@ -297,10 +542,10 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
         float *Cn = Cm[(it + 1) & 1];
         unsigned long long *Dc = D[it % 3], *Dn = D[(it + 1) % 3], *Dz = D[(it + 2) % 3];
         switch (NV4) {
-            case 1: launch_ppr<1>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
-            case 2: launch_ppr<2>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
-            case 4: launch_ppr<4>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
-            default: launch_ppr<8>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n); break;
+            case 1: launch_ppr<1>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
+            case 2: launch_ppr<2>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
+            case 4: launch_ppr<4>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
+            default: launch_ppr<8>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
         }
         TC_LAUNCH_CHECK();
         ++launches;

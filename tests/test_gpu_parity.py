@@ -446,3 +446,17 @@ def test_ppr_batch_tocab_parity(T, name, n, B):
     for j in range(n):
         assert l1_rel(R[:, j], want[:, j]) <= TOL, j
     assert np.array_equal(R, T.ppr_batch(G, srcs, iters=20, part=P).cpu().numpy())  # deterministic
+
+
+@pytest.mark.parametrize("tocab", [False, True])
+def test_ppr_batch_long_rows_are_split(T, tocab):
+    """A hub with more in-edges than a piece (2048 for rows, 1024 for tiles) runs as pieces."""
+    g = gg.star(6000)
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 2, merge_range=256) if tocab else None
+    srcs = np.array([0, 1, 77, 5999, 0], np.int32)
+    R = T.ppr_batch(G, srcs, iters=20, part=P).cpu().numpy()
+    rp, ci = g.numpy()
+    want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
+    for j in range(len(srcs)):
+        assert l1_rel(R[:, j], want[:, j]) <= TOL, j

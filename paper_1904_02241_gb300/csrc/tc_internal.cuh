@@ -35,16 +35,29 @@ int fail(int status, const char *fmt, ...);   // sets last error, returns status
         if (st__ != TC_OK) return st__; \
     } while (0)
 
+// ---- device block cache -----------------------------------------------------------------
+// Preprocessing allocates and frees GB-sized temporaries on every call, and a fresh
+// cudaMalloc/cudaFree of that size costs milliseconds (page mapping, plus the device-wide
+// synchronisation inside cudaFree).  Freed blocks are therefore kept per device and handed
+// out again for requests of between half and all of their size.  Returning a block
+// synchronises the device first, exactly as cudaFree would, so no kernel still in flight can
+// see its memory reused.  At most cache_limit bytes stay cached (larger leftovers go back to
+// the driver), and an allocation that fails empties the cache and retries once.
+cudaError_t cache_alloc(size_t n, void **p, size_t *got, int *device);
+void cache_free(void *p, size_t bytes, int device);
+size_t cache_limit();
+
 // ---- device buffer that frees itself --------------------------------------------------
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    int device = 0;
     DevBuf() = default;
     DevBuf(const DevBuf &) = delete;
     DevBuf &operator=(const DevBuf &) = delete;
     ~DevBuf() { release(); }
     void release() {
-        if (p) cudaFree(p);
+        if (p) cache_free(p, bytes, device);
         p = nullptr;
         bytes = 0;
     }
@@ -52,12 +65,13 @@ struct DevBuf {
         if (n <= bytes && p) return TC_OK;
         release();
         if (n == 0) n = 16;
-        cudaError_t e = cudaMalloc(&p, n);
+        size_t got = 0;
+        cudaError_t e = cache_alloc(n, &p, &got, &device);
         if (e != cudaSuccess) {
             p = nullptr;
             return fail(TC_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
         }
-        bytes = n;
+        bytes = got;
         return TC_OK;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }

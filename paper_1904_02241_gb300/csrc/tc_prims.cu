@@ -2,9 +2,96 @@
 // exclusive scans, a stable LSD bucket sort, offsets from sorted keys, row expansion.
 #include <stdarg.h>
 
+#include <map>
+#include <mutex>
+
 #include "tc_internal.cuh"
 
 namespace tc {
+
+// ---- device block cache -----------------------------------------------------------------
+namespace {
+struct BlockCache {
+    std::mutex mu;
+    std::multimap<std::pair<int, size_t>, void *> free_blocks;  // (device, bytes) -> block
+    size_t cached = 0;
+    void drop_all() {  // caller holds mu
+        int cur = -1;
+        cudaGetDevice(&cur);
+        for (auto &kv : free_blocks) {
+            cudaSetDevice(kv.first.first);
+            cudaFree(kv.second);
+        }
+        if (cur >= 0) cudaSetDevice(cur);
+        free_blocks.clear();
+        cached = 0;
+    }
+};
+BlockCache &block_cache() {
+    static BlockCache *c = new BlockCache();  // never destroyed: frees at exit would race the driver teardown
+    return *c;
+}
+}  // namespace
+
+size_t cache_limit() { return size_t(16) << 30; }
+
+cudaError_t cache_alloc(size_t n, void **p, size_t *got, int *device) {
+    n = (n + 255) & ~size_t(255);
+    cudaError_t e = cudaGetDevice(device);
+    if (e != cudaSuccess) return e;
+    BlockCache &c = block_cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.free_blocks.lower_bound({*device, n});
+        if (it != c.free_blocks.end() && it->first.first == *device && it->first.second <= 2 * n) {
+            *p = it->second;
+            *got = it->first.second;
+            c.cached -= *got;
+            c.free_blocks.erase(it);
+            return cudaSuccess;
+        }
+    }
+    e = cudaMalloc(p, n);
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        {
+            std::lock_guard<std::mutex> lk(c.mu);
+            c.drop_all();
+        }
+        e = cudaMalloc(p, n);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e;
+    }
+    *got = n;
+    return cudaSuccess;
+}
+
+void cache_free(void *p, size_t bytes, int device) {
+    if (!p) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != device) cudaSetDevice(device);
+    cudaDeviceSynchronize();  // the same ordering guarantee cudaFree gives
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    if (bytes > cache_limit()) {
+        cudaFree(p);
+    } else {
+        c.free_blocks.insert({{device, bytes}, p});
+        c.cached += bytes;
+        // evict the largest blocks until the cache fits its limit again
+        while (c.cached > cache_limit() && !c.free_blocks.empty()) {
+            auto last = std::prev(c.free_blocks.end());
+            cudaSetDevice(last->first.first);
+            cudaFree(last->second);
+            c.cached -= last->first.second;
+            c.free_blocks.erase(last);
+        }
+    }
+    if (cur >= 0) cudaSetDevice(cur);
+}
 
 static thread_local char g_last_error[1024] = "";
 
@@ -136,9 +223,9 @@ int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s) 
 int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s) { return scan_impl<int64_t>(in, n, out, s); }
 
 // ----------------------------------------------------------------------------------------
-// Stable bucket pass: 256 buckets, tiles of 4096 items processed in 16 ordered rounds of
-// 256 items; ranks inside a round come from warp match masks, so equal buckets keep their
-// input order (stability is what keeps in-rows sorted by source).
+// Stable LSD bucket sort: 8-bit digits of key/divisor, 256 buckets, tiles of 4096 items.
+// Each pass is a per-tile histogram, an exclusive scan of the bucket-major count table and a
+// stable scatter; stability is what keeps in-rows sorted by source.
 // ----------------------------------------------------------------------------------------
 constexpr int RX_THREADS = 256;
 constexpr int RX_ROUNDS = 16;
@@ -150,59 +237,120 @@ __device__ __forceinline__ int rx_bucket(int32_t key, int32_t divisor, int shift
     return (int)(((uint32_t)key / (uint32_t)divisor) >> shift) & (RX_BUCKETS - 1);
 }
 
+// Per-tile bucket counts.  All 16 keys of a thread are loaded before any counting so that the
+// loads overlap; every warp counts into its own shared histogram (plain shared atomics: keys
+// of one warp rarely share a bucket), and the 8 warp histograms are summed at the end.
 __global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int64_t n, int32_t divisor, int shift,
                                                         int32_t *counts, int64_t ntiles) {
-    __shared__ int32_t h[RX_BUCKETS];
-    h[threadIdx.x] = 0;
+    __shared__ int32_t h[RX_WARPS][RX_BUCKETS];
+    const int warp = threadIdx.x >> 5;
+    for (int w = 0; w < RX_WARPS; ++w) h[w][threadIdx.x] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RX_TILE;
+    int32_t k[RX_ROUNDS];
+#pragma unroll
     for (int r = 0; r < RX_ROUNDS; ++r) {
-        int64_t i = base + r * RX_THREADS + threadIdx.x;
-        const int b = (i < n) ? rx_bucket(keys[i], divisor, shift) : RX_BUCKETS;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (b < RX_BUCKETS && (peers & ((1u << (threadIdx.x & 31)) - 1u)) == 0)
-            atomicAdd(&h[b], __popc(peers));
+        const int64_t i = base + r * RX_THREADS + threadIdx.x;
+        k[r] = (i < n) ? keys[i] : -1;
+    }
+#pragma unroll
+    for (int r = 0; r < RX_ROUNDS; ++r) {
+        const int64_t i = base + r * RX_THREADS + threadIdx.x;
+        if (i < n) atomicAdd(&h[warp][rx_bucket(k[r], divisor, shift)], 1);
     }
     __syncthreads();
-    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+    int tot = 0;
+    for (int w = 0; w < RX_WARPS; ++w) tot += h[w][threadIdx.x];
+    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = tot;
 }
 
+// Stable scatter of one tile.  Warp w owns items [w*512, (w+1)*512) of the tile, 16 rounds of
+// 32 in order, held in registers.  (A) count per warp and bucket with match masks;  (B) one
+// thread per bucket turns the counts into per-warp offsets inside the tile's bucket-ordered
+// layout (warps in order, buckets by a CTA scan);  (C) every item goes to its slot in shared
+// memory;  (D) consecutive threads copy consecutive slots out, so each bucket run of the tile
+// leaves as one contiguous store stream.  Equal buckets keep their input order throughout.
+constexpr int RX_PER_WARP = RX_TILE / RX_WARPS;  // 512
+constexpr int RX_WROUNDS = RX_PER_WARP / 32;     // 16
 __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, const int32_t *vin, int32_t *kout,
                                                            int32_t *vout, int64_t n, int32_t divisor, int shift,
                                                            const int64_t *offs, int64_t ntiles) {
-    __shared__ int64_t running[RX_BUCKETS];
-    __shared__ int32_t wcnt[RX_WARPS][RX_BUCKETS];
+    __shared__ int32_t skey[RX_TILE];
+    __shared__ int32_t sval[RX_TILE];
+    __shared__ int32_t wpos[RX_WARPS][RX_BUCKETS];
+    __shared__ int32_t lstart[RX_BUCKETS];
+    __shared__ int64_t gstart[RX_BUCKETS];
+    __shared__ int32_t wsum[RX_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    running[threadIdx.x] = offs[(int64_t)threadIdx.x * ntiles + blockIdx.x];
-    const int64_t base = (int64_t)blockIdx.x * RX_TILE;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int r = 0; r < RX_ROUNDS; ++r) {
-        for (int w = 0; w < RX_WARPS; ++w) wcnt[w][threadIdx.x] = 0;
-        __syncthreads();
-        const int64_t i = base + r * RX_THREADS + threadIdx.x;
-        const bool valid = i < n;
-        int32_t key = 0, val = 0;
-        int b = RX_BUCKETS;  // sentinel for invalid lanes
-        if (valid) {
-            key = kin[i];
-            val = vin[i];
-            b = rx_bucket(key, divisor, shift);
-        }
+    for (int b = lane; b < RX_BUCKETS; b += 32) wpos[warp][b] = 0;
+    __syncwarp();
+    const int64_t tile0 = (int64_t)blockIdx.x * RX_TILE;
+    const int64_t base = tile0 + (int64_t)warp * RX_PER_WARP;
+    int32_t key[RX_WROUNDS], val[RX_WROUNDS];
+#pragma unroll
+    for (int r = 0; r < RX_WROUNDS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        key[r] = (i < n) ? kin[i] : 0;
+        val[r] = (i < n) ? vin[i] : 0;
+    }
+    // (A)
+#pragma unroll
+    for (int r = 0; r < RX_WROUNDS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const int b = (i < n) ? rx_bucket(key[r], divisor, shift) : RX_BUCKETS;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int rank = __popc(peers & lt_mask);
-        if (valid && rank == 0) wcnt[warp][b] = __popc(peers);
-        __syncthreads();
-        if (valid) {
-            int64_t pos = running[b] + rank;
-            for (int w = 0; w < warp; ++w) pos += wcnt[w][b];
-            kout[pos] = key;
-            vout[pos] = val;
+        if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // (B) thread = bucket: per-warp offsets inside the bucket, then a CTA scan of bucket totals
+    {
+        const int b = threadIdx.x;
+        int run = 0;
+        for (int w = 0; w < RX_WARPS; ++w) {
+            const int c = wpos[w][b];
+            wpos[w][b] = run;
+            run += c;
         }
+        int inc = run;  // inclusive warp scan of the bucket totals
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += y;
+        }
+        if (lane == 31) wsum[warp] = inc;
+        gstart[b] = offs[(int64_t)b * ntiles + blockIdx.x];
         __syncthreads();
-        int32_t add = 0;
-        for (int w = 0; w < RX_WARPS; ++w) add += wcnt[w][threadIdx.x];
-        running[threadIdx.x] += add;
-        __syncthreads();
+        int before = 0;
+        for (int w = 0; w < warp; ++w) before += wsum[w];
+        lstart[b] = before + inc - run;
+    }
+    __syncthreads();
+    // (C)
+#pragma unroll
+    for (int r = 0; r < RX_WROUNDS; ++r) {
+        const int64_t i = base + r * 32 + lane;
+        const int b = (i < n) ? rx_bucket(key[r], divisor, shift) : RX_BUCKETS;
+        const unsigned peers = __match_any_sync(0xffffffffu, b);
+        if (b < RX_BUCKETS) {
+            const int slot = lstart[b] + wpos[warp][b] + __popc(peers & lt_mask);
+            skey[slot] = key[r];
+            sval[slot] = val[r];
+        }
+        __syncwarp();
+        if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] += __popc(peers);
+        __syncwarp();
+    }
+    __syncthreads();
+    // (D)
+    const int count = (int)((n - tile0) < RX_TILE ? (n - tile0) : RX_TILE);
+    for (int t = threadIdx.x; t < count; t += RX_THREADS) {
+        const int32_t k = skey[t];
+        const int b = rx_bucket(k, divisor, shift);
+        const int64_t pos = gstart[b] + (t - lstart[b]);
+        kout[pos] = k;
+        vout[pos] = sval[t];
     }
 }
 

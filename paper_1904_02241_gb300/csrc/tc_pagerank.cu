@@ -264,76 +264,87 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
     grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
 }
 
-// Exact fixed point of x (an FP32 value already scaled by a power of two, |x| < 2^47) with
-// integer operations only: x = sign * m * 2^(e-150) (m the 24-bit significand), shifted to an
-// integer (rounded half up below 1) and split as v = hi * 2^32 + mid * 2^16 + lo (two's
-// complement; mid, lo in [0, 2^16)).  No FP64 and no 64-bit float conversion: on GB300 those
-// run on the slow FP64 pipe.
-__device__ __forceinline__ void fx_split(float x, int32_t &hi, uint32_t &mid, uint32_t &lo) {
-    const uint32_t b = __float_as_uint(x);
-    const int32_t e = (int32_t)((b >> 23) & 0xFFu);
-    const uint32_t m = (b & 0x7FFFFFu) | (e ? 0x800000u : 0u);
-    const int32_t sh = (e ? e : 1) - 150;  // exponent of the significand's last bit
-    uint64_t v;
-    if (sh >= 0) v = (uint64_t)m << sh;
-    else if (sh > -25) v = (uint64_t)((m + (1u << (-sh - 1))) >> (-sh));
-    else v = 0;
-    const int64_t sv = (b >> 31) ? -(int64_t)v : (int64_t)v;
-    hi = (int32_t)(sv >> 32);
-    mid = (uint32_t)(sv >> 16) & 0xFFFFu;
-    lo = (uint32_t)sv & 0xFFFFu;
+// Rounding to an integer by adding 1.5 * 2^23: for |y| <= 2^22 the sum's low significand
+// bits hold round(y) (to nearest, ties to even), and its bit pattern minus that of
+// 1.5 * 2^23 is round(y) as an integer.  FP32 adds only: no conversion instruction and no
+// FP64 (both slow on GB300).
+constexpr float kRndMagic = 12582912.0f;  // 1.5 * 2^23
+constexpr int32_t kRndBits = 0x4B400000;  // its bit pattern
+
+// Two-part exact fixed point of xs (an FP32 value scaled by a power of two, |xs| <= 2^44):
+// v = hi * 2^22 + lo = round(xs), |hi| <= 2^22, |lo| <= 2^21.  The remainder
+// xs - round(xs * 2^-22) * 2^22 is a multiple of the ulp of xs no larger than 2^21, so the FMA
+// that forms it is exact; only the last step rounds.  With fewer than 1024 entries per
+// vertex neither 32-bit sum can overflow.
+__device__ __forceinline__ void fx_split2(float xs, int32_t &hi, int32_t &lo) {
+    const float fh = fmaf(xs, 0x1p-22f, kRndMagic);
+    hi = __float_as_int(fh) - kRndBits;
+    const float r = fmaf(-(fh - kRndMagic), 0x1p22f, xs);
+    lo = __float_as_int(r + kRndMagic) - kRndBits;
 }
 
-// Same slices and chunks as k_pull_merge_ordered, but one shared accumulator per CTA updated
-// with shared-memory atomics.  FIXED: each partial becomes a 64-bit fixed-point integer v
-// (scale 2^48 / max(1, mass), so no vertex sum exceeds 2^48) split as
-// v = hi * 2^32 + mid * 2^16 + lo; the three parts are added with native 32-bit shared
-// reductions (hi signed; mid and lo stay below 2^32 for fewer than 65536 entries per vertex)
-// and recombined exactly, so the result does not depend on the order: deterministic.
-// Otherwise FP32 atomics (the order of the additions, and so the last bits, may vary).
-template <bool FIXED>
+// Three-part form for up to 65535 entries per vertex (|xs| <= 2^48):
+// v = hi * 2^32 + mid * 2^16 + lo = round(xs), |hi| <= 2^16, |mid|, |lo| <= 2^15.
+__device__ __forceinline__ void fx_split3(float xs, int32_t &hi, int32_t &mid, int32_t &lo) {
+    const float fh = fmaf(xs, 0x1p-32f, kRndMagic);
+    hi = __float_as_int(fh) - kRndBits;
+    const float r1 = fmaf(-(fh - kRndMagic), 0x1p32f, xs);
+    const float fm = fmaf(r1, 0x1p-16f, kRndMagic);
+    mid = __float_as_int(fm) - kRndBits;
+    const float r2 = fmaf(-(fm - kRndMagic), 0x1p16f, r1);
+    lo = __float_as_int(r2 + kRndMagic) - kRndBits;
+}
+
+// Same slices as k_pull_merge_ordered, one shared accumulator per CTA updated with
+// shared-memory atomics, and the slices cut into granules of 4 partials (one 16-byte load
+// of sums and one 8-byte load of 2-byte ids; a granule may reach into the neighbouring
+// ranges' entries, which are masked).  The CTA's granules are numbered slice after slice
+// and grouped in chunks of 32; a warp takes MG_GUNROLL consecutive chunks, lane l granule l
+// of each.  The lane finds the first granule's slice from a chunk-to-slice map in shared
+// memory (binary search for chunks beyond the map) and the following ones by a forward scan.
+// MODE 2 / 3: each partial becomes the fixed-point integer of fx_split2 (scale 2^44 per unit
+// of mass, fewer than 1024 blocks) or fx_split3 (2^48, fewer than 65536 blocks); the parts
+// are added with 32-bit shared reductions and recombined exactly, so the result does not
+// depend on the order of the additions: deterministic.  (FP32 shared atomics measured about
+// 3.4x slower than 32-bit integer ones on GB300, and 64-bit ones 6.5x.)
+// MODE 0: FP32 atomics (the order of the additions, and so the last bits, may vary).
+constexpr int MG_GRAN = 4;
+constexpr int MG_GUNROLL = 4;
+template <int MODE>
 __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *__restrict__ partial,
                                                                   const int32_t *__restrict__ id_map,
                                                                   const uint16_t *__restrict__ id16,
                                                                   const int32_t *__restrict__ offT, int32_t B,
                                                                   int32_t k, UpdateArgs u) {
+    constexpr int NACC = MODE == 0 ? 1 : MODE;
     extern __shared__ __align__(16) unsigned char msm[];
-    int32_t *acc_hi = reinterpret_cast<int32_t *>(msm);        // FIXED: [k] each
-    uint32_t *acc_mid = reinterpret_cast<uint32_t *>(acc_hi + k);
-    uint32_t *acc_lo = acc_mid + k;
-    float *acc32 = reinterpret_cast<float *>(msm);               // FP32: [k]
-    int32_t *lo = reinterpret_cast<int32_t *>(msm + (size_t)k * (FIXED ? 12 : 4));  // [B]
-    int32_t *len = lo + B;
-    int32_t *cpre = len + B;
-    uint16_t *cmap = reinterpret_cast<uint16_t *>(cpre + B + 1);
+    int32_t *acc_hi = reinterpret_cast<int32_t *>(msm);  // fixed point: NACC arrays of [k]
+    int32_t *acc_mid = acc_hi + k;                       // MODE 3 only
+    int32_t *acc_lo = acc_hi + (size_t)(NACC - 1) * k;
+    float *acc32 = reinterpret_cast<float *>(msm);       // MODE 0: [k]
+    int32_t *e_lo = reinterpret_cast<int32_t *>(msm + (size_t)k * 4 * NACC);  // [B] first entry
+    int32_t *e_hi = e_lo + B;                                                  // [B] end entry
+    int32_t *gpre = e_hi + B;                                                  // [B + 1] granule prefix
+    uint16_t *cmap = reinterpret_cast<uint16_t *>(gpre + B + 1);
     const int32_t cmap_cap = B + MG_CMAP_EXTRA;
     __shared__ int32_t wsum[MG_WARPS];
     __shared__ float fred[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t j = blockIdx.x;
     const int32_t vbase = j * k;
-    // 2^48 per unit of mass: a power of two, so partial * scale is exact in FP32 and the
-    // conversion to an integer only rounds below 2^-48 of the mass (no FP64 in the loop)
-    const double scale = FIXED ? *u.fx_scale * (1.0 / 8192.0) : 1.0;
-    const float scalef = (float)scale;
-    for (int t = tid; t < k; t += MG_THREADS) {
-        if (FIXED) {
-            acc_hi[t] = 0;
-            acc_mid[t] = 0u;
-            acc_lo[t] = 0u;
-        } else {
-            acc32[t] = 0.0f;
-        }
-    }
+    // u.fx_scale = 2^61 / mass (a power of two); the parts want 2^44 or 2^48 per unit of mass
+    const float scalef = MODE == 2 ? (float)(*u.fx_scale * 0x1p-17) : MODE == 3 ? (float)(*u.fx_scale * 0x1p-13) : 1.0f;
+    for (int t = tid; t < k * NACC; t += MG_THREADS) acc_hi[t] = 0;  // also clears acc32
+    // slice bounds and granule counts, then an exclusive CTA scan of the counts
     const int per = (B + MG_THREADS - 1) / MG_THREADS;
     int32_t run = 0;
     for (int q = 0; q < per; ++q) {
         const int32_t b = tid * per + q;
         if (b < B) {
             const int32_t l0 = __ldg(offT + (int64_t)j * B + b), l1 = __ldg(offT + (int64_t)(j + 1) * B + b);
-            lo[b] = l0;
-            len[b] = l1 - l0;
-            run += (l1 - l0 + 31) >> 5;
+            e_lo[b] = l0;
+            e_hi[b] = l1;
+            run += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
         }
     }
     int incl = run;
@@ -359,71 +370,114 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
     for (int q = 0; q < per; ++q) {
         const int32_t b = tid * per + q;
         if (b < B) {
-            cpre[b] = base;
-            base += (len[b] + 31) >> 5;
+            gpre[b] = base;
+            const int32_t l0 = e_lo[b], l1 = e_hi[b];
+            base += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
         }
     }
-    if (tid == MG_THREADS - 1) cpre[B] = base;
+    if (tid == MG_THREADS - 1) gpre[B] = base;
     __syncthreads();
+    // cmap[c] = slice holding granule 32 c (the last slice starting at or before it)
     for (int q = 0; q < per; ++q) {
         const int32_t b = tid * per + q;
-        if (b < B)
-            for (int32_t c = cpre[b]; c < cpre[b + 1] && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
+        if (b < B) {
+            const int32_t g0 = gpre[b], g1 = gpre[b + 1];
+            for (int32_t c = (g0 + 31) >> 5; (c << 5) < g1 && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
+        }
     }
     __syncthreads();
-    const int32_t nchunks = cpre[B];
-    for (int32_t c0 = warp; c0 < nchunks; c0 += MG_WARPS * MG_UNROLL) {
-        int32_t idq[MG_UNROLL];
-        float vq[MG_UNROLL];
-#pragma unroll
-        for (int q = 0; q < MG_UNROLL; ++q) {
-            const int32_t c = c0 + q * MG_WARPS;
-            idq[q] = -1;
-            vq[q] = 0.0f;
-            if (c < nchunks) {
-                int32_t bp;
-                if (c < cmap_cap) {
-                    bp = cmap[c];
-                } else {
-                    bp = cmap[cmap_cap - 1];
-                    while (cpre[bp + 1] <= c) ++bp;
+    const int32_t ngran = gpre[B];
+    const int32_t nchunks = (ngran + 31) >> 5;
+    for (int32_t cb = warp * MG_GUNROLL; cb < nchunks; cb += MG_WARPS * MG_GUNROLL) {
+        float4 xv[MG_GUNROLL];
+        uint2 iv[MG_GUNROLL];   // 2-byte ids (id16) ...
+        int4 iw[MG_GUNROLL];    // ... or 4-byte global ids
+        int32_t first[MG_GUNROLL];
+        uint32_t valid[MG_GUNROLL];  // bit e: entry first + e belongs to the slice
+        int32_t bp = 0;
+        {
+            const int32_t g = (cb << 5) + lane;
+            if (cb < cmap_cap) {
+                bp = cmap[cb];
+            } else {  // beyond the map: last slice with gpre <= g (or the last slice)
+                int32_t lo = 0, hi = B - 1;
+                const int32_t gq = g < ngran ? g : ngran - 1;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
                 }
-                const int32_t i = ((c - cpre[bp]) << 5) + lane;
-                if (i < len[bp]) {
-                    const int32_t r = lo[bp] + i;
-                    idq[q] = id16 ? (int32_t)__ldg(id16 + r) : __ldg(id_map + r) - vbase;
-                    vq[q] = __ldg(partial + r);
-                }
+                bp = lo;
             }
         }
 #pragma unroll
-        for (int q = 0; q < MG_UNROLL; ++q) {
-            if (idq[q] >= 0) {
-                if (FIXED) {
-                    int32_t h;
-                    uint32_t md, lw;
-                    fx_split(vq[q] * scalef, h, md, lw);
-                    if (h) atomicAdd(acc_hi + idq[q], h);
-                    if (md) atomicAdd(acc_mid + idq[q], md);
-                    atomicAdd(acc_lo + idq[q], lw);
+        for (int q = 0; q < MG_GUNROLL; ++q) {
+            const int32_t g = ((cb + q) << 5) + lane;
+            valid[q] = 0u;
+            first[q] = 0;
+            if (g < ngran) {
+                while (gpre[bp + 1] <= g) ++bp;
+                const int32_t l0 = e_lo[bp], l1 = e_hi[bp];
+                const int32_t f = (l0 / MG_GRAN + (g - gpre[bp])) * MG_GRAN;
+                const int32_t a = l0 - f > 0 ? l0 - f : 0;              // first valid offset
+                const int32_t z = l1 - f < MG_GRAN ? l1 - f : MG_GRAN;  // end offset
+                valid[q] = (0xFu >> (MG_GRAN - z)) & (0xFu << a);
+                first[q] = f;
+                xv[q] = __ldg(reinterpret_cast<const float4 *>(partial + f));
+                if (id16) iv[q] = __ldg(reinterpret_cast<const uint2 *>(id16 + f));
+                else iw[q] = __ldg(reinterpret_cast<const int4 *>(id_map + f));
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < MG_GUNROLL; ++q) {
+            if (!valid[q]) continue;
+            const float x4[MG_GRAN] = {xv[q].x, xv[q].y, xv[q].z, xv[q].w};
+            int32_t id4[MG_GRAN];
+            if (id16) {
+                id4[0] = (int32_t)(iv[q].x & 0xFFFFu);
+                id4[1] = (int32_t)(iv[q].x >> 16);
+                id4[2] = (int32_t)(iv[q].y & 0xFFFFu);
+                id4[3] = (int32_t)(iv[q].y >> 16);
+            } else {
+                id4[0] = iw[q].x - vbase;
+                id4[1] = iw[q].y - vbase;
+                id4[2] = iw[q].z - vbase;
+                id4[3] = iw[q].w - vbase;
+            }
+#pragma unroll
+            for (int e = 0; e < MG_GRAN; ++e) {
+                if (!((valid[q] >> e) & 1u)) continue;
+                const int32_t id = id4[e];
+                if (MODE == 2) {
+                    int32_t h, lw;
+                    fx_split2(x4[e] * scalef, h, lw);
+                    atomicAdd(acc_hi + id, h);
+                    atomicAdd(acc_lo + id, lw);
+                } else if (MODE == 3) {
+                    int32_t h, md, lw;
+                    fx_split3(x4[e] * scalef, h, md, lw);
+                    if (h) atomicAdd(acc_hi + id, h);
+                    atomicAdd(acc_mid + id, md);
+                    atomicAdd(acc_lo + id, lw);
                 } else {
-                    atomicAdd(acc32 + idq[q], vq[q]);
+                    atomicAdd(acc32 + id, x4[e]);
                 }
             }
         }
     }
     __syncthreads();
     const float spread = spread_of(u);
-    const float inv_scalef = (float)(1.0 / scale);  // a power of two
+    const float inv_scalef = 1.0f / scalef;  // a power of two
     float dsum = 0.0f;
     for (int t = tid; t < k; t += MG_THREADS) {
         const int32_t v = vbase + t;
         if (v >= u.V) break;
         float sum;
-        if (FIXED) {
+        if (MODE != 0) {
             // exact 64-bit total, converted with 32-bit integer-to-float steps (no FP64)
-            const long long tot = ((long long)acc_hi[t] << 32) + ((long long)acc_mid[t] << 16) + (long long)acc_lo[t];
-            const float th = (float)(int32_t)(tot >> 24);            // |tot| < 2^56
+            const long long tot = MODE == 2 ? ((long long)acc_hi[t] << 22) + (long long)acc_lo[t]
+                                            : ((long long)acc_hi[t] << 32) + ((long long)acc_mid[t] << 16) +
+                                                  (long long)acc_lo[t];
+            const float th = (float)(int32_t)(tot >> 24);            // |tot| < 2^49
             const float tl = (float)(uint32_t)(tot & 0xFFFFFFll);     // < 2^24, exact
             sum = fmaf(th, 16777216.0f, tl) * inv_scalef;
         } else {
@@ -435,8 +489,12 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
     grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
 }
 
+// Entries per vertex are at most B (one per block): two-part fixed point below 1024 blocks.
+int merge_fixed_parts(int32_t B) { return B < 1024 ? 2 : 3; }
+
 size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed) {
-    return (size_t)k * (fixed ? 12 : 4) + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+    return (size_t)k * 4 * (fixed ? merge_fixed_parts(B) : 1) + ((size_t)3 * B + 2) * 4 +
+           ((size_t)B + MG_CMAP_EXTRA) * 2;
 }
 
 // Initial ranks (1/V or caller's), first contributions, their dangling mass, and the
@@ -688,9 +746,11 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
         } else {
             const bool fx = merge_mode == TC_MERGE_FIXED;
             merge_smem = merge_atomic_smem_bytes(part->k, part->B, fx);
+            const void *kmerge = !fx ? (const void *)k_pull_merge_atomic<0>
+                                     : merge_fixed_parts(part->B) == 2 ? (const void *)k_pull_merge_atomic<2>
+                                                                       : (const void *)k_pull_merge_atomic<3>;
             if (merge_smem > 48 * 1024)
-                TC_CUDA(cudaFuncSetAttribute(fx ? k_pull_merge_atomic<true> : k_pull_merge_atomic<false>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
+                TC_CUDA(cudaFuncSetAttribute(kmerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
         }
     }
     int g_init = 1;
@@ -779,12 +839,16 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
                     k_pull_merge_ordered<<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
                         part->B, part->k, u);
+                else if (merge_mode == TC_MERGE_FIXED && merge_fixed_parts(part->B) == 2)
+                    k_pull_merge_atomic<2><<<g_merge, MG_THREADS, merge_smem, s>>>(
+                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
+                        part->B, part->k, u);
                 else if (merge_mode == TC_MERGE_FIXED)
-                    k_pull_merge_atomic<true><<<g_merge, MG_THREADS, merge_smem, s>>>(
+                    k_pull_merge_atomic<3><<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
                         part->B, part->k, u);
                 else
-                    k_pull_merge_atomic<false><<<g_merge, MG_THREADS, merge_smem, s>>>(
+                    k_pull_merge_atomic<0><<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
                         part->B, part->k, u);
             }

@@ -196,7 +196,7 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     }
     const int64_t R = p->R;
     TC_TRY(p->rowptr.alloc(((size_t)R + 1) * 4));
-    TC_TRY(p->id_map.alloc((size_t)(R > 0 ? R : 1) * 4));
+    TC_TRY(p->id_map.alloc((size_t)(R + 8) * 4));  // padded: the merge reads whole 4-entry granules
     DevBuf blk_edges, blk_rows;
     TC_TRY(blk_edges.alloc(((size_t)B + 1) * 8));
     TC_TRY(blk_rows.alloc(((size_t)B + 1) * 8));
@@ -232,12 +232,12 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     }
     TC_TRY(collect_hubs(p->rowptr.as<int32_t>(), R, p->hub_degree, &p->hubs, &p->num_hubs, s));
     if (R > 0 && (p->k & (p->k - 1)) == 0 && p->k <= 65536) {  // 2-byte local ids for the merge
-        TC_TRY(p->id16.alloc((size_t)R * 2));
+        TC_TRY(p->id16.alloc((size_t)(R + 8) * 2));
         k_id16<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), R, p->k - 1, p->id16.as<uint16_t>());
         TC_LAUNCH_CHECK();
     }
     p->num_groups = (R + 31) / 32;
-    TC_TRY(p->partial.alloc((size_t)(R > 0 ? R : 1) * 4));
+    TC_TRY(p->partial.alloc((size_t)(R + 8) * 4));
     TC_TRY(p->rowbits.alloc((size_t)((R + 31) / 32 + 1) * 4));
     TC_CUDA(cudaStreamSynchronize(s));
     const int stage = pp ? pp->smem_stage : 0;

@@ -142,7 +142,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_gather(const int32_t *__res
 constexpr int MG_THREADS = 512;
 constexpr int MG_WARPS = MG_THREADS / 32;
 constexpr int MG_UNROLL = 16;
-constexpr int MG_CMAP_EXTRA = 2048;  // chunk-to-block map entries beyond one per block
+constexpr int MG_CMAP_EXTRA = 1024;  // chunk-to-block map entries beyond one per block
 
 size_t merge_smem_bytes(int32_t k, int32_t B) {
     return (size_t)MG_WARPS * k * 4 + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
@@ -296,20 +296,28 @@ __device__ __forceinline__ void fx_split3(float xs, int32_t &hi, int32_t &mid, i
 }
 
 // Same slices as k_pull_merge_ordered, one shared accumulator per CTA updated with
-// shared-memory atomics, and the slices cut into granules of 4 partials (one 16-byte load
-// of sums and one 8-byte load of 2-byte ids; a granule may reach into the neighbouring
-// ranges' entries, which are masked).  The CTA's granules are numbered slice after slice
-// and grouped in chunks of 32; a warp takes MG_GUNROLL consecutive chunks, lane l granule l
-// of each.  The lane finds the first granule's slice from a chunk-to-slice map in shared
-// memory (binary search for chunks beyond the map) and the following ones by a forward scan.
+// shared-memory atomics, and the slices cut into aligned granules of 8 partials (two 16-byte
+// loads of sums and one of 2-byte ids; a granule may reach into the neighbouring ranges'
+// entries, which are masked).  The CTA's granules are numbered slice after slice
+// and grouped in chunks of 32; warp w takes the w-th sixteenth of the chunks, in order, lane l
+// granule l of each, MG_GUNROLL chunks at a time.  The lane finds its first granule's slice
+// from a chunk-to-slice map in shared memory (binary search for chunks beyond the map) and the
+// following ones by a forward scan.
 // MODE 2 / 3: each partial becomes the fixed-point integer of fx_split2 (scale 2^44 per unit
 // of mass, fewer than 1024 blocks) or fx_split3 (2^48, fewer than 65536 blocks); the parts
 // are added with 32-bit shared reductions and recombined exactly, so the result does not
 // depend on the order of the additions: deterministic.  (FP32 shared atomics measured about
 // 3.4x slower than 32-bit integer ones on GB300, and 64-bit ones 6.5x.)
 // MODE 0: FP32 atomics (the order of the additions, and so the last bits, may vary).
-constexpr int MG_GRAN = 4;
-constexpr int MG_GUNROLL = 4;
+constexpr int MG_GRAN = 8;     // entries per granule: 32 bytes of sums, 16 bytes of 2-byte ids
+constexpr int MG_GUNROLL = 2;  // granules of a lane in flight
+
+// Shared-memory layout of k_pull_merge_atomic: nacc accumulator arrays of [k], slice bounds
+// and granule prefix ([3B + 1] ints), then the chunk-to-slice map.
+__host__ __device__ inline size_t merge_atomic_layout_bytes(int32_t k, int32_t B, int nacc) {
+    return (size_t)k * 4 * nacc + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *__restrict__ partial,
                                                                   const int32_t *__restrict__ id_map,
@@ -388,78 +396,92 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
     __syncthreads();
     const int32_t ngran = gpre[B];
     const int32_t nchunks = (ngran + 31) >> 5;
-    for (int32_t cb = warp * MG_GUNROLL; cb < nchunks; cb += MG_WARPS * MG_GUNROLL) {
-        float4 xv[MG_GUNROLL];
-        uint2 iv[MG_GUNROLL];   // 2-byte ids (id16) ...
-        int4 iw[MG_GUNROLL];    // ... or 4-byte global ids
-        int32_t first[MG_GUNROLL];
-        uint32_t valid[MG_GUNROLL];  // bit e: entry first + e belongs to the slice
-        int32_t bp = 0;
-        {
-            const int32_t g = (cb << 5) + lane;
-            if (cb < cmap_cap) {
-                bp = cmap[cb];
-            } else {  // beyond the map: last slice with gpre <= g (or the last slice)
-                int32_t lo = 0, hi = B - 1;
-                const int32_t gq = g < ngran ? g : ngran - 1;
-                while (lo < hi) {
-                    const int32_t mid = (lo + hi + 1) >> 1;
-                    if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
-                }
-                bp = lo;
+    const int32_t dummy = lane < k ? lane : 0;  // target of the zero adds of masked entries
+    const int32_t c_begin = (int32_t)((int64_t)nchunks * warp / MG_WARPS);
+    const int32_t c_end = (int32_t)((int64_t)nchunks * (warp + 1) / MG_WARPS);
+    int32_t bp = 0;
+    if (c_begin < c_end) {
+        if (c_begin < cmap_cap) {
+            bp = cmap[c_begin];
+        } else {  // beyond the map: last slice with gpre <= the chunk's first granule
+            int32_t lo = 0, hi = B - 1;
+            const int32_t gq = c_begin << 5;
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;
+                if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
             }
+            bp = lo;
         }
+    }
+    for (int32_t c0 = c_begin; c0 < c_end; c0 += MG_GUNROLL) {
+        float4 xa[MG_GUNROLL], xb[MG_GUNROLL];
+        uint4 iv[MG_GUNROLL];
+        uint32_t valid[MG_GUNROLL];  // bit e: entry first + e belongs to the slice
 #pragma unroll
         for (int q = 0; q < MG_GUNROLL; ++q) {
-            const int32_t g = ((cb + q) << 5) + lane;
+            const int32_t c = c0 + q;
+            const int32_t g = (c << 5) + lane;
             valid[q] = 0u;
-            first[q] = 0;
-            if (g < ngran) {
+            xa[q] = xb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+            iv[q] = make_uint4(0u, 0u, 0u, 0u);
+            if (c < c_end && g < ngran) {
                 while (gpre[bp + 1] <= g) ++bp;
                 const int32_t l0 = e_lo[bp], l1 = e_hi[bp];
-                const int32_t f = (l0 / MG_GRAN + (g - gpre[bp])) * MG_GRAN;
+                const int32_t f = ((l0 >> 3) + (g - gpre[bp])) << 3;  // MG_GRAN = 8, l0 >= 0
                 const int32_t a = l0 - f > 0 ? l0 - f : 0;              // first valid offset
                 const int32_t z = l1 - f < MG_GRAN ? l1 - f : MG_GRAN;  // end offset
-                valid[q] = (0xFu >> (MG_GRAN - z)) & (0xFu << a);
-                first[q] = f;
-                xv[q] = __ldg(reinterpret_cast<const float4 *>(partial + f));
-                if (id16) iv[q] = __ldg(reinterpret_cast<const uint2 *>(id16 + f));
-                else iw[q] = __ldg(reinterpret_cast<const int4 *>(id_map + f));
+                valid[q] = (0xFFu >> (MG_GRAN - z)) & (0xFFu << a);
+                const float4 *px = reinterpret_cast<const float4 *>(partial + f);
+                xa[q] = __ldg(px);
+                xb[q] = __ldg(px + 1);
+                if (id16) {
+                    iv[q] = __ldg(reinterpret_cast<const uint4 *>(id16 + f));
+                } else {  // global ids: keep the granule's position, read them below
+                    iv[q].x = (uint32_t)f;
+                }
             }
         }
 #pragma unroll
         for (int q = 0; q < MG_GUNROLL; ++q) {
-            if (!valid[q]) continue;
-            const float x4[MG_GRAN] = {xv[q].x, xv[q].y, xv[q].z, xv[q].w};
-            int32_t id4[MG_GRAN];
+            float x8[MG_GRAN] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
+            int32_t id8[MG_GRAN];
             if (id16) {
-                id4[0] = (int32_t)(iv[q].x & 0xFFFFu);
-                id4[1] = (int32_t)(iv[q].x >> 16);
-                id4[2] = (int32_t)(iv[q].y & 0xFFFFu);
-                id4[3] = (int32_t)(iv[q].y >> 16);
+                const uint32_t w[4] = {iv[q].x, iv[q].y, iv[q].z, iv[q].w};
+#pragma unroll
+                for (int h = 0; h < 4; ++h) {
+                    id8[2 * h] = (int32_t)(w[h] & 0xFFFFu);
+                    id8[2 * h + 1] = (int32_t)(w[h] >> 16);
+                }
             } else {
-                id4[0] = iw[q].x - vbase;
-                id4[1] = iw[q].y - vbase;
-                id4[2] = iw[q].z - vbase;
-                id4[3] = iw[q].w - vbase;
+                int4 w0 = make_int4(vbase, vbase, vbase, vbase), w1 = w0;
+                if (valid[q]) {
+                    const int4 *pi = reinterpret_cast<const int4 *>(id_map + (int32_t)iv[q].x);
+                    w0 = __ldg(pi);
+                    w1 = __ldg(pi + 1);
+                }
+                id8[0] = w0.x - vbase; id8[1] = w0.y - vbase; id8[2] = w0.z - vbase; id8[3] = w0.w - vbase;
+                id8[4] = w1.x - vbase; id8[5] = w1.y - vbase; id8[6] = w1.z - vbase; id8[7] = w1.w - vbase;
             }
+            // Entries outside the slice add zero to a slot of their own lane (no branches: the
+            // atomics of a warp stay converged).
 #pragma unroll
             for (int e = 0; e < MG_GRAN; ++e) {
-                if (!((valid[q] >> e) & 1u)) continue;
-                const int32_t id = id4[e];
+                const bool ok = (valid[q] >> e) & 1u;
+                const int32_t id = ok ? id8[e] : dummy;
+                const float x = ok ? x8[e] : 0.0f;
                 if (MODE == 2) {
                     int32_t h, lw;
-                    fx_split2(x4[e] * scalef, h, lw);
+                    fx_split2(x * scalef, h, lw);
                     atomicAdd(acc_hi + id, h);
                     atomicAdd(acc_lo + id, lw);
                 } else if (MODE == 3) {
                     int32_t h, md, lw;
-                    fx_split3(x4[e] * scalef, h, md, lw);
+                    fx_split3(x * scalef, h, md, lw);
                     if (h) atomicAdd(acc_hi + id, h);
                     atomicAdd(acc_mid + id, md);
                     atomicAdd(acc_lo + id, lw);
                 } else {
-                    atomicAdd(acc32 + id, x4[e]);
+                    atomicAdd(acc32 + id, x);
                 }
             }
         }
@@ -493,8 +515,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *_
 int merge_fixed_parts(int32_t B) { return B < 1024 ? 2 : 3; }
 
 size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed) {
-    return (size_t)k * 4 * (fixed ? merge_fixed_parts(B) : 1) + ((size_t)3 * B + 2) * 4 +
-           ((size_t)B + MG_CMAP_EXTRA) * 2;
+    return merge_atomic_layout_bytes(k, B, fixed ? merge_fixed_parts(B) : 1);
 }
 
 // Initial ranks (1/V or caller's), first contributions, their dangling mass, and the
@@ -740,17 +761,16 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
             merge_mode = TC_MERGE_FIXED;
         if (merge_mode == TC_MERGE_ORDERED) {
             merge_smem = merge_smem_bytes(part->k, part->B);
-            if (merge_smem > 48 * 1024)
-                TC_CUDA(cudaFuncSetAttribute(k_pull_merge_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)merge_smem));
+            TC_CUDA(cudaFuncSetAttribute(k_pull_merge_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)merge_smem));
         } else {
             const bool fx = merge_mode == TC_MERGE_FIXED;
             merge_smem = merge_atomic_smem_bytes(part->k, part->B, fx);
             const void *kmerge = !fx ? (const void *)k_pull_merge_atomic<0>
                                      : merge_fixed_parts(part->B) == 2 ? (const void *)k_pull_merge_atomic<2>
                                                                        : (const void *)k_pull_merge_atomic<3>;
-            if (merge_smem > 48 * 1024)
-                TC_CUDA(cudaFuncSetAttribute(kmerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
+            // always: the 48 KB default also counts the kernel's static shared memory
+            TC_CUDA(cudaFuncSetAttribute(kmerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
         }
     }
     int g_init = 1;

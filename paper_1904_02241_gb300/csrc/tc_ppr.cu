@@ -495,8 +495,7 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
                             &th_ppc, &th, s, PT_PIECE));
         TC_TRY(Pbuf.alloc((size_t)(part->R > 0 ? part->R : 1) * 32 * 4));
         tm_smem = (size_t)part->k * 32 * 4;
-        if (tm_smem > 48 * 1024)
-            TC_CUDA(cudaFuncSetAttribute(k_ppr_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tm_smem));
+        TC_CUDA(cudaFuncSetAttribute(k_ppr_tile_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tm_smem));
         int ps = 1;
         TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ps, k_ppr_tile_gather, PT_THREADS, 0));
         tg_grid = caps.sms * (ps > 0 ? ps : 1);

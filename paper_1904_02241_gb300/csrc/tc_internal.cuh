@@ -35,6 +35,27 @@ int fail(int status, const char *fmt, ...);   // sets last error, returns status
         if (st__ != TC_OK) return st__; \
     } while (0)
 
+// ---- division by a launch-invariant divisor ---------------------------------------------
+// key / d for 0 <= key < 2^31 and d >= 1 as a multiply and a shift (Granlund and Montgomery,
+// "Division by invariant integers using multiplication", 1994): with l = ceil(log2 d),
+// m = ceil(2^(31+l) / d) and s = 31 + l, (key * m) >> s = key / d exactly, because the error
+// key * (m*d - 2^s) / (d * 2^s) stays below 2^-l <= 1/d; m <= 2^32 keeps key * m below 2^63.
+struct DivBy {
+    uint64_t m;
+    int s;
+};
+inline DivBy div_by(int32_t d) {
+    int l = 0;
+    while (((int64_t)1 << l) < (int64_t)d) ++l;
+    DivBy q;
+    q.s = 31 + l;
+    q.m = (((uint64_t)1 << q.s) + (uint64_t)d - 1) / (uint64_t)d;
+    return q;
+}
+__device__ __forceinline__ int32_t div_apply(int32_t key, DivBy q) {
+    return (int32_t)(((uint64_t)(uint32_t)key * q.m) >> q.s);
+}
+
 // ---- device block cache -----------------------------------------------------------------
 // Preprocessing allocates and frees GB-sized temporaries on every call, and a fresh
 // cudaMalloc/cudaFree of that size costs milliseconds (page mapping, plus the device-wide

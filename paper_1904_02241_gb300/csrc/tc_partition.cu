@@ -6,10 +6,10 @@
 namespace tc {
 
 // head[i] = 1 when edge i starts a new local row: first edge, new block or new row.
-__global__ void k_row_heads(const int32_t *col, const int32_t *row, int64_t E, int32_t W, int32_t *head) {
+__global__ void k_row_heads(const int32_t *col, const int32_t *row, int64_t E, DivBy W, int32_t *head) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
         int32_t h = 1;
-        if (i > 0) h = (col[i] / W != col[i - 1] / W) || (row[i] != row[i - 1]);
+        if (i > 0) h = (div_apply(col[i], W) != div_apply(col[i - 1], W)) || (row[i] != row[i - 1]);
         head[i] = h;
     }
 }
@@ -182,7 +182,8 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
         rows_in.release();
         TC_TRY(head.alloc((size_t)E * 4));
         TC_TRY(rowid.alloc((size_t)E * 8));
-        k_row_heads<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), rows_sorted.as<int32_t>(), E, W, head.as<int32_t>());
+        k_row_heads<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), rows_sorted.as<int32_t>(), E, div_by(W),
+                                          head.as<int32_t>());
         TC_LAUNCH_CHECK();
         TC_TRY(scan_i32_to_i64(head.as<int32_t>(), E, rowid.as<int64_t>(), s));
         int64_t last_id = 0;

@@ -158,13 +158,41 @@ __device__ __forceinline__ T block_exclusive_sum(T x, T *total) {
     return r;
 }
 
+// A thread's SCAN_ITEMS consecutive inputs (8 items start 32- or 64-byte aligned: vector
+// loads for whole groups, element loads at the ragged end).
 template <class Tin, class Tout>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const Tin *in, int64_t n, Tout *tile_sums) {
+__device__ __forceinline__ void load_items(const Tin *in, int64_t n, int64_t base, bool vec, Tout (&v)[SCAN_ITEMS]) {
+    static_assert(SCAN_ITEMS == 8, "vector loads assume 8 items");
+    if (vec && base + SCAN_ITEMS <= n) {
+        if (sizeof(Tin) == 4) {
+            const int4 *p = reinterpret_cast<const int4 *>(in + base);
+            const int4 a = p[0], b = p[1];
+            const int32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = (Tout)w[i];
+        } else {
+            const longlong2 *p = reinterpret_cast<const longlong2 *>(in + base);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const longlong2 x = p[i];
+                v[2 * i] = (Tout)x.x;
+                v[2 * i + 1] = (Tout)x.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i) v[i] = (base + i < n) ? (Tout)in[base + i] : Tout(0);
+    }
+}
+
+template <class Tin, class Tout>
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const Tin *in, int64_t n, Tout *tile_sums, bool vec) {
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    Tout v[SCAN_ITEMS];
+    load_items(in, n, base, vec, v);
     Tout s = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i)
-        if (base + i < n) s += (Tout)in[base + i];
+    for (int i = 0; i < SCAN_ITEMS; ++i) s += v[i];
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
     __shared__ Tout ws[SCAN_THREADS / 32];
@@ -178,22 +206,30 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_reduce(const Tin *in, int
 }
 
 template <class Tin, class Tout>
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const Tin *in, int64_t n, const Tout *tile_prefix, Tout *out) {
+__global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const Tin *in, int64_t n, const Tout *tile_prefix, Tout *out, bool vec) {
     const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
     Tout v[SCAN_ITEMS];
+    load_items(in, n, base, vec, v);
     Tout s = 0;
 #pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        v[i] = (base + i < n) ? (Tout)in[base + i] : Tout(0);
-        s += v[i];
-    }
+    for (int i = 0; i < SCAN_ITEMS; ++i) s += v[i];
     __shared__ Tout total;
     Tout run = block_exclusive_sum<Tout>(s, &total);
     run += tile_prefix ? tile_prefix[blockIdx.x] : Tout(0);
+    Tout o[SCAN_ITEMS];
 #pragma unroll
     for (int i = 0; i < SCAN_ITEMS; ++i) {
-        if (base + i < n) out[base + i] = run;
+        o[i] = run;
         run += v[i];
+    }
+    if (vec && base + SCAN_ITEMS <= n) {  // 64 aligned bytes per thread: four 16-byte stores
+        longlong2 *q = reinterpret_cast<longlong2 *>(out + base);
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS / 2; ++i) q[i] = make_longlong2(o[2 * i], o[2 * i + 1]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < SCAN_ITEMS; ++i)
+            if (base + i < n) out[base + i] = o[i];
     }
 }
 
@@ -201,18 +237,20 @@ template <class Tin>
 static int scan_impl(const Tin *in, int64_t n, int64_t *out, cudaStream_t s) {
     if (n <= 0) return TC_OK;
     const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    // vector access needs 8 items' worth of alignment on both sides
+    const bool vec = ((uintptr_t)in % (8 * sizeof(Tin))) == 0 && ((uintptr_t)out % 64) == 0;
     if (tiles == 1) {
-        k_scan_apply<Tin, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out);
+        k_scan_apply<Tin, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out, vec);
         TC_LAUNCH_CHECK();
         return TC_OK;
     }
     DevBuf sums, pref;
     TC_TRY(sums.alloc(tiles * sizeof(int64_t)));
     TC_TRY(pref.alloc(tiles * sizeof(int64_t)));
-    k_scan_reduce<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums.as<int64_t>());
+    k_scan_reduce<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums.as<int64_t>(), vec);
     TC_LAUNCH_CHECK();
     TC_TRY(scan_impl<int64_t>(sums.as<int64_t>(), tiles, pref.as<int64_t>(), s));
-    k_scan_apply<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, pref.as<int64_t>(), out);
+    k_scan_apply<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, pref.as<int64_t>(), out, vec);
     TC_LAUNCH_CHECK();
     // DevBuf frees are stream-unordered: make sure the kernels using them are done.
     TC_CUDA(cudaStreamSynchronize(s));
@@ -233,14 +271,31 @@ constexpr int RX_TILE = RX_THREADS * RX_ROUNDS;
 constexpr int RX_BUCKETS = 256;
 constexpr int RX_WARPS = RX_THREADS / 32;
 
-__device__ __forceinline__ int rx_bucket(int32_t key, int32_t divisor, int shift) {
-    return (int)(((uint32_t)key / (uint32_t)divisor) >> shift) & (RX_BUCKETS - 1);
+// Digit of key / divisor: the multiply-and-shift of DivBy with the digit's shift folded into
+// the same shift.
+struct RxDigit {
+    uint64_t m;
+    int sh;
+};
+static RxDigit rx_digit(int32_t divisor, int shift) {
+    const DivBy q = div_by(divisor);
+    RxDigit r;
+    r.m = q.m;
+    r.sh = q.s + shift;
+    if (r.sh > 63) {  // key * m < 2^63: this digit is zero for every key
+        r.m = 0;
+        r.sh = 0;
+    }
+    return r;
+}
+__device__ __forceinline__ int rx_bucket(int32_t key, RxDigit dg) {
+    return (int)(((uint64_t)(uint32_t)key * dg.m) >> dg.sh) & (RX_BUCKETS - 1);
 }
 
 // Per-tile bucket counts.  All 16 keys of a thread are loaded before any counting so that the
 // loads overlap; every warp counts into its own shared histogram (plain shared atomics: keys
 // of one warp rarely share a bucket), and the 8 warp histograms are summed at the end.
-__global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int64_t n, int32_t divisor, int shift,
+__global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int64_t n, RxDigit dg,
                                                         int32_t *counts, int64_t ntiles) {
     __shared__ int32_t h[RX_WARPS][RX_BUCKETS];
     const int warp = threadIdx.x >> 5;
@@ -256,7 +311,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int
 #pragma unroll
     for (int r = 0; r < RX_ROUNDS; ++r) {
         const int64_t i = base + r * RX_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[warp][rx_bucket(k[r], divisor, shift)], 1);
+        if (i < n) atomicAdd(&h[warp][rx_bucket(k[r], dg)], 1);
     }
     __syncthreads();
     int tot = 0;
@@ -273,7 +328,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int
 constexpr int RX_PER_WARP = RX_TILE / RX_WARPS;  // 512
 constexpr int RX_WROUNDS = RX_PER_WARP / 32;     // 16
 __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, const int32_t *vin, int32_t *kout,
-                                                           int32_t *vout, int64_t n, int32_t divisor, int shift,
+                                                           int32_t *vout, int64_t n, RxDigit dg,
                                                            const int64_t *offs, int64_t ntiles) {
     __shared__ int32_t skey[RX_TILE];
     __shared__ int32_t sval[RX_TILE];
@@ -298,7 +353,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
-        const int b = (i < n) ? rx_bucket(key[r], divisor, shift) : RX_BUCKETS;
+        const int b = (i < n) ? rx_bucket(key[r], dg) : RX_BUCKETS;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] += __popc(peers);
         __syncwarp();
@@ -331,7 +386,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
-        const int b = (i < n) ? rx_bucket(key[r], divisor, shift) : RX_BUCKETS;
+        const int b = (i < n) ? rx_bucket(key[r], dg) : RX_BUCKETS;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
         if (b < RX_BUCKETS) {
             const int slot = lstart[b] + wpos[warp][b] + __popc(peers & lt_mask);
@@ -347,7 +402,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
     const int count = (int)((n - tile0) < RX_TILE ? (n - tile0) : RX_TILE);
     for (int t = threadIdx.x; t < count; t += RX_THREADS) {
         const int32_t k = skey[t];
-        const int b = rx_bucket(k, divisor, shift);
+        const int b = rx_bucket(k, dg);
         const int64_t pos = gstart[b] + (t - lstart[b]);
         kout[pos] = k;
         vout[pos] = sval[t];
@@ -372,10 +427,11 @@ int stable_bucket_sort(const int32_t *k_in, const int32_t *v_in, int32_t *k_out,
         int32_t *kd = to_out ? k_out : k_tmp;
         int32_t *vd = to_out ? v_out : v_tmp;
         (void)last;
-        k_rx_hist<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, n, divisor, 8 * p, counts.as<int32_t>(), ntiles);
+        const RxDigit dg = rx_digit(divisor, 8 * p);
+        k_rx_hist<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, n, dg, counts.as<int32_t>(), ntiles);
         TC_LAUNCH_CHECK();
         TC_TRY(scan_i32_to_i64(counts.as<int32_t>(), ntiles * RX_BUCKETS, offs.as<int64_t>(), s));
-        k_rx_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, vsrc, kd, vd, n, divisor, 8 * p,
+        k_rx_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, vsrc, kd, vd, n, dg,
                                                            offs.as<int64_t>(), ntiles);
         TC_LAUNCH_CHECK();
         ksrc = kd;
@@ -406,12 +462,23 @@ int offsets_from_sorted(const int32_t *keys, int64_t n, int32_t V, int32_t *rowp
 }
 
 // One warp per row: lanes write the row id over the row's edge range.
+// A warp takes 32 rows at a time: one coalesced load of their offsets, then the rows' edge
+// ranges are filled one row after the other (no dependent load per row).
 __global__ void k_expand_rows(const int32_t *rowptr, int32_t V, int32_t *row_of_edge) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t u = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; u < V; u += warps) {
-        const int32_t b = rowptr[u], e = rowptr[u + 1];
-        for (int32_t i = b + lane; i < e; i += 32) row_of_edge[i] = (int32_t)u;
+    for (int64_t u0 = ((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5) * 32; u0 < V; u0 += warps * 32) {
+        const int64_t u = u0 + lane;
+        int32_t b = 0, e = 0;
+        if (u < V) {
+            b = rowptr[u];
+            e = rowptr[u + 1];
+        }
+        const int nrows = (V - u0) < 32 ? (int)(V - u0) : 32;
+        for (int j = 0; j < nrows; ++j) {
+            const int32_t bj = __shfl_sync(0xffffffffu, b, j), ej = __shfl_sync(0xffffffffu, e, j);
+            for (int32_t i = bj + lane; i < ej; i += 32) row_of_edge[i] = (int32_t)(u0 + j);
+        }
     }
 }
 

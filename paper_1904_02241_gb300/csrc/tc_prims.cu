@@ -320,11 +320,12 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int
 }
 
 // Stable scatter of one tile.  Warp w owns items [w*512, (w+1)*512) of the tile, 16 rounds of
-// 32 in order, held in registers.  (A) count per warp and bucket with match masks;  (B) one
-// thread per bucket turns the counts into per-warp offsets inside the tile's bucket-ordered
-// layout (warps in order, buckets by a CTA scan);  (C) every item goes to its slot in shared
-// memory;  (D) consecutive threads copy consecutive slots out, so each bucket run of the tile
-// leaves as one contiguous store stream.  Equal buckets keep their input order throughout.
+// 32 in order, held in registers.  (A) count per warp and bucket with match masks, noting each
+// item's rank among the warp's items of its bucket;  (B) one thread per bucket turns the
+// counts into per-warp offsets inside the tile's bucket-ordered layout (warps in order,
+// buckets by a CTA scan);  (C) every item goes to its slot in shared memory;  (D) consecutive
+// threads copy consecutive slots out, so each bucket run of the tile leaves as one contiguous
+// store stream.  Equal buckets keep their input order throughout.
 constexpr int RX_PER_WARP = RX_TILE / RX_WARPS;  // 512
 constexpr int RX_WROUNDS = RX_PER_WARP / 32;     // 16
 __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, const int32_t *vin, int32_t *kout,
@@ -334,7 +335,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
     __shared__ int32_t sval[RX_TILE];
     __shared__ int32_t wpos[RX_WARPS][RX_BUCKETS];
     __shared__ int32_t lstart[RX_BUCKETS];
-    __shared__ int64_t gstart[RX_BUCKETS];
+    __shared__ int64_t gdelta[RX_BUCKETS];  // global position of the bucket's run minus lstart
     __shared__ int32_t wsum[RX_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -343,19 +344,26 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
     const int64_t tile0 = (int64_t)blockIdx.x * RX_TILE;
     const int64_t base = tile0 + (int64_t)warp * RX_PER_WARP;
     int32_t key[RX_WROUNDS], val[RX_WROUNDS];
+    uint32_t local[RX_WROUNDS / 2];  // rank of each item among its warp's items of its bucket (16 bits each)
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
         key[r] = (i < n) ? kin[i] : 0;
         val[r] = (i < n) ? vin[i] : 0;
     }
-    // (A)
+    // (A) counts per warp and bucket, and each item's rank among them (earlier rounds first,
+    // then lower lanes)
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
         const int b = (i < n) ? rx_bucket(key[r], dg) : RX_BUCKETS;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] += __popc(peers);
+        const int prev = b < RX_BUCKETS ? wpos[warp][b] : 0;
+        const uint32_t rank = (uint32_t)(prev + __popc(peers & lt_mask));
+        if (r & 1) local[r >> 1] |= rank << 16;
+        else local[r >> 1] = rank;
+        __syncwarp();
+        if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] = prev + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
@@ -375,35 +383,32 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
             if (lane >= o) inc += y;
         }
         if (lane == 31) wsum[warp] = inc;
-        gstart[b] = offs[(int64_t)b * ntiles + blockIdx.x];
+        const int64_t g = offs[(int64_t)b * ntiles + blockIdx.x];
         __syncthreads();
         int before = 0;
         for (int w = 0; w < warp; ++w) before += wsum[w];
-        lstart[b] = before + inc - run;
+        const int ls = before + inc - run;
+        lstart[b] = ls;
+        gdelta[b] = g - ls;
     }
     __syncthreads();
-    // (C)
+    // (C) every item to its slot of the tile's bucket-ordered layout
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
-        const int b = (i < n) ? rx_bucket(key[r], dg) : RX_BUCKETS;
-        const unsigned peers = __match_any_sync(0xffffffffu, b);
-        if (b < RX_BUCKETS) {
-            const int slot = lstart[b] + wpos[warp][b] + __popc(peers & lt_mask);
+        if (i < n) {
+            const int b = rx_bucket(key[r], dg);
+            const int slot = lstart[b] + wpos[warp][b] + (int)((local[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
             skey[slot] = key[r];
             sval[slot] = val[r];
         }
-        __syncwarp();
-        if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] += __popc(peers);
-        __syncwarp();
     }
     __syncthreads();
     // (D)
     const int count = (int)((n - tile0) < RX_TILE ? (n - tile0) : RX_TILE);
     for (int t = threadIdx.x; t < count; t += RX_THREADS) {
         const int32_t k = skey[t];
-        const int b = rx_bucket(k, dg);
-        const int64_t pos = gstart[b] + (t - lstart[b]);
+        const int64_t pos = gdelta[rx_bucket(k, dg)] + t;
         kout[pos] = k;
         vout[pos] = sval[t];
     }

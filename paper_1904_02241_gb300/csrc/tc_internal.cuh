@@ -110,6 +110,7 @@ int device_caps(DeviceCaps *caps);
 // Exclusive scan of n int32 values into int64 out (out may not alias in); writes n outputs.
 int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s);
 int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s);
+int scan_i32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t s);  // total < 2^31
 
 // Stable sort of (key, val) int32 pairs by bucket(key) for bucket values < 2^bits,
 // where bucket(key) = key / divisor (divisor >= 1).  LSD passes of 8 bits.

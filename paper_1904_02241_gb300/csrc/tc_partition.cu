@@ -14,7 +14,7 @@ __global__ void k_row_heads(const int32_t *col, const int32_t *row, int64_t E, D
     }
 }
 
-__global__ void k_fill_rows(const int32_t *head, const int64_t *rowid, const int32_t *row, int64_t E,
+__global__ void k_fill_rows(const int32_t *head, const int32_t *rowid, const int32_t *row, int64_t E,
                             int32_t *rowptr, int32_t *id_map) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
         if (head[i]) {
@@ -27,7 +27,7 @@ __global__ void k_fill_rows(const int32_t *head, const int64_t *rowid, const int
 
 // blk_edges[b] = first edge whose column is >= b*W (columns are block-major after the sort);
 // blk_rows[b] = local row of that edge (R when past the end).
-__global__ void k_block_bounds(const int32_t *col, const int64_t *rowid, const int32_t *head, int64_t E, int64_t R,
+__global__ void k_block_bounds(const int32_t *col, const int32_t *rowid, const int32_t *head, int64_t E, int64_t R,
                                int32_t W, int32_t B, int64_t *blk_edges, int64_t *blk_rows) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += gridDim.x * blockDim.x) {
         const int64_t bound = (int64_t)b * W;
@@ -181,17 +181,17 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
         }
         rows_in.release();
         TC_TRY(head.alloc((size_t)E * 4));
-        TC_TRY(rowid.alloc((size_t)E * 8));
+        TC_TRY(rowid.alloc((size_t)E * 4));  // E < 2^31: row numbers fit int32
         k_row_heads<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), rows_sorted.as<int32_t>(), E, div_by(W),
                                           head.as<int32_t>());
         TC_LAUNCH_CHECK();
-        TC_TRY(scan_i32_to_i64(head.as<int32_t>(), E, rowid.as<int64_t>(), s));
-        int64_t last_id = 0;
+        TC_TRY(scan_i32(head.as<int32_t>(), E, rowid.as<int32_t>(), s));
+        int32_t last_id = 0;
         int32_t last_head = 0;
-        TC_CUDA(cudaMemcpyAsync(&last_id, rowid.as<int64_t>() + E - 1, 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaMemcpyAsync(&last_id, rowid.as<int32_t>() + E - 1, 4, cudaMemcpyDeviceToHost, s));
         TC_CUDA(cudaMemcpyAsync(&last_head, head.as<int32_t>() + E - 1, 4, cudaMemcpyDeviceToHost, s));
         TC_CUDA(cudaStreamSynchronize(s));
-        p->R = last_id + last_head;  // rowid is an exclusive scan of the row heads
+        p->R = (int64_t)last_id + last_head;  // rowid is an exclusive scan of the row heads
     } else {
         p->R = 0;
     }
@@ -202,10 +202,10 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     TC_TRY(blk_edges.alloc(((size_t)B + 1) * 8));
     TC_TRY(blk_rows.alloc(((size_t)B + 1) * 8));
     if (E > 0) {
-        k_fill_rows<<<grid, 256, 0, s>>>(head.as<int32_t>(), rowid.as<int64_t>(), rows_sorted.as<int32_t>(), E,
+        k_fill_rows<<<grid, 256, 0, s>>>(head.as<int32_t>(), rowid.as<int32_t>(), rows_sorted.as<int32_t>(), E,
                                          p->rowptr.as<int32_t>(), p->id_map.as<int32_t>());
         TC_LAUNCH_CHECK();
-        k_block_bounds<<<(B + 256) / 256, 256, 0, s>>>(p->colidx.as<int32_t>(), rowid.as<int64_t>(), head.as<int32_t>(),
+        k_block_bounds<<<(B + 256) / 256, 256, 0, s>>>(p->colidx.as<int32_t>(), rowid.as<int32_t>(), head.as<int32_t>(),
                                                        E, R, W, B, blk_edges.as<int64_t>(), blk_rows.as<int64_t>());
         TC_LAUNCH_CHECK();
     } else {

@@ -222,10 +222,17 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const Tin *in, int6
         o[i] = run;
         run += v[i];
     }
-    if (vec && base + SCAN_ITEMS <= n) {  // 64 aligned bytes per thread: four 16-byte stores
-        longlong2 *q = reinterpret_cast<longlong2 *>(out + base);
+    if (vec && base + SCAN_ITEMS <= n) {  // 8 aligned items per thread: 16-byte stores
+        if (sizeof(Tout) == 8) {
+            longlong2 *q = reinterpret_cast<longlong2 *>(out + base);
 #pragma unroll
-        for (int i = 0; i < SCAN_ITEMS / 2; ++i) q[i] = make_longlong2(o[2 * i], o[2 * i + 1]);
+            for (int i = 0; i < SCAN_ITEMS / 2; ++i) q[i] = make_longlong2((long long)o[2 * i], (long long)o[2 * i + 1]);
+        } else {
+            int4 *q = reinterpret_cast<int4 *>(out + base);
+#pragma unroll
+            for (int i = 0; i < SCAN_ITEMS / 4; ++i)
+                q[i] = make_int4((int)o[4 * i], (int)o[4 * i + 1], (int)o[4 * i + 2], (int)o[4 * i + 3]);
+        }
     } else {
 #pragma unroll
         for (int i = 0; i < SCAN_ITEMS; ++i)
@@ -233,32 +240,35 @@ __global__ void __launch_bounds__(SCAN_THREADS) k_scan_apply(const Tin *in, int6
     }
 }
 
-template <class Tin>
-static int scan_impl(const Tin *in, int64_t n, int64_t *out, cudaStream_t s) {
+template <class Tin, class Tout>
+static int scan_impl(const Tin *in, int64_t n, Tout *out, cudaStream_t s) {
     if (n <= 0) return TC_OK;
     const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
     // vector access needs 8 items' worth of alignment on both sides
-    const bool vec = ((uintptr_t)in % (8 * sizeof(Tin))) == 0 && ((uintptr_t)out % 64) == 0;
+    const bool vec = ((uintptr_t)in % (8 * sizeof(Tin))) == 0 && ((uintptr_t)out % (8 * sizeof(Tout))) == 0;
     if (tiles == 1) {
-        k_scan_apply<Tin, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out, vec);
+        k_scan_apply<Tin, Tout><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out, vec);
         TC_LAUNCH_CHECK();
         return TC_OK;
     }
     DevBuf sums, pref;
-    TC_TRY(sums.alloc(tiles * sizeof(int64_t)));
-    TC_TRY(pref.alloc(tiles * sizeof(int64_t)));
-    k_scan_reduce<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums.as<int64_t>(), vec);
+    TC_TRY(sums.alloc(tiles * sizeof(Tout)));
+    TC_TRY(pref.alloc(tiles * sizeof(Tout)));
+    k_scan_reduce<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums.as<Tout>(), vec);
     TC_LAUNCH_CHECK();
-    TC_TRY(scan_impl<int64_t>(sums.as<int64_t>(), tiles, pref.as<int64_t>(), s));
-    k_scan_apply<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, pref.as<int64_t>(), out, vec);
+    TC_TRY((scan_impl<Tout, Tout>(sums.as<Tout>(), tiles, pref.as<Tout>(), s)));
+    k_scan_apply<Tin, Tout><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, pref.as<Tout>(), out, vec);
     TC_LAUNCH_CHECK();
     // DevBuf frees are stream-unordered: make sure the kernels using them are done.
     TC_CUDA(cudaStreamSynchronize(s));
     return TC_OK;
 }
 
-int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s) { return scan_impl<int32_t>(in, n, out, s); }
-int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s) { return scan_impl<int64_t>(in, n, out, s); }
+int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s) {
+    return scan_impl<int32_t, int64_t>(in, n, out, s);
+}
+int scan_i32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t s) { return scan_impl<int32_t, int32_t>(in, n, out, s); }
+int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s) { return scan_impl<int64_t, int64_t>(in, n, out, s); }
 
 // ----------------------------------------------------------------------------------------
 // Stable LSD bucket sort: 8-bit digits of key/divisor, 256 buckets, tiles of 4096 items.

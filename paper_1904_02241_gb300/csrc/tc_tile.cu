@@ -236,19 +236,38 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
 __global__ void k_tile_fill(const int32_t *rowptr, const int32_t *colidx, int64_t R, const int64_t *blk_rows,
                             const int64_t *blk_edges, const int64_t *pbase, int32_t B, int32_t W, uint16_t *col16,
                             uint32_t *heads32) {
-    // one thread per local row: copy its edges (block-relative sources), set its head bit
-    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
-        int32_t lo = 0, hi = B;  // block of row r: last b with blk_rows[b] <= r, non-empty
-        while (hi - lo > 1) {
-            const int32_t mid = (lo + hi) >> 1;
-            if (blk_rows[mid] <= r) lo = mid; else hi = mid;
+    // one thread per local row: copy its edges (block-relative sources), set its head bit.
+    // A warp's 32 rows are consecutive, so their head positions increase with the lane: lanes
+    // whose heads share a 32-bit word OR their bits together (segmented shuffle reduction)
+    // and one atomic per word remains.
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < R; r0 += stride) {
+        const int64_t r = r0 + lane;
+        uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past R: a group of their own, no atomic
+        if (r < R) {
+            int32_t lo = 0, hi = B;  // block of row r: last b with blk_rows[b] <= r, non-empty
+            while (hi - lo > 1) {
+                const int32_t mid = (lo + hi) >> 1;
+                if (blk_rows[mid] <= r) lo = mid; else hi = mid;
+            }
+            const int32_t b = lo;
+            const int32_t s = rowptr[r], e = rowptr[r + 1];
+            const int64_t dst = pbase[b] + (s - blk_edges[b]);
+            const int32_t base = b * W;
+            for (int32_t i = s; i < e; ++i) col16[dst + (i - s)] = (uint16_t)(colidx[i] - base);
+            word = (uint32_t)(dst >> 5);
+            bit = 1u << (dst & 31);
         }
-        const int32_t b = lo;
-        const int32_t s = rowptr[r], e = rowptr[r + 1];
-        const int64_t dst = pbase[b] + (s - blk_edges[b]);
-        const int32_t base = b * W;
-        for (int32_t i = s; i < e; ++i) col16[dst + (i - s)] = (uint16_t)(colidx[i] - base);
-        atomicOr(heads32 + (dst >> 5), 1u << (dst & 31));
+        uint32_t v = bit;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
+            const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
+            if (lane + d < 32 && wy == word) v |= y;
+        }
+        const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
+        if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
     }
 }
 

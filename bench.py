@@ -149,6 +149,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
+# of `bench.py --steps 2 --warmup 1 --quick` (one pass, full workload; the command and the
+# numbers are in profiles/launches_pagerank_pull_tocab_rmat24.md).  Keyed by kernel, R-MAT
+# scale and block count; any other workload reports null.  Must be re-captured (or removed)
+# whenever one of these kernels changes.
+NCU_TRAFFIC = {
+    ("k_tile_gather", 24, 456): 1175393024,
+    ("k_pull_merge_atomic<2>", 24, 456): 1005947904,
+}
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -259,7 +270,10 @@ def bench_tocab(args, world, rank, local):
                    "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 2)},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": None, "algorithmic_bytes": gather_bytes,
+                     "traffic": NCU_TRAFFIC.get((kname, args.scale, P.num_blocks)),
+                     "merge_traffic": NCU_TRAFFIC.get(("k_pull_merge_atomic<2>", args.scale, P.num_blocks))
+                     if args.merge == "fixed" else None,
+                     "algorithmic_bytes": gather_bytes,
                      "gather_ms": round(gather_ms, 4), "merge_ms": round(merge_ms, 4),
                      "merge_gbs": round(merge_bytes / (merge_ms * 1e-3) / 1e9, 1),
                      "iteration_bmin_frac": round(bmin / (ms_step / ITERS * 1e-3) / 1e9 / peak, 4)},

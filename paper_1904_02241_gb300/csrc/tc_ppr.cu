@@ -102,24 +102,23 @@ __global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__res
                                                             float *R_out, int32_t n,
                                                             const int32_t *__restrict__ hub_rows,
                                                             const int32_t *__restrict__ hub_piece0, int32_t nhubs,
-                                                            const float4 *__restrict__ Ppc) {
+                                                            const float4 *__restrict__ Ppc,
+                                                            const uint8_t *__restrict__ is_src) {
     constexpr int NP = 128 * NV4;
+    // per-column constants live in shared memory (registers go to rows in flight): the source
+    // vertex and teleport term of each column, and each warp's dangling sums
     __shared__ float dsh[PPR_WARPS][NP];
+    __shared__ int32_t ssrc[NP];
+    __shared__ float stele[NP];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (blockIdx.x == 0)
         for (int j = threadIdx.x; j < NP; j += PPR_THREADS) Dzero[j] = 0ull;
-    int32_t src[NV4][4];
-    float tele[NV4][4];
-    float dl[NV4][4];
-#pragma unroll
-    for (int q = 0; q < NV4; ++q)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int j = 128 * q + 4 * lane + c;
-            src[q][c] = src_of_col[j];
-            tele[q][c] = (1.0f - damping) + damping * (float)((double)Dcur[j] / PPR_FX);
-            dl[q][c] = 0.0f;
-        }
+    for (int j = threadIdx.x; j < NP; j += PPR_THREADS) {
+        ssrc[j] = src_of_col[j];
+        stele[j] = (1.0f - damping) + damping * (float)((double)Dcur[j] / PPR_FX);
+    }
+    for (int j = lane; j < NP; j += 32) dsh[warp][j] = 0.0f;
+    __syncthreads();
     const int64_t nw = (int64_t)gridDim.x * PPR_WARPS;
     // the hub rows (finished from their pieces) come first, then every other row
     for (int64_t w = (int64_t)blockIdx.x * PPR_WARPS + warp; w < (int64_t)V + nhubs; w += nw) {
@@ -146,13 +145,15 @@ __global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__res
             ppr_row_sum<NV4>(colidx, s, e, C, lane, acc);
         }
         const float inv = __ldg(inv_outdeg + v);
+        const bool vsrc = __ldg(is_src + v) != 0;  // the same byte for the whole warp
 #pragma unroll
         for (int q = 0; q < NV4; ++q) {
             float r[4] = {acc[q].x, acc[q].y, acc[q].z, acc[q].w};
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                r[c] = damping * r[c] + (src[q][c] == (int32_t)v ? tele[q][c] : 0.0f);
-                if (inv == 0.0f) dl[q][c] += r[c];
+                const int j = 128 * q + 4 * lane + c;
+                r[c] = damping * r[c] + ((vsrc && ssrc[j] == (int32_t)v) ? stele[j] : 0.0f);
+                if (inv == 0.0f) dsh[warp][j] += r[c];  // lane-owned columns: no race
             }
             Cn[v * (NP / 4) + 32 * q + lane] = make_float4(r[0] * inv, r[1] * inv, r[2] * inv, r[3] * inv);
             if (R_out) {
@@ -165,10 +166,6 @@ __global__ void __launch_bounds__(PPR_THREADS) k_ppr_gather(const int32_t *__res
         }
     }
     // per-column dangling sums: warps -> shared -> one fixed-point atomic per column per CTA
-#pragma unroll
-    for (int q = 0; q < NV4; ++q)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) dsh[warp][128 * q + 4 * lane + c] = dl[q][c];
     __syncthreads();
     for (int j = threadIdx.x; j < NP; j += PPR_THREADS) {
         float t = 0.0f;
@@ -327,6 +324,11 @@ __global__ void __launch_bounds__(PT_THREADS) k_ppr_tile_merge(const float *__re
     }
 }
 
+__global__ void k_mark_sources(const int32_t *src_of_col, int32_t NP, uint8_t *is_src) {
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < NP; j += gridDim.x * blockDim.x)
+        if (src_of_col[j] >= 0) is_src[src_of_col[j]] = 1;
+}
+
 struct Hubs {
     const int32_t *rows, *piece0;
     const int2 *pieces;
@@ -337,7 +339,7 @@ struct Hubs {
 template <int NV4>
 static void launch_ppr(int grid, cudaStream_t s, const tc_graph *g, const float *C, float *Cn, const int32_t *srcc,
                        const unsigned long long *Dc, unsigned long long *Dn, unsigned long long *Dz, float d,
-                       float *R_out, int32_t n, const Hubs &h) {
+                       float *R_out, int32_t n, const Hubs &h, const uint8_t *is_src) {
     if (h.npieces > 0)
         k_ppr_piece<NV4><<<grid, PPR_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), h.pieces,
                                                      h.npieces, reinterpret_cast<const float4 *>(C),
@@ -345,7 +347,7 @@ static void launch_ppr(int grid, cudaStream_t s, const tc_graph *g, const float 
     k_ppr_gather<NV4><<<grid, PPR_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), g->V,
                                                   reinterpret_cast<const float4 *>(C), reinterpret_cast<float4 *>(Cn),
                                                   srcc, Dc, Dn, Dz, g->inv_outdeg.as<float>(), d, R_out, n, h.rows,
-                                                  h.piece0, h.nhubs, reinterpret_cast<const float4 *>(h.Ppc));
+                                                  h.piece0, h.nhubs, reinterpret_cast<const float4 *>(h.Ppc), is_src);
 }
 
 __global__ void k_row_bounds(const int32_t *rowptr, const int32_t *rows, int32_t n, int32_t *out) {
@@ -527,9 +529,14 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
         }
     }
     Hubs hubs;
-    DevBuf hub_list, hub_rows, hub_p0, hub_pcs, hub_ppc;
+    DevBuf hub_list, hub_rows, hub_p0, hub_pcs, hub_ppc, isrc;
     int32_t nh = 0;
     if (!part) {
+        // one byte per vertex: 1 where some column teleports to it
+        TC_TRY(isrc.alloc((size_t)V));
+        TC_CUDA(cudaMemsetAsync(isrc.p, 0, (size_t)V, s));
+        k_mark_sources<<<(NP + 255) / 256, 256, 0, s>>>(srcbuf.as<int32_t>(), NP, isrc.as<uint8_t>());
+        TC_LAUNCH_CHECK();
         TC_TRY(collect_hubs(g->in_rowptr.as<int32_t>(), g->V, PPR_PIECE, &hub_list, &nh, s));
         TC_TRY(build_pieces(g->in_rowptr.as<int32_t>(), hub_list.as<int32_t>(), nh, NP, &hub_rows, &hub_p0, &hub_pcs,
                             &hub_ppc, &hubs, s));
@@ -541,10 +548,14 @@ static int ppr_impl(const tc_graph *cg, const tc_part *part, const int32_t *sour
         float *Cn = Cm[(it + 1) & 1];
         unsigned long long *Dc = D[it % 3], *Dn = D[(it + 1) % 3], *Dz = D[(it + 2) % 3];
         switch (NV4) {
-            case 1: launch_ppr<1>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
-            case 2: launch_ppr<2>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
-            case 4: launch_ppr<4>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
-            default: launch_ppr<8>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs); break;
+            case 1: launch_ppr<1>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs,
+                                    isrc.as<uint8_t>()); break;
+            case 2: launch_ppr<2>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs,
+                                    isrc.as<uint8_t>()); break;
+            case 4: launch_ppr<4>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs,
+                                    isrc.as<uint8_t>()); break;
+            default: launch_ppr<8>(grid, s, g, Cc, Cn, srcbuf.as<int32_t>(), Dc, Dn, Dz, pp->damping, Rw, n, hubs,
+                                    isrc.as<uint8_t>()); break;
         }
         TC_LAUNCH_CHECK();
         ++launches;

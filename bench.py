@@ -298,20 +298,31 @@ def variants(args, ctx, world):
         torch.cuda.synchronize()
         return statistics.median(time_runs(fn, steps, stream))
 
+    peak, _ = load_peaks()
+    V = g.V
+    bmin = 4 * E + 4 * (V + 1) + 12 * V  # method-independent bytes of one iteration
+
+    def bmin_frac(ms_run):
+        return round(bmin / (ms_run / ITERS * 1e-3) / 1e9 / peak, 4)
+
     ms = run(lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out))
     res["pull_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res["pull_unblocked_bmin_frac"] = bmin_frac(ms)
     res["pull_tocab_blocks"] = P.num_blocks
     other = "l2" if args.policy == "smem" else "smem"
     Po = T.tocab_partition(G, T.TC_PULL, 0, block_policy=other)
     ms = run(lambda: T.pagerank_pull(G, Po, damping=DAMPING, iters=ITERS, out=out))
     res[f"pull_tocab_{other}_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res[f"pull_tocab_{other}_bmin_frac"] = bmin_frac(ms)
     res[f"pull_tocab_{other}_blocks"] = Po.num_blocks
     del Po
     Pp = T.tocab_partition(G, T.TC_PUSH, args.blocks, block_policy="l2")
     ms = run(lambda: T.pagerank_push(G, Pp, damping=DAMPING, iters=ITERS, out=out))
     res["push_tocab_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res["push_tocab_bmin_frac"] = bmin_frac(ms)
     ms = run(lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))
     res["push_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res["push_unblocked_bmin_frac"] = bmin_frac(ms)
     del Pp
     # BFS on the symmetrised graph, 64 seeded sources (TEPS counts each undirected edge once)
     gs = gg.symmetrize(g)
@@ -337,7 +348,45 @@ def variants(args, ctx, world):
     res["bfs_graph"] = {"V": gs.V, "E_directed": gs.E, "sources": len(srcs)}
     del Gs, Ps, gs, lv
     torch.cuda.empty_cache()
+    # block-count sweep around the L2 capacity (paper's source-range blocks, unstaged gather)
+    sweep = {}
+    for B in (1, 2, 4, 8, 16, 32, 64):
+        Pb = T.tocab_partition(G, T.TC_PULL, B)
+        ms = run(lambda: T.pagerank_pull(G, Pb, damping=DAMPING, iters=ITERS, out=out))
+        sweep[str(B)] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+        del Pb
+    res["pull_tocab_block_sweep_gteps"] = sweep
+    torch.cuda.empty_cache()
+    res.update(graph_variants(args, stream, E, run))
     res.update(batch_variants(args, stream))
+    return res
+
+
+def graph_variants(args, stream, E_rmat, run):
+    """The other two graph shapes of the PageRank workload: an Erdos-Renyi graph with the R-MAT's
+    vertex and edge count, and the 4096 x 4096 grid with 5% of its edges removed.  Pull TOCAB
+    (the default block policy), unblocked pull and unblocked push on each."""
+    import paper_1904_02241_gb300 as T
+    peak, _ = load_peaks()
+    res = {}
+    V24 = 1 << args.scale
+    for name, make in (("er", lambda: gg.erdos_renyi(V24, E_rmat, seed=3, device="cuda")),
+                       ("grid4096", lambda: gg.grid2d(4096, 4096, drop=0.05, seed=11, device="cuda"))):
+        g = make()
+        G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+        P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy)
+        out = torch.empty(g.V, dtype=torch.float32, device="cuda")
+        bmin = 4 * g.E + 4 * (g.V + 1) + 12 * g.V
+        row = {"V": g.V, "E": g.E, "blocks": P.num_blocks}
+        for key, fn in (("pull_tocab", lambda: T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out)),
+                        ("pull_unblocked", lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out)),
+                        ("push_unblocked", lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))):
+            ms = run(fn)
+            row[key + "_gteps"] = round(g.E * ITERS / (ms * 1e-3) / 1e9, 2)
+            row[key + "_bmin_frac"] = round(bmin / (ms / ITERS * 1e-3) / 1e9 / peak, 4)
+        res[name] = row
+        del P, G, g, out
+        torch.cuda.empty_cache()
     return res
 
 
@@ -354,10 +403,18 @@ def batch_variants(args, stream):
     T.ppr_batch(G22, srcs, iters=ITERS, out=R)
     torch.cuda.synchronize()
     ms = statistics.median(time_runs(lambda: T.ppr_batch(G22, srcs, iters=ITERS, out=R), 3, stream))
-    res["ppr_batch"] = {"graph": "rmat22", "V": g22.V, "E": g22.E, "sources": 256, "iters": ITERS,
+    peak, _ = load_peaks()
+    V22, E22, NP = g22.V, g22.E, 256
+    # bytes of one iteration: without reuse every in-edge reads its source's 1 KB row; the
+    # floor reads every row once (the whole [V x 256] matrix in, the next one out)
+    row_bytes = 4 * E22 + 4 * (V22 + 1) + 4 * NP * E22 + 8 * V22 * NP
+    floor_bytes = 4 * E22 + 4 * V22 + 2 * 4 * NP * V22
+    res["ppr_batch"] = {"graph": "rmat22", "V": V22, "E": E22, "sources": 256, "iters": ITERS,
                         "ms": round(ms, 2), "ms_per_iter": round(ms / ITERS, 3),
-                        "edge_columns_per_s_G": round(g22.E * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
-                        "gteps_equiv": round(g22.E * ITERS / (ms * 1e-3) / 1e9, 3)}
+                        "edge_columns_per_s_G": round(E22 * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
+                        "gteps_equiv": round(E22 * ITERS / (ms * 1e-3) / 1e9, 3),
+                        "row_bytes_frac": round(row_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4),
+                        "floor_bytes_frac": round(floor_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4)}
     # TOCAB per 32-column tile: source blocks whose 128-byte row segments fit in L2
     P22 = T.tocab_partition(G22, T.TC_PULL, 0, l2_fraction=1.0 / 88, merge_range=256)
     T.ppr_batch(G22, srcs, iters=ITERS, out=R, part=P22)
@@ -366,7 +423,8 @@ def batch_variants(args, stream):
     res["ppr_batch_tocab"] = {"blocks": P22.num_blocks, "block_width": P22.block_width, "ms": round(ms, 2),
                               "ms_per_iter": round(ms / ITERS, 3),
                               "edge_columns_per_s_G": round(g22.E * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
-                              "gteps_equiv": round(g22.E * ITERS / (ms * 1e-3) / 1e9, 3)}
+                              "gteps_equiv": round(g22.E * ITERS / (ms * 1e-3) / 1e9, 3),
+                              "floor_bytes_frac": round(floor_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4)}
     del R, G22, g22, P22
     torch.cuda.empty_cache()
     scales = gg.batch_scales(1000, 10, 16, seed=19)
@@ -380,6 +438,7 @@ def batch_variants(args, stream):
     res["many_graphs"] = {"graphs": 1000, "scales": "U{10..16}", "V": gb.V, "E": gb.E, "iters": ITERS,
                           "autotuned_lanes_per_vertex": best, "autotune_ms": {str(k): round(v, 3) for k, v in times.items()},
                           "ms": round(ms, 3), "gteps": round(gb.E * ITERS / (ms * 1e-3) / 1e9, 2),
+                          "bmin_frac": round((4 * gb.E + 4 * (gb.V + 1) + 12 * gb.V) / (ms / ITERS * 1e-3) / 1e9 / peak, 4),
                           "launches_per_run": 1, "cuda_graph": True}
     del M, gb, out
     torch.cuda.empty_cache()
@@ -408,7 +467,22 @@ def e2e(args, ctx):
         times.append(t0.elapsed_time(t1))
         del P2, G2
     ms = statistics.median(times)
+    # the one-time preprocessing on its own (inputs already on the device)
+    tl, tp = [], []
+    for i in range(3):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        G2 = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks, block_policy=args.policy)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        tl.append((t1 - t0) * 1e3)
+        tp.append((t2 - t1) * 1e3)
+        del P2, G2
     return {"value": round(g.E * ITERS / (ms * 1e-3) / 1e9, 3), "unit": "GTEPS",
+            "load_transpose_ms": round(statistics.median(tl), 2), "partition_ms": round(statistics.median(tp), 2),
             "h2d_bytes_per_step": int(rp_h.numel() * 4 + ci_h.numel() * 4),
             "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": round(ms, 3),
             "includes": "H2D CSR + load/transpose + partition + 20 iters + D2H ranks"}

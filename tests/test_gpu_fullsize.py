@@ -1,0 +1,127 @@
+"""Full-size parity: the workloads the benchmark times, in the launch configuration it times them
+in, checked against the FP64 oracle on the host cores.  Every output is checked where the oracle
+(OpenMP over destinations) finishes in seconds; PPR columns and the many-graph batch are checked
+on a seeded sample.  Invariants (mass conservation, run-to-run identity) are checked beside.
+The small configuration (R-MAT 16, unblocked and 4 source-range blocks) is checked in full."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+from gpu_util import l1_rel
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-5
+CORES = os.cpu_count() or 1
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_02241_gb300 as T
+    T.lib()
+    oracle.build()
+    return T
+
+
+def _load(T, g):
+    return T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+
+
+def test_rmat16_unblocked_and_four_blocks(T):
+    """R-MAT 16 (V = 65,536, ~1M edges): unblocked pull and TOCAB with 4 source-range blocks."""
+    g = gg.rmat(16)
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    want = oracle.pagerank_pull(g.V, rp, ci, nthreads=CORES)
+    assert l1_rel(T.pagerank_pull(G, None).cpu().numpy(), want) <= TOL
+    P = T.tocab_partition(G, T.TC_PULL, 4)
+    assert P.num_blocks == 4
+    assert l1_rel(T.pagerank_pull(G, P).cpu().numpy(), want) <= TOL
+    assert l1_rel(T.pagerank_push(G, None).cpu().numpy(), want) <= TOL
+
+
+@pytest.fixture(scope="module")
+def rmat24(T):
+    g = gg.rmat(24, device="cuda")
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    rp, ci = g.numpy()
+    tr = oracle.transpose(g.V, rp, ci)
+    return g, G, rp, ci, tr
+
+
+def test_rmat24_transpose_bit_exact(T, rmat24):
+    g, G, rp, ci, tr = rmat24
+    grp, gci = G.export_transpose()
+    np.testing.assert_array_equal(grp.numpy(), tr[0])
+    np.testing.assert_array_equal(gci.numpy(), tr[1])
+
+
+def test_rmat24_pagerank_in_the_benchmark_configuration(T, rmat24):
+    """Shared-memory blocks (B = 456 on GB300), fixed-point merge, 20 iterations: every rank
+    against the oracle, mass 1, and bit-identical reruns."""
+    g, G, rp, ci, tr = rmat24
+    want = oracle.pagerank_pull(g.V, rp, ci, nthreads=CORES, transposed=tr)
+    P = T.tocab_partition(G, T.TC_PULL, 0, block_policy="smem")
+    assert P.staged
+    r1 = T.pagerank_pull(G, P, merge="fixed")
+    r2 = T.pagerank_pull(G, P, merge="fixed")
+    got = r1.cpu().numpy()
+    assert l1_rel(got, want) <= TOL
+    assert abs(float(np.sum(got, dtype=np.float64)) - 1.0) < 1e-4
+    assert torch.equal(r1, r2)
+    assert l1_rel(T.pagerank_pull(G, None).cpu().numpy(), want) <= TOL
+
+
+def test_rmat24_bfs_bit_exact(T, rmat24):
+    """Symmetrised R-MAT 24 (~521M directed edges), two seeded sources, direction-optimised with
+    and without TOCAB pull levels, and pure pull."""
+    g = rmat24[0]
+    gs = gg.symmetrize(g)
+    Gs = T.graph_load_csr(gs.rowptr, gs.colidx, V=gs.V)
+    Ps = T.tocab_partition(Gs, T.TC_PULL, 0, block_policy="l2")
+    rp, ci = gs.numpy()
+    for s in gg.sources(gs, 2, seed=13):
+        want = oracle.bfs(gs.V, rp, ci, s)
+        for thr, push in [(0.05, 1.0 / 24), (-1.0, 1.0 / 24), (0.05, 0.0)]:
+            lv, st = T.bfs_pull(Gs, Ps, s, tocab_threshold=thr, push_threshold=push, return_stats=True)
+            np.testing.assert_array_equal(lv.cpu().numpy(), want)
+            assert st.reached == int((want >= 0).sum())
+
+
+def test_rmat22_ppr_batch_sampled_columns(T):
+    """256 sources on R-MAT 22 in one [V x 256] batch: four seeded columns against the oracle
+    (columns are independent problems)."""
+    g = gg.rmat(22, device="cuda")
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    srcs = gg.sources(g, 256, seed=17)
+    R = T.ppr_batch(G, srcs, iters=20).cpu().numpy()
+    cols = [0, 85, 170, 255]
+    rp, ci = g.numpy()
+    want = oracle.ppr_pull(g.V, rp, ci, [srcs[j] for j in cols], iters=20)
+    for k, j in enumerate(cols):
+        assert l1_rel(R[:, j], want[:, k]) <= TOL, j
+
+
+def test_thousand_graphs_sampled(T):
+    """1,000 R-MAT graphs (scales 10-16) in one persistent launch: 24 seeded graphs against the
+    oracle one by one, and every graph's mass."""
+    scales = gg.batch_scales(1000, 10, 16, seed=19)
+    gb, off = gg.rmat_batch(scales, seed=19, device="cuda")
+    M = T.multigraph_load(gb.rowptr, gb.colidx, off)
+    r = T.pagerank_multi(M, iters=20).cpu().numpy()
+    rp, ci = gb.numpy()
+    off = off.cpu().numpy().astype(np.int64)
+    pick = np.random.default_rng(23).choice(len(off) - 1, size=24, replace=False)
+    for k in pick:
+        lo, hi = int(off[k]), int(off[k + 1])
+        sub_rp = rp[lo:hi + 1] - rp[lo]
+        sub_ci = ci[rp[lo]:rp[hi]] - lo
+        want = oracle.pagerank_pull(hi - lo, sub_rp, sub_ci)
+        assert l1_rel(r[lo:hi], want) <= TOL, k
+    sums = np.add.reduceat(r.astype(np.float64), off[:-1])
+    assert np.all(np.abs(sums - 1.0) < 1e-4)

@@ -90,12 +90,6 @@ struct TileArgs {
     int *err;
 };
 
-// Segmented-scan element: flag = "a row starts inside this piece", val = open-row value.
-__device__ __forceinline__ void seg_combine(bool &f, float &v, bool fp, float vp) {
-    // (fp, vp) precedes (f, v): if this piece restarts, keep it; else add the earlier value
-    if (!f) v += vp;
-    f = f || fp;
-}
 
 __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -175,16 +169,17 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
                 val[i] = ((valid >> i) & 1u) ? slice[col] : 0.0f;
             }
         }
-        // rows of this chunk: exclusive scan of head counts over lanes
+        // rows of this chunk: exclusive scan of head counts over lanes, from bit-sliced ballots
+        // of the counts (at most 16, so five slices) instead of shuffles
         const int nh_l = __popc(hd);
-        int incl = nh_l;
+        const uint32_t lt_mask = (1u << lane) - 1u;
+        int before = 0, total = 0;  // heads in earlier lanes; heads in the chunk
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
+        for (int bit = 0; bit < 5; ++bit) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (nh_l >> bit) & 1);
+            before += __popc(m & lt_mask) << bit;
+            total += __popc(m) << bit;
         }
-        const int before = incl - nh_l;                       // heads in earlier lanes
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
         // walk the lane's 16 edges (branch-free): the piece before the first head goes to the
         // carry scan; every later head closes a whole row, written to the stage
         float seg = 0.0f, first = 0.0f;
@@ -200,19 +195,23 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
         }
         const bool seen = seenm != 0u;
         if (!seen) first = seg;
-        // carry of the open row across lanes: segmented inclusive scan
-        bool f = seen;
-        float v = seen ? seg : first;
+        // carry of the open row across lanes: segmented inclusive scan (Hillis-Steele). The
+        // flag of lane l after the step of distance d is "a head in lanes (l - 2d, l]", read
+        // from one ballot of the heads instead of being shuffled along with the values.
+        const uint32_t F = __ballot_sync(0xffffffffu, seen);
+        float v = seg;  // the open row's value at the lane's end (== first when no head)
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const bool fp = __shfl_up_sync(0xffffffffu, f, d);
             const float vp = __shfl_up_sync(0xffffffffu, v, d);
-            if (lane >= d) seg_combine(f, v, fp, vp);
+            const int lo = lane - d + 1;  // flag window of this lane before the step: [lo, lane]
+            const uint32_t win = lo > 0 ? (F >> lo) & ((1u << d) - 1u) : F & ((2u << lane) - 1u);
+            if (lane >= d && win == 0u) v += vp;
         }
+        const bool f = (F & ((2u << lane) - 1u)) != 0u;  // a head in lanes [0, lane]
         // open-row value at the end of lane l: f ? v : carry + v (no head yet: the chunk's
         // carry flows through); the row closed at lane l's first head gets X(l-1) + first
         const float vprev = __shfl_up_sync(0xffffffffu, v, 1);
-        const bool fprev = __shfl_up_sync(0xffffffffu, f, 1);
+        const bool fprev = (F & lt_mask) != 0u;
         const float xprev = (lane == 0) ? carry : (fprev ? vprev : carry + vprev);
         if (seen) stage[before] = xprev + first;
         const float xlast = __shfl_sync(0xffffffffu, f ? v : carry + v, 31);

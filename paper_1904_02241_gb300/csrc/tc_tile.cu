@@ -26,10 +26,14 @@ constexpr int TWARPS = TILE_THREADS / 32;
 
 __host__ __device__ static inline size_t slice_bytes(int32_t W) { return ((size_t)W * 4 + 127) / 128 * 128; }
 
-size_t tile_smem_bytes(int32_t W) { return slice_bytes(W) + (size_t)TWARPS * WCH * 4; }
+// per warp: WCH rows of stage plus 4 floats, so that the stage can be shifted to the alignment
+// of the global rows it holds (bulk stores need matching 16-byte alignment on both sides)
+constexpr int WSTAGE = WCH + 4;
+
+size_t tile_smem_bytes(int32_t W) { return slice_bytes(W) + (size_t)TWARPS * WSTAGE * 4; }
 
 int32_t tile_max_width(int max_smem_optin) {
-    const int64_t budget = (int64_t)max_smem_optin - 1024 - (int64_t)TWARPS * WCH * 4;
+    const int64_t budget = (int64_t)max_smem_optin - 1024 - (int64_t)TWARPS * WSTAGE * 4;
     int64_t W = budget / 4;
     W = W / 32 * 32;
     if (W > 65536) W = 65536;
@@ -80,6 +84,21 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t by
         : "memory");
 }
 
+// Bulk store shared -> global (TMA unit), one per call, committed as its own group; both
+// addresses 16-byte aligned and the size a multiple of 16.
+__device__ __forceinline__ void bulk_store_s2g(void *gdst, const void *ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+// Waits until this thread's bulk stores have read their shared-memory sources.
+__device__ __forceinline__ void bulk_store_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+// Waits until this thread's bulk stores are complete.
+__device__ __forceinline__ void bulk_store_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+// Orders this thread's generic-proxy shared-memory writes before later bulk-copy reads.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
 struct TileArgs {
     const uint16_t *col16;
     const uint16_t *heads;
@@ -97,7 +116,7 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t b = blockIdx.x;
     float *slice = reinterpret_cast<float *>(smem);
-    float *stage = reinterpret_cast<float *>(smem + slice_bytes(t.W)) + warp * WCH;
+    float *stage_base = reinterpret_cast<float *>(smem + slice_bytes(t.W)) + warp * WSTAGE;
 
     // ---- the block's contributions -> shared memory (bulk copies on one mbarrier) ----
     if (tid == 0) {
@@ -182,18 +201,23 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
         }
         // walk the lane's 16 edges (branch-free): the piece before the first head goes to the
         // carry scan; every later head closes a whole row, written to the stage
+        // stage[i] holds row rowbase - 1 + i; it starts (rowbase - 1) mod 4 floats into the
+        // warp's buffer so that stage and partial[] agree modulo 16 bytes.  The previous
+        // chunk's bulk store must have finished reading the buffer before it is rewritten.
+        float *stage = stage_base + ((rowbase - 1) & 3);
+        if (lane == 0) bulk_store_wait_read();
+        __syncwarp();
         float seg = 0.0f, first = 0.0f;
         float *out = stage + before + 1;
-        uint32_t seenm = 0u;  // all ones once a head has been seen
+        const uint32_t close_m = hd & (hd - 1u);  // heads after the lane's first: each closes a row
+        const uint32_t first_m = hd & (0u - hd);  // the lane's first head
 #pragma unroll
         for (int i = 0; i < 16; ++i) {
-            const uint32_t h = 0u - ((hd >> i) & 1u);  // all ones at a head
-            if (h & seenm) *out++ = seg;               // close the row before this head
-            first = (h & ~seenm) ? seg : first;
-            seenm |= h;
-            seg = h ? val[i] : seg + val[i];
+            if ((close_m >> i) & 1u) *out++ = seg;  // close the row before this head
+            if ((first_m >> i) & 1u) first = seg;   // the piece before the first head
+            seg = ((hd >> i) & 1u) ? val[i] : seg + val[i];
         }
-        const bool seen = seenm != 0u;
+        const bool seen = hd != 0u;
         if (!seen) first = seg;
         // carry of the open row across lanes: segmented inclusive scan (Hillis-Steele). The
         // flag of lane l after the step of distance d is "a head in lanes (l - 2d, l]", read
@@ -215,18 +239,30 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
         const float xprev = (lane == 0) ? carry : (fprev ? vprev : carry + vprev);
         if (seen) stage[before] = xprev + first;
         const float xlast = __shfl_sync(0xffffffffu, f ? v : carry + v, 31);
+        // Rows rowbase - 1 + [i0, total) leave: stage[0] is the open row only when it belongs
+        // to this warp.  The 16-byte aligned middle goes out as one bulk store (TMA) issued by
+        // lane 0 after every lane's proxy fence; the at most 3 + 3 rows at the ends are plain
+        // stores.
+        fence_proxy_async_smem();
         __syncwarp();
-        // stage[i] holds row (rowbase - 1 + i) for i < total; stage[0] is the open row only
-        // when it belongs to this warp
-        for (int i = lane; i < total; i += 32) {
-            if (i > 0 || open) t.partial[rowbase - 1 + i] = stage[i];
+        {
+            const int32_t r0 = rowbase - 1;
+            const int32_t g0 = r0 + (open ? 0 : 1), g1 = r0 + total;
+            const int32_t ga = (g0 + 3) & ~3, gb = g1 & ~3;
+            if (g1 < ga) {  // no aligned group of 4 inside
+                if (g0 + lane < g1) t.partial[g0 + lane] = stage[g0 + lane - r0];
+            } else {
+                if (g0 + lane < ga) t.partial[g0 + lane] = stage[g0 + lane - r0];
+                if (gb + lane < g1) t.partial[gb + lane] = stage[gb + lane - r0];
+                if (gb > ga && lane == 0) bulk_store_s2g(t.partial + ga, stage + (ga - r0), (uint32_t)(gb - ga) * 4u);
+            }
         }
-        __syncwarp();
         if (total > 0) open = true;
         rowbase += total;
         carry = xlast;
     }
     if (open && lane == 0) t.partial[rowbase - 1] = carry;
+    if (lane == 0) bulk_store_wait_all();
 }
 
 // ---------------------------------------------------------------------------------------------

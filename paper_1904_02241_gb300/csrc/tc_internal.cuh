@@ -111,6 +111,9 @@ int device_caps(DeviceCaps *caps);
 int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s);
 int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s);
 int scan_i32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t s);  // total < 2^31
+int head_tiles(const uint8_t *head, int64_t E, DevBuf *prefix, int64_t *R, cudaStream_t s);
+int head_fill(const uint8_t *head, int64_t E, const int32_t *prefix, const int32_t *row, int32_t *rowptr,
+              int32_t *id_map, cudaStream_t s);
 
 // Stable sort of (key, val) int32 pairs by bucket(key) for bucket values < 2^bits,
 // where bucket(key) = key / divisor (divisor >= 1).  LSD passes of 8 bits.

@@ -6,29 +6,18 @@
 namespace tc {
 
 // head[i] = 1 when edge i starts a new local row: first edge, new block or new row.
-__global__ void k_row_heads(const int32_t *col, const int32_t *row, int64_t E, DivBy W, int32_t *head) {
+__global__ void k_row_heads(const int32_t *col, const int32_t *row, int64_t E, DivBy W, uint8_t *head) {
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
-        int32_t h = 1;
+        bool h = true;
         if (i > 0) h = (div_apply(col[i], W) != div_apply(col[i - 1], W)) || (row[i] != row[i - 1]);
-        head[i] = h;
-    }
-}
-
-__global__ void k_fill_rows(const int32_t *head, const int32_t *rowid, const int32_t *row, int64_t E,
-                            int32_t *rowptr, int32_t *id_map) {
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < E; i += (int64_t)gridDim.x * blockDim.x) {
-        if (head[i]) {
-            const int64_t r = rowid[i];
-            rowptr[r] = (int32_t)i;
-            id_map[r] = row[i];
-        }
+        head[i] = h ? 1 : 0;
     }
 }
 
 // blk_edges[b] = first edge whose column is >= b*W (columns are block-major after the sort);
-// blk_rows[b] = local row of that edge (R when past the end).
-__global__ void k_block_bounds(const int32_t *col, const int32_t *rowid, const int32_t *head, int64_t E, int64_t R,
-                               int32_t W, int32_t B, int64_t *blk_edges, int64_t *blk_rows) {
+// blk_rows[b] = the local row starting at that edge (every block starts a row), R past the end.
+__global__ void k_block_bounds(const int32_t *col, const int32_t *rowptr, int64_t E, int64_t R, int32_t W, int32_t B,
+                               int64_t *blk_edges, int64_t *blk_rows) {
     for (int b = blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += gridDim.x * blockDim.x) {
         const int64_t bound = (int64_t)b * W;
         int64_t lo = 0, hi = E;
@@ -37,8 +26,12 @@ __global__ void k_block_bounds(const int32_t *col, const int32_t *rowid, const i
             if ((int64_t)col[mid] < bound) lo = mid + 1; else hi = mid;
         }
         blk_edges[b] = lo;
-        blk_rows[b] = (lo < E) ? rowid[lo] : R;
-        (void)head;
+        int64_t rl = 0, rh = R;  // first row whose first edge is >= lo
+        while (rl < rh) {
+            const int64_t mid = (rl + rh) >> 1;
+            if ((int64_t)rowptr[mid] < lo) rl = mid + 1; else rh = mid;
+        }
+        blk_rows[b] = rl;
     }
 }
 
@@ -163,7 +156,7 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     const int grid = caps.sms * 8;
 
     TC_TRY(p->colidx.alloc((size_t)E * 4));
-    DevBuf rows_sorted, rows_in, head, rowid, ktmp, vtmp;
+    DevBuf rows_sorted, rows_in, head, head_prefix, ktmp, vtmp;
     TC_TRY(rows_sorted.alloc((size_t)E * 4));
     if (E > 0) {
         TC_TRY(rows_in.alloc((size_t)E * 4));
@@ -180,18 +173,11 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
             TC_CUDA(cudaMemcpyAsync(rows_sorted.p, rows_in.p, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
         }
         rows_in.release();
-        TC_TRY(head.alloc((size_t)E * 4));
-        TC_TRY(rowid.alloc((size_t)E * 4));  // E < 2^31: row numbers fit int32
+        TC_TRY(head.alloc((size_t)E + 8));
         k_row_heads<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), rows_sorted.as<int32_t>(), E, div_by(W),
-                                          head.as<int32_t>());
+                                          head.as<uint8_t>());
         TC_LAUNCH_CHECK();
-        TC_TRY(scan_i32(head.as<int32_t>(), E, rowid.as<int32_t>(), s));
-        int32_t last_id = 0;
-        int32_t last_head = 0;
-        TC_CUDA(cudaMemcpyAsync(&last_id, rowid.as<int32_t>() + E - 1, 4, cudaMemcpyDeviceToHost, s));
-        TC_CUDA(cudaMemcpyAsync(&last_head, head.as<int32_t>() + E - 1, 4, cudaMemcpyDeviceToHost, s));
-        TC_CUDA(cudaStreamSynchronize(s));
-        p->R = (int64_t)last_id + last_head;  // rowid is an exclusive scan of the row heads
+        TC_TRY(head_tiles(head.as<uint8_t>(), E, &head_prefix, &p->R, s));
     } else {
         p->R = 0;
     }
@@ -202,11 +188,10 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     TC_TRY(blk_edges.alloc(((size_t)B + 1) * 8));
     TC_TRY(blk_rows.alloc(((size_t)B + 1) * 8));
     if (E > 0) {
-        k_fill_rows<<<grid, 256, 0, s>>>(head.as<int32_t>(), rowid.as<int32_t>(), rows_sorted.as<int32_t>(), E,
-                                         p->rowptr.as<int32_t>(), p->id_map.as<int32_t>());
-        TC_LAUNCH_CHECK();
-        k_block_bounds<<<(B + 256) / 256, 256, 0, s>>>(p->colidx.as<int32_t>(), rowid.as<int32_t>(), head.as<int32_t>(),
-                                                       E, R, W, B, blk_edges.as<int64_t>(), blk_rows.as<int64_t>());
+        TC_TRY(head_fill(head.as<uint8_t>(), E, head_prefix.as<int32_t>(), rows_sorted.as<int32_t>(),
+                         p->rowptr.as<int32_t>(), p->id_map.as<int32_t>(), s));
+        k_block_bounds<<<(B + 256) / 256, 256, 0, s>>>(p->colidx.as<int32_t>(), p->rowptr.as<int32_t>(), E, R, W, B,
+                                                       blk_edges.as<int64_t>(), blk_rows.as<int64_t>());
         TC_LAUNCH_CHECK();
     } else {
         TC_CUDA(cudaMemsetAsync(blk_edges.p, 0, ((size_t)B + 1) * 8, s));

@@ -164,7 +164,14 @@ template <class Tin, class Tout>
 __device__ __forceinline__ void load_items(const Tin *in, int64_t n, int64_t base, bool vec, Tout (&v)[SCAN_ITEMS]) {
     static_assert(SCAN_ITEMS == 8, "vector loads assume 8 items");
     if (vec && base + SCAN_ITEMS <= n) {
-        if (sizeof(Tin) == 4) {
+        if (sizeof(Tin) == 1) {
+            const uint2 w = *reinterpret_cast<const uint2 *>(in + base);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                v[i] = (Tout)((w.x >> (8 * i)) & 0xFFu);
+                v[4 + i] = (Tout)((w.y >> (8 * i)) & 0xFFu);
+            }
+        } else if (sizeof(Tin) == 4) {
             const int4 *p = reinterpret_cast<const int4 *>(in + base);
             const int4 a = p[0], b = p[1];
             const int32_t w[8] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w};
@@ -261,6 +268,59 @@ static int scan_impl(const Tin *in, int64_t n, Tout *out, cudaStream_t s) {
     TC_LAUNCH_CHECK();
     // DevBuf frees are stream-unordered: make sure the kernels using them are done.
     TC_CUDA(cudaStreamSynchronize(s));
+    return TC_OK;
+}
+
+// ---- row starts of a sorted edge list ---------------------------------------------------
+// head[i] = 1 where edge i starts a row.  head_tiles: exclusive prefix of the head counts per
+// scan tile (prefix[t]) and their total R.  head_fill: for every head i with rank r among the
+// heads, rowptr[r] = i and id_map[r] = row[i] (a scan whose result is written only at heads,
+// so no per-edge row number array is stored).
+__global__ void __launch_bounds__(SCAN_THREADS) k_head_fill(const uint8_t *head, int64_t n, const int32_t *tile_prefix,
+                                                           const int32_t *row, int32_t *rowptr, int32_t *id_map) {
+    const int64_t base = (int64_t)blockIdx.x * SCAN_TILE + (int64_t)threadIdx.x * SCAN_ITEMS;
+    int32_t v[SCAN_ITEMS];
+    load_items(head, n, base, true, v);
+    int32_t s = 0;
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) s += v[i];
+    __shared__ int32_t total;
+    int32_t run = block_exclusive_sum<int32_t>(s, &total) + tile_prefix[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < SCAN_ITEMS; ++i) {
+        if (v[i]) {
+            rowptr[run] = (int32_t)(base + i);
+            id_map[run] = row[base + i];
+            ++run;
+        }
+    }
+}
+
+int head_tiles(const uint8_t *head, int64_t E, DevBuf *prefix, int64_t *R, cudaStream_t s) {
+    *R = 0;
+    if (E <= 0) return TC_OK;
+    if ((uintptr_t)head % 8 != 0) return fail(TC_ERR_INVALID_ARG, "head_tiles: head must be 8-byte aligned");
+    const int64_t tiles = (E + SCAN_TILE - 1) / SCAN_TILE;
+    DevBuf sums;
+    TC_TRY(sums.alloc((size_t)tiles * 4));
+    TC_TRY(prefix->alloc((size_t)tiles * 4));
+    k_scan_reduce<uint8_t, int32_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(head, E, sums.as<int32_t>(), true);
+    TC_LAUNCH_CHECK();
+    TC_TRY((scan_impl<int32_t, int32_t>(sums.as<int32_t>(), tiles, prefix->as<int32_t>(), s)));
+    int32_t last[2] = {0, 0};
+    TC_CUDA(cudaMemcpyAsync(&last[0], prefix->as<int32_t>() + tiles - 1, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(&last[1], sums.as<int32_t>() + tiles - 1, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    *R = (int64_t)last[0] + last[1];
+    return TC_OK;
+}
+
+int head_fill(const uint8_t *head, int64_t E, const int32_t *prefix, const int32_t *row, int32_t *rowptr,
+              int32_t *id_map, cudaStream_t s) {
+    if (E <= 0) return TC_OK;
+    const int64_t tiles = (E + SCAN_TILE - 1) / SCAN_TILE;
+    k_head_fill<<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(head, E, prefix, row, rowptr, id_map);
+    TC_LAUNCH_CHECK();
     return TC_OK;
 }
 

@@ -75,7 +75,7 @@ int orc_pagerank_pull(int32_t V, const int32_t *in_rowptr, const int32_t *in_col
 #endif
     for (int32_t it = 0; it < iters; ++it) {
         double dangling = 0.0;
-        for (int32_t u = 0; u < V; ++u) {                 /* Alg. 1, lines 2-3 */
+        for (int32_t u = 0; u < V; ++u) {                 /* Alg. 1: contributions   */
             if (out_degree[u] > 0) contrib[u] = rank[u] / (double)out_degree[u];
             else { contrib[u] = 0.0; dangling += rank[u]; }
         }
@@ -84,10 +84,10 @@ int orc_pagerank_pull(int32_t V, const int32_t *in_rowptr, const int32_t *in_col
 #ifdef _OPENMP
 #pragma omp parallel for schedule(dynamic, 4096) if (nthreads > 1)
 #endif
-        for (int32_t v = 0; v < V; ++v) {                 /* Alg. 1, lines 4-8 */
+        for (int32_t v = 0; v < V; ++v) {                 /* Alg. 1: in-edge sums    */
             double sum = 0.0;
             for (int64_t e = in_rowptr[v]; e < in_rowptr[v + 1]; ++e) sum += contrib[in_colidx[e]];
-            rank[v] = base + damping * (sum + spread);    /* Alg. 1, lines 9-10 */
+            rank[v] = base + damping * (sum + spread);    /* Alg. 1: rank update     */
         }
     }
     free(contrib);
@@ -113,9 +113,9 @@ int orc_pagerank_push(int32_t V, const int32_t *rowptr, const int32_t *colidx,
         for (int32_t src = 0; src < V; ++src) {
             int64_t deg = (int64_t)rowptr[src + 1] - rowptr[src];
             if (deg == 0) { dangling += rank[src]; continue; }
-            double c = rank[src] / (double)deg;           /* Alg. 2, line 3 */
+            double c = rank[src] / (double)deg;           /* Alg. 2: contribution */
             for (int64_t e = rowptr[src]; e < rowptr[src + 1]; ++e)
-                sums[colidx[e]] += c;                     /* Alg. 2, line 7 */
+                sums[colidx[e]] += c;                     /* Alg. 2: scatter      */
         }
         double base = (1.0 - damping) / (double)V;
         double spread = (dangling_mode == 0) ? dangling / (double)V : 0.0;

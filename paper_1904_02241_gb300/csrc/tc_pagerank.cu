@@ -136,7 +136,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_pull_gather(const int32_t *__res
 // flattened chunk list, several at a time, and adds them into its own shared-memory
 // accumulator (the rows of one chunk have distinct IDs, so no atomics are needed).  The 16
 // accumulators are then added in warp order: the summation order is fixed, so the merge is
-// deterministic.  The update of Alg. 1 (lines 9-10), the next contributions and the dangling
+// deterministic.  The rank update of Alg. 1, the next contributions and the dangling
 // mass are fused in.
 // ---------------------------------------------------------------------------------------------
 constexpr int MG_THREADS = 512;

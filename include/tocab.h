@@ -164,9 +164,10 @@ int tc_part_set_lb(tc_part *p, const int32_t *warp_min_per_block);
 int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
 
 /* ---- PageRank ------------------------------------------------------------------------------ */
-#define TC_MERGE_FIXED    0          /* one accumulator per CTA, exact fixed-point adds (three
-                                        32-bit shared reductions per partial): deterministic;
-                                        the default, fastest measured on GB300               */
+#define TC_MERGE_FIXED    0          /* one accumulator per CTA, exact fixed-point adds (two
+                                        32-bit shared reductions per partial below 1,024
+                                        blocks, three from 1,024): deterministic; the default,
+                                        fastest measured on GB300                             */
 #define TC_MERGE_ORDERED  1          /* per-warp FP32 accumulators added in a fixed order:
                                         deterministic; when 16 accumulators of merge_range
                                         floats do not fit in shared memory the call uses

@@ -307,9 +307,14 @@ int tc_multigraph_load(int32_t num_graphs, const int32_t *vtx_off, int32_t V, in
                        tc_multigraph **out);
 void tc_multigraph_free(tc_multigraph *m);
 
+#define TC_MULTI_RESIDENT 1024    /* lanes_per_vertex value: each graph stays in one CTA for all
+                                     iterations, its contributions in shared memory (needs every
+                                     graph's non-dangling vertex count to fit; TC_ERR_UNSUPPORTED
+                                     otherwise)                                                  */
 typedef struct tc_multi_params {
     int32_t lanes_per_vertex; /* 0 = the autotuned choice (hybrid until tuned), -1 = a lane per
-                                 vertex with rows of 32+ edges taken by the warp, or 1/4/8/32 */
+                                 vertex with rows of 32+ edges taken by the warp, 1/4/8/32, or
+                                 TC_MULTI_RESIDENT */
     int32_t ctas_per_sm;      /* 0 = as many as fit (then the launch is graph-captured) */
     int32_t use_graph;        /* 1 = launch through the cached captured CUDA graph */
 } tc_multi_params;
@@ -318,8 +323,9 @@ typedef struct tc_multi_params {
  * tc_pagerank_multi -- Alg. 1 on every graph of the batch at once; graph g uses its own
  * teleport (1-d)/V_g and its own dangling mass D_g (redistributed over its own vertices).
  * All iterations run in one persistent cooperative kernel with a grid barrier between them
- * (a bounded spin: TC_ERR_TIMEOUT if it ever gives up); with use_graph the launch is captured
- * once into a CUDA graph (cached in the handle per parameter set) and replayed.
+ * (a bounded spin: TC_ERR_TIMEOUT if it ever gives up), or, for TC_MULTI_RESIDENT, in one
+ * kernel whose CTAs each run a whole graph; with use_graph the launch is captured once into a
+ * CUDA graph (cached in the handle per parameter set) and replayed.
  *   ranks_out : float[V] (params->out_mem), in the union's vertex order.  params->init must
  *               be NULL (TC_ERR_UNSUPPORTED otherwise).
  * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED, TC_ERR_TIMEOUT, TC_ERR_CUDA.
@@ -329,9 +335,11 @@ int tc_pagerank_multi(const tc_multigraph *m, const tc_pr_params *params, const 
 
 /*
  * tc_multi_autotune -- the project's autotuner for the batch: times every lanes-per-vertex
- * variant (-1, 1, 4, 8, 32; one warm-up and one timed run each, CUDA events) with `params`,
- * stores the fastest in the handle (used when lanes_per_vertex = 0) and returns it.
- *   times_ms : optional float[5], time of each variant in the order -1, 1, 4, 8, 32.
+ * variant (-1, 1, 4, 8, 32, and TC_MULTI_RESIDENT when the graphs fit; one warm-up and one
+ * timed run each, CUDA events) with `params`, stores the fastest in the handle (used when
+ * lanes_per_vertex = 0) and returns it.
+ *   times_ms : optional float[6], time of each variant in the order -1, 1, 4, 8, 32,
+ *              TC_MULTI_RESIDENT (a negative time: the variant does not apply to this batch).
  */
 int tc_multi_autotune(tc_multigraph *m, const tc_pr_params *params, int32_t *best_lanes,
                       float *times_ms, void *stream);

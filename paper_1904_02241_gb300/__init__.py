@@ -21,7 +21,7 @@ import torch
 
 from . import _lib as L
 from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
-                   TC_PULL, TC_PUSH)
+                   TC_MULTI_RESIDENT, TC_PULL, TC_PUSH)
 
 __all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "multigraph_load",
            "pagerank_multi", "multi_autotune", "MultiGraph",
@@ -304,11 +304,12 @@ def multi_autotune(mg: MultiGraph, damping: float = 0.85, iters: int = 20, strea
     """tc_multi_autotune: time the lanes-per-vertex variants; returns (best, {lanes: ms})."""
     pp = L.tc_pr_params(float(damping), int(iters), 0, L.TC_MEM_DEVICE, None, 0, 0, 0)
     best = C.c_int32()
-    times = (C.c_float * 5)()
+    times = (C.c_float * 6)()
     _check(L.load().tc_multi_autotune(mg.handle, C.byref(pp), C.byref(best), times, _stream(stream)),
            "tc_multi_autotune")
     mg.tuned_lanes = best.value
-    return best.value, dict(zip([-1, 1, 4, 8, 32], list(times)))
+    # a negative time: the variant does not apply to this batch
+    return best.value, {k: t for k, t in zip([-1, 1, 4, 8, 32, TC_MULTI_RESIDENT], list(times)) if t >= 0}
 
 
 def bfs_pull(graph: Graph, part: Partition | None, source: int, tocab_threshold: float = 0.05,

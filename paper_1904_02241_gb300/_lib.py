@@ -45,6 +45,7 @@ class tc_part_info(C.Structure):
 TC_MERGE_FIXED = 0
 TC_MERGE_ORDERED = 1
 TC_MERGE_FLOAT = 2
+TC_MULTI_RESIDENT = 1024
 
 
 class tc_pr_params(C.Structure):

@@ -4,7 +4,14 @@
 // with a bounded spin) that is captured once into a CUDA graph and replayed.  The mapping of
 // lanes to vertices (1, 4, 8 or 32 lanes per vertex, or the thread/warp hybrid) is a template
 // parameter; tc_multi_autotune times every variant on the batch and keeps the fastest.
+// A further variant (TC_MULTI_RESIDENT) keeps each graph inside one CTA for all iterations:
+// the graph's contributions live in shared memory (compacted to its non-dangling vertices,
+// 16-bit source indices), so no grid barrier and no L2 gather is needed; CTAs take graphs
+// from a queue, largest first.
 #include <cooperative_groups.h>
+
+#include <algorithm>
+#include <vector>
 
 #include "tc_common_dev.cuh"
 
@@ -14,8 +21,9 @@ constexpr int MU_THREADS = 256;
 constexpr int MU_WARPS = MU_THREADS / 32;
 constexpr int MU_CHUNK = 512;                  // vertices per warp work item
 constexpr double MU_FX = 2305843009213693952.0;  // 2^61 fixed point: a graph's mass is <= 1
-constexpr int MU_NVARIANTS = 5;
-static const int kLanes[MU_NVARIANTS] = {-1, 1, 4, 8, 32};  // -1: thread/warp hybrid
+constexpr int MU_NVARIANTS = 6;
+static const int kLanes[MU_NVARIANTS] = {-1, 1, 4, 8, 32, TC_MULTI_RESIDENT};  // -1: thread/warp hybrid
+constexpr int MR_THREADS = 1024;                 // resident variant: one CTA per graph at a time
 
 }  // namespace tc
 
@@ -25,6 +33,11 @@ struct tc_multigraph {
     tc::DevBuf vtx_off, gid, invVg;        // int32[n+1], int32[V], float[n]
     tc::DevBuf rank, contrib, dacc, sync;  // float[V], float[2V], u64[3n], barrier words
     int32_t tuned_lanes = 0;               // 0: not tuned yet
+    // resident variant (built on first use): compact index of every non-dangling vertex inside
+    // its graph, in-edges as 16-bit compact sources, graph queue (largest first)
+    bool res_built = false, res_ok = false;
+    int32_t res_max = 0;                   // largest non-dangling count of a graph
+    tc::DevBuf cpos, src16, order, scratch;  // int32[V+1], uint16[E], int32[n], float[V]
     // captured CUDA graph of the persistent launch, for one parameter set
     cudaGraphExec_t exec = nullptr;
     float cached_damping = -1.0f;
@@ -227,6 +240,130 @@ __global__ void __launch_bounds__(MU_THREADS) k_multi_pagerank(MultiArgs a) {
     }
 }
 
+// ---- resident variant -----------------------------------------------------------------------
+struct ResArgs {
+    const int32_t *rowptr;      // in-CSR of the union
+    const uint16_t *src16;      // compact source of every in-edge (inside its graph)
+    const int32_t *cpos;        // [V+1] exclusive count of non-dangling vertices before v
+    const int32_t *vtx_off, *order;
+    const float *inv_outdeg;
+    int32_t n, iters, drop;
+    float damping;
+    float *scratch;             // [cpos[V]] next contributions, at cpos[v]
+    float *rank;                // [V]
+    unsigned *next;             // queue counter
+};
+
+// Hybrid row sum over shared-memory contributions: a lane per row, rows of 32+ edges by the
+// whole warp (same shape as gather_hybrid).
+__device__ __forceinline__ float res_row_sum(const ResArgs &a, const float *c, int64_t v, bool valid) {
+    const int lane = threadIdx.x & 31;
+    int32_t s = 0, e = 0;
+    if (valid) {
+        s = __ldg(a.rowptr + v);
+        e = __ldg(a.rowptr + v + 1);
+    }
+    float sum = 0.0f;
+    if (e - s < 32)
+        for (int32_t i = s; i < e; ++i) sum += c[__ldg(a.src16 + i)];
+    unsigned wm = __ballot_sync(0xffffffffu, valid && e - s >= 32);
+    while (wm) {
+        const int l = __ffs(wm) - 1;
+        wm &= wm - 1;
+        const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
+        float acc = 0.0f;
+        for (int32_t i = ws + lane; i < we; i += 32) acc += c[__ldg(a.src16 + i)];
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        if (lane == l) sum = acc;
+    }
+    return sum;
+}
+
+// CTA-wide sum of one float per thread, returned to every thread (fixed order: deterministic).
+__device__ __forceinline__ float res_block_sum(float x, float *red) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
+    __syncthreads();  // red may still be read from the previous call
+    if (lane == 0) red[warp] = x;
+    __syncthreads();
+    float t = lane < MR_THREADS / 32 ? red[lane] : 0.0f;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
+    return t;
+}
+
+// One CTA runs all iterations of a graph (Alg. 1 with the graph's own teleport and dangling
+// mass), then takes the next graph of the queue.  Contributions of the graph's non-dangling
+// vertices stay in shared memory; the next ones go to global scratch (Jacobi) and are copied
+// back after a CTA barrier.
+__global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
+    extern __shared__ __align__(16) float cs[];
+    __shared__ float red[32];
+    __shared__ int32_t gnext;
+    const int tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) gnext = (int32_t)atomicAdd(a.next, 1u);
+        __syncthreads();
+        const int32_t gi = gnext;
+        __syncthreads();
+        if (gi >= a.n) break;
+        const int32_t g = a.order[gi];
+        const int32_t v0 = a.vtx_off[g], v1 = a.vtx_off[g + 1];
+        const int32_t nv = v1 - v0;
+        if (nv <= 0) continue;
+        const int32_t c0 = a.cpos[v0];
+        const float ivg = 1.0f / (float)nv;
+        // r0 = 1/V_g: contributions and the dangling mass
+        float dl = 0.0f;
+        for (int32_t v = v0 + tid; v < v1; v += MR_THREADS) {
+            const float inv = __ldg(a.inv_outdeg + v);
+            if (inv == 0.0f) dl += ivg;
+            else cs[__ldg(a.cpos + v) - c0] = ivg * inv;
+            if (a.iters == 0) a.rank[v] = ivg;
+        }
+        float D = res_block_sum(dl, red);
+        __syncthreads();
+        for (int32_t it = 0; it < a.iters; ++it) {
+            const bool last = it == a.iters - 1;
+            const float spread = a.drop ? 0.0f : D * ivg;
+            const float base = (1.0f - a.damping) * ivg;
+            dl = 0.0f;
+            // warps take 32 consecutive rows at a time
+            for (int32_t vb = v0 + (tid & ~31); vb < v1; vb += MR_THREADS) {
+                const int32_t v = vb + (tid & 31);
+                const bool valid = v < v1;
+                const float sum = res_row_sum(a, cs, v, valid);
+                if (valid) {
+                    const float r = base + a.damping * (sum + spread);
+                    const float inv = __ldg(a.inv_outdeg + v);
+                    if (inv == 0.0f) dl += r;
+                    else a.scratch[__ldg(a.cpos + v)] = r * inv;
+                    if (last) a.rank[v] = r;
+                }
+            }
+            D = res_block_sum(dl, red);  // its barriers also order the scratch writes
+            const int32_t nc = a.cpos[v1] - c0;
+            for (int32_t i = tid; i < nc; i += MR_THREADS) cs[i] = a.scratch[c0 + i];
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void k_multi_src16(const int32_t *colidx, int64_t E, const int32_t *cpos, const int32_t *gid,
+                              const int32_t *vtx_off, uint16_t *src16) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t u = colidx[e];
+        src16[e] = (uint16_t)(cpos[u] - cpos[vtx_off[gid[u]]]);
+    }
+}
+
+__global__ void k_multi_nondangling(const float *inv_outdeg, int32_t V, int32_t *flag) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+        flag[v] = inv_outdeg[v] != 0.0f ? 1 : 0;
+}
+
 __global__ void k_multi_gid(const int32_t *vtx_off, int32_t n, int32_t V, int32_t *gid, float *invVg) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         int32_t lo = 0, hi = n;  // last g with vtx_off[g] <= v
@@ -254,6 +391,74 @@ __global__ void k_multi_check(const int32_t *rowptr, const int32_t *colidx, cons
     }
 }
 
+__global__ void k_multi_graph_sizes(const int32_t *vtx_off, int32_t n, const int32_t *cpos, const int32_t *in_rowptr,
+                                    int32_t *ndang_free, int32_t *edges) {
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g < n; g += gridDim.x * blockDim.x) {
+        ndang_free[g] = cpos[vtx_off[g + 1]] - cpos[vtx_off[g]];
+        edges[g] = in_rowptr[vtx_off[g + 1]] - in_rowptr[vtx_off[g]];
+    }
+}
+
+__global__ void k_multi_cpos_end(int32_t *cpos, const int32_t *flag, int32_t V) {
+    cpos[V] = V > 0 ? cpos[V - 1] + flag[V - 1] : 0;
+}
+
+// Builds (once) what the resident variant reads; sets m->res_ok when every graph's
+// non-dangling vertices fit one CTA's shared memory and 16-bit indices.
+static int build_resident(tc_multigraph *m, cudaStream_t s) {
+    if (m->res_built) return TC_OK;
+    const int32_t V = m->g->V, n = m->n;
+    const int64_t E = m->g->E;
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    DevBuf flag, sizes, edges;
+    TC_TRY(flag.alloc((size_t)(V > 0 ? V : 1) * 4));
+    TC_TRY(m->cpos.alloc(((size_t)V + 1) * 4));
+    TC_TRY(sizes.alloc((size_t)n * 4));
+    TC_TRY(edges.alloc((size_t)n * 4));
+    k_multi_nondangling<<<caps.sms * 8, 256, 0, s>>>(m->g->inv_outdeg.as<float>(), V, flag.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32(flag.as<int32_t>(), V, m->cpos.as<int32_t>(), s));
+    k_multi_cpos_end<<<1, 1, 0, s>>>(m->cpos.as<int32_t>(), flag.as<int32_t>(), V);
+    TC_LAUNCH_CHECK();
+    k_multi_graph_sizes<<<(n + 255) / 256, 256, 0, s>>>(m->vtx_off.as<int32_t>(), n, m->cpos.as<int32_t>(),
+                                                       m->g->in_rowptr.as<int32_t>(), sizes.as<int32_t>(),
+                                                       edges.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    int32_t *hs = new (std::nothrow) int32_t[2 * (size_t)n];
+    if (!hs) return fail(TC_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(hs, sizes.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(hs + n, edges.p, (size_t)n * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+        delete[] hs;
+        return fail(TC_ERR_CUDA, "build_resident: %s", cudaGetErrorString(e));
+    }
+    int32_t mx = 0;
+    for (int32_t g = 0; g < n; ++g) mx = hs[g] > mx ? hs[g] : mx;
+    std::vector<int32_t> ord((size_t)n);
+    for (int32_t g = 0; g < n; ++g) ord[g] = g;
+    std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return hs[n + x] > hs[n + y]; });
+    delete[] hs;
+    m->res_max = mx;
+    m->res_ok = mx <= 65536 && (size_t)mx * 4 + 1024 <= (size_t)caps.max_smem_optin;
+    if (m->res_ok) {
+        TC_TRY(m->order.alloc((size_t)n * 4));
+        TC_TRY(m->src16.alloc((size_t)(E > 0 ? E : 1) * 2));
+        TC_TRY(m->scratch.alloc((size_t)(V > 0 ? V : 1) * 4));
+        TC_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        if (E > 0) {
+            k_multi_src16<<<caps.sms * 8, 256, 0, s>>>(m->g->in_colidx.as<int32_t>(), E, m->cpos.as<int32_t>(),
+                                                       m->gid.as<int32_t>(), m->vtx_off.as<int32_t>(),
+                                                       m->src16.as<uint16_t>());
+            TC_LAUNCH_CHECK();
+        }
+        TC_CUDA(cudaStreamSynchronize(s));
+    }
+    m->res_built = true;
+    return TC_OK;
+}
+
 typedef void (*MultiKernel)(MultiArgs);
 static MultiKernel multi_kernel(int lanes) {
     switch (lanes) {
@@ -265,11 +470,16 @@ static MultiKernel multi_kernel(int lanes) {
     }
 }
 
-static int multi_grid(int lanes, int ctas_per_sm, int *grid) {
+static int multi_grid(int lanes, int ctas_per_sm, int *grid, size_t res_smem = 0) {
     DeviceCaps caps;
     TC_TRY(device_caps(&caps));
     int per_sm = 0;
-    TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)multi_kernel(lanes), MU_THREADS, 0));
+    if (lanes == TC_MULTI_RESIDENT) {
+        TC_CUDA(cudaFuncSetAttribute(k_multi_resident, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)res_smem));
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_multi_resident, MR_THREADS, res_smem));
+    } else {
+        TC_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void *)multi_kernel(lanes), MU_THREADS, 0));
+    }
     if (per_sm < 1) return fail(TC_ERR_CUDA, "k_multi_pagerank cannot be resident");
     if (ctas_per_sm > 0 && ctas_per_sm < per_sm) per_sm = ctas_per_sm;
     *grid = caps.sms * per_sm;
@@ -279,6 +489,25 @@ static int multi_grid(int lanes, int ctas_per_sm, int *grid) {
 // Clears the barrier words and the dangling accumulators, then launches the persistent kernel.
 static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int grid, cudaStream_t s) {
     TC_CUDA(cudaMemsetAsync(m->sync.p, 0, 16, s));
+    if (lanes == TC_MULTI_RESIDENT) {
+        ResArgs r;
+        r.rowptr = a.rowptr;
+        r.src16 = m->src16.as<uint16_t>();
+        r.cpos = m->cpos.as<int32_t>();
+        r.vtx_off = m->vtx_off.as<int32_t>();
+        r.order = m->order.as<int32_t>();
+        r.inv_outdeg = a.inv_outdeg;
+        r.n = a.n;
+        r.iters = a.iters;
+        r.drop = a.drop;
+        r.damping = a.damping;
+        r.scratch = m->scratch.as<float>();
+        r.rank = a.rank;
+        r.next = m->sync.as<unsigned>() + 3;
+        k_multi_resident<<<grid, MR_THREADS, (size_t)m->res_max * 4, s>>>(r);
+        TC_LAUNCH_CHECK();
+        return TC_OK;
+    }
     TC_CUDA(cudaMemsetAsync(m->dacc.p, 0, (size_t)3 * m->n * 8, s));
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
@@ -320,7 +549,13 @@ static MultiArgs make_args(tc_multigraph *m, const tc_pr_params *pp) {
 static int run_multi(tc_multigraph *m, const tc_pr_params *pp, int lanes, int ctas_per_sm, bool use_graph,
                      cudaStream_t s) {
     int grid = 0;
-    TC_TRY(multi_grid(lanes, ctas_per_sm, &grid));
+    if (lanes == TC_MULTI_RESIDENT) {
+        TC_TRY(build_resident(m, s));
+        if (!m->res_ok)
+            return fail(TC_ERR_UNSUPPORTED, "TC_MULTI_RESIDENT: a graph has %d non-dangling vertices, more than one "
+                        "CTA's shared memory holds", m->res_max);
+    }
+    TC_TRY(multi_grid(lanes, ctas_per_sm, &grid, (size_t)m->res_max * 4));
     const MultiArgs a = make_args(m, pp);
     if (!use_graph) return launch_multi(m, a, lanes, grid, s);
     const bool same = m->exec && m->cached_damping == pp->damping && m->cached_iters == pp->iters &&
@@ -449,8 +684,13 @@ extern "C" int tc_multi_autotune(tc_multigraph *m, const tc_pr_params *params, i
     cudaStream_t s = (cudaStream_t)stream;
     float best = 3.4e38f;
     int best_l = -1;
+    TC_TRY(build_resident(m, s));
     for (int k = 0; k < MU_NVARIANTS; ++k) {
         float ms = 0, ms2 = 0;
+        if (kLanes[k] == TC_MULTI_RESIDENT && !m->res_ok) {
+            if (times_ms) times_ms[k] = -1.0f;
+            continue;
+        }
         TC_TRY(timed_run(m, params, kLanes[k], s, &ms));   // warm-up
         TC_TRY(timed_run(m, params, kLanes[k], s, &ms2));
         if (times_ms) times_ms[k] = ms2;
@@ -482,8 +722,9 @@ extern "C" int tc_pagerank_multi(const tc_multigraph *cm, const tc_pr_params *pa
     if (params->init) return fail(TC_ERR_UNSUPPORTED, "tc_pagerank_multi: init ranks are not supported");
     int lanes = mp ? mp->lanes_per_vertex : 0;
     if (lanes == 0) lanes = m->tuned_lanes ? m->tuned_lanes : -1;
-    if (lanes != -1 && lanes != 1 && lanes != 4 && lanes != 8 && lanes != 32)
-        return fail(TC_ERR_INVALID_ARG, "tc_pagerank_multi: lanes_per_vertex must be 0, -1, 1, 4, 8 or 32");
+    if (lanes != -1 && lanes != 1 && lanes != 4 && lanes != 8 && lanes != 32 && lanes != TC_MULTI_RESIDENT)
+        return fail(TC_ERR_INVALID_ARG,
+                    "tc_pagerank_multi: lanes_per_vertex must be 0, -1, 1, 4, 8, 32 or TC_MULTI_RESIDENT");
     const bool use_graph = mp ? mp->use_graph != 0 : true;
     const int ctas = mp ? mp->ctas_per_sm : 0;
     cudaStream_t s = (cudaStream_t)stream;

@@ -114,6 +114,8 @@ def test_thousand_graphs_sampled(T):
     gb, off = gg.rmat_batch(scales, seed=19, device="cuda")
     M = T.multigraph_load(gb.rowptr, gb.colidx, off)
     r = T.pagerank_multi(M, iters=20).cpu().numpy()
+    r_res = T.pagerank_multi(M, iters=20, lanes_per_vertex=T.TC_MULTI_RESIDENT).cpu().numpy()
+    assert l1_rel(r_res, r) <= TOL  # the graph-per-CTA variant agrees with the grid-wide one
     rp, ci = gb.numpy()
     off = off.cpu().numpy().astype(np.int64)
     pick = np.random.default_rng(23).choice(len(off) - 1, size=24, replace=False)

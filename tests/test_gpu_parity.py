@@ -371,7 +371,7 @@ def batch():
     return gg.rmat_batch([6, 9, 4, 10, 7, 8, 5, 9, 11, 3], seed=19)
 
 
-@pytest.mark.parametrize("lanes", [0, -1, 1, 4, 8, 32])
+@pytest.mark.parametrize("lanes", [0, -1, 1, 4, 8, 32, 1024])
 @pytest.mark.parametrize("use_graph", [True, False])
 def test_pagerank_multi_parity(T, batch, lanes, use_graph):
     g, off = batch
@@ -383,12 +383,13 @@ def test_pagerank_multi_parity(T, batch, lanes, use_graph):
         assert abs(r[off[k]:off[k + 1]].sum() - 1.0) < 1e-4
 
 
-def test_pagerank_multi_modes_and_reuse(T, batch):
+@pytest.mark.parametrize("lanes", [0, 1024])
+def test_pagerank_multi_modes_and_reuse(T, batch, lanes):
     g, off = batch
     M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), off)
     for iters, mode, d in [(0, "redistribute", 0.85), (3, "drop", 0.85), (20, "redistribute", 0.5),
                            (20, "redistribute", 0.85)]:
-        r = T.pagerank_multi(M, iters=iters, dangling=mode, damping=d).cpu().numpy()
+        r = T.pagerank_multi(M, iters=iters, dangling=mode, damping=d, lanes_per_vertex=lanes).cpu().numpy()
         assert l1_rel(r, _multi_oracle(g, off, iters=iters, dangling=mode, damping=d)) <= TOL
 
 
@@ -396,9 +397,24 @@ def test_multi_autotune_picks_a_variant(T, batch):
     g, off = batch
     M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), off)
     best, times = T.multi_autotune(M)
-    assert best in (-1, 1, 4, 8, 32) and times[best] == min(times.values())
+    assert best in (-1, 1, 4, 8, 32, T.TC_MULTI_RESIDENT) and times[best] == min(times.values())
+    assert T.TC_MULTI_RESIDENT in times  # these graphs fit one CTA's shared memory
     r = T.pagerank_multi(M).cpu().numpy()  # uses the tuned variant
     assert l1_rel(r, _multi_oracle(g, off)) <= TOL
+
+
+def test_multi_resident_rejects_graphs_too_large_for_one_cta(T):
+    """A cycle of 70,000 vertices has 70,000 non-dangling vertices: 280 KB of contributions, more
+    than one CTA's shared memory, so the resident variant is refused and the tuner skips it."""
+    g = gg.cycle(70000)
+    M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), [0, 70000])
+    with pytest.raises(T.TocabError) as e:
+        T.pagerank_multi(M, lanes_per_vertex=T.TC_MULTI_RESIDENT)
+    assert e.value.status == -6
+    best, times = T.multi_autotune(M)
+    assert T.TC_MULTI_RESIDENT not in times and best in (-1, 1, 4, 8, 32)
+    r = T.pagerank_multi(M).cpu().numpy()
+    assert np.allclose(r, 1.0 / 70000, rtol=1e-5)
 
 
 def test_multigraph_rejects_cross_edges(T):

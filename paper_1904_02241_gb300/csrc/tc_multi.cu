@@ -37,6 +37,7 @@ struct tc_multigraph {
     // its graph, in-edges as 16-bit compact sources, graph queue (largest first)
     bool res_built = false, res_ok = false;
     int32_t res_max = 0;                   // largest non-dangling count of a graph
+    int32_t res_wbuf = 0;                  // edges of each warp's source buffer (0: none)
     tc::DevBuf cpos, src16, order, scratch;  // int32[V+1], uint16[E], int32[n], float[V]
     // captured CUDA graph of the persistent launch, for one parameter set
     cudaGraphExec_t exec = nullptr;
@@ -252,27 +253,31 @@ struct ResArgs {
     float *scratch;             // [cpos[V]] next contributions, at cpos[v]
     float *rank;                // [V]
     unsigned *next;             // queue counter
+    int32_t cap;                // floats of contributions at the start of shared memory
+    int32_t wbuf;               // edges of each warp's source buffer after them (0: none)
 };
 
 // Hybrid row sum over shared-memory contributions: a lane per row, rows of 32+ edges by the
-// whole warp (same shape as gather_hybrid).
-__device__ __forceinline__ float res_row_sum(const ResArgs &a, const float *c, int64_t v, bool valid) {
+// whole warp (same shape as gather_hybrid).  `src` holds the sources of edges [base, ...):
+// either the warp's shared-memory copy of its 32 rows' edges, or global memory (base 0).
+__device__ __forceinline__ float res_row_sum(const ResArgs &a, const float *c, const uint16_t *src, int32_t base,
+                                             int64_t v, bool valid) {
     const int lane = threadIdx.x & 31;
     int32_t s = 0, e = 0;
     if (valid) {
-        s = __ldg(a.rowptr + v);
-        e = __ldg(a.rowptr + v + 1);
+        s = __ldg(a.rowptr + v) - base;
+        e = __ldg(a.rowptr + v + 1) - base;
     }
     float sum = 0.0f;
     if (e - s < 32)
-        for (int32_t i = s; i < e; ++i) sum += c[__ldg(a.src16 + i)];
+        for (int32_t i = s; i < e; ++i) sum += c[src[i]];
     unsigned wm = __ballot_sync(0xffffffffu, valid && e - s >= 32);
     while (wm) {
         const int l = __ffs(wm) - 1;
         wm &= wm - 1;
         const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
         float acc = 0.0f;
-        for (int32_t i = ws + lane; i < we; i += 32) acc += c[__ldg(a.src16 + i)];
+        for (int32_t i = ws + lane; i < we; i += 32) acc += c[src[i]];
 #pragma unroll
         for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
         if (lane == l) sum = acc;
@@ -303,6 +308,7 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
     __shared__ float red[32];
     __shared__ int32_t gnext;
     const int tid = threadIdx.x;
+    uint16_t *wsrc = reinterpret_cast<uint16_t *>(cs + a.cap) + (size_t)(tid >> 5) * a.wbuf;
     for (;;) {
         if (tid == 0) gnext = (int32_t)atomicAdd(a.next, 1u);
         __syncthreads();
@@ -328,15 +334,27 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
         for (int32_t it = 0; it < a.iters; ++it) {
             const bool last = it == a.iters - 1;
             const float spread = a.drop ? 0.0f : D * ivg;
-            const float base = (1.0f - a.damping) * ivg;
+            const float tele = (1.0f - a.damping) * ivg;
             dl = 0.0f;
-            // warps take 32 consecutive rows at a time
+            // warps take 32 consecutive rows at a time; their edges are contiguous and, when they
+            // fit, first copied into the warp's shared-memory buffer with coalesced loads
             for (int32_t vb = v0 + (tid & ~31); vb < v1; vb += MR_THREADS) {
                 const int32_t v = vb + (tid & 31);
                 const bool valid = v < v1;
-                const float sum = res_row_sum(a, cs, v, valid);
+                const int32_t vl = vb + 32 < v1 ? vb + 32 : v1;
+                const int32_t gs = __ldg(a.rowptr + vb), ge = __ldg(a.rowptr + vl);
+                const uint16_t *src = a.src16;
+                int32_t ebase = 0;  // first edge held by src
+                if (ge - gs <= a.wbuf) {
+                    for (int32_t i = (tid & 31); i < ge - gs; i += 32) wsrc[i] = __ldg(a.src16 + gs + i);
+                    __syncwarp();
+                    src = wsrc;
+                    ebase = gs;
+                }
+                const float sum = res_row_sum(a, cs, src, ebase, v, valid);
+                __syncwarp();  // the buffer is refilled by the next group
                 if (valid) {
-                    const float r = base + a.damping * (sum + spread);
+                    const float r = tele + a.damping * (sum + spread);
                     const float inv = __ldg(a.inv_outdeg + v);
                     if (inv == 0.0f) dl += r;
                     else a.scratch[__ldg(a.cpos + v)] = r * inv;
@@ -442,6 +460,15 @@ static int build_resident(tc_multigraph *m, cudaStream_t s) {
     delete[] hs;
     m->res_max = mx;
     m->res_ok = mx <= 65536 && (size_t)mx * 4 + 1024 <= (size_t)caps.max_smem_optin;
+    // each warp's buffer for its 32 rows' sources: what the rest of shared memory holds, at most
+    // 1,024 edges, a multiple of 8; below 256 edges the sources are read from global memory
+    {
+        const int64_t left = (int64_t)caps.max_smem_optin - 1024 - (int64_t)((mx + 3) & ~3) * 4;
+        int64_t wb = left / ((MR_THREADS / 32) * 2);
+        wb = wb > 1024 ? 1024 : wb;
+        wb &= ~(int64_t)7;
+        m->res_wbuf = wb >= 256 ? (int32_t)wb : 0;
+    }
     if (m->res_ok) {
         TC_TRY(m->order.alloc((size_t)n * 4));
         TC_TRY(m->src16.alloc((size_t)(E > 0 ? E : 1) * 2));
@@ -457,6 +484,10 @@ static int build_resident(tc_multigraph *m, cudaStream_t s) {
     }
     m->res_built = true;
     return TC_OK;
+}
+
+static size_t res_smem_bytes(const tc_multigraph *m) {
+    return (size_t)((m->res_max + 3) & ~3) * 4 + (size_t)(MR_THREADS / 32) * m->res_wbuf * 2;
 }
 
 typedef void (*MultiKernel)(MultiArgs);
@@ -504,7 +535,9 @@ static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int gri
         r.scratch = m->scratch.as<float>();
         r.rank = a.rank;
         r.next = m->sync.as<unsigned>() + 3;
-        k_multi_resident<<<grid, MR_THREADS, (size_t)m->res_max * 4, s>>>(r);
+        r.cap = (m->res_max + 3) & ~3;
+        r.wbuf = m->res_wbuf;
+        k_multi_resident<<<grid, MR_THREADS, res_smem_bytes(m), s>>>(r);
         TC_LAUNCH_CHECK();
         return TC_OK;
     }
@@ -555,7 +588,7 @@ static int run_multi(tc_multigraph *m, const tc_pr_params *pp, int lanes, int ct
             return fail(TC_ERR_UNSUPPORTED, "TC_MULTI_RESIDENT: a graph has %d non-dangling vertices, more than one "
                         "CTA's shared memory holds", m->res_max);
     }
-    TC_TRY(multi_grid(lanes, ctas_per_sm, &grid, (size_t)m->res_max * 4));
+    TC_TRY(multi_grid(lanes, ctas_per_sm, &grid, res_smem_bytes(m)));
     const MultiArgs a = make_args(m, pp);
     if (!use_graph) return launch_multi(m, a, lanes, grid, s);
     const bool same = m->exec && m->cached_damping == pp->damping && m->cached_iters == pp->iters &&

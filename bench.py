@@ -346,6 +346,7 @@ def variants(args, ctx, world):
             tot_edges += st.edges_reached // 2
         res[key + "_gteps"] = round(tot_edges / (tot_ms * 1e-3) / 1e9, 2)
     res["bfs_graph"] = {"V": gs.V, "E_directed": gs.E, "sources": len(srcs)}
+    res["bfs_oracle"] = oracle_bfs_rate(gs, srcs[0])
     del Gs, Ps, gs, lv
     torch.cuda.empty_cache()
     # block-count sweep around the L2 capacity (paper's source-range blocks, unstaged gather)
@@ -409,6 +410,7 @@ def batch_variants(args, stream):
     # floor reads every row once (the whole [V x 256] matrix in, the next one out)
     row_bytes = 4 * E22 + 4 * (V22 + 1) + 4 * NP * E22 + 8 * V22 * NP
     floor_bytes = 4 * E22 + 4 * V22 + 2 * 4 * NP * V22
+    res["ppr_oracle"] = oracle_ppr_rate(g22, srcs[0])
     res["ppr_batch"] = {"graph": "rmat22", "V": V22, "E": E22, "sources": 256, "iters": ITERS,
                         "ms": round(ms, 2), "ms_per_iter": round(ms / ITERS, 3),
                         "edge_columns_per_s_G": round(E22 * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
@@ -435,6 +437,7 @@ def batch_variants(args, stream):
     T.pagerank_multi(M, iters=ITERS, out=out)
     torch.cuda.synchronize()
     ms = statistics.median(time_runs(lambda: T.pagerank_multi(M, iters=ITERS, out=out), 5, stream))
+    res["many_graphs_oracle"] = oracle_multi_rate(gb, off)
     res["many_graphs"] = {"graphs": 1000, "scales": "U{10..16}", "V": gb.V, "E": gb.E, "iters": ITERS,
                           "autotuned_lanes_per_vertex": best, "autotune_ms": {str(k): round(v, 3) for k, v in times.items()},
                           "ms": round(ms, 3), "gteps": round(gb.E * ITERS / (ms * 1e-3) / 1e9, 2),
@@ -486,6 +489,50 @@ def e2e(args, ctx):
             "h2d_bytes_per_step": int(rp_h.numel() * 4 + ci_h.numel() * 4),
             "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": round(ms, 3),
             "includes": "H2D CSR + load/transpose + partition + 20 iters + D2H ranks"}
+
+
+# ---- the FP64 oracle timed beside the variant rows (bounded samples, single thread) ----------
+
+def oracle_bfs_rate(gs, source):
+    """The oracle's level-synchronous BFS from one source on the same symmetrised graph."""
+    import oracle
+    oracle.build()
+    rp, ci = gs.numpy()
+    t0 = time.time()
+    lv = oracle.bfs(gs.V, rp, ci, source)
+    dt = time.time() - t0
+    edges = int(np.diff(rp)[lv >= 0].sum()) // 2
+    return {"gteps": round(edges / dt / 1e9, 4), "cores": 1, "sample": "1 source (of the 64)"}
+
+
+def oracle_ppr_rate(g, source):
+    """The oracle's personalised PageRank for one column (of the 256) and 20 iterations."""
+    import oracle
+    oracle.build()
+    rp, ci = g.numpy()
+    tr = oracle.transpose(g.V, rp, ci)
+    t0 = time.time()
+    oracle.ppr_pull(g.V, rp, ci, [source], iters=ITERS, transposed=tr)
+    dt = time.time() - t0
+    return {"edge_columns_per_s_G": round(g.E * ITERS / dt / 1e9, 4), "cores": 1,
+            "sample": "1 column (of the 256), 20 iterations"}
+
+
+def oracle_multi_rate(gb, off, count: int = 50):
+    """The oracle's PageRank on a seeded sample of the batch's graphs, one after the other."""
+    import oracle
+    oracle.build()
+    rp, ci = gb.numpy()
+    o = off.cpu().numpy().astype(np.int64)
+    pick = np.random.default_rng(29).choice(len(o) - 1, size=min(count, len(o) - 1), replace=False)
+    edges, t0 = 0, time.time()
+    for k in pick:
+        lo, hi = int(o[k]), int(o[k + 1])
+        oracle.pagerank_pull(hi - lo, rp[lo:hi + 1] - rp[lo], ci[rp[lo]:rp[hi]] - lo, iters=ITERS)
+        edges += int(rp[hi] - rp[lo])
+    dt = time.time() - t0
+    return {"gteps": round(edges * ITERS / dt / 1e9, 4), "cores": 1,
+            "sample": f"{len(pick)} of the {len(o) - 1} graphs, 20 iterations each"}
 
 
 def cpu_baseline(g, budget_s: float):

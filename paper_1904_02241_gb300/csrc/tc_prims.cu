@@ -331,7 +331,8 @@ int scan_i32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t s) { retur
 int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s) { return scan_impl<int64_t, int64_t>(in, n, out, s); }
 
 // ----------------------------------------------------------------------------------------
-// Stable LSD bucket sort: 8-bit digits of key/divisor, 256 buckets, tiles of 4096 items.
+// Stable LSD bucket sort: 8-bit digits of key/divisor (256 buckets; one 9-bit pass with 512
+// buckets for 9-bit keys), tiles of 4096 items.
 // Each pass is a per-tile histogram, an exclusive scan of the bucket-major count table and a
 // stable scatter; stability is what keeps in-rows sorted by source.
 // ----------------------------------------------------------------------------------------
@@ -358,18 +359,22 @@ static RxDigit rx_digit(int32_t divisor, int shift) {
     }
     return r;
 }
+template <int NB>
 __device__ __forceinline__ int rx_bucket(int32_t key, RxDigit dg) {
-    return (int)(((uint64_t)(uint32_t)key * dg.m) >> dg.sh) & (RX_BUCKETS - 1);
+    return (int)(((uint64_t)(uint32_t)key * dg.m) >> dg.sh) & (NB - 1);
 }
 
-// Per-tile bucket counts.  All 16 keys of a thread are loaded before any counting so that the
-// loads overlap; every warp counts into its own shared histogram (plain shared atomics: keys
-// of one warp rarely share a bucket), and the 8 warp histograms are summed at the end.
+// Per-tile bucket counts (NB = 256 or 512 buckets).  All 16 keys of a thread are loaded before
+// any counting so that the loads overlap; every warp counts into its own shared histogram
+// (plain shared atomics: keys of one warp rarely share a bucket), and the 8 warp histograms
+// are summed at the end.
+template <int NB>
 __global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int64_t n, RxDigit dg,
                                                         int32_t *counts, int64_t ntiles) {
-    __shared__ int32_t h[RX_WARPS][RX_BUCKETS];
+    __shared__ int32_t h[RX_WARPS][NB];
     const int warp = threadIdx.x >> 5;
-    for (int w = 0; w < RX_WARPS; ++w) h[w][threadIdx.x] = 0;
+    for (int w = 0; w < RX_WARPS; ++w)
+        for (int b = threadIdx.x; b < NB; b += RX_THREADS) h[w][b] = 0;
     __syncthreads();
     const int64_t base = (int64_t)blockIdx.x * RX_TILE;
     int32_t k[RX_ROUNDS];
@@ -381,35 +386,44 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_hist(const int32_t *keys, int
 #pragma unroll
     for (int r = 0; r < RX_ROUNDS; ++r) {
         const int64_t i = base + r * RX_THREADS + threadIdx.x;
-        if (i < n) atomicAdd(&h[warp][rx_bucket(k[r], dg)], 1);
+        if (i < n) atomicAdd(&h[warp][rx_bucket<NB>(k[r], dg)], 1);
     }
     __syncthreads();
-    int tot = 0;
-    for (int w = 0; w < RX_WARPS; ++w) tot += h[w][threadIdx.x];
-    counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = tot;
+    for (int b = threadIdx.x; b < NB; b += RX_THREADS) {
+        int tot = 0;
+        for (int w = 0; w < RX_WARPS; ++w) tot += h[w][b];
+        counts[(int64_t)b * ntiles + blockIdx.x] = tot;
+    }
 }
 
 // Stable scatter of one tile.  Warp w owns items [w*512, (w+1)*512) of the tile, 16 rounds of
 // 32 in order, held in registers.  (A) count per warp and bucket with match masks, noting each
-// item's rank among the warp's items of its bucket;  (B) one thread per bucket turns the
-// counts into per-warp offsets inside the tile's bucket-ordered layout (warps in order,
-// buckets by a CTA scan);  (C) every item goes to its slot in shared memory;  (D) consecutive
-// threads copy consecutive slots out, so each bucket run of the tile leaves as one contiguous
-// store stream.  Equal buckets keep their input order throughout.
+// item's rank among the warp's items of its bucket;  (B) each thread takes NB/256 consecutive
+// buckets and turns their counts into per-warp offsets inside the tile's bucket-ordered layout
+// (warps in order, buckets by a CTA scan);  (C) every item goes to its slot in shared memory;
+// (D) consecutive threads copy consecutive slots out, so each bucket run of the tile leaves as
+// one contiguous store stream.  Equal buckets keep their input order throughout.
 constexpr int RX_PER_WARP = RX_TILE / RX_WARPS;  // 512
 constexpr int RX_WROUNDS = RX_PER_WARP / 32;     // 16
+template <int NB>
+constexpr size_t rx_scatter_smem() {
+    return (size_t)RX_TILE * 8 + (size_t)RX_WARPS * NB * 4 + (size_t)NB * 4 + (size_t)NB * 8;
+}
+template <int NB>
 __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, const int32_t *vin, int32_t *kout,
                                                            int32_t *vout, int64_t n, RxDigit dg,
                                                            const int64_t *offs, int64_t ntiles) {
-    __shared__ int32_t skey[RX_TILE];
-    __shared__ int32_t sval[RX_TILE];
-    __shared__ int32_t wpos[RX_WARPS][RX_BUCKETS];
-    __shared__ int32_t lstart[RX_BUCKETS];
-    __shared__ int64_t gdelta[RX_BUCKETS];  // global position of the bucket's run minus lstart
+    constexpr int PER = NB / RX_THREADS;  // buckets per thread in (B)
+    extern __shared__ __align__(16) unsigned char rsm[];
+    int64_t *gdelta = reinterpret_cast<int64_t *>(rsm);                   // [NB] global run start minus lstart
+    int32_t *skey = reinterpret_cast<int32_t *>(gdelta + NB);             // [RX_TILE]
+    int32_t *sval = skey + RX_TILE;                                       // [RX_TILE]
+    int32_t *wpos = sval + RX_TILE;                                       // [RX_WARPS][NB]
+    int32_t *lstart = wpos + RX_WARPS * NB;                               // [NB]
     __shared__ int32_t wsum[RX_WARPS];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t lt_mask = (1u << lane) - 1u;
-    for (int b = lane; b < RX_BUCKETS; b += 32) wpos[warp][b] = 0;
+    for (int b = lane; b < NB; b += 32) wpos[warp * NB + b] = 0;
     __syncwarp();
     const int64_t tile0 = (int64_t)blockIdx.x * RX_TILE;
     const int64_t base = tile0 + (int64_t)warp * RX_PER_WARP;
@@ -426,40 +440,50 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
-        const int b = (i < n) ? rx_bucket(key[r], dg) : RX_BUCKETS;
+        const int b = (i < n) ? rx_bucket<NB>(key[r], dg) : NB;
         const unsigned peers = __match_any_sync(0xffffffffu, b);
-        const int prev = b < RX_BUCKETS ? wpos[warp][b] : 0;
+        const int prev = b < NB ? wpos[warp * NB + b] : 0;
         const uint32_t rank = (uint32_t)(prev + __popc(peers & lt_mask));
         if (r & 1) local[r >> 1] |= rank << 16;
         else local[r >> 1] = rank;
         __syncwarp();
-        if (b < RX_BUCKETS && (peers & lt_mask) == 0) wpos[warp][b] = prev + __popc(peers);
+        if (b < NB && (peers & lt_mask) == 0) wpos[warp * NB + b] = prev + __popc(peers);
         __syncwarp();
     }
     __syncthreads();
-    // (B) thread = bucket: per-warp offsets inside the bucket, then a CTA scan of bucket totals
+    // (B) per-warp offsets inside each bucket, then a CTA scan of the bucket totals
     {
-        const int b = threadIdx.x;
-        int run = 0;
-        for (int w = 0; w < RX_WARPS; ++w) {
-            const int c = wpos[w][b];
-            wpos[w][b] = run;
-            run += c;
+        int tot[PER];
+        int run_all = 0;
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int b = threadIdx.x * PER + q;
+            int run = 0;
+            for (int w = 0; w < RX_WARPS; ++w) {
+                const int c = wpos[w * NB + b];
+                wpos[w * NB + b] = run;
+                run += c;
+            }
+            tot[q] = run;
+            run_all += run;
         }
-        int inc = run;  // inclusive warp scan of the bucket totals
+        int inc = run_all;  // inclusive warp scan of the threads' totals
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const int y = __shfl_up_sync(0xffffffffu, inc, o);
             if (lane >= o) inc += y;
         }
         if (lane == 31) wsum[warp] = inc;
-        const int64_t g = offs[(int64_t)b * ntiles + blockIdx.x];
         __syncthreads();
-        int before = 0;
-        for (int w = 0; w < warp; ++w) before += wsum[w];
-        const int ls = before + inc - run;
-        lstart[b] = ls;
-        gdelta[b] = g - ls;
+        int ls = inc - run_all;
+        for (int w = 0; w < warp; ++w) ls += wsum[w];
+#pragma unroll
+        for (int q = 0; q < PER; ++q) {
+            const int b = threadIdx.x * PER + q;
+            lstart[b] = ls;
+            gdelta[b] = offs[(int64_t)b * ntiles + blockIdx.x] - ls;
+            ls += tot[q];
+        }
     }
     __syncthreads();
     // (C) every item to its slot of the tile's bucket-ordered layout
@@ -467,8 +491,8 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
         if (i < n) {
-            const int b = rx_bucket(key[r], dg);
-            const int slot = lstart[b] + wpos[warp][b] + (int)((local[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
+            const int b = rx_bucket<NB>(key[r], dg);
+            const int slot = lstart[b] + wpos[warp * NB + b] + (int)((local[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
             skey[slot] = key[r];
             sval[slot] = val[r];
         }
@@ -478,10 +502,28 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
     const int count = (int)((n - tile0) < RX_TILE ? (n - tile0) : RX_TILE);
     for (int t = threadIdx.x; t < count; t += RX_THREADS) {
         const int32_t k = skey[t];
-        const int64_t pos = gdelta[rx_bucket(k, dg)] + t;
+        const int64_t pos = gdelta[rx_bucket<NB>(k, dg)] + t;
         kout[pos] = k;
         vout[pos] = sval[t];
     }
+}
+
+// One pass of the sort: digit of key / divisor at bit `shift`, NB buckets.
+template <int NB>
+static int rx_pass(const int32_t *ksrc, const int32_t *vsrc, int32_t *kd, int32_t *vd, int64_t n, int64_t ntiles,
+                   int32_t divisor, int shift, DevBuf *counts, DevBuf *offs, cudaStream_t s) {
+    TC_TRY(counts->alloc((size_t)ntiles * NB * sizeof(int32_t)));
+    TC_TRY(offs->alloc((size_t)ntiles * NB * sizeof(int64_t)));
+    const RxDigit dg = rx_digit(divisor, shift);
+    k_rx_hist<NB><<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, n, dg, counts->as<int32_t>(), ntiles);
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32_to_i64(counts->as<int32_t>(), ntiles * NB, offs->as<int64_t>(), s));
+    constexpr size_t smem = rx_scatter_smem<NB>();
+    TC_CUDA(cudaFuncSetAttribute(k_rx_scatter<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    k_rx_scatter<NB><<<(unsigned)ntiles, RX_THREADS, smem, s>>>(ksrc, vsrc, kd, vd, n, dg, offs->as<int64_t>(),
+                                                               ntiles);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
 }
 
 int stable_bucket_sort(const int32_t *k_in, const int32_t *v_in, int32_t *k_out, int32_t *v_out,
@@ -489,26 +531,21 @@ int stable_bucket_sort(const int32_t *k_in, const int32_t *v_in, int32_t *k_out,
                        cudaStream_t s) {
     if (n <= 0) return TC_OK;
     if (divisor < 1) return fail(TC_ERR_INVALID_ARG, "stable_bucket_sort: divisor < 1");
-    const int passes = bits <= 0 ? 1 : (bits + 7) / 8;
+    // 8-bit digits; a 9-bit key (up to 512 blocks) takes one 9-bit pass instead of two
+    const bool nine = bits == 9;
+    const int passes = nine ? 1 : (bits <= 0 ? 1 : (bits + 7) / 8);
     const int64_t ntiles = (n + RX_TILE - 1) / RX_TILE;
     DevBuf counts, offs;
-    TC_TRY(counts.alloc(ntiles * RX_BUCKETS * sizeof(int32_t)));
-    TC_TRY(offs.alloc(ntiles * RX_BUCKETS * sizeof(int64_t)));
     // ping-pong so that the last pass writes (k_out, v_out)
     const int32_t *ksrc = k_in, *vsrc = v_in;
     for (int p = 0; p < passes; ++p) {
-        const bool last = (p == passes - 1);
         const bool to_out = ((passes - 1 - p) % 2) == 0;
         int32_t *kd = to_out ? k_out : k_tmp;
         int32_t *vd = to_out ? v_out : v_tmp;
-        (void)last;
-        const RxDigit dg = rx_digit(divisor, 8 * p);
-        k_rx_hist<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, n, dg, counts.as<int32_t>(), ntiles);
-        TC_LAUNCH_CHECK();
-        TC_TRY(scan_i32_to_i64(counts.as<int32_t>(), ntiles * RX_BUCKETS, offs.as<int64_t>(), s));
-        k_rx_scatter<<<(unsigned)ntiles, RX_THREADS, 0, s>>>(ksrc, vsrc, kd, vd, n, dg,
-                                                           offs.as<int64_t>(), ntiles);
-        TC_LAUNCH_CHECK();
+        if (nine)
+            TC_TRY(rx_pass<2 * RX_BUCKETS>(ksrc, vsrc, kd, vd, n, ntiles, divisor, 0, &counts, &offs, s));
+        else
+            TC_TRY(rx_pass<RX_BUCKETS>(ksrc, vsrc, kd, vd, n, ntiles, divisor, 8 * p, &counts, &offs, s));
         ksrc = kd;
         vsrc = vd;
     }

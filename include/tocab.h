@@ -58,6 +58,20 @@ const char *tc_last_error(void);
 /* Library version as 10000*major + 100*minor + patch. */
 int tc_version(void);
 
+/* ---- device memory budget ---------------------------------------------------------------- */
+/*
+ * tc_set_device_memory_limit -- caps the device memory the library holds at once (graphs,
+ * partitions, workspaces and temporaries, on all devices together; blocks kept by its
+ * allocation cache count as held; setting a cap returns the cached ones to the driver).
+ * bytes = 0 removes the cap (the default).  An allocation
+ * that would exceed the cap fails with TC_ERR_OOM and a message naming the cap; nothing
+ * already allocated is freed.  tc_device_memory_held reports the bytes held now.  The paper
+ * has no counterpart: this is for processes that share the GPU with other users of its
+ * memory, and for testing the out-of-memory paths without exhausting the device.
+ */
+int tc_set_device_memory_limit(int64_t bytes);
+int64_t tc_device_memory_held(void);
+
 /* ---- graph ----------------------------------------------------------------------------- */
 /*
  * tc_graph_load_csr -- copy a directed graph G = (V, E) given as an out-edge CSR

@@ -25,7 +25,8 @@ from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC
 
 __all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "multigraph_load",
            "pagerank_multi", "multi_autotune", "MultiGraph",
-           "Graph", "Partition", "TocabError", "lib", "default_block_width"]
+           "Graph", "Partition", "TocabError", "lib", "default_block_width", "set_device_memory_limit",
+           "device_memory_held"]
 
 
 class TocabError(RuntimeError):
@@ -39,6 +40,16 @@ class TocabError(RuntimeError):
 
 def lib():
     return L.load()
+
+
+def set_device_memory_limit(nbytes: int) -> None:
+    """tc_set_device_memory_limit: cap the library's device memory (0 removes the cap)."""
+    _check(L.load().tc_set_device_memory_limit(int(nbytes)), "tc_set_device_memory_limit")
+
+
+def device_memory_held() -> int:
+    """tc_device_memory_held: bytes of device memory the library holds now."""
+    return int(L.load().tc_device_memory_held())
 
 
 def _check(status: int, where: str):

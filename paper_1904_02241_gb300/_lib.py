@@ -84,6 +84,8 @@ SIGNATURES = {
     "tc_status_string": (C.c_char_p, [C.c_int]),
     "tc_last_error": (C.c_char_p, []),
     "tc_version": (C.c_int, []),
+    "tc_set_device_memory_limit": (C.c_int, [C.c_int64]),
+    "tc_device_memory_held": (C.c_int64, []),
     "tc_graph_load_csr": (C.c_int, [C.c_int32, C.c_int64, VP, VP, C.c_int, VP, C.POINTER(VP)]),
     "tc_graph_free": (None, [VP]),
     "tc_graph_get_info": (C.c_int, [VP, C.POINTER(tc_graph_info)]),

@@ -67,6 +67,9 @@ __device__ __forceinline__ int32_t div_apply(int32_t key, DivBy q) {
 cudaError_t cache_alloc(size_t n, void **p, size_t *got, int *device);
 void cache_free(void *p, size_t bytes, int device);
 size_t cache_limit();
+size_t cache_held();                // bytes obtained from the driver and not returned
+void cache_set_limit(size_t bytes);  // 0: no cap
+size_t cache_get_limit();
 
 // ---- device buffer that frees itself --------------------------------------------------
 struct DevBuf {
@@ -90,6 +93,9 @@ struct DevBuf {
         cudaError_t e = cache_alloc(n, &p, &got, &device);
         if (e != cudaSuccess) {
             p = nullptr;
+            if (cache_get_limit())
+                return fail(TC_ERR_OOM, "device allocation of %zu bytes refused: %s (memory cap %zu bytes, %zu held)",
+                            n, cudaGetErrorString(e), cache_get_limit(), cache_held());
             return fail(TC_ERR_OOM, "cudaMalloc(%zu) failed: %s", n, cudaGetErrorString(e));
         }
         bytes = got;

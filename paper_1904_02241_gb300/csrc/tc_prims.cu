@@ -15,12 +15,15 @@ struct BlockCache {
     std::mutex mu;
     std::multimap<std::pair<int, size_t>, void *> free_blocks;  // (device, bytes) -> block
     size_t cached = 0;
+    size_t held = 0;   // bytes obtained from cudaMalloc and not yet returned to the driver
+    size_t limit = 0;  // 0: no cap
     void drop_all() {  // caller holds mu
         int cur = -1;
         cudaGetDevice(&cur);
         for (auto &kv : free_blocks) {
             cudaSetDevice(kv.first.first);
             cudaFree(kv.second);
+            held -= kv.first.second;
         }
         if (cur >= 0) cudaSetDevice(cur);
         free_blocks.clear();
@@ -51,6 +54,11 @@ cudaError_t cache_alloc(size_t n, void **p, size_t *got, int *device) {
             return cudaSuccess;
         }
     }
+    {  // the caller's memory cap: cached blocks are released first, then the request is refused
+        std::lock_guard<std::mutex> lk(c.mu);
+        if (c.limit && c.held + n > c.limit) c.drop_all();
+        if (c.limit && c.held + n > c.limit) return cudaErrorMemoryAllocation;
+    }
     e = cudaMalloc(p, n);
     if (e == cudaErrorMemoryAllocation) {
         cudaGetLastError();
@@ -65,7 +73,29 @@ cudaError_t cache_alloc(size_t n, void **p, size_t *got, int *device) {
         return e;
     }
     *got = n;
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.held += n;
     return cudaSuccess;
+}
+
+size_t cache_held() {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    return c.held;
+}
+
+void cache_set_limit(size_t bytes) {
+    cudaDeviceSynchronize();  // cached blocks may go back to the driver below
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.limit = bytes;
+    if (bytes) c.drop_all();  // a cap counts what is held: release the cached blocks first
+}
+
+size_t cache_get_limit() {
+    BlockCache &c = block_cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    return c.limit;
 }
 
 void cache_free(void *p, size_t bytes, int device) {
@@ -78,6 +108,7 @@ void cache_free(void *p, size_t bytes, int device) {
     std::lock_guard<std::mutex> lk(c.mu);
     if (bytes > cache_limit()) {
         cudaFree(p);
+        c.held -= bytes;
     } else {
         c.free_blocks.insert({{device, bytes}, p});
         c.cached += bytes;
@@ -87,6 +118,7 @@ void cache_free(void *p, size_t bytes, int device) {
             cudaSetDevice(last->first.first);
             cudaFree(last->second);
             c.cached -= last->first.second;
+            c.held -= last->first.second;
             c.free_blocks.erase(last);
         }
     }
@@ -620,5 +652,13 @@ extern "C" const char *tc_status_string(int status) {
 }
 
 extern "C" const char *tc_last_error(void) { return tc::g_last_error; }
+
+extern "C" int tc_set_device_memory_limit(int64_t bytes) {
+    if (bytes < 0) return tc::fail(TC_ERR_INVALID_ARG, "tc_set_device_memory_limit: negative byte count");
+    tc::cache_set_limit((size_t)bytes);
+    return TC_OK;
+}
+
+extern "C" int64_t tc_device_memory_held(void) { return (int64_t)tc::cache_held(); }
 
 extern "C" int tc_version(void) { return 100; }

@@ -72,3 +72,10 @@ def test_default_block_width_scales_with_l2_and_clamps(lib):
     assert lib.tc_default_block_width(1 << 24, 4096, 0.0) == 372
     assert lib.tc_default_block_width(1 << 24, 64, 0.0) == 32                    # floor of 32
     assert lib.tc_default_block_width(1 << 26, gb300_l2, 0.5) == int(0.5 * gb300_l2 / 4)
+
+
+def test_memory_cap_arguments(lib):
+    """The cap is host state: a negative byte count is refused, 0 clears it (no device needed)."""
+    assert lib.tc_set_device_memory_limit(-1) == -1
+    assert lib.tc_set_device_memory_limit(0) == 0
+    assert lib.tc_device_memory_held() >= 0

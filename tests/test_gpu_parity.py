@@ -61,6 +61,24 @@ def test_transpose_bit_exact(T, name, device):
     assert G.max_out_degree == int(deg.max(initial=0))
 
 
+def test_device_memory_cap_gives_oom_and_recovers(T):
+    """Failure injection on the host: a memory cap far below what a load needs makes the
+    allocation fail with TC_ERR_OOM (naming the cap); after the cap is lifted the same call
+    works and the results are unchanged."""
+    g = GRAPHS["rmat12"]
+    rp, ci = g.rowptr.cuda(), g.colidx.cuda()
+    T.set_device_memory_limit(1)  # returns the cached blocks, so that `held` is what is in use
+    T.set_device_memory_limit(T.device_memory_held() + 4096)
+    try:
+        with pytest.raises(T.TocabError) as e:
+            T.graph_load_csr(rp, ci, V=g.V)
+        assert e.value.status == -3 and "memory cap" in str(e.value)
+    finally:
+        T.set_device_memory_limit(0)
+    G = T.graph_load_csr(rp, ci, V=g.V)
+    assert l1_rel(T.pagerank_pull(G, None).cpu().numpy(), _oracle_pr(g)) <= TOL
+
+
 def test_invalid_csr_rejected(T):
     bad_rp = torch.tensor([0, 2, 1], dtype=torch.int32)
     ci = torch.tensor([1, 0], dtype=torch.int32)

@@ -291,6 +291,8 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_stats(const int32_t *level,
     }
 }
 
+__global__ void k_set_int(int32_t *p, int32_t v) { *p = v; }
+
 static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, const tc_bfs_params *bp,
                     int32_t *levels_out, tc_bfs_stats *stats, cudaStream_t s) {
     tc_graph *g = const_cast<tc_graph *>(cg);
@@ -318,20 +320,24 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
     k_bfs_init<<<grid, BFS_THREADS, 0, s>>>(level, visited, bufs[0], V, nwords, source);
     TC_LAUNCH_CHECK();
     const bool can_push = bp->push_threshold > 0.0f;
-    DevBuf queues, qcnt, qpos;
+    // push-level buffers live with the graph (no allocation, and so no synchronisation, per call)
+    DevBuf &queues = g->ws_queue, &qcnt = g->ws_qcnt, &qpos = g->ws_qpos;
     int32_t *q[2] = {nullptr, nullptr};
+    const int64_t cap = (int64_t)(V > nwords ? V : nwords) + 16;
     if (can_push) {
         TC_TRY(queues.alloc((size_t)2 * V * 4 + 64));
-        const size_t cap = (size_t)(V > nwords ? V : nwords) + 16;
-        TC_TRY(qcnt.alloc(cap * 4));
-        TC_TRY(qpos.alloc(cap * 8));
+        TC_TRY(qcnt.alloc((size_t)cap * 4));
+        TC_TRY(qpos.alloc((size_t)cap * 8));
+        TC_TRY(g->ws_scan.alloc((size_t)(scan_ws_elems(cap) + 16) * 8));
         q[0] = queues.as<int32_t>();
         q[1] = q[0] + V;
-        TC_CUDA(cudaMemcpyAsync(q[0], &source, 4, cudaMemcpyHostToDevice, s));
+        k_set_int<<<1, 1, 0, s>>>(q[0], source);
+        TC_LAUNCH_CHECK();
     }
     bool have_queue = can_push;  // the queue q[lvl & 1] holds the current frontier
-    unsigned long long front_count = 1, *h_cnt = nullptr;
-    TC_CUDA(cudaMallocHost(&h_cnt, 16));
+    unsigned long long front_count = 1;
+    if (!g->h_counts) TC_CUDA(cudaMallocHost(&g->h_counts, 16));
+    unsigned long long *h_cnt = g->h_counts;
     // direction switching (Beamer et al.): edges out of the frontier (m_f) against edges out of
     // unvisited vertices (m_u); push -> pull when m_f > m_u / 14, pull -> push when the
     // frontier holds fewer than push_threshold * V vertices
@@ -369,7 +375,7 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
             if (!have_queue) {  // frontier came from a pull level: bitmap -> queue
                 k_bitmap_count<<<grid, BFS_THREADS, 0, s>>>(front, nwords, qcnt.as<int32_t>());
                 if (cudaGetLastError() != cudaSuccess) { st = fail(TC_ERR_CUDA, "launch failed"); break; }
-                st = scan_i32_to_i64(qcnt.as<int32_t>(), nwords, qpos.as<int64_t>(), s);
+                st = scan_i32_to_i64_ws(qcnt.as<int32_t>(), nwords, qpos.as<int64_t>(), g->ws_scan.as<int64_t>(), s);
                 if (st != TC_OK) break;
                 k_bitmap_queue<<<grid, BFS_THREADS, 0, s>>>(front, nwords, qpos.as<int64_t>(), q[lvl & 1]);
             }
@@ -379,7 +385,7 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
             k_push_degrees<<<grid, BFS_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), q[lvl & 1], qn,
                                                         qcnt.as<int32_t>());
             if (cudaGetLastError() != cudaSuccess) { st = fail(TC_ERR_CUDA, "launch failed"); break; }
-            st = scan_i32_to_i64(qcnt.as<int32_t>(), qn, qpos.as<int64_t>(), s);
+            st = scan_i32_to_i64_ws(qcnt.as<int32_t>(), qn, qpos.as<int64_t>(), g->ws_scan.as<int64_t>(), s);
             if (st != TC_OK) break;
             const int64_t total = (int64_t)(m_f + 0.5);
             if (total > 0)
@@ -420,7 +426,6 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
         cudaEventDestroy(lev[0]);
         cudaEventDestroy(lev[1]);
     }
-    cudaFreeHost(h_cnt);
     TC_TRY(st);
     if (bp->profile) {
         TC_CUDA(cudaEventRecord(ev[1], s));

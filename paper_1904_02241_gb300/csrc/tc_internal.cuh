@@ -117,6 +117,10 @@ int device_caps(DeviceCaps *caps);
 int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s);
 int scan_i64(const int64_t *in, int64_t n, int64_t *out, cudaStream_t s);
 int scan_i32(const int32_t *in, int64_t n, int32_t *out, cudaStream_t s);  // total < 2^31
+// The same scan with caller scratch (scan_ws_elems(n) int64 words): no allocation and no
+// synchronisation, so it can sit between kernels of a level loop.
+int64_t scan_ws_elems(int64_t n);
+int scan_i32_to_i64_ws(const int32_t *in, int64_t n, int64_t *out, int64_t *ws, cudaStream_t s);
 int head_tiles(const uint8_t *head, int64_t E, DevBuf *prefix, int64_t *R, cudaStream_t s);
 int head_fill(const uint8_t *head, int64_t E, const int32_t *prefix, const int32_t *row, int32_t *rowptr,
               int32_t *id_map, cudaStream_t s);
@@ -154,6 +158,11 @@ struct tc_graph {
     tc::DevBuf in_hubs, out_hubs;
     // reusable scratch (grown on demand, freed with the graph)
     tc::DevBuf ws_contrib, ws_scalars, ws_partials, ws_bits, ws_misc;
+    tc::DevBuf ws_queue, ws_qcnt, ws_qpos, ws_scan;  // BFS push levels
+    unsigned long long *h_counts = nullptr;          // pinned host words read after each BFS level
+    ~tc_graph() {
+        if (h_counts) cudaFreeHost(h_counts);
+    }
 };
 
 struct tc_part {

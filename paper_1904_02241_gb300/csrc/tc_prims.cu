@@ -356,6 +356,34 @@ int head_fill(const uint8_t *head, int64_t E, const int32_t *prefix, const int32
     return TC_OK;
 }
 
+int64_t scan_ws_elems(int64_t n) {
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    return tiles <= 1 ? 0 : 2 * tiles + scan_ws_elems(tiles);
+}
+
+template <class Tin>
+static int scan_ws_impl(const Tin *in, int64_t n, int64_t *out, int64_t *ws, cudaStream_t s) {
+    if (n <= 0) return TC_OK;
+    const int64_t tiles = (n + SCAN_TILE - 1) / SCAN_TILE;
+    const bool vec = ((uintptr_t)in % (8 * sizeof(Tin))) == 0 && ((uintptr_t)out % 64) == 0;
+    if (tiles == 1) {
+        k_scan_apply<Tin, int64_t><<<1, SCAN_THREADS, 0, s>>>(in, n, nullptr, out, vec);
+        TC_LAUNCH_CHECK();
+        return TC_OK;
+    }
+    int64_t *sums = ws, *pref = ws + tiles;
+    k_scan_reduce<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, sums, vec);
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_ws_impl<int64_t>(sums, tiles, pref, ws + 2 * tiles, s));
+    k_scan_apply<Tin, int64_t><<<(unsigned)tiles, SCAN_THREADS, 0, s>>>(in, n, pref, out, vec);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}
+
+int scan_i32_to_i64_ws(const int32_t *in, int64_t n, int64_t *out, int64_t *ws, cudaStream_t s) {
+    return scan_ws_impl<int32_t>(in, n, out, ws, s);
+}
+
 int scan_i32_to_i64(const int32_t *in, int64_t n, int64_t *out, cudaStream_t s) {
     return scan_impl<int32_t, int64_t>(in, n, out, s);
 }

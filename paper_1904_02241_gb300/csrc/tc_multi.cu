@@ -37,8 +37,10 @@ struct tc_multigraph {
     // its graph, in-edges as 16-bit compact sources, graph queue (largest first)
     bool res_built = false, res_ok = false;
     int32_t res_max = 0;                   // largest non-dangling count of a graph
-    int32_t res_wbuf = 0;                  // edges of each warp's source buffer (0: none)
-    tc::DevBuf cpos, src16, order, scratch;  // int32[V+1], uint16[E], int32[n], float[V]
+    // in-edge sources (uint16, padded to whole chunks), head bits (a bit per in-edge), heads
+    // before every 512-edge chunk, rank of every vertex's row among the non-empty rows (-1: empty)
+    // and the row sums of one iteration (float, by rank)
+    tc::DevBuf cpos, src16, heads, hpre, slot, order, scratch;
     // captured CUDA graph of the persistent launch, for one parameter set
     cudaGraphExec_t exec = nullptr;
     float cached_damping = -1.0f;
@@ -242,47 +244,123 @@ __global__ void __launch_bounds__(MU_THREADS) k_multi_pagerank(MultiArgs a) {
 }
 
 // ---- resident variant -----------------------------------------------------------------------
+constexpr int MR_WARPS = MR_THREADS / 32;
+constexpr int MR_CHUNK = 512;  // edges per warp chunk: 16 consecutive in-edges per lane
+
 struct ResArgs {
     const int32_t *rowptr;      // in-CSR of the union
-    const uint16_t *src16;      // compact source of every in-edge (inside its graph)
+    const uint16_t *src16;      // compact source of every in-edge (inside its graph), padded
+    const uint16_t *heads;      // bit i of heads[q]: in-edge 16q + i is the first of its row
+    const int32_t *hpre;        // [chunks + 1] heads before in-edge 512c
+    const int32_t *slot;        // [V] rank of v's row among the non-empty rows, -1 when empty
     const int32_t *cpos;        // [V+1] exclusive count of non-dangling vertices before v
     const int32_t *vtx_off, *order;
     const float *inv_outdeg;
     int32_t n, iters, drop;
     float damping;
-    float *scratch;             // [cpos[V]] next contributions, at cpos[v]
+    float *sums;                // [non-empty rows] in-edge sums of one iteration, by rank
     float *rank;                // [V]
     unsigned *next;             // queue counter
-    int32_t cap;                // floats of contributions at the start of shared memory
-    int32_t wbuf;               // edges of each warp's source buffer after them (0: none)
+    int32_t cap;                // floats of contributions in shared memory
 };
 
-// Hybrid row sum over shared-memory contributions: a lane per row, rows of 32+ edges by the
-// whole warp (same shape as gather_hybrid).  `src` holds the sources of edges [base, ...):
-// either the warp's shared-memory copy of its 32 rows' edges, or global memory (base 0).
-__device__ __forceinline__ float res_row_sum(const ResArgs &a, const float *c, const uint16_t *src, int32_t base,
-                                             int64_t v, bool valid) {
+// One warp sums the rows of the in-edges [es, ee) over the contributions in shared memory
+// (line 6 of Alg. 1, edge-balanced): 16 consecutive edges per lane and chunk, a row break at
+// every head bit.  Rows that start in the range are written to a.sums by rank (rs = heads
+// before es); the piece of the row already open at es is returned to the caller, which adds
+// it once every warp has finished (rows may cross warp ranges).
+__device__ __forceinline__ float res_walk(const ResArgs &a, const float *cs, int32_t es, int32_t ee, int32_t rs) {
     const int lane = threadIdx.x & 31;
-    int32_t s = 0, e = 0;
-    if (valid) {
-        s = __ldg(a.rowptr + v) - base;
-        e = __ldg(a.rowptr + v + 1) - base;
+    const uint32_t lt_mask = (1u << lane) - 1u;
+    int32_t rowbase = rs;  // rank of the row started by the next head
+    float carry = 0.0f;    // value of the open row rowbase - 1 so far
+    bool open = false;     // whether row rowbase - 1 started inside [es, ee)
+    float lead = 0.0f;     // the open row's piece before the range's first head
+    if (es >= ee) return 0.0f;
+    const int32_t qb = es & ~(MR_CHUNK - 1);
+    // software pipeline: the next chunk's sources and heads are loaded before this one is summed
+    uint4 nc0, nc1;
+    uint32_t nh;
+    {
+        const uint4 *p = reinterpret_cast<const uint4 *>(a.src16 + qb + 16 * lane);
+        nc0 = __ldg(p);
+        nc1 = __ldg(p + 1);
+        nh = __ldg(a.heads + (qb >> 4) + lane);
     }
-    float sum = 0.0f;
-    if (e - s < 32)
-        for (int32_t i = s; i < e; ++i) sum += c[src[i]];
-    unsigned wm = __ballot_sync(0xffffffffu, valid && e - s >= 32);
-    while (wm) {
-        const int l = __ffs(wm) - 1;
-        wm &= wm - 1;
-        const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
-        float acc = 0.0f;
-        for (int32_t i = ws + lane; i < we; i += 32) acc += c[src[i]];
+    for (int32_t q0 = qb; q0 < ee; q0 += MR_CHUNK) {
+        const uint4 c0 = nc0, c1 = nc1;
+        uint32_t hd = nh;
+        if (q0 + MR_CHUNK < ee) {
+            const uint4 *p = reinterpret_cast<const uint4 *>(a.src16 + q0 + MR_CHUNK + 16 * lane);
+            nc0 = __ldg(p);
+            nc1 = __ldg(p + 1);
+            nh = __ldg(a.heads + ((q0 + MR_CHUNK) >> 4) + lane);
+        }
+        const uint32_t words[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
+        float val[16];
+        if (q0 >= es && q0 + MR_CHUNK <= ee) {  // whole chunk inside the range (warp-uniform)
 #pragma unroll
-        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-        if (lane == l) sum = acc;
+            for (int i = 0; i < 16; ++i) val[i] = cs[(words[i >> 1] >> (16 * (i & 1))) & 0xFFFFu];
+        } else {
+            const int32_t e0 = q0 + 16 * lane;  // valid edges of this lane: [max(es, e0), min(ee, e0 + 16))
+            const int32_t lo_i = es - e0, hi_i = ee - e0;
+            uint32_t valid = 0xFFFFu;
+            if (lo_i > 0) valid = lo_i >= 16 ? 0u : (valid & (0xFFFFu << lo_i));
+            if (hi_i < 16) valid = hi_i <= 0 ? 0u : (valid & ((1u << hi_i) - 1u));
+            hd &= valid;
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+                const uint32_t col = (words[i >> 1] >> (16 * (i & 1))) & 0xFFFFu;
+                val[i] = ((valid >> i) & 1u) ? cs[col] : 0.0f;
+            }
+        }
+        // heads in earlier lanes and in the whole chunk, from bit-sliced ballots of the counts
+        const int nh_l = __popc(hd);
+        int before = 0, total = 0;
+#pragma unroll
+        for (int bit = 0; bit < 5; ++bit) {
+            const uint32_t m = __ballot_sync(0xffffffffu, (nh_l >> bit) & 1);
+            before += __popc(m & lt_mask) << bit;
+            total += __popc(m) << bit;
+        }
+        // the lane's 16 edges: every head after the lane's first closes a whole row (rank
+        // rowbase + before + j), the piece before its first head goes to the carry scan
+        float seg = 0.0f, first = 0.0f;
+        int32_t orow = rowbase + before;
+        const uint32_t close_m = hd & (hd - 1u);
+        const uint32_t first_m = hd & (0u - hd);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+            if ((close_m >> i) & 1u) a.sums[orow++] = seg;
+            if ((first_m >> i) & 1u) first = seg;
+            seg = ((hd >> i) & 1u) ? val[i] : seg + val[i];
+        }
+        const bool seen = hd != 0u;
+        if (!seen) first = seg;
+        // the open row's value across lanes: segmented inclusive scan, flags from one ballot
+        const uint32_t F = __ballot_sync(0xffffffffu, seen);
+        float v = seg;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const float vp = __shfl_up_sync(0xffffffffu, v, d);
+            const int lo = lane - d + 1;
+            const uint32_t win = lo > 0 ? (F >> lo) & ((1u << d) - 1u) : F & ((2u << lane) - 1u);
+            if (lane >= d && win == 0u) v += vp;
+        }
+        const bool f = (F & ((2u << lane) - 1u)) != 0u;
+        const float vprev = __shfl_up_sync(0xffffffffu, v, 1);
+        const bool fprev = (F & lt_mask) != 0u;
+        const float xprev = (lane == 0) ? carry : (fprev ? vprev : carry + vprev);
+        const float closed = xprev + first;  // the row closed at the lane's first head
+        if (seen && (before > 0 || open)) a.sums[rowbase + before - 1] = closed;
+        if (!open && total > 0) lead = __shfl_sync(0xffffffffu, closed, __ffs(F) - 1);
+        carry = __shfl_sync(0xffffffffu, f ? v : carry + v, 31);
+        if (total > 0) open = true;
+        rowbase += total;
     }
-    return sum;
+    if (!open) return carry;  // no head in the range: all of it belongs to the row open at es
+    if (lane == 0) a.sums[rowbase - 1] = carry;
+    return lead;
 }
 
 // CTA-wide sum of one float per thread, returned to every thread (fixed order: deterministic).
@@ -293,22 +371,26 @@ __device__ __forceinline__ float res_block_sum(float x, float *red) {
     __syncthreads();  // red may still be read from the previous call
     if (lane == 0) red[warp] = x;
     __syncthreads();
-    float t = lane < MR_THREADS / 32 ? red[lane] : 0.0f;
+    float t = lane < MR_WARPS ? red[lane] : 0.0f;
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) t += __shfl_xor_sync(0xffffffffu, t, d);
     return t;
 }
 
 // One CTA runs all iterations of a graph (Alg. 1 with the graph's own teleport and dangling
-// mass), then takes the next graph of the queue.  Contributions of the graph's non-dangling
-// vertices stay in shared memory; the next ones go to global scratch (Jacobi) and are copied
-// back after a CTA barrier.
+// mass), then takes the next graph of the queue.  The contributions of the graph's
+// non-dangling vertices stay in shared memory.  An iteration: every warp sums an equal share
+// of the graph's in-edges into a.sums; one warp adds the pieces of rows that cross warp
+// ranges, in warp order; then a lane per vertex applies the update of Alg. 1 and overwrites its
+// contribution in place (all sums are complete by then, so this is still a Jacobi step).
 __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
     extern __shared__ __align__(16) float cs[];
     __shared__ float red[32];
+    __shared__ float lead[MR_WARPS];
+    __shared__ int32_t lrow[MR_WARPS];
     __shared__ int32_t gnext;
-    const int tid = threadIdx.x;
-    uint16_t *wsrc = reinterpret_cast<uint16_t *>(cs + a.cap) + (size_t)(tid >> 5) * a.wbuf;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t lt_mask = (1u << lane) - 1u;
     for (;;) {
         if (tid == 0) gnext = (int32_t)atomicAdd(a.next, 1u);
         __syncthreads();
@@ -321,6 +403,20 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
         if (nv <= 0) continue;
         const int32_t c0 = a.cpos[v0];
         const float ivg = 1.0f / (float)nv;
+        // this warp's share of the graph's in-edges, and rs = heads before its first edge
+        const int32_t E0 = __ldg(a.rowptr + v0), ne = __ldg(a.rowptr + v1) - E0;
+        const int32_t per = ((ne + MR_WARPS - 1) / MR_WARPS + 15) & ~15;
+        const int32_t es = E0 + min(warp * per, ne), ee = E0 + min((warp + 1) * per, ne);
+        int32_t rs;
+        {
+            const int32_t qb = es & ~(MR_CHUNK - 1);
+            const uint32_t h = __ldg(a.heads + (qb >> 4) + lane);
+            const int32_t below = es - (qb + 16 * lane);  // edges of this lane before es
+            const uint32_t m = below >= 16 ? 0xFFFFu : (below <= 0 ? 0u : (1u << below) - 1u);
+            rs = __ldg(a.hpre + (qb >> 9)) + __reduce_add_sync(0xffffffffu, __popc(h & m));
+            const uint32_t hes = __shfl_sync(0xffffffffu, h, (es - qb) >> 4);
+            if (lane == 0) lrow[warp] = (es < ee && !((hes >> ((es - qb) & 15)) & 1u)) ? rs - 1 : -1;
+        }
         // r0 = 1/V_g: contributions and the dangling mass
         float dl = 0.0f;
         for (int32_t v = v0 + tid; v < v1; v += MR_THREADS) {
@@ -335,36 +431,39 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
             const bool last = it == a.iters - 1;
             const float spread = a.drop ? 0.0f : D * ivg;
             const float tele = (1.0f - a.damping) * ivg;
-            dl = 0.0f;
-            // warps take 32 consecutive rows at a time; their edges are contiguous and, when they
-            // fit, first copied into the warp's shared-memory buffer with coalesced loads
-            for (int32_t vb = v0 + (tid & ~31); vb < v1; vb += MR_THREADS) {
-                const int32_t v = vb + (tid & 31);
-                const bool valid = v < v1;
-                const int32_t vl = vb + 32 < v1 ? vb + 32 : v1;
-                const int32_t gs = __ldg(a.rowptr + vb), ge = __ldg(a.rowptr + vl);
-                const uint16_t *src = a.src16;
-                int32_t ebase = 0;  // first edge held by src
-                if (ge - gs <= a.wbuf) {
-                    for (int32_t i = (tid & 31); i < ge - gs; i += 32) wsrc[i] = __ldg(a.src16 + gs + i);
-                    __syncwarp();
-                    src = wsrc;
-                    ebase = gs;
+            const float lv = res_walk(a, cs, es, ee, rs);
+            if (lane == 0) lead[warp] = lv;
+            __syncthreads();
+            if (warp == 0) {  // rows crossing warp ranges: the later pieces, in warp order
+                const int32_t lr = lrow[lane];
+                if (lr >= 0 && (lane == 0 || lrow[lane - 1] != lr)) {
+                    float acc = 0.0f;
+                    for (int w = lane; w < MR_WARPS && lrow[w] == lr; ++w) acc += lead[w];
+                    a.sums[lr] += acc;
                 }
-                const float sum = res_row_sum(a, cs, src, ebase, v, valid);
-                __syncwarp();  // the buffer is refilled by the next group
+            }
+            __syncthreads();
+            dl = 0.0f;
+            for (int32_t vb = v0 + warp * 32; vb < v1; vb += MR_THREADS) {
+                const int32_t v = vb + lane;
+                const bool valid = v < v1;
+                float inv = 0.0f;
+                int32_t sl = -1;
                 if (valid) {
-                    const float r = tele + a.damping * (sum + spread);
-                    const float inv = __ldg(a.inv_outdeg + v);
+                    inv = __ldg(a.inv_outdeg + v);
+                    sl = __ldg(a.slot + v);
+                }
+                const float sum = sl >= 0 ? a.sums[sl] : 0.0f;
+                const float r = tele + a.damping * (sum + spread);
+                const uint32_t nd = __ballot_sync(0xffffffffu, valid && inv != 0.0f);
+                const int32_t cb = __ldg(a.cpos + vb) - c0;
+                if (valid) {
                     if (inv == 0.0f) dl += r;
-                    else a.scratch[__ldg(a.cpos + v)] = r * inv;
+                    else cs[cb + __popc(nd & lt_mask)] = r * inv;
                     if (last) a.rank[v] = r;
                 }
             }
-            D = res_block_sum(dl, red);  // its barriers also order the scratch writes
-            const int32_t nc = a.cpos[v1] - c0;
-            for (int32_t i = tid; i < nc; i += MR_THREADS) cs[i] = a.scratch[c0 + i];
-            __syncthreads();
+            D = res_block_sum(dl, red);  // its barriers order the new contributions and sums
         }
     }
 }
@@ -421,6 +520,32 @@ __global__ void k_multi_cpos_end(int32_t *cpos, const int32_t *flag, int32_t V) 
     cpos[V] = V > 0 ? cpos[V - 1] + flag[V - 1] : 0;
 }
 
+// a head bit at the first in-edge of every non-empty row; flag = row is non-empty
+__global__ void k_res_heads(const int32_t *rowptr, int32_t V, int32_t *flag, uint32_t *heads32) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t s = rowptr[v];
+        const bool ne = rowptr[v + 1] > s;
+        flag[v] = ne ? 1 : 0;
+        if (ne) atomicOr(heads32 + (s >> 5), 1u << (s & 31));
+    }
+}
+
+// heads of every 512-edge chunk (16 words)
+__global__ void k_res_chunk_heads(const uint32_t *heads32, int64_t chunks, int32_t *cnt) {
+    for (int64_t c = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; c < chunks; c += (int64_t)gridDim.x * blockDim.x) {
+        int k = 0;
+#pragma unroll
+        for (int i = 0; i < 16; ++i) k += __popc(heads32[16 * c + i]);
+        cnt[c] = k;
+    }
+}
+
+// slot[v] holds the exclusive count of non-empty rows before v; empty rows get -1
+__global__ void k_res_slot(const int32_t *flag, int32_t V, int32_t *slot) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+        if (!flag[v]) slot[v] = -1;
+}
+
 // Builds (once) what the resident variant reads; sets m->res_ok when every graph's
 // non-dangling vertices fit one CTA's shared memory and 16-bit indices.
 static int build_resident(tc_multigraph *m, cudaStream_t s) {
@@ -460,26 +585,39 @@ static int build_resident(tc_multigraph *m, cudaStream_t s) {
     delete[] hs;
     m->res_max = mx;
     m->res_ok = mx <= 65536 && (size_t)mx * 4 + 1024 <= (size_t)caps.max_smem_optin;
-    // each warp's buffer for its 32 rows' sources: what the rest of shared memory holds, at most
-    // 1,024 edges, a multiple of 8; below 256 edges the sources are read from global memory
-    {
-        const int64_t left = (int64_t)caps.max_smem_optin - 1024 - (int64_t)((mx + 3) & ~3) * 4;
-        int64_t wb = left / ((MR_THREADS / 32) * 2);
-        wb = wb > 1024 ? 1024 : wb;
-        wb &= ~(int64_t)7;
-        m->res_wbuf = wb >= 256 ? (int32_t)wb : 0;
-    }
     if (m->res_ok) {
+        // whole 512-edge chunks plus one: a warp reads its last chunk (and the head words of
+        // its first) in full, past the final edge
+        const int64_t chunks = E / MR_CHUNK + 2;
         TC_TRY(m->order.alloc((size_t)n * 4));
-        TC_TRY(m->src16.alloc((size_t)(E > 0 ? E : 1) * 2));
+        TC_TRY(m->src16.alloc((size_t)chunks * MR_CHUNK * 2));
+        TC_TRY(m->heads.alloc((size_t)chunks * (MR_CHUNK / 8)));
+        TC_TRY(m->hpre.alloc((size_t)(chunks + 1) * 4));
+        TC_TRY(m->slot.alloc((size_t)(V > 0 ? V : 1) * 4));
         TC_TRY(m->scratch.alloc((size_t)(V > 0 ? V : 1) * 4));
+        DevBuf cnt;
+        TC_TRY(cnt.alloc((size_t)chunks * 4));
         TC_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+        TC_CUDA(cudaMemsetAsync(m->src16.p, 0, (size_t)chunks * MR_CHUNK * 2, s));
+        TC_CUDA(cudaMemsetAsync(m->heads.p, 0, (size_t)chunks * (MR_CHUNK / 8), s));
         if (E > 0) {
             k_multi_src16<<<caps.sms * 8, 256, 0, s>>>(m->g->in_colidx.as<int32_t>(), E, m->cpos.as<int32_t>(),
                                                        m->gid.as<int32_t>(), m->vtx_off.as<int32_t>(),
                                                        m->src16.as<uint16_t>());
             TC_LAUNCH_CHECK();
         }
+        if (V > 0) {
+            k_res_heads<<<caps.sms * 8, 256, 0, s>>>(m->g->in_rowptr.as<int32_t>(), V, flag.as<int32_t>(),
+                                                     m->heads.as<uint32_t>());
+            TC_LAUNCH_CHECK();
+            TC_TRY(scan_i32(flag.as<int32_t>(), V, m->slot.as<int32_t>(), s));
+            k_res_slot<<<caps.sms * 8, 256, 0, s>>>(flag.as<int32_t>(), V, m->slot.as<int32_t>());
+            TC_LAUNCH_CHECK();
+        }
+        k_res_chunk_heads<<<(int)((chunks + 255) / 256), 256, 0, s>>>(m->heads.as<uint32_t>(), chunks,
+                                                                      cnt.as<int32_t>());
+        TC_LAUNCH_CHECK();
+        TC_TRY(scan_i32(cnt.as<int32_t>(), chunks, m->hpre.as<int32_t>(), s));
         TC_CUDA(cudaStreamSynchronize(s));
     }
     m->res_built = true;
@@ -487,7 +625,7 @@ static int build_resident(tc_multigraph *m, cudaStream_t s) {
 }
 
 static size_t res_smem_bytes(const tc_multigraph *m) {
-    return (size_t)((m->res_max + 3) & ~3) * 4 + (size_t)(MR_THREADS / 32) * m->res_wbuf * 2;
+    return (size_t)((m->res_max + 3) & ~3) * 4;
 }
 
 typedef void (*MultiKernel)(MultiArgs);
@@ -524,6 +662,9 @@ static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int gri
         ResArgs r;
         r.rowptr = a.rowptr;
         r.src16 = m->src16.as<uint16_t>();
+        r.heads = m->heads.as<uint16_t>();
+        r.hpre = m->hpre.as<int32_t>();
+        r.slot = m->slot.as<int32_t>();
         r.cpos = m->cpos.as<int32_t>();
         r.vtx_off = m->vtx_off.as<int32_t>();
         r.order = m->order.as<int32_t>();
@@ -532,11 +673,10 @@ static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int gri
         r.iters = a.iters;
         r.drop = a.drop;
         r.damping = a.damping;
-        r.scratch = m->scratch.as<float>();
+        r.sums = m->scratch.as<float>();
         r.rank = a.rank;
         r.next = m->sync.as<unsigned>() + 3;
         r.cap = (m->res_max + 3) & ~3;
-        r.wbuf = m->res_wbuf;
         k_multi_resident<<<grid, MR_THREADS, res_smem_bytes(m), s>>>(r);
         TC_LAUNCH_CHECK();
         return TC_OK;

@@ -435,6 +435,37 @@ def test_multi_resident_rejects_graphs_too_large_for_one_cta(T):
     assert np.allclose(r, 1.0 / 70000, rtol=1e-5)
 
 
+def _union(graphs):
+    """Disjoint union of CSR graphs, with the vertex offset table."""
+    rps, cis, off, e0 = [np.zeros(1, dtype=np.int64)], [], [0], 0
+    for h in graphs:
+        rp, ci = h.numpy()
+        rps.append(rp[1:].astype(np.int64) + e0)
+        cis.append(ci.astype(np.int64) + off[-1])
+        e0 += len(ci)
+        off.append(off[-1] + h.V)
+    rp = torch.from_numpy(np.concatenate(rps).astype(np.int32))
+    ci = torch.from_numpy(np.concatenate(cis).astype(np.int32))
+    return gg.CSRGraph(off[-1], rp, ci, "union"), off
+
+
+def test_multi_resident_edge_cases(T):
+    """The resident variant splits every graph's in-edges evenly over 32 warps, so rows cross
+    warp ranges.  Here a hub row of 20,000 in-edges crosses all of them, graphs without edges
+    give warps empty ranges, and single vertices give empty graphs.  The result must match the
+    oracle and repeat bit for bit."""
+    parts = [gg.empty_graph(5), gg.star(20000), gg.path(3000), gg.cycle(1), gg.complete(40),
+             gg.rmat(9, seed=5), gg.empty_graph(1), gg.path(700, directed=True), gg.cycle(33)]
+    g, off = _union(parts)
+    M = T.multigraph_load(g.rowptr.cuda(), g.colidx.cuda(), off)
+    for mode in ("redistribute", "drop"):
+        r = T.pagerank_multi(M, iters=20, dangling=mode, lanes_per_vertex=T.TC_MULTI_RESIDENT)
+        want = _multi_oracle(g, off, iters=20, dangling=mode)
+        assert l1_rel(r.cpu().numpy(), want) <= TOL, mode
+        again = T.pagerank_multi(M, iters=20, dangling=mode, lanes_per_vertex=T.TC_MULTI_RESIDENT)
+        assert torch.equal(r.cpu(), again.cpu())
+
+
 def test_multigraph_rejects_cross_edges(T):
     g = gg.from_edge_list(4, [(0, 1), (1, 2), (2, 3)])
     with pytest.raises(T.TocabError) as e:

@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--merge-range", type=int, default=0, help="vertices per merge CTA (0 = library default)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
+    ap.add_argument("--row", default="", choices=["", "many_graphs"],
+                    help="profiling runs: time only this row and print its figures")
     return ap.parse_args()
 
 
@@ -429,6 +431,16 @@ def batch_variants(args, stream):
                               "floor_bytes_frac": round(floor_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4)}
     del R, G22, g22, P22
     torch.cuda.empty_cache()
+    res.update(many_graphs(stream))
+    return res
+
+
+def many_graphs(stream, with_oracle: bool = True):
+    """1,000 R-MAT graphs with scales 10..16, all iterations in one persistent, graph-captured
+    launch with the variant chosen by the autotuner."""
+    import paper_1904_02241_gb300 as T
+    res = {}
+    peak, _ = load_peaks()
     scales = gg.batch_scales(1000, 10, 16, seed=19)
     gb, off = gg.rmat_batch(scales, seed=19, device="cuda")
     M = T.multigraph_load(gb.rowptr, gb.colidx, off)
@@ -437,11 +449,19 @@ def batch_variants(args, stream):
     T.pagerank_multi(M, iters=ITERS, out=out)
     torch.cuda.synchronize()
     ms = statistics.median(time_runs(lambda: T.pagerank_multi(M, iters=ITERS, out=out), 5, stream))
-    res["many_graphs_oracle"] = oracle_multi_rate(gb, off)
+    if with_oracle:
+        res["many_graphs_oracle"] = oracle_multi_rate(gb, off)
+    # the resident kernel's bytes per iteration: 2 B of source and 1/8 B of head bits per
+    # stream edge (the in-edges plus one placeholder per vertex without in-edges) and the
+    # out-degree reciprocal of every vertex
+    empties = int((torch.bincount(gb.colidx.long(), minlength=gb.V) == 0).sum())
+    res_bytes = 2.125 * (gb.E + empties) + 4 * gb.V
     res["many_graphs"] = {"graphs": 1000, "scales": "U{10..16}", "V": gb.V, "E": gb.E, "iters": ITERS,
                           "autotuned_lanes_per_vertex": best, "autotune_ms": {str(k): round(v, 3) for k, v in times.items()},
                           "ms": round(ms, 3), "gteps": round(gb.E * ITERS / (ms * 1e-3) / 1e9, 2),
                           "bmin_frac": round((4 * gb.E + 4 * (gb.V + 1) + 12 * gb.V) / (ms / ITERS * 1e-3) / 1e9 / peak, 4),
+                          "resident_bytes_frac": round(res_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4)
+                          if best == T.TC_MULTI_RESIDENT else None,
                           "launches_per_run": 1, "cuda_graph": True}
     del M, gb, out
     torch.cuda.empty_cache()
@@ -595,6 +615,10 @@ def main():
         return
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the TOCAB path has no CPU fallback)")
+    if args.row == "many_graphs":
+        res = many_graphs(torch.cuda.current_stream(), with_oracle=False)
+        print(json.dumps(res), flush=True)
+        return
     res, ctx = bench_tocab(args, world, rank, local)
     if rank == 0 and not args.quick:
         if not args.no_variants:

@@ -37,10 +37,10 @@ struct tc_multigraph {
     // its graph, in-edges as 16-bit compact sources, graph queue (largest first)
     bool res_built = false, res_ok = false;
     int32_t res_max = 0;                   // largest non-dangling count of a graph
-    // in-edge sources (uint16, padded to whole chunks), head bits (a bit per in-edge), heads
-    // before every 512-edge chunk, rank of every vertex's row among the non-empty rows (-1: empty)
-    // and the row sums of one iteration (float, by rank)
-    tc::DevBuf cpos, src16, heads, hpre, slot, order, scratch;
+    // the in-edge stream: every row's compact sources (uint16), one placeholder edge for an
+    // empty row, padded to whole chunks; a head bit at every row's first edge; heads before every
+    // 512-edge chunk; every graph's first stream edge; the row sums of one iteration (by vertex)
+    tc::DevBuf cpos, src16, heads, hpre, eoff, order, scratch;
     // captured CUDA graph of the persistent launch, for one parameter set
     cudaGraphExec_t exec = nullptr;
     float cached_damping = -1.0f;
@@ -245,30 +245,31 @@ __global__ void __launch_bounds__(MU_THREADS) k_multi_pagerank(MultiArgs a) {
 
 // ---- resident variant -----------------------------------------------------------------------
 constexpr int MR_WARPS = MR_THREADS / 32;
-constexpr int MR_CHUNK = 512;  // edges per warp chunk: 16 consecutive in-edges per lane
+constexpr int MR_CHUNK = 512;  // edges per warp chunk: 16 consecutive stream edges per lane
+constexpr int MR_VB = 4;       // vertex groups per warp and step of the update
 
 struct ResArgs {
-    const int32_t *rowptr;      // in-CSR of the union
-    const uint16_t *src16;      // compact source of every in-edge (inside its graph), padded
-    const uint16_t *heads;      // bit i of heads[q]: in-edge 16q + i is the first of its row
-    const int32_t *hpre;        // [chunks + 1] heads before in-edge 512c
-    const int32_t *slot;        // [V] rank of v's row among the non-empty rows, -1 when empty
+    const uint16_t *src16;      // the in-edge stream: compact sources inside the graph; an empty
+                                // row has one edge from the graph's zero slot (its non-dangling count)
+    const uint16_t *heads;      // bit i of heads[q]: stream edge 16q + i is the first of its row
+    const int32_t *hpre;        // [chunks] heads before stream edge 512c = rows started before it
+    const int32_t *eoff;        // [n+1] first stream edge of every graph
     const int32_t *cpos;        // [V+1] exclusive count of non-dangling vertices before v
     const int32_t *vtx_off, *order;
     const float *inv_outdeg;
     int32_t n, iters, drop;
     float damping;
-    float *sums;                // [non-empty rows] in-edge sums of one iteration, by rank
+    float *sums;                // [V] in-edge sums of one iteration
     float *rank;                // [V]
     unsigned *next;             // queue counter
-    int32_t cap;                // floats of contributions in shared memory
 };
 
-// One warp sums the rows of the in-edges [es, ee) over the contributions in shared memory
-// (line 6 of Alg. 1, edge-balanced): 16 consecutive edges per lane and chunk, a row break at
-// every head bit.  Rows that start in the range are written to a.sums by rank (rs = heads
-// before es); the piece of the row already open at es is returned to the caller, which adds
-// it once every warp has finished (rows may cross warp ranges).
+// One warp sums the rows of the stream edges [es, ee) over the contributions in shared memory
+// (the in-edge sum of Alg. 1, edge-balanced): 16 consecutive edges per lane and chunk, a row
+// break at every head bit.  Every vertex owns one row, so the k-th head is vertex k: rows that
+// start in the range are written to a.sums[vertex] (rs = heads before es); the piece of the row
+// already open at es is returned to the caller, which adds it once every warp has finished
+// (rows may cross warp ranges).
 __device__ __forceinline__ float res_walk(const ResArgs &a, const float *cs, int32_t es, int32_t ee, int32_t rs) {
     const int lane = threadIdx.x & 31;
     const uint32_t lt_mask = (1u << lane) - 1u;
@@ -403,8 +404,8 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
         if (nv <= 0) continue;
         const int32_t c0 = a.cpos[v0];
         const float ivg = 1.0f / (float)nv;
-        // this warp's share of the graph's in-edges, and rs = heads before its first edge
-        const int32_t E0 = __ldg(a.rowptr + v0), ne = __ldg(a.rowptr + v1) - E0;
+        // this warp's share of the graph's stream edges, and rs = heads before its first edge
+        const int32_t E0 = __ldg(a.eoff + g), ne = __ldg(a.eoff + g + 1) - E0;
         const int32_t per = ((ne + MR_WARPS - 1) / MR_WARPS + 15) & ~15;
         const int32_t es = E0 + min(warp * per, ne), ee = E0 + min((warp + 1) * per, ne);
         int32_t rs;
@@ -417,7 +418,8 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
             const uint32_t hes = __shfl_sync(0xffffffffu, h, (es - qb) >> 4);
             if (lane == 0) lrow[warp] = (es < ee && !((hes >> ((es - qb) & 15)) & 1u)) ? rs - 1 : -1;
         }
-        // r0 = 1/V_g: contributions and the dangling mass
+        // r0 = 1/V_g: contributions and the dangling mass; the zero slot after them
+        if (tid == 0) cs[a.cpos[v1] - c0] = 0.0f;
         float dl = 0.0f;
         for (int32_t v = v0 + tid; v < v1; v += MR_THREADS) {
             const float inv = __ldg(a.inv_outdeg + v);
@@ -444,35 +446,37 @@ __global__ void __launch_bounds__(MR_THREADS, 1) k_multi_resident(ResArgs a) {
             }
             __syncthreads();
             dl = 0.0f;
-            for (int32_t vb = v0 + warp * 32; vb < v1; vb += MR_THREADS) {
-                const int32_t v = vb + lane;
-                const bool valid = v < v1;
-                float inv = 0.0f;
-                int32_t sl = -1;
-                if (valid) {
-                    inv = __ldg(a.inv_outdeg + v);
-                    sl = __ldg(a.slot + v);
+            // MR_VB groups of 32 vertices per warp and step: their loads are issued together
+            for (int32_t vb = v0 + warp * 32; vb < v1; vb += MR_VB * MR_THREADS) {
+                float inv[MR_VB], sum[MR_VB];
+                int32_t cb[MR_VB];
+#pragma unroll
+                for (int k = 0; k < MR_VB; ++k) {
+                    const int32_t gb = vb + k * MR_THREADS, v = gb + lane;
+                    inv[k] = 0.0f;
+                    sum[k] = 0.0f;
+                    cb[k] = 0;
+                    if (v < v1) {
+                        inv[k] = __ldg(a.inv_outdeg + v);
+                        sum[k] = a.sums[v];
+                    }
+                    if (gb < v1) cb[k] = __ldg(a.cpos + gb) - c0;
                 }
-                const float sum = sl >= 0 ? a.sums[sl] : 0.0f;
-                const float r = tele + a.damping * (sum + spread);
-                const uint32_t nd = __ballot_sync(0xffffffffu, valid && inv != 0.0f);
-                const int32_t cb = __ldg(a.cpos + vb) - c0;
-                if (valid) {
-                    if (inv == 0.0f) dl += r;
-                    else cs[cb + __popc(nd & lt_mask)] = r * inv;
-                    if (last) a.rank[v] = r;
+#pragma unroll
+                for (int k = 0; k < MR_VB; ++k) {
+                    const int32_t v = vb + k * MR_THREADS + lane;
+                    const bool valid = v < v1;
+                    const float r = tele + a.damping * (sum[k] + spread);
+                    const uint32_t nd = __ballot_sync(0xffffffffu, valid && inv[k] != 0.0f);
+                    if (valid) {
+                        if (inv[k] == 0.0f) dl += r;
+                        else cs[cb[k] + __popc(nd & lt_mask)] = r * inv[k];
+                        if (last) a.rank[v] = r;
+                    }
                 }
             }
             D = res_block_sum(dl, red);  // its barriers order the new contributions and sums
         }
-    }
-}
-
-__global__ void k_multi_src16(const int32_t *colidx, int64_t E, const int32_t *cpos, const int32_t *gid,
-                              const int32_t *vtx_off, uint16_t *src16) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t u = colidx[e];
-        src16[e] = (uint16_t)(cpos[u] - cpos[vtx_off[gid[u]]]);
     }
 }
 
@@ -520,13 +524,38 @@ __global__ void k_multi_cpos_end(int32_t *cpos, const int32_t *flag, int32_t V) 
     cpos[V] = V > 0 ? cpos[V - 1] + flag[V - 1] : 0;
 }
 
-// a head bit at the first in-edge of every non-empty row; flag = row is non-empty
-__global__ void k_res_heads(const int32_t *rowptr, int32_t V, int32_t *flag, uint32_t *heads32) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t s = rowptr[v];
-        const bool ne = rowptr[v + 1] > s;
-        flag[v] = ne ? 1 : 0;
-        if (ne) atomicOr(heads32 + (s >> 5), 1u << (s & 31));
+__global__ void k_res_empty(const int32_t *rowptr, int32_t V, int32_t *flag) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
+        flag[v] = rowptr[v + 1] == rowptr[v] ? 1 : 0;
+}
+
+// first stream edge of every graph (g = n: the stream's length)
+__global__ void k_res_eoff(const int32_t *vtx_off, int32_t n, const int32_t *rowptr, const int32_t *emp,
+                           int32_t *eoff) {
+    for (int32_t g = blockIdx.x * blockDim.x + threadIdx.x; g <= n; g += gridDim.x * blockDim.x) {
+        const int32_t v = vtx_off[g];
+        eoff[g] = rowptr[v] + emp[v];
+    }
+}
+
+// A warp per vertex v: its row goes to stream position rowptr[v] + emp[v] (emp = empty rows
+// before v) as sources relative to the graph's compact numbering, or, when it has no in-edge,
+// as one edge from the graph's zero slot; the row's first edge gets a head bit.
+__global__ void k_res_stream(const int32_t *rowptr, const int32_t *colidx, const int32_t *cpos, const int32_t *gid,
+                             const int32_t *vtx_off, const int32_t *emp, int32_t V, uint16_t *src16,
+                             uint32_t *heads32) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; v < V; v += warps) {
+        const int32_t s = rowptr[v], e = rowptr[v + 1], p = s + emp[v];
+        const int32_t g = gid[v];
+        const int32_t cg = cpos[vtx_off[g]];
+        if (lane == 0) atomicOr(heads32 + (p >> 5), 1u << (p & 31));
+        if (s == e) {
+            if (lane == 0) src16[p] = (uint16_t)(cpos[vtx_off[g + 1]] - cg);
+        } else {
+            for (int32_t i = s + lane; i < e; i += 32) src16[p + (i - s)] = (uint16_t)(cpos[colidx[i]] - cg);
+        }
     }
 }
 
@@ -538,12 +567,6 @@ __global__ void k_res_chunk_heads(const uint32_t *heads32, int64_t chunks, int32
         for (int i = 0; i < 16; ++i) k += __popc(heads32[16 * c + i]);
         cnt[c] = k;
     }
-}
-
-// slot[v] holds the exclusive count of non-empty rows before v; empty rows get -1
-__global__ void k_res_slot(const int32_t *flag, int32_t V, int32_t *slot) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x)
-        if (!flag[v]) slot[v] = -1;
 }
 
 // Builds (once) what the resident variant reads; sets m->res_ok when every graph's
@@ -584,48 +607,62 @@ static int build_resident(tc_multigraph *m, cudaStream_t s) {
     std::stable_sort(ord.begin(), ord.end(), [&](int32_t x, int32_t y) { return hs[n + x] > hs[n + y]; });
     delete[] hs;
     m->res_max = mx;
-    m->res_ok = mx <= 65536 && (size_t)mx * 4 + 1024 <= (size_t)caps.max_smem_optin;
+    // shared memory holds the contributions and the zero slot; sources are 16-bit
+    m->res_ok = mx + 1 <= 65536 && (size_t)(mx + 1) * 4 + 1024 <= (size_t)caps.max_smem_optin;
     if (m->res_ok) {
-        // whole 512-edge chunks plus one: a warp reads its last chunk (and the head words of
-        // its first) in full, past the final edge
-        const int64_t chunks = E / MR_CHUNK + 2;
-        TC_TRY(m->order.alloc((size_t)n * 4));
-        TC_TRY(m->src16.alloc((size_t)chunks * MR_CHUNK * 2));
-        TC_TRY(m->heads.alloc((size_t)chunks * (MR_CHUNK / 8)));
-        TC_TRY(m->hpre.alloc((size_t)(chunks + 1) * 4));
-        TC_TRY(m->slot.alloc((size_t)(V > 0 ? V : 1) * 4));
-        TC_TRY(m->scratch.alloc((size_t)(V > 0 ? V : 1) * 4));
-        DevBuf cnt;
-        TC_TRY(cnt.alloc((size_t)chunks * 4));
-        TC_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
-        TC_CUDA(cudaMemsetAsync(m->src16.p, 0, (size_t)chunks * MR_CHUNK * 2, s));
-        TC_CUDA(cudaMemsetAsync(m->heads.p, 0, (size_t)chunks * (MR_CHUNK / 8), s));
-        if (E > 0) {
-            k_multi_src16<<<caps.sms * 8, 256, 0, s>>>(m->g->in_colidx.as<int32_t>(), E, m->cpos.as<int32_t>(),
-                                                       m->gid.as<int32_t>(), m->vtx_off.as<int32_t>(),
-                                                       m->src16.as<uint16_t>());
-            TC_LAUNCH_CHECK();
-        }
+        DevBuf emp;
+        TC_TRY(emp.alloc(((size_t)V + 1) * 4));
+        TC_TRY(m->eoff.alloc(((size_t)n + 1) * 4));
         if (V > 0) {
-            k_res_heads<<<caps.sms * 8, 256, 0, s>>>(m->g->in_rowptr.as<int32_t>(), V, flag.as<int32_t>(),
-                                                     m->heads.as<uint32_t>());
+            k_res_empty<<<caps.sms * 8, 256, 0, s>>>(m->g->in_rowptr.as<int32_t>(), V, flag.as<int32_t>());
             TC_LAUNCH_CHECK();
-            TC_TRY(scan_i32(flag.as<int32_t>(), V, m->slot.as<int32_t>(), s));
-            k_res_slot<<<caps.sms * 8, 256, 0, s>>>(flag.as<int32_t>(), V, m->slot.as<int32_t>());
-            TC_LAUNCH_CHECK();
+            TC_TRY(scan_i32(flag.as<int32_t>(), V, emp.as<int32_t>(), s));
         }
-        k_res_chunk_heads<<<(int)((chunks + 255) / 256), 256, 0, s>>>(m->heads.as<uint32_t>(), chunks,
-                                                                      cnt.as<int32_t>());
+        k_multi_cpos_end<<<1, 1, 0, s>>>(emp.as<int32_t>(), flag.as<int32_t>(), V);
         TC_LAUNCH_CHECK();
-        TC_TRY(scan_i32(cnt.as<int32_t>(), chunks, m->hpre.as<int32_t>(), s));
+        k_res_eoff<<<(n + 256) / 256, 256, 0, s>>>(m->vtx_off.as<int32_t>(), n, m->g->in_rowptr.as<int32_t>(),
+                                                   emp.as<int32_t>(), m->eoff.as<int32_t>());
+        TC_LAUNCH_CHECK();
+        int32_t empties = 0;
+        TC_CUDA(cudaMemcpyAsync(&empties, emp.as<int32_t>() + V, 4, cudaMemcpyDeviceToHost, s));
         TC_CUDA(cudaStreamSynchronize(s));
+        const int64_t Ep = E + empties;
+        if (Ep + 2 * MR_CHUNK > INT32_MAX) {
+            m->res_ok = false;
+        } else {
+            // whole 512-edge chunks plus one: a warp reads its last chunk (and the head words of
+            // its first) in full, past the final edge
+            const int64_t chunks = Ep / MR_CHUNK + 2;
+            TC_TRY(m->order.alloc((size_t)n * 4));
+            TC_TRY(m->src16.alloc((size_t)chunks * MR_CHUNK * 2));
+            TC_TRY(m->heads.alloc((size_t)chunks * (MR_CHUNK / 8)));
+            TC_TRY(m->hpre.alloc((size_t)chunks * 4));
+            TC_TRY(m->scratch.alloc((size_t)(V > 0 ? V : 1) * 4));
+            DevBuf cnt;
+            TC_TRY(cnt.alloc((size_t)chunks * 4));
+            TC_CUDA(cudaMemcpyAsync(m->order.p, ord.data(), (size_t)n * 4, cudaMemcpyHostToDevice, s));
+            TC_CUDA(cudaMemsetAsync(m->src16.p, 0, (size_t)chunks * MR_CHUNK * 2, s));
+            TC_CUDA(cudaMemsetAsync(m->heads.p, 0, (size_t)chunks * (MR_CHUNK / 8), s));
+            if (V > 0) {
+                k_res_stream<<<caps.sms * 8, 256, 0, s>>>(m->g->in_rowptr.as<int32_t>(), m->g->in_colidx.as<int32_t>(),
+                                                          m->cpos.as<int32_t>(), m->gid.as<int32_t>(),
+                                                          m->vtx_off.as<int32_t>(), emp.as<int32_t>(), V,
+                                                          m->src16.as<uint16_t>(), m->heads.as<uint32_t>());
+                TC_LAUNCH_CHECK();
+            }
+            k_res_chunk_heads<<<(int)((chunks + 255) / 256), 256, 0, s>>>(m->heads.as<uint32_t>(), chunks,
+                                                                          cnt.as<int32_t>());
+            TC_LAUNCH_CHECK();
+            TC_TRY(scan_i32(cnt.as<int32_t>(), chunks, m->hpre.as<int32_t>(), s));
+            TC_CUDA(cudaStreamSynchronize(s));
+        }
     }
     m->res_built = true;
     return TC_OK;
 }
 
 static size_t res_smem_bytes(const tc_multigraph *m) {
-    return (size_t)((m->res_max + 3) & ~3) * 4;
+    return (size_t)((m->res_max + 1 + 3) & ~3) * 4;
 }
 
 typedef void (*MultiKernel)(MultiArgs);
@@ -660,11 +697,10 @@ static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int gri
     TC_CUDA(cudaMemsetAsync(m->sync.p, 0, 16, s));
     if (lanes == TC_MULTI_RESIDENT) {
         ResArgs r;
-        r.rowptr = a.rowptr;
         r.src16 = m->src16.as<uint16_t>();
         r.heads = m->heads.as<uint16_t>();
         r.hpre = m->hpre.as<int32_t>();
-        r.slot = m->slot.as<int32_t>();
+        r.eoff = m->eoff.as<int32_t>();
         r.cpos = m->cpos.as<int32_t>();
         r.vtx_off = m->vtx_off.as<int32_t>();
         r.order = m->order.as<int32_t>();
@@ -676,7 +712,6 @@ static int launch_multi(tc_multigraph *m, const MultiArgs &a, int lanes, int gri
         r.sums = m->scratch.as<float>();
         r.rank = a.rank;
         r.next = m->sync.as<unsigned>() + 3;
-        r.cap = (m->res_max + 3) & ~3;
         k_multi_resident<<<grid, MR_THREADS, res_smem_bytes(m), s>>>(r);
         TC_LAUNCH_CHECK();
         return TC_OK;

@@ -7,7 +7,8 @@
 // A further variant (TC_MULTI_RESIDENT) keeps each graph inside one CTA for all iterations:
 // the graph's contributions live in shared memory (compacted to its non-dangling vertices,
 // 16-bit source indices), so no grid barrier and no L2 gather is needed; CTAs take graphs
-// from a queue, largest first.
+// from a queue, largest first.  Inside the CTA the graph's in-edges are split evenly over the
+// warps (head bits mark row starts), so skewed degrees leave no lane idle.
 #include <cooperative_groups.h>
 
 #include <algorithm>

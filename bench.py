@@ -317,6 +317,12 @@ def variants(args, ctx, world):
     res[f"pull_tocab_{other}_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
     res[f"pull_tocab_{other}_bmin_frac"] = bmin_frac(ms)
     res[f"pull_tocab_{other}_blocks"] = Po.num_blocks
+    # the unstaged gathers again, with an L2 access-policy window over the contributions
+    ms = run(lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out, l2_window=True))
+    res["pull_unblocked_l2window_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    if other == "l2":
+        ms = run(lambda: T.pagerank_pull(G, Po, damping=DAMPING, iters=ITERS, out=out, l2_window=True))
+        res["pull_tocab_l2_l2window_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
     del Po
     Pp = T.tocab_partition(G, T.TC_PUSH, args.blocks, block_policy="l2")
     ms = run(lambda: T.pagerank_push(G, Pp, damping=DAMPING, iters=ITERS, out=out))

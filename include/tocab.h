@@ -200,6 +200,14 @@ typedef struct tc_pr_params {
                                  by one lane, longer rows by a warp (hubs by a CTA); 0 = 32,
                                  1 = a warp for every row, large = lane-serial; a partition's
                                  per-block table (tc_part_set_lb) overrides it */
+    int32_t l2_window;        /* nonzero: unstaged pull gathers (unblocked, or a partition without
+                                 the staged format) run with an L2 access-policy window over the
+                                 contributions they read, so that the cache keeps the block's
+                                 vertex values (Sec. 3.1) while the edges stream past.  The
+                                 context's persisting L2 set-aside is raised for the call and
+                                 restored before it returns, and the call synchronises the stream.
+                                 A device without a set-aside runs the call without a window.
+                                 Results are bitwise those of l2_window = 0 */
 } tc_pr_params;
 
 typedef struct tc_pr_stats {

@@ -203,7 +203,7 @@ _MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED, "float": L.T
 
 
 def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream, merge="fixed",
-              lb_warp_min=0):
+              lb_warp_min=0, l2_window=False):
     if out is None:
         out = torch.empty(graph.V, dtype=torch.float32, device="cuda")
     if out.dtype != torch.float32 or out.numel() < graph.V or not out.is_contiguous():
@@ -217,7 +217,7 @@ def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profil
         init = init.contiguous()
         init_ptr = init.data_ptr()
     pp = L.tc_pr_params(float(damping), int(iters), mode, _mem(out), init_ptr, 1 if profile else 0,
-                        _MERGE[merge], int(lb_warp_min))
+                        _MERGE[merge], int(lb_warp_min), 1 if l2_window else 0)
     st = L.tc_pr_stats()
     _check(fn(graph.handle, part.handle if part is not None else None, C.byref(pp), out.data_ptr(),
               C.byref(st), _stream(stream)), name)
@@ -227,11 +227,12 @@ def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profil
 def pagerank_pull(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
                   dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
                   profile: bool = False, stream=None, return_stats: bool = False, merge: str = "fixed",
-                  lb_warp_min: int = 0):
+                  lb_warp_min: int = 0, l2_window: bool = False):
     """tc_pagerank_pull (Alg. 1; TOCAB Alg. 4 + merge when part is given).
-    merge: "fixed" (default) or "ordered" (both deterministic), or "float"."""
+    merge: "fixed" (default) or "ordered" (both deterministic), or "float".
+    l2_window: an L2 access-policy window over the contributions of the unstaged gathers."""
     r, st = _pagerank(L.load().tc_pagerank_pull, "tc_pagerank_pull", graph, part, damping, iters, dangling, out,
-                      init, profile, stream, merge, lb_warp_min)
+                      init, profile, stream, merge, lb_warp_min, l2_window)
     return (r, st) if return_stats else r
 
 

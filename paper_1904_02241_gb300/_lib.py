@@ -51,7 +51,7 @@ TC_MULTI_RESIDENT = 1024
 class tc_pr_params(C.Structure):
     _fields_ = [("damping", C.c_float), ("iters", C.c_int32), ("dangling", C.c_int32),
                 ("out_mem", C.c_int32), ("init", C.c_void_p), ("profile", C.c_int32),
-                ("merge_mode", C.c_int32), ("lb_warp_min", C.c_int32)]
+                ("merge_mode", C.c_int32), ("lb_warp_min", C.c_int32), ("l2_window", C.c_int32)]
 
 
 class tc_pr_stats(C.Structure):

@@ -79,3 +79,34 @@ def test_memory_cap_arguments(lib):
     assert lib.tc_set_device_memory_limit(-1) == -1
     assert lib.tc_set_device_memory_limit(0) == 0
     assert lib.tc_device_memory_held() >= 0
+
+
+def _header_structs():
+    """Field names of every `typedef struct X { ... } X;` in include/tocab.h, in order."""
+    txt = open(os.path.join(ROOT, "include", "tocab.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for m in re.finditer(r"typedef struct (tc_[a-z_]+)\s*\{(.*?)\}\s*\1\s*;", txt, flags=re.S):
+        fields = []
+        for decl in m.group(2).split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            for part in decl.split(","):  # "int32_t a, b" declares two fields
+                part = part.split("[")[0]  # "float x[N]": the name is before the bound
+                fields.append(re.findall(r"[A-Za-z_][A-Za-z0-9_]*", part)[-1])
+        out[m.group(1)] = fields
+    return out
+
+
+def test_ctypes_structs_mirror_the_header():
+    """Every struct the binding passes by pointer has the header's fields in the header's order
+    (a field missing or out of place would shift every later one)."""
+    from paper_1904_02241_gb300 import _lib as L
+    hdr = _header_structs()
+    mirrored = [n for n in dir(L) if n.startswith("tc_") and isinstance(getattr(L, n), type)
+                and issubclass(getattr(L, n), L.C.Structure)]
+    assert {"tc_pr_params", "tc_part_params", "tc_bfs_params", "tc_multi_params"} <= set(mirrored)
+    for name in mirrored:
+        assert name in hdr, name
+        assert [f[0] for f in getattr(L, name)._fields_] == hdr[name], name

@@ -266,6 +266,21 @@ def test_pagerank_pull_staged_vs_unstaged(T, name, B, stage):
     assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
 
 
+@pytest.mark.parametrize("B", [None, 3])
+def test_pagerank_pull_l2_window_changes_no_bit(T, B):
+    """The L2 access-policy window only changes what the cache keeps: the ranks are bitwise those
+    without it, for the unblocked and the unstaged TOCAB gather."""
+    g = GRAPHS["rmat14_noperm"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B, smem_stage=-1) if B is not None else None
+    plain = T.pagerank_pull(G, P).cpu()
+    win = T.pagerank_pull(G, P, l2_window=True).cpu()
+    assert torch.equal(plain, win)
+    assert l1_rel(win.numpy(), _oracle_pr(g)) <= TOL
+    again = T.pagerank_pull(G, P).cpu()  # the set-aside is back: a plain call still agrees
+    assert torch.equal(plain, again)
+
+
 def test_smem_block_policy(T):
     g = gg.rmat(16)
     G = _load(T, g)

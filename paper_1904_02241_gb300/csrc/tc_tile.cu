@@ -268,41 +268,49 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
 // ---------------------------------------------------------------------------------------------
 // building the staged format from a base partition
 // ---------------------------------------------------------------------------------------------
-__global__ void k_tile_fill(const int32_t *rowptr, const int32_t *colidx, int64_t R, const int64_t *blk_rows,
-                            const int64_t *blk_edges, const int64_t *pbase, int32_t B, int32_t W, uint16_t *col16,
-                            uint32_t *heads32) {
-    // one thread per local row: copy its edges (block-relative sources), set its head bit.
-    // A warp's 32 rows are consecutive, so their head positions increase with the lane: lanes
-    // whose heads share a 32-bit word OR their bits together (segmented shuffle reduction)
-    // and one atomic per word remains.
+// Block b's edges are contiguous in the partition and keep their order in the staged stream, so
+// filling it is a straight copy: col16[pbase[b] + (i - eb)] = colidx[i] - b*W (grid.y strides
+// over blocks, grid.x over a block's edges).
+__global__ void k_tile_copy(const int32_t *colidx, const int64_t *blk_edges, const int64_t *pbase, int32_t B,
+                            int32_t W, uint16_t *col16) {
+    for (int32_t b = blockIdx.y; b < B; b += gridDim.y) {
+        const int64_t eb = blk_edges[b], ee = blk_edges[b + 1];
+        const int64_t off = pbase[b] - eb;
+        const int32_t base = b * W;
+        for (int64_t i = eb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ee;
+             i += (int64_t)gridDim.x * blockDim.x)
+            col16[i + off] = (uint16_t)(__ldg(colidx + i) - base);
+    }
+}
+
+// A head bit at the first staged edge of every local row.  A warp's 32 rows are consecutive, so
+// their head positions increase with the lane: lanes whose heads share a 32-bit word OR their
+// bits together (segmented shuffle reduction) and one atomic per word remains.
+__global__ void k_tile_heads(const int32_t *rowptr, const int64_t *blk_rows, const int64_t *blk_edges,
+                             const int64_t *pbase, int32_t B, uint32_t *heads32) {
     const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < R; r0 += stride) {
-        const int64_t r = r0 + lane;
-        uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past R: a group of their own, no atomic
-        if (r < R) {
-            int32_t lo = 0, hi = B;  // block of row r: last b with blk_rows[b] <= r, non-empty
-            while (hi - lo > 1) {
-                const int32_t mid = (lo + hi) >> 1;
-                if (blk_rows[mid] <= r) lo = mid; else hi = mid;
+    for (int32_t b = blockIdx.y; b < B; b += gridDim.y) {
+        const int64_t r1 = blk_rows[b + 1];
+        const int64_t off = pbase[b] - blk_edges[b];
+        for (int64_t r0 = blk_rows[b] + blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < r1;
+             r0 += (int64_t)gridDim.x * blockDim.x) {
+            const int64_t r = r0 + lane;
+            uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past the block: a group of their own, no atomic
+            if (r < r1) {
+                const int64_t dst = rowptr[r] + off;
+                word = (uint32_t)(dst >> 5);
+                bit = 1u << (dst & 31);
             }
-            const int32_t b = lo;
-            const int32_t s = rowptr[r], e = rowptr[r + 1];
-            const int64_t dst = pbase[b] + (s - blk_edges[b]);
-            const int32_t base = b * W;
-            for (int32_t i = s; i < e; ++i) col16[dst + (i - s)] = (uint16_t)(colidx[i] - base);
-            word = (uint32_t)(dst >> 5);
-            bit = 1u << (dst & 31);
-        }
-        uint32_t v = bit;
+            uint32_t v = bit;
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
-            const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
-            if (lane + d < 32 && wy == word) v |= y;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
+                const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
+                if (lane + d < 32 && wy == word) v |= y;
+            }
+            const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
+            if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
         }
-        const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
-        if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
     }
 }
 
@@ -324,7 +332,6 @@ __global__ void k_tile_wtab(const int32_t *rowptr, const int64_t *blk_rows, cons
 }
 
 int build_tiles(tc_part *p, int sms, cudaStream_t s) {
-    (void)sms;
     p->tiled = false;
     const int64_t R = p->R;
     const int32_t B = p->B;
@@ -358,10 +365,14 @@ int build_tiles(tc_part *p, int sms, cudaStream_t s) {
     TC_CUDA(cudaMemsetAsync(p->col16.p, 0, (size_t)(npad + WCH) * 2, s));
     TC_CUDA(cudaMemsetAsync(p->heads.p, 0, (size_t)(npad + WCH) / 8 + 64, s));
     TC_TRY(p->wtab.alloc((size_t)B * (TWARPS + 1) * 8));
-    const int grid = 152 * 8;
-    k_tile_fill<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->colidx.as<int32_t>(), R, p->blk_rows_dev.as<int64_t>(),
-                                     blk_edges.as<int64_t>(), pbase.as<int64_t>(), B, p->W, p->col16.as<uint16_t>(),
-                                     p->heads.as<uint32_t>());
+    // grid.y over blocks, grid.x over each block's share: about 8 CTAs per SM in all
+    const int gy = B < 65535 ? B : 65535;
+    const dim3 grid((unsigned)((sms * 8 + gy - 1) / gy), (unsigned)gy);
+    k_tile_copy<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), blk_edges.as<int64_t>(), pbase.as<int64_t>(), B, p->W,
+                                     p->col16.as<uint16_t>());
+    TC_LAUNCH_CHECK();
+    k_tile_heads<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->blk_rows_dev.as<int64_t>(), blk_edges.as<int64_t>(),
+                                      pbase.as<int64_t>(), B, p->heads.as<uint32_t>());
     TC_LAUNCH_CHECK();
     k_tile_wtab<<<(B * (TWARPS + 1) + 255) / 256, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->blk_rows_dev.as<int64_t>(),
                                                                blk_edges.as<int64_t>(), pbase.as<int64_t>(), B,

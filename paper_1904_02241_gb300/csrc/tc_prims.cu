@@ -487,14 +487,13 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
     __syncwarp();
     const int64_t tile0 = (int64_t)blockIdx.x * RX_TILE;
     const int64_t base = tile0 + (int64_t)warp * RX_PER_WARP;
-    // keys stay in registers from the start; values are loaded only when they are placed (C),
-    // which keeps registers low enough for more CTAs per SM during the ranking
-    int32_t key[RX_WROUNDS];
+    int32_t key[RX_WROUNDS], val[RX_WROUNDS];
     uint32_t local[RX_WROUNDS / 2];  // rank of each item among its warp's items of its bucket (16 bits each)
 #pragma unroll
     for (int r = 0; r < RX_WROUNDS; ++r) {
         const int64_t i = base + r * 32 + lane;
         key[r] = (i < n) ? kin[i] : 0;
+        val[r] = (i < n) ? vin[i] : 0;
     }
     // (A) counts per warp and bucket, and each item's rank among them (earlier rounds first,
     // then lower lanes)
@@ -555,7 +554,7 @@ __global__ void __launch_bounds__(RX_THREADS) k_rx_scatter(const int32_t *kin, c
             const int b = rx_bucket<NB>(key[r], dg);
             const int slot = lstart[b] + wpos[warp * NB + b] + (int)((local[r >> 1] >> (16 * (r & 1))) & 0xFFFFu);
             skey[slot] = key[r];
-            sval[slot] = vin[i];
+            sval[slot] = val[r];
         }
     }
     __syncthreads();

@@ -277,9 +277,17 @@ __global__ void k_tile_copy(const int32_t *colidx, const int64_t *blk_edges, con
         const int64_t eb = blk_edges[b], ee = blk_edges[b + 1];
         const int64_t off = pbase[b] - eb;
         const int32_t base = b * W;
-        for (int64_t i = eb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < ee;
-             i += (int64_t)gridDim.x * blockDim.x)
-            col16[i + off] = (uint16_t)(__ldg(colidx + i) - base);
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        int64_t i = eb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+        // eight independent loads in flight per thread, then their stores
+        for (; i + 7 * stride < ee; i += 8 * stride) {
+            int32_t c[8];
+#pragma unroll
+            for (int k = 0; k < 8; ++k) c[k] = __ldg(colidx + i + k * stride);
+#pragma unroll
+            for (int k = 0; k < 8; ++k) col16[i + k * stride + off] = (uint16_t)(c[k] - base);
+        }
+        for (; i < ee; i += stride) col16[i + off] = (uint16_t)(__ldg(colidx + i) - base);
     }
 }
 
@@ -292,24 +300,35 @@ __global__ void k_tile_heads(const int32_t *rowptr, const int64_t *blk_rows, con
     for (int32_t b = blockIdx.y; b < B; b += gridDim.y) {
         const int64_t r1 = blk_rows[b + 1];
         const int64_t off = pbase[b] - blk_edges[b];
+        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+        // four groups of 32 rows per step: their row offsets are loaded together
         for (int64_t r0 = blk_rows[b] + blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < r1;
-             r0 += (int64_t)gridDim.x * blockDim.x) {
-            const int64_t r = r0 + lane;
-            uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past the block: a group of their own, no atomic
-            if (r < r1) {
-                const int64_t dst = rowptr[r] + off;
-                word = (uint32_t)(dst >> 5);
-                bit = 1u << (dst & 31);
-            }
-            uint32_t v = bit;
+             r0 += 4 * stride) {
+            int32_t s4[4];
 #pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
-                const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
-                if (lane + d < 32 && wy == word) v |= y;
+            for (int k = 0; k < 4; ++k) {
+                const int64_t r = r0 + k * stride + lane;
+                s4[k] = r < r1 ? rowptr[r] : 0;
             }
-            const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
-            if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                const int64_t r = r0 + k * stride + lane;
+                uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past the block: a group of their own, no atomic
+                if (r < r1) {
+                    const int64_t dst = s4[k] + off;
+                    word = (uint32_t)(dst >> 5);
+                    bit = 1u << (dst & 31);
+                }
+                uint32_t v = bit;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
+                    const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
+                    if (lane + d < 32 && wy == word) v |= y;
+                }
+                const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
+                if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
+            }
         }
     }
 }

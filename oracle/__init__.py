@@ -10,6 +10,8 @@ Functions (each cites the paper passage it restates; see ``oracle.c``):
   ppr_pull            -- personalised PageRank per source (teleport and dangling to s)
   bfs                 -- level-synchronous BFS hop levels (status arrays, Sec. 3.3)
   partition           -- TOCAB static 1D blocking with local IDs (Sec. 3.1, Fig. 3/4)
+  bc_forward          -- Alg. 3: depth (delta) and shortest-path counts (sigma) from a source
+  bc                  -- betweenness scores: Alg. 3 forward + dependency back-propagation
   mlp_*               -- the cost model's MLP forward/backward in FP64 (oracle/mlp.py)
 """
 from __future__ import annotations
@@ -63,8 +65,11 @@ def _load():
             lib.orc_bfs.argtypes = [c.c_int32, i32p, i32p, c.c_int32, i32p]
             lib.orc_partition.argtypes = [c.c_int32, i32p, i32p, c.c_int32, c.c_int32,
                                           i64p, i64p, c.c_void_p, c.c_void_p, c.c_void_p]
+            lib.orc_bc_forward.argtypes = [c.c_int32, i32p, i32p, c.c_int32, i32p, f64p, i32p,
+                                           c.POINTER(c.c_int32)]
+            lib.orc_bc.argtypes = [c.c_int32, i32p, i32p, c.c_int32, i32p, f64p]
             for f in ("orc_transpose", "orc_pagerank_pull", "orc_pagerank_push", "orc_ppr_pull",
-                      "orc_bfs", "orc_partition"):
+                      "orc_bfs", "orc_partition", "orc_bc_forward", "orc_bc"):
                 getattr(lib, f).restype = c.c_int
             _lib = lib
     return _lib
@@ -167,6 +172,30 @@ def partition(V, rowptr, colidx, W: int):
                              idm.ctypes.data, col.ctypes.data), "partition")
     return {"B": B, "W": W, "blk_rows": blk_rows, "blk_edges": blk_edges, "rowptr": rp,
             "id_map": idm[:R], "colidx": col[:E]}
+
+
+def bc_forward(V, rowptr, colidx, source):
+    """Alg. 3 from ``source`` over out-edges: (depth int32[V], -1 unreached; sigma float64[V])."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    depth = np.zeros(V, np.int32)
+    sigma = np.zeros(V, np.float64)
+    order = np.zeros(V, np.int32)
+    count = ctypes.c_int32(0)
+    cc = colidx if colidx.size else np.zeros(1, np.int32)
+    _check(_load().orc_bc_forward(V, rowptr, cc, int(source), depth, sigma, order, ctypes.byref(count)),
+           "bc_forward")
+    return depth, sigma
+
+
+def bc(V, rowptr, colidx, sources=None):
+    """Betweenness scores summed over ``sources`` (all vertices when None) and ordered targets."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    srcs = _i32(np.arange(V) if sources is None else sources)
+    score = np.zeros(V, np.float64)
+    cc = colidx if colidx.size else np.zeros(1, np.int32)
+    sp = srcs if srcs.size else np.zeros(1, np.int32)
+    _check(_load().orc_bc(V, rowptr, cc, srcs.size, sp, score), "bc")
+    return score
 
 
 from .mlp import mlp_forward, mlp_backward, mlp_loss  # noqa: E402,F401

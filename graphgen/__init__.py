@@ -306,6 +306,14 @@ def rmat_batch(scales, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, 
     return g, vtx_off.to(torch.int32)
 
 
+def edge_values(g: CSRGraph, seed: int = 23, lo: float = -1.0, hi: float = 1.0) -> torch.Tensor:
+    """Seeded FP32 value per stored entry (a weighted graph or a sparse matrix), uniform in
+    [lo, hi), drawn from the counter hash of (seed, entry index): float32[E], on g's device."""
+    e = torch.arange(g.E, dtype=torch.int64, device=g.colidx.device)
+    u = (hash_u32(seed, e).to(torch.float64) + 0.5) / 2**32
+    return (lo + (hi - lo) * u).to(torch.float32)
+
+
 def batch_scales(count: int = 1000, lo: int = 10, hi: int = 16, seed: int = 19) -> list[int]:
     """Seeded scales drawn uniformly from [lo, hi] for a many-graph batch."""
     u = hash_u32(seed, torch.arange(count, dtype=torch.int64))

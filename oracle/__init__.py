@@ -12,6 +12,7 @@ Functions (each cites the paper passage it restates; see ``oracle.c``):
   partition           -- TOCAB static 1D blocking with local IDs (Sec. 3.1, Fig. 3/4)
   bc_forward          -- Alg. 3: depth (delta) and shortest-path counts (sigma) from a source
   bc                  -- betweenness scores: Alg. 3 forward + dependency back-propagation
+  spmv                -- y = A x for a CSR matrix with values (Sec. 4's SpMV benchmark)
   mlp_*               -- the cost model's MLP forward/backward in FP64 (oracle/mlp.py)
 """
 from __future__ import annotations
@@ -68,8 +69,9 @@ def _load():
             lib.orc_bc_forward.argtypes = [c.c_int32, i32p, i32p, c.c_int32, i32p, f64p, i32p,
                                            c.POINTER(c.c_int32)]
             lib.orc_bc.argtypes = [c.c_int32, i32p, i32p, c.c_int32, i32p, f64p]
+            lib.orc_spmv.argtypes = [c.c_int32, i32p, i32p, f64p, f64p, f64p]
             for f in ("orc_transpose", "orc_pagerank_pull", "orc_pagerank_push", "orc_ppr_pull",
-                      "orc_bfs", "orc_partition", "orc_bc_forward", "orc_bc"):
+                      "orc_bfs", "orc_partition", "orc_bc_forward", "orc_bc", "orc_spmv"):
                 getattr(lib, f).restype = c.c_int
             _lib = lib
     return _lib
@@ -196,6 +198,19 @@ def bc(V, rowptr, colidx, sources=None):
     sp = srcs if srcs.size else np.zeros(1, np.int32)
     _check(_load().orc_bc(V, rowptr, cc, srcs.size, sp, score), "bc")
     return score
+
+
+def spmv(nrows, rowptr, colidx, vals, x):
+    """y = A x in FP64 for A in CSR (rows = outputs), values ``vals`` per stored entry."""
+    rowptr, colidx = _i32(rowptr), _i32(colidx)
+    vals = np.ascontiguousarray(vals, dtype=np.float64)
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    y = np.zeros(nrows, np.float64)
+    cc = colidx if colidx.size else np.zeros(1, np.int32)
+    vv = vals if vals.size else np.zeros(1, np.float64)
+    xx = x if x.size else np.zeros(1, np.float64)
+    _check(_load().orc_spmv(int(nrows), rowptr, cc, vv, xx, y), "spmv")
+    return y
 
 
 from .mlp import mlp_forward, mlp_backward, mlp_loss  # noqa: E402,F401

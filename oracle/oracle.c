@@ -310,3 +310,22 @@ int orc_bc(int32_t V, const int32_t *rowptr, const int32_t *colidx, int32_t nsrc
     free(depth); free(order); free(sigma); free(dep);
     return rc;
 }
+
+/* ------------------------------------------------------------------------------------
+ * Sparse matrix-vector product y = A x (Sec. 4: SpMV as the generalised form of the graph
+ * operators), with A in CSR: row i holds the entries A[i][colidx[k]] = vals[k] for
+ * k in [rowptr[i], rowptr[i+1]).  Each y[i] is the sum of its row's products in the
+ * row's storage order, in FP64.  In graph terms this is the pull gather of Alg. 1 with a
+ * value on every edge (rows = destinations, columns = sources).
+ * ---------------------------------------------------------------------------------- */
+int orc_spmv(int32_t nrows, const int32_t *rowptr, const int32_t *colidx, const double *vals,
+             const double *x, double *y)
+{
+    if (nrows < 0) return ORC_EINVAL;
+    for (int32_t i = 0; i < nrows; ++i) {
+        double acc = 0.0;
+        for (int64_t k = rowptr[i]; k < rowptr[i + 1]; ++k) acc += vals[k] * x[colidx[k]];
+        y[i] = acc;
+    }
+    return ORC_OK;
+}

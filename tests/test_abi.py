@@ -112,17 +112,14 @@ def test_ctypes_structs_mirror_the_header():
         assert [f[0] for f in getattr(L, name)._fields_] == hdr[name], name
 
 
-def test_missing_library_fails_loudly(tmp_path):
+def test_missing_library_fails_loudly():
     """Without the built library the binding raises: there is no CPU fallback to land on."""
     from paper_1904_02241_gb300 import _lib as L
-    with pytest.raises(ImportError, match="missing"):
-        L.load(str(tmp_path / "libtocab.so")) if L._lib is None else _fresh_load(L, tmp_path)
-
-
-def _fresh_load(L, tmp_path):
+    absent = os.path.join(ROOT, "paper_1904_02241_gb300", "no_such_dir", "libtocab.so")
     saved = L._lib
     L._lib = None
     try:
-        return L.load(str(tmp_path / "libtocab.so"))
+        with pytest.raises(ImportError, match="missing"):
+            L.load(absent)
     finally:
         L._lib = saved

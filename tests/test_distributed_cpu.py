@@ -48,7 +48,7 @@ def test_two_gloo_ranks_reduce_like_bench():
         assert ndig == 1         # identical seeded replicas
 
 
-def test_reference_arm_runs_on_cpu(tmp_path):
+def test_reference_arm_runs_on_cpu():
     import json
     import subprocess
     import sys

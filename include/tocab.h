@@ -313,6 +313,37 @@ int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
 int tc_ppr_batch(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t n,
                  const tc_pr_params *params, float *R_out, tc_pr_stats *stats, void *stream);
 
+/* ---- betweenness centrality ----------------------------------------------------------------- */
+/*
+ * tc_bc_forward -- the shortest-path calculation of Alg. 3 from one source over the out-edges
+ * of G: depth_out[v] = hop distance from `source` (-1 when unreachable; the paper's delta) and
+ * sigma_out[v] = number of shortest paths from `source` to v (the paper's sigma, FP64, exact
+ * below 2^53; 0 when unreachable).  Computed topology-driven in the pull direction (every level
+ * scans the in-rows of the vertices not yet reached), with no atomics.
+ *   out_mem : memory space of depth_out (int32[V]) and sigma_out (double[V]).
+ * Synchronises the stream.  Errors: TC_ERR_INVALID_ARG (source outside [0, V), bad out_mem),
+ * TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int32_t *depth_out, double *sigma_out,
+                  void *stream);
+
+/*
+ * tc_bc -- betweenness-centrality scores from a set of sources (Sec. 3.3's BC benchmark): for
+ * each source, Alg. 3's forward sweep, then the dependency back-propagation over the levels in
+ * reverse,
+ *   dep[v] = sum over out-neighbours w with depth[w] = depth[v] + 1 of sigma[v]/sigma[w] (1 + dep[w]),
+ * pulled over the out-edges of G; scores_out[v] = the sum of dep[v] over the sources other than
+ * v itself.  Scores are not normalised and count ordered targets (an undirected graph given
+ * with both edge directions counts every pair twice).  FP64 throughout; every product, quotient
+ * and sum is rounded separately, in the formula's order, so the result is deterministic.
+ *   sources : host int32[num_sources], each in [0, V) (repeats allowed; 0 sources gives zeros).
+ *   out_mem : memory space of scores_out (double[V]).
+ * Scratch: int32[V] + 3 double[V] (+ double[V] for host output), per call.
+ * Synchronises the stream.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int out_mem, double *scores_out,
+          void *stream);
+
 /* ---- many small graphs in one batch ---------------------------------------------------------- */
 typedef struct tc_multigraph tc_multigraph;   /* opaque: a batch of independent graphs */
 

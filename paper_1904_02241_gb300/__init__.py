@@ -245,6 +245,28 @@ def pagerank_push(graph: Graph, part: Partition | None = None, damping: float = 
     return (r, st) if return_stats else r
 
 
+def bc_forward(graph: Graph, source: int, stream=None):
+    """tc_bc_forward (Alg. 3): (depth int32[V], -1 unreachable; sigma float64[V]) on the device."""
+    depth = torch.empty(graph.V, dtype=torch.int32, device="cuda")
+    sigma = torch.empty(graph.V, dtype=torch.float64, device="cuda")
+    _check(L.load().tc_bc_forward(graph.handle, int(source), L.TC_MEM_DEVICE, depth.data_ptr(), sigma.data_ptr(),
+                                  _stream(stream)), "tc_bc_forward")
+    return depth, sigma
+
+
+def bc(graph: Graph, sources=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """tc_bc: betweenness scores summed over ``sources`` (all vertices when None) -> float64[V]."""
+    src = torch.arange(graph.V, dtype=torch.int32) if sources is None else \
+        torch.as_tensor(sources, dtype=torch.int32).reshape(-1).contiguous().cpu()
+    if out is None:
+        out = torch.empty(graph.V, dtype=torch.float64, device="cuda")
+    if out.dtype != torch.float64 or out.numel() < graph.V or not out.is_contiguous():
+        raise ValueError("out must be a contiguous float64 tensor with V elements")
+    _check(L.load().tc_bc(graph.handle, src.data_ptr() if src.numel() else None, src.numel(), _mem(out),
+                          out.data_ptr(), _stream(stream)), "tc_bc")
+    return out
+
+
 def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out: torch.Tensor | None = None,
               profile: bool = False, stream=None, return_stats: bool = False, part: Partition | None = None):
     """tc_ppr_batch: personalised PageRank, one column per source -> [V, n] float32.

@@ -1,0 +1,98 @@
+"""Betweenness centrality through the C ABI against the FP64 oracle: Alg. 3's depths and
+shortest-path counts exactly, the scores within rounding of the oracle's, on graphs with
+branching shortest paths (grids, hypercubes), skew (R-MAT), directed reachability gaps,
+isolated vertices and no edges."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_02241_gb300 as T
+    T.lib()
+    return T
+
+
+def _hypercube(k):
+    return gg.from_edge_list(1 << k, [(x, x ^ (1 << b)) for x in range(1 << k) for b in range(k)])
+
+
+GRAPHS = {
+    "path": gg.path(40),
+    "dpath": gg.path(30, directed=True),
+    "star": gg.star(50),
+    "grid": gg.grid2d(12, 15, drop=0.0),
+    "grid_drop": gg.grid2d(20, 20, drop=0.2, seed=3),
+    "cube": _hypercube(7),
+    "rmat": gg.symmetrize(gg.rmat(9)),
+    "rmat_dir": gg.rmat(9, seed=4),
+    "er": gg.random_small(300, 1400, 6),
+    "empty": gg.empty_graph(9),
+}
+
+
+def _load(T, g):
+    return T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_forward_depths_and_counts_exact(T, name):
+    g = GRAPHS[name]
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    for s in sorted({0, g.V // 2, g.V - 1}):
+        depth, sigma = T.bc_forward(G, s)
+        want_d, want_s = oracle.bc_forward(g.V, rp, ci, s)
+        assert np.array_equal(depth.cpu().numpy(), want_d), (name, s)
+        assert np.array_equal(sigma.cpu().numpy(), want_s), (name, s)
+
+
+@pytest.mark.parametrize("name", list(GRAPHS))
+def test_scores_all_sources(T, name):
+    g = GRAPHS[name]
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    got = T.bc(G).cpu().numpy()
+    want = oracle.bc(g.V, rp, ci)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-9)
+    assert torch.equal(T.bc(G).cpu(), torch.from_numpy(got))  # deterministic
+
+
+def test_scores_source_subset_and_host_output(T):
+    g = gg.symmetrize(gg.rmat(12))
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    srcs = gg.sources(g, 8, seed=13)
+    want = oracle.bc(g.V, rp, ci, srcs)
+    dev = T.bc(G, srcs).cpu().numpy()
+    np.testing.assert_allclose(dev, want, rtol=1e-12, atol=1e-9)
+    host = torch.empty(g.V, dtype=torch.float64)
+    T.bc(G, srcs, out=host)
+    assert np.array_equal(host.numpy(), dev)
+    assert np.all(T.bc(G, []).cpu().numpy() == 0.0)
+
+
+def test_closed_forms_on_device(T):
+    n = 25
+    G = _load(T, gg.path(n))
+    assert np.array_equal(T.bc(G).cpu().numpy(), np.array([2.0 * i * (n - 1 - i) for i in range(n)]))
+    G = _load(T, gg.star(30))
+    s = T.bc(G).cpu().numpy()
+    assert s[0] == 30 * 29 and np.all(s[1:] == 0.0)
+
+
+def test_invalid_source_is_refused(T):
+    G = _load(T, gg.path(5))
+    with pytest.raises(T.TocabError) as e:
+        T.bc(G, [7])
+    assert e.value.status == -1
+    with pytest.raises(T.TocabError):
+        T.bc_forward(G, -1)

@@ -344,6 +344,19 @@ int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int32_t *depth
 int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int out_mem, double *scores_out,
           void *stream);
 
+/* ---- sparse matrix-vector product ---------------------------------------------------------- */
+/*
+ * tc_spmv -- y = A x (the SpMV benchmark of Sec. 4).  A is the CSR loaded with
+ * tc_graph_load_csr, read as rows = outputs: y[i] = sum over the stored entries k of row i of
+ * vals[k] * x[colidx[k]], with vals in the loaded entry order.  FP32 values, vectors and
+ * accumulation; a warp per row with a fixed reduction order (deterministic).  The graph's
+ * preprocessing (transpose, degrees) is not used.
+ *   vals : float[E], x : float[V], y : float[V] (y[i] for every row i < V), all device pointers.
+ *   mem  : TC_MEM_DEVICE (TC_MEM_HOST is refused with TC_ERR_UNSUPPORTED).
+ * Asynchronous on `stream`.  Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED, TC_ERR_CUDA.
+ */
+int tc_spmv(const tc_graph *g, const float *vals, const float *x, float *y, int mem, void *stream);
+
 /* ---- many small graphs in one batch ---------------------------------------------------------- */
 typedef struct tc_multigraph tc_multigraph;   /* opaque: a batch of independent graphs */
 

@@ -267,6 +267,21 @@ def bc(graph: Graph, sources=None, out: torch.Tensor | None = None, stream=None)
     return out
 
 
+def spmv(matrix: Graph, vals: torch.Tensor, x: torch.Tensor, out: torch.Tensor | None = None,
+         stream=None) -> torch.Tensor:
+    """tc_spmv: y = A x for the CSR loaded as ``matrix`` (rows = outputs); float32 on the device."""
+    for t, n, what in ((vals, matrix.E, "vals"), (x, matrix.V, "x")):
+        if t.dtype != torch.float32 or not t.is_cuda or not t.is_contiguous() or t.numel() < n:
+            raise ValueError(f"{what} must be a contiguous float32 CUDA tensor with {n} elements")
+    if out is None:
+        out = torch.empty(matrix.V, dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() < matrix.V:
+        raise ValueError("out must be a contiguous float32 CUDA tensor with V elements")
+    _check(L.load().tc_spmv(matrix.handle, vals.data_ptr() if vals.numel() else None, x.data_ptr(), out.data_ptr(),
+                            L.TC_MEM_DEVICE, _stream(stream)), "tc_spmv")
+    return out
+
+
 def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out: torch.Tensor | None = None,
               profile: bool = False, stream=None, return_stats: bool = False, part: Partition | None = None):
     """tc_ppr_batch: personalised PageRank, one column per source -> [V, n] float32.

@@ -101,6 +101,7 @@ SIGNATURES = {
     "tc_bfs_pull": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_bfs_params), VP, C.POINTER(tc_bfs_stats), VP]),
     "tc_bc_forward": (C.c_int, [VP, C.c_int32, C.c_int, VP, VP, VP]),
     "tc_bc": (C.c_int, [VP, VP, C.c_int32, C.c_int, VP, VP]),
+    "tc_spmv": (C.c_int, [VP, VP, VP, VP, C.c_int, VP]),
     "tc_ppr_batch": (C.c_int, [VP, VP, VP, C.c_int32, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_multigraph_load": (C.c_int, [C.c_int32, VP, C.c_int32, C.c_int64, VP, VP, C.c_int, VP, C.POINTER(VP)]),
     "tc_multigraph_free": (None, [VP]),

@@ -1,0 +1,77 @@
+"""SpMV through the C ABI against the FP64 oracle.  The GPU sums in FP32 (fused multiply-adds per
+lane, then a 5-level shuffle tree), so row i may differ from the exact product by at most
+(d_i + 6) * 2^-24 * sum_k |a_ik x_k| (d_i = stored entries of the row): the standard bound for a
+summation whose longest chain has at most d_i + 5 roundings.  The inputs are the same FP32 values
+on both sides."""
+import numpy as np
+import pytest
+import torch
+
+import graphgen as gg
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def T():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_1904_02241_gb300 as T
+    T.lib()
+    return T
+
+
+def _check(T, g, vals, x):
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+    y = T.spmv(G, vals.cuda(), x.cuda()).cpu().numpy().astype(np.float64)
+    rp, ci = g.numpy()
+    v64, x64 = vals.numpy().astype(np.float64), x.numpy().astype(np.float64)
+    want = oracle.spmv(g.V, rp, ci, v64, x64)
+    mag = oracle.spmv(g.V, rp, ci, np.abs(v64), np.abs(x64))
+    bound = (np.diff(rp) + 6) * 2.0 ** -24 * mag
+    assert np.all(np.abs(y - want) <= bound + 1e-30)
+    again = T.spmv(G, vals.cuda(), x.cuda()).cpu().numpy().astype(np.float64)
+    assert np.array_equal(y, again)  # fixed reduction order
+    return y
+
+
+@pytest.mark.parametrize("name", ["rmat", "er", "plc", "grid"])
+def test_matches_oracle_within_the_fp32_bound(T, name):
+    g = {"rmat": gg.rmat(12), "er": gg.random_small(3000, 40000, 2), "plc": gg.powerlaw_config(4000, 8, 2.2, seed=5),
+         "grid": gg.grid2d(60, 70)}[name]
+    vals = gg.edge_values(g, seed=31)
+    x = torch.from_numpy(np.random.default_rng(3).standard_normal(g.V).astype(np.float32))
+    _check(T, g, vals, x)
+
+
+def test_hub_rows_and_empty_rows(T):
+    g = gg.star(5000)  # one row of 5,000 entries, 5,000 rows of one
+    vals = gg.edge_values(g, seed=2)
+    x = torch.ones(g.V, dtype=torch.float32)
+    _check(T, g, vals, x)
+    e = gg.empty_graph(100)
+    y = _check(T, e, torch.zeros(0, dtype=torch.float32), torch.ones(100, dtype=torch.float32))
+    assert np.all(y == 0.0)
+
+
+def test_identity_permutation_exact(T):
+    n = 1000
+    perm = torch.from_numpy(np.random.default_rng(4).permutation(n).astype(np.int32))
+    rp = torch.arange(n + 1, dtype=torch.int32)  # row i holds one entry, at column perm[i]
+    x = torch.from_numpy(np.random.default_rng(5).standard_normal(n).astype(np.float32))
+    G = T.graph_load_csr(rp.cuda(), perm.cuda(), V=n)
+    y = T.spmv(G, torch.ones(n, dtype=torch.float32, device="cuda"), x.cuda()).cpu()
+    assert torch.equal(y, x[perm.long()])
+    y = T.spmv(G, torch.full((n,), 2.0, device="cuda"), x.cuda()).cpu()
+    assert torch.equal(y, 2.0 * x[perm.long()])
+
+
+def test_host_memory_is_refused(T):
+    g = gg.path(4)
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+    from paper_1904_02241_gb300 import _lib as L
+    v = torch.ones(g.E, dtype=torch.float32)  # host buffers: refused before any access
+    x = torch.ones(g.V, dtype=torch.float32)
+    st = L.load().tc_spmv(G.handle, v.data_ptr(), x.data_ptr(), x.data_ptr(), L.TC_MEM_HOST, None)
+    assert st == -6

@@ -56,7 +56,7 @@ def parse():
     ap.add_argument("--merge-range", type=int, default=0, help="vertices per merge CTA (0 = library default)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
-    ap.add_argument("--row", default="", choices=["", "many_graphs"],
+    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc"],
                     help="profiling runs: time only this row and print its figures")
     return ap.parse_args()
 
@@ -474,6 +474,42 @@ def many_graphs(stream, with_oracle: bool = True):
     return res
 
 
+def spmv_row(stream, scale: int = 22):
+    """y = A x with A the R-MAT 22 CSR and seeded FP32 values (Sec. 4's SpMV benchmark).  The
+    algorithmic bytes of one product are the values and column indices (8 B per entry), the row
+    offsets, x once and y: 8E + 4(V+1) + 8V."""
+    import paper_1904_02241_gb300 as T
+    g = gg.rmat(scale, device="cuda")
+    A = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    vals = gg.edge_values(g).cuda()
+    x = torch.randn(g.V, device="cuda")
+    y = torch.empty(g.V, device="cuda")
+    for _ in range(3):
+        T.spmv(A, vals, x, out=y)
+    torch.cuda.synchronize()
+    ms = statistics.median(time_runs(lambda: T.spmv(A, vals, x, out=y), 10, stream))
+    peak, _ = load_peaks()
+    nbytes = 8 * g.E + 4 * (g.V + 1) + 8 * g.V
+    return {"spmv": {"graph": f"rmat{scale}", "V": g.V, "E": g.E, "ms": round(ms, 4),
+                     "gflops": round(2 * g.E / (ms * 1e-3) / 1e9, 2),
+                     "bytes_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}}
+
+
+def bc_row(stream, scale: int = 18, nsrc: int = 4):
+    """Betweenness centrality from a few seeded sources on the symmetrised R-MAT; TEPS counts each
+    undirected edge once per source."""
+    import paper_1904_02241_gb300 as T
+    gs = gg.symmetrize(gg.rmat(scale, device="cuda"))
+    G = T.graph_load_csr(gs.rowptr, gs.colidx, V=gs.V)
+    srcs = gg.sources(gs, nsrc, seed=13)
+    out = torch.empty(gs.V, dtype=torch.float64, device="cuda")
+    T.bc(G, srcs[:1], out=out)
+    torch.cuda.synchronize()
+    ms = statistics.median(time_runs(lambda: T.bc(G, srcs, out=out), 3, stream))
+    return {"bc": {"graph": f"rmat{scale}_sym", "V": gs.V, "E_directed": gs.E, "sources": nsrc, "ms": round(ms, 3),
+                   "gteps": round(gs.E / 2 * nsrc / (ms * 1e-3) / 1e9, 3)}}
+
+
 def e2e(args, ctx):
     """Same metric through the C ABI from host buffers: H2D of the CSR, graph load
     (validation + transpose), partition, 20 iterations, D2H of the ranks."""
@@ -621,8 +657,10 @@ def main():
         return
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA device (the TOCAB path has no CPU fallback)")
-    if args.row == "many_graphs":
-        res = many_graphs(torch.cuda.current_stream(), with_oracle=False)
+    if args.row:
+        stream = torch.cuda.current_stream()
+        res = {"many_graphs": lambda: many_graphs(stream, with_oracle=False), "spmv": lambda: spmv_row(stream),
+               "bc": lambda: bc_row(stream)}[args.row]()
         print(json.dumps(res), flush=True)
         return
     res, ctx = bench_tocab(args, world, rank, local)

@@ -51,11 +51,12 @@ typedef struct tc_graph tc_graph;    /* opaque: a graph resident on one device  
 typedef struct tc_part  tc_part;     /* opaque: a TOCAB partition of a tc_graph           */
 
 /* ---- status ---------------------------------------------------------------------------- */
-/* Static text for a status code. */
+/* Static text for a status code (library utility, no counterpart in the paper; never fails). */
 const char *tc_status_string(int status);
-/* Message of the last failed call on this thread ("" if none). */
+/* Message of the last failed call on this thread, "" if none (library utility, no counterpart
+ * in the paper; the string is owned by the library and valid until the thread's next call). */
 const char *tc_last_error(void);
-/* Library version as 10000*major + 100*minor + patch. */
+/* Library version as 10000*major + 100*minor + patch (no counterpart in the paper). */
 int tc_version(void);
 
 /* ---- device memory budget ---------------------------------------------------------------- */
@@ -88,7 +89,8 @@ int64_t tc_device_memory_held(void);
  */
 int tc_graph_load_csr(int32_t V, int64_t E, const int32_t *rowptr, const int32_t *colidx,
                       int mem, void *stream, tc_graph **out);
-/* Release a graph and its device memory (NULL is ignored). */
+/* Release a graph and its device memory; NULL is ignored (handle management, no counterpart in
+ * the paper).  Waits for the device before freeing. */
 void tc_graph_free(tc_graph *g);
 
 typedef struct tc_graph_info {
@@ -99,11 +101,15 @@ typedef struct tc_graph_info {
     int64_t num_dangling;     /* vertices with out-degree 0 */
     int32_t device;
 } tc_graph_info;
+/* Sizes and degree statistics of a loaded graph: V and E of Sec. 2.1, and the dangling vertices
+ * (out-degree 0) whose contribution step in Alg. 1 divides by zero.  Errors: TC_ERR_INVALID_ARG
+ * for a NULL argument. */
 int tc_graph_get_info(const tc_graph *g, tc_graph_info *info);
 
 /*
- * tc_graph_export_transpose -- copy the device-built G^T out (rowptr[V+1], colidx[E],
- * in-rows sorted by source id) to host or device buffers per `mem`.  Synchronises.
+ * tc_graph_export_transpose -- copy the device-built G^T that Alg. 1 pulls over (Sec. 2.1 CSR;
+ * rowptr[V+1], colidx[E], in-rows sorted by source id) to caller-owned host or device buffers per
+ * `mem`.  Synchronises.  Errors: TC_ERR_INVALID_ARG (NULL graph, bad mem), TC_ERR_CUDA.
  */
 int tc_graph_export_transpose(const tc_graph *g, int32_t *rowptr, int32_t *colidx, int mem,
                               void *stream);
@@ -141,9 +147,15 @@ typedef struct tc_part_params {
                                  -1 = never, 1 = require it (TC_ERR_UNSUPPORTED if W does not fit) */
 } tc_part_params;
 
+/* tc_tocab_partition -- build the static 1D blocking described above (Sec. 3.1, Fig. 3/4), the
+ * merge range table of Fig. 5 and, for pull partitions that fit, the staged format.  `out`
+ * receives a library-owned handle (free with tc_part_free); the graph must outlive it.
+ * Synchronises.  Errors as listed above, plus TC_ERR_UNSUPPORTED for more than 65,535 blocks or
+ * smem_stage = 1 with a width that does not fit. */
 int tc_tocab_partition(const tc_graph *g, int dir, int32_t num_blocks,
                        const tc_part_params *params /* NULL = defaults */, void *stream,
                        tc_part **out);
+/* Release a partition; NULL is ignored (handle management, no counterpart in the paper). */
 void tc_part_free(tc_part *p);
 
 typedef struct tc_part_info {
@@ -157,10 +169,13 @@ typedef struct tc_part_info {
     int32_t staged;           /* 1: the gather stages block contributions in shared memory */
     int64_t staged_edges;     /* edges of the staged stream incl. per-block padding (0 if not) */
 } tc_part_info;
+/* Shape of a partition: B and W of Sec. 3.1, R local rows (Fig. 4), k of Fig. 5.  Errors:
+ * TC_ERR_INVALID_ARG for a NULL argument. */
 int tc_part_get_info(const tc_part *p, tc_part_info *info);
 
 /*
- * tc_part_export -- copy the blocked CSR out (mem = host or device), for inspection:
+ * tc_part_export -- copy the blocked CSR of Sec. 3.1 (Fig. 3, local IDs of Fig. 4) out to
+ * caller-owned buffers (mem = host or device), for inspection:
  *   blk_rows[B+1]  first local row of each block;   blk_edges[B+1] first edge of each block
  *   rowptr[R+1]    edge offset of every local row;  id_map[R] global ID of every local row
  *   colidx[E]      global column (source for pull, destination for push) of every edge.
@@ -169,12 +184,15 @@ int tc_part_get_info(const tc_part *p, tc_part_info *info);
 int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_edges, int32_t *rowptr,
                    int32_t *id_map, int32_t *colidx, int mem, void *stream);
 
-/* Per-subgraph load balancing: warp_min_per_block (host int32[B], each >= 1) replaces
- * tc_pr_params.lb_warp_min for the unstaged gathers of this partition; NULL clears it. */
+/* Per-subgraph load balancing (Sec. 3.2, chosen per subgraph by the cost model):
+ * warp_min_per_block (host int32[B], each >= 1, copied) replaces tc_pr_params.lb_warp_min for
+ * the unstaged gathers of this partition; NULL clears it.  Errors: TC_ERR_INVALID_ARG (NULL
+ * partition, an entry < 1), TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_part_set_lb(tc_part *p, const int32_t *warp_min_per_block);
 
-/* Default block width W for a vertex count V and an L2 size (host-only helper, the rule
- * used when num_blocks == 0). */
+/* Default block width W for a vertex count V and an L2 size: the rule used when num_blocks == 0,
+ * W FP32 values in l2_fraction of the L2 (Sec. 4.3's 256 Ki vertices on a 2.75 MB L2, pinned by
+ * Table 3).  Host-only; returns 0 for invalid sizes. */
 int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
 
 /* ---- PageRank ------------------------------------------------------------------------------ */
@@ -366,11 +384,14 @@ typedef struct tc_multigraph tc_multigraph;   /* opaque: a batch of independent 
  * in those global IDs (layout and rules as tc_graph_load_csr).  Every edge must join two
  * vertices of the same graph (TC_ERR_INVALID_GRAPH otherwise).
  *   vtx_off : host int32[num_graphs + 1], vtx_off[0] = 0, non-decreasing, vtx_off[n] = V.
+ * Batching of independent graphs has no counterpart in the paper; each graph runs Alg. 1.
  * Errors: those of tc_graph_load_csr, TC_ERR_INVALID_ARG for a bad vtx_off.
  */
 int tc_multigraph_load(int32_t num_graphs, const int32_t *vtx_off, int32_t V, int64_t E,
                        const int32_t *rowptr, const int32_t *colidx, int mem, void *stream,
                        tc_multigraph **out);
+/* Release a batch; NULL is ignored (handle management, no counterpart in the paper).  Waits for
+ * the device before freeing. */
 void tc_multigraph_free(tc_multigraph *m);
 
 #define TC_MULTI_RESIDENT 1024    /* lanes_per_vertex value: each graph stays in one CTA for all
@@ -400,7 +421,8 @@ int tc_pagerank_multi(const tc_multigraph *m, const tc_pr_params *params, const 
                       float *ranks_out, tc_pr_stats *stats, void *stream);
 
 /*
- * tc_multi_autotune -- the project's autotuner for the batch: times every lanes-per-vertex
+ * tc_multi_autotune -- the project's autotuner for the batch (no counterpart in the paper; the
+ * variants are the thread/warp mappings of Sec. 3.2 plus the resident form): times every lanes-per-vertex
  * variant (-1, 1, 4, 8, 32, and TC_MULTI_RESIDENT when the graphs fit; one warm-up and one
  * timed run each, CUDA events) with `params`, stores the fastest in the handle (used when
  * lanes_per_vertex = 0) and returns it.
@@ -420,8 +442,9 @@ int tc_multi_autotune(tc_multigraph *m, const tc_pr_params *params, int32_t *bes
  * (mean |first source - row| / V), log2(1 + max/mean out-degree).  Synchronises.
  */
 int tc_graph_features(const tc_graph *g, float *features /* host [16] */);
-/* Features of every block of a partition: host float[B][16] (the out-degree features and the
- * vertex-value bytes are the graph's and the block width's). */
+/* Features of every block of a partition (the subgraphs of Sec. 3.1): host float[B][16] (the
+ * out-degree features and the vertex-value bytes are the graph's and the block width's).
+ * Synchronises.  Errors: TC_ERR_INVALID_ARG (NULL argument), TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_part_features(const tc_part *p, float *features);
 
 /*
@@ -433,23 +456,35 @@ int tc_part_features(const tc_part *p, float *features);
  * W1[n_in][n_hidden], b1, W2[n_hidden][n_hidden], b2, W3[n_hidden][n_out], b3 (row-major).
  */
 typedef struct tc_mlp tc_mlp;
+/* Create the network above (no counterpart in the paper) with zero parameters; `out` receives
+ * a library-owned handle.  Errors: TC_ERR_INVALID_ARG (sizes < 1, NULL head sizes), TC_ERR_OOM. */
 int tc_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_heads, const int32_t *head_sizes,
                   tc_mlp **out);
+/* Release a network; NULL is ignored (no counterpart in the paper). */
 void tc_mlp_free(tc_mlp *m);
+/* Number of parameters of the flat vector (no counterpart in the paper); -1 for NULL. */
 int64_t tc_mlp_num_params(const tc_mlp *m);
-/* Set the parameters (host float[num_params]); resets the Adam moments. */
+/* Set the parameters (host float[num_params]); resets the Adam moments (cost model, no
+ * counterpart in the paper).  Errors: TC_ERR_INVALID_ARG, TC_ERR_CUDA. */
 int tc_mlp_set_params(tc_mlp *m, const float *params);
-/* Copy parameters and/or the last computed gradients to host (either may be NULL). */
+/* Copy parameters and/or the last computed gradients to host, either may be NULL (cost model,
+ * no counterpart in the paper).  Errors: TC_ERR_INVALID_ARG, TC_ERR_CUDA. */
 int tc_mlp_get_params(const tc_mlp *m, float *params, float *grads);
-/* Z[N][n_out] = network outputs (logits) for X[N][n_in]; X and Z in `mem` space. */
+/* Z[N][n_out] = network outputs (logits) for X[N][n_in]; X and Z in `mem` space (cost model, no
+ * counterpart in the paper).  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_mlp_forward(tc_mlp *m, const float *X, int32_t N, float *Z, int mem, void *stream);
-/* Loss (host *loss) and gradients (kept in the handle) for X[N][n_in], labels Y[N][n_heads]. */
+/* Loss (host *loss) and gradients (kept in the handle) for X[N][n_in], labels Y[N][n_heads]
+ * (cost model, no counterpart in the paper).  Every label must lie in [0, size of its head);
+ * labels are not checked.  Errors: TC_ERR_INVALID_ARG (NULL argument, N < 1), TC_ERR_OOM,
+ * TC_ERR_CUDA. */
 int tc_mlp_loss_grad(tc_mlp *m, const float *X, const int32_t *Y, int32_t N, int mem,
                      double *loss, void *stream);
-/* One Adam step (Kingma & Ba) with the gradients of the last tc_mlp_loss_grad. */
+/* One Adam step (Kingma & Ba) with the gradients of the last tc_mlp_loss_grad (cost model, no
+ * counterpart in the paper).  Errors: TC_ERR_INVALID_ARG, TC_ERR_CUDA. */
 int tc_mlp_adam_step(tc_mlp *m, float lr, float beta1, float beta2, float eps, void *stream);
 /* `epochs` passes of minibatch Adam (lr, beta 0.9/0.999, eps 1e-8) over the samples in the
- * given order; *final_loss = loss over all samples afterwards. */
+ * given order; *final_loss = loss over all samples afterwards (cost model, no counterpart in the
+ * paper).  Labels as for tc_mlp_loss_grad.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_mlp_train(tc_mlp *m, const float *X, const int32_t *Y, int32_t N, int32_t epochs,
                  int32_t batch, float lr, int mem, double *final_loss, void *stream);
 

@@ -192,7 +192,7 @@ int tc_part_set_lb(tc_part *p, const int32_t *warp_min_per_block);
 
 /* Default block width W for a vertex count V and an L2 size: the rule used when num_blocks == 0,
  * W FP32 values in l2_fraction of the L2 (Sec. 4.3's 256 Ki vertices on a 2.75 MB L2, pinned by
- * Table 3).  Host-only; returns 0 for invalid sizes. */
+ * Table 3).  Host-only and never fails: W is at least 32, and at most V when V > 0. */
 int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
 
 /* ---- PageRank ------------------------------------------------------------------------------ */

@@ -457,7 +457,8 @@ int tc_part_features(const tc_part *p, float *features);
  */
 typedef struct tc_mlp tc_mlp;
 /* Create the network above (no counterpart in the paper) with zero parameters; `out` receives
- * a library-owned handle.  Errors: TC_ERR_INVALID_ARG (sizes < 1, NULL head sizes), TC_ERR_OOM. */
+ * a library-owned handle.  Errors: TC_ERR_INVALID_ARG (a size < 1, more than 8 heads, NULL head
+ * sizes or out), TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_mlp_create(int32_t n_in, int32_t n_hidden, int32_t n_heads, const int32_t *head_sizes,
                   tc_mlp **out);
 /* Release a network; NULL is ignored (no counterpart in the paper). */

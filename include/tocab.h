@@ -475,9 +475,10 @@ int tc_mlp_get_params(const tc_mlp *m, float *params, float *grads);
  * counterpart in the paper).  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_mlp_forward(tc_mlp *m, const float *X, int32_t N, float *Z, int mem, void *stream);
 /* Loss (host *loss) and gradients (kept in the handle) for X[N][n_in], labels Y[N][n_heads]
- * (cost model, no counterpart in the paper).  Every label must lie in [0, size of its head);
- * labels are not checked.  Errors: TC_ERR_INVALID_ARG (NULL argument, N < 1), TC_ERR_OOM,
- * TC_ERR_CUDA. */
+ * (cost model, no counterpart in the paper).  Every label must lie in [0, size of its head):
+ * the labels are checked on the device before any kernel uses them, and a label outside its
+ * head fails the call with TC_ERR_INVALID_ARG (nothing is updated).  Errors:
+ * TC_ERR_INVALID_ARG (NULL argument, N < 1, label out of range), TC_ERR_OOM, TC_ERR_CUDA. */
 int tc_mlp_loss_grad(tc_mlp *m, const float *X, const int32_t *Y, int32_t N, int mem,
                      double *loss, void *stream);
 /* One Adam step (Kingma & Ba) with the gradients of the last tc_mlp_loss_grad (cost model, no
@@ -503,6 +504,12 @@ int tc_mlp_train(tc_mlp *m, const float *X, const int32_t *Y, int32_t N, int32_t
  * allocating library routine.  Its scratch (contributions, out-degree reciprocals,
  * dangling-mass partials) is a static device array of TC_NOALLOC_SCRATCH_BYTES (about
  * 12.6 MB) that every GPU which loads the library holds until the process exits.
+ * Under CUDA's default lazy module loading, that array's device memory is reserved when
+ * the library's module is first used on a device -- by the first call of this entry point
+ * there -- so the first call can still fail with TC_ERR_CUDA when the device has no room
+ * left.  A caller whose memory budget or pool is fixed later should make one call (any
+ * valid V, iters = 0 will do) on every device at start-up, before the pool is taken, or
+ * load modules eagerly (environment CUDA_MODULE_LOADING=EAGER).  Later calls reserve nothing.
  *   V          : 1 <= V <= TC_NOALLOC_MAX_V, else TC_ERR_UNSUPPORTED (nothing is launched).
  *   in_rowptr  : device int32[V+1], in-edge CSR of G^T (row v lists the sources of v's
  *   in_colidx    in-edges; device int32[E]).  Not validated: pass a well-formed CSR.

@@ -15,6 +15,7 @@ struct tc_mlp {
     int64_t step = 0;
     tc::DevBuf params, grads, adam_m, adam_v;
     tc::DevBuf work;      // activations of the current batch
+    tc::DevBuf flag;      // int: set by the label check
     int32_t work_n = 0;
 };
 
@@ -52,6 +53,16 @@ struct Heads {
     int32_t n;
     int32_t size[8];
 };
+
+// *bad = 1 when some label lies outside [0, size of its head); checked before any kernel
+// indexes the logits with a label.
+__global__ void k_check_labels(const int32_t *Y, int32_t N, Heads h, int *bad) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= (int64_t)N * h.n) return;
+    const int32_t k = (int32_t)(t % h.n);
+    const int32_t y = Y[t];
+    if (y < 0 || y >= h.size[k]) *bad = 1;
+}
 
 // per sample: cross-entropy of every head, dZ = (softmax - onehot) / N
 __global__ void k_softmax_ce(const float *Z, const int32_t *Y, int32_t N, int32_t O, Heads h, float *dZ,
@@ -202,6 +213,19 @@ static int mlp_loss_grad_dev(tc_mlp *m, const MlpWork &w, int32_t N, bool want_g
 
 static int copy_to_dev(void *dst, const void *src, size_t bytes, int mem, cudaStream_t s) {
     TC_CUDA(cudaMemcpyAsync(dst, src, bytes, mem == TC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+    return TC_OK;
+}
+
+// Every label of Y (device, N x nheads) inside its head, else TC_ERR_INVALID_ARG.
+static int check_labels(tc_mlp *m, const int32_t *Y, int32_t N, cudaStream_t s) {
+    TC_TRY(m->flag.alloc(16));
+    TC_CUDA(cudaMemsetAsync(m->flag.p, 0, 4, s));
+    k_check_labels<<<grid_for((int64_t)N * m->nheads), 256, 0, s>>>(Y, N, heads_of(m), m->flag.as<int>());
+    TC_LAUNCH_CHECK();
+    int bad = 0;
+    TC_CUDA(cudaMemcpyAsync(&bad, m->flag.p, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    if (bad) return fail(TC_ERR_INVALID_ARG, "mlp: a label lies outside [0, size of its head)");
     return TC_OK;
 }
 
@@ -384,6 +408,7 @@ extern "C" int tc_mlp_loss_grad(tc_mlp *m, const float *X, const int32_t *Y, int
     TC_TRY(mlp_work(m, N, &w));
     TC_TRY(copy_to_dev(w.X, X, (size_t)N * m->nin * 4, mem, s));
     TC_TRY(copy_to_dev(w.Y, Y, (size_t)N * m->nheads * 4, mem, s));
+    TC_TRY(check_labels(m, w.Y, N, s));
     TC_TRY(mlp_loss_grad_dev(m, w, N, true, s));
     double l = 0;
     TC_CUDA(cudaMemcpyAsync(&l, w.loss_sum, 8, cudaMemcpyDeviceToHost, s));
@@ -409,6 +434,7 @@ extern "C" int tc_mlp_train(tc_mlp *m, const float *X, const int32_t *Y, int32_t
     TC_TRY(Yall.alloc((size_t)N * m->nheads * 4));
     TC_TRY(copy_to_dev(Xall.p, X, (size_t)N * m->nin * 4, mem, s));
     TC_TRY(copy_to_dev(Yall.p, Y, (size_t)N * m->nheads * 4, mem, s));
+    TC_TRY(check_labels(m, Yall.as<int32_t>(), N, s));
     MlpWork w;
     const int32_t B = batch < N ? batch : N;
     TC_TRY(mlp_work(m, B, &w));

@@ -6,7 +6,10 @@
 // caller passes its device-resident in-edge CSR, out-degrees and output buffer; the
 // iteration's scratch (contributions, out-degree reciprocals, dangling-mass partials) lives
 // in the file-scope device array below, which every GPU that loads this library holds
-// until the process exits.
+// until the process exits.  Under CUDA's default lazy module loading that array is reserved
+// on a device when this module is first used there, i.e. by the first call of the entry
+// point on that device; a caller whose memory budget is fixed later should make that first
+// call at start-up (or load modules eagerly with CUDA_MODULE_LOADING=EAGER).
 #include <mutex>
 
 #include "tc_common_dev.cuh"
@@ -96,7 +99,8 @@ __global__ void __launch_bounds__(THREADS) k_gather(const int32_t *__restrict__ 
             wm &= wm - 1;
             const int32_t ws = __shfl_sync(0xffffffffu, s, ln), we = __shfl_sync(0xffffffffu, e, ln);
             float acc = 0.0f;
-            for (int32_t i = ws + lane; i < we; i += 32) acc += contrib[__ldg(colidx + i)];
+            // 64-bit index: ws + lane + 32 k may pass INT32_MAX when a row ends near 2^31 - 1
+            for (int64_t i = (int64_t)ws + lane; i < we; i += 32) acc += contrib[__ldg(colidx + i)];
 #pragma unroll
             for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
             if (lane == ln) sum = acc;

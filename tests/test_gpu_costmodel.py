@@ -140,3 +140,22 @@ def test_learned_model_gains_over_heuristic(CM):
     print(f"held-out time / exhaustive best: model {model:.3f}, heuristic {heur:.3f}, "
           f"gain {heur / model:.3f}x")
     assert model <= heur * 1.05
+
+
+@pytest.mark.parametrize("bad", [-1, 3])
+def test_mlp_rejects_labels_outside_their_head(CM, bad):
+    """A label outside [0, head size) fails the call before any kernel indexes the logits with
+    it, for the gradient call and for training; the parameters stay as they were."""
+    from paper_1904_02241_gb300 import TocabError
+    m = CM.MLP(heads=HEADS)
+    m.init(seed=7)
+    X, Y = _data(11, 8)
+    Y[5, 1] = bad  # head 1 has 3 classes
+    before = m.get()
+    with pytest.raises(TocabError):
+        m.loss_grad(X, Y)
+    with pytest.raises(TocabError):
+        m.train(X, Y, epochs=1, batch=4)
+    after = m.get()
+    for k in before:
+        assert np.array_equal(before[k], after[k]), k

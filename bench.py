@@ -51,9 +51,11 @@ def parse():
     ap.add_argument("--bfs-sources", type=int, default=64)
     ap.add_argument("--no-variants", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
-    ap.add_argument("--merge", default="fixed", choices=["fixed", "ordered", "float"],
-                    help="TOCAB pull merge: fixed-point (deterministic), ordered (deterministic), float")
+    ap.add_argument("--merge", default="fixed", choices=["fixed", "ordered"],
+                    help="TOCAB pull merge: fixed-point or ordered (both deterministic)")
     ap.add_argument("--merge-range", type=int, default=0, help="vertices per merge CTA (0 = library default)")
+    ap.add_argument("--order", default="outdegree", choices=["outdegree", "natural"],
+                    help="vertex numbering the TOCAB blocks are cut in (renumbered by out-degree, or as given)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
     ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc"],
@@ -151,15 +153,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one ncu capture
-# of `bench.py --steps 2 --warmup 1 --quick` (one pass, full workload; the command and the
-# numbers are in profiles/launches_pagerank_pull_tocab_rmat24.md).  Keyed by kernel, R-MAT
-# scale and block count; any other workload reports null.  Must be re-captured (or removed)
-# whenever one of these kernels changes.
-NCU_TRAFFIC = {
-    ("k_tile_gather", 24, 456): 1177993216,
-    ("k_pull_merge_atomic<2>", 24, 456): 1005967104,
-}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one single-pass ncu
+# capture of `bench.py --steps 2 --warmup 1 --quick` on the full workload.  Keyed by kernel, R-MAT
+# scale and block count, and tied to the library sources it was taken on (SHA-256 over
+# csrc/*.cu and *.cuh): after any change to them the figure no longer describes the kernel and
+# the bench reports null.
+NCU_TRAFFIC = {}
+NCU_TRAFFIC_SRC = ""
+
+
+def library_source_hash() -> str:
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1904_02241_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + b"\0" + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str, scale: int, blocks: int):
+    if NCU_TRAFFIC_SRC != library_source_hash():
+        return None
+    return NCU_TRAFFIC.get((kernel, scale, blocks))
 
 
 def load_peaks():
@@ -199,7 +216,8 @@ def bench_tocab(args, world, rank, local):
     V, E = g.V, g.E
     gen_s = time.time() - t0
     G = T.graph_load_csr(g.rowptr, g.colidx, V=V)
-    P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy, merge_range=args.merge_range)
+    P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy, merge_range=args.merge_range,
+                          order=args.order)
     torch.cuda.synchronize()
     out = torch.empty(V, dtype=torch.float32, device=dev)
 
@@ -246,10 +264,18 @@ def bench_tocab(args, world, rank, local):
     else:
         gather_bytes = 4 * E + 4 * (R + 1) + 4 * V + 4 * R
         kname = "k_pull_gather<false>"
-    merge_bytes = 4 * R + (2 if P.merge_range <= 65536 else 4) * R + 8 * P.num_blocks * ((V + P.merge_range - 1)
-                                                                                        // P.merge_range) + 8 * V
+    # merge: partial sums (4 B) and local ids (2 B) per local row, the range table, and the out-degree
+    # reciprocal read and contribution written per vertex with out-edges (renumbered: the others
+    # are skipped; natural order: every vertex)
+    per_vertex = 8 * (P.num_sources if P.vertex_order == T.TC_ORDER_OUTDEGREE else V)
+    merge_bytes = 6 * R + 8 * P.num_blocks * (P.num_ranges + 1) + per_vertex
     peak, peak_kind = load_peaks()
-    achieved = gather_bytes / (gather_ms * 1e-3) / 1e9
+    # Roofline of the dominant kernel (the gather), against the method-independent bytes that
+    # its part of an iteration must move: every column index (4E) and every contribution (4V).
+    # The kernel's own format moves 2 B per staged edge instead, plus row heads and partial sums:
+    # reported beside as own_format_*.  The whole iteration against B_min is the headline figure.
+    gather_bmin = 4 * E + 4 * V
+    achieved = gather_bmin / (gather_ms * 1e-3) / 1e9
     bmin = 4 * E + 4 * (V + 1) + 4 * V + 4 * V + 4 * V
     res = {
         "metric": METRIC,
@@ -265,20 +291,23 @@ def bench_tocab(args, world, rank, local):
         "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": f"pagerank_pull_tocab rmat{args.scale} ef16 20 iters d=0.85",
-                   "merge": args.merge, "merge_range": P.merge_range,
+                   "merge": args.merge, "merge_range": P.merge_range, "vertex_order": args.order,
                    "graph": f"rmat{args.scale}", "V": V, "E": E, "iters": ITERS,
                    "blocks": P.num_blocks, "block_width": P.block_width, "local_rows": R,
                    "l2": "inputs larger than L2 (colidx %.2f GB vs 135 MB L2); no flush" % (4 * E / 1e9),
                    "parallelism": f"replicas x{world}", "generate_s": round(gen_s, 2)},
         "roofline": {"bound": "hbm", "kernel": kname, "achieved": round(achieved, 1),
                      "peak": peak, "peak_kind": peak_kind, "unit": "GB/s", "frac": round(achieved / peak, 4),
-                     "traffic": NCU_TRAFFIC.get((kname, args.scale, P.num_blocks)),
-                     "merge_traffic": NCU_TRAFFIC.get(("k_pull_merge_atomic<2>", args.scale, P.num_blocks))
-                     if args.merge == "fixed" else None,
-                     "algorithmic_bytes": gather_bytes,
+                     "traffic": ncu_traffic(kname, args.scale, P.num_blocks),
+                     "algorithmic_bytes": gather_bmin,
+                     "headline": "iteration_bmin_frac",
+                     "iteration_bmin_frac": round(bmin / (ms_step / ITERS * 1e-3) / 1e9 / peak, 4),
+                     "iteration_bmin_bytes": bmin,
+                     "own_format_bytes": gather_bytes,
+                     "own_format_frac": round(gather_bytes / (gather_ms * 1e-3) / 1e9 / peak, 4),
                      "gather_ms": round(gather_ms, 4), "merge_ms": round(merge_ms, 4),
-                     "merge_gbs": round(merge_bytes / (merge_ms * 1e-3) / 1e9, 1),
-                     "iteration_bmin_frac": round(bmin / (ms_step / ITERS * 1e-3) / 1e9 / peak, 4)},
+                     "merge_traffic": ncu_traffic("k_pull_merge_atomic<2>", args.scale, P.num_blocks),
+                     "merge_gbs": round(merge_bytes / (merge_ms * 1e-3) / 1e9, 1)},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
@@ -639,7 +668,7 @@ def reference_arm(args, world, rank):
     sample = f"1 FP64 pull iteration per step (of the 20) on rmat{args.scale} (V={g.V}, E={g.E})"
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "GTEPS", "n_gpus": world,
-        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_iter * 1e3 * ITERS, 2),
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_iter * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"pagerank_pull rmat{args.scale} ef16 20 iters d=0.85 (FP64 CPU oracle)",
                    "graph": f"rmat{args.scale}", "V": g.V, "E": g.E, "iters": ITERS},

@@ -145,7 +145,27 @@ typedef struct tc_part_params {
     int32_t smem_stage;       /* pull only: 0 = stage each block's contributions in shared
                                  memory whenever W fits (W <= about 41K sources, W % 32 == 0),
                                  -1 = never, 1 = require it (TC_ERR_UNSUPPORTED if W does not fit) */
+    int32_t vertex_order;     /* pull only: TC_ORDER_NATURAL (0) or TC_ORDER_OUTDEGREE (1), below */
 } tc_part_params;
+
+/*
+ * Vertex order of a pull partition.  The paper cuts blocks as ranges of the graph's own
+ * vertex IDs (Sec. 3.1).  TC_ORDER_OUTDEGREE first renumbers the vertices by out-degree,
+ * highest first (ties by ID; among the vertices without out-edges, those without any edge
+ * come last), and cuts the source ranges, local rows and merge ranges in that numbering:
+ * the sources that feed most destinations then share blocks, so each destination has fewer
+ * (block, row) pieces and the partial-sum traffic of the merge shrinks; the blocks past the
+ * last vertex with out-edges would hold no edges and are dropped.  The merge ranges are cut
+ * to hold about equal work (at most merge_range vertices each, merge_range >= 128) and cover
+ * only the vertices with some edge; the rest all get the rank of an empty sum, set in closed
+ * form.  Everything the caller sees stays
+ * in the graph's own numbering: PageRank takes `init` and returns ranks by original ID.
+ * tc_part_export reports the renumbered structure and tc_part_export_order the numbering.
+ * BFS and the PPR batch do not take renumbered partitions (TC_ERR_UNSUPPORTED), and push
+ * partitions cannot be renumbered (TC_ERR_UNSUPPORTED).
+ */
+#define TC_ORDER_NATURAL    0
+#define TC_ORDER_OUTDEGREE  1
 
 /* tc_tocab_partition -- build the static 1D blocking described above (Sec. 3.1, Fig. 3/4), the
  * merge range table of Fig. 5 and, for pull partitions that fit, the staged format.  `out`
@@ -168,6 +188,10 @@ typedef struct tc_part_info {
     int32_t num_hubs;         /* rows handled one CTA per row */
     int32_t staged;           /* 1: the gather stages block contributions in shared memory */
     int64_t staged_edges;     /* edges of the staged stream incl. per-block padding (0 if not) */
+    int32_t vertex_order;     /* TC_ORDER_NATURAL or TC_ORDER_OUTDEGREE */
+    int32_t num_ranges;       /* merge ranges (CTAs of the merge) */
+    int32_t num_items;        /* work items of the staged gather (0 if not staged) */
+    int32_t num_sources;      /* vertices with out-edges (TC_ORDER_OUTDEGREE: they come first) */
 } tc_part_info;
 /* Shape of a partition: B and W of Sec. 3.1, R local rows (Fig. 4), k of Fig. 5.  Errors:
  * TC_ERR_INVALID_ARG for a NULL argument. */
@@ -183,6 +207,15 @@ int tc_part_get_info(const tc_part *p, tc_part_info *info);
  */
 int tc_part_export(const tc_part *p, int64_t *blk_rows, int64_t *blk_edges, int32_t *rowptr,
                    int32_t *id_map, int32_t *colidx, int mem, void *stream);
+
+/*
+ * tc_part_export_order -- the vertex numbering of a partition (no counterpart in the paper;
+ * see TC_ORDER_OUTDEGREE above): perm[n] = original ID of the vertex numbered n, V entries, to
+ * a caller-owned buffer in `mem` space.  For a TC_ORDER_NATURAL partition perm[n] = n.  The IDs
+ * that tc_part_export reports are the numbers n.  Synchronises.  Errors: TC_ERR_INVALID_ARG
+ * (NULL partition or output, bad mem), TC_ERR_CUDA.
+ */
+int tc_part_export_order(const tc_part *p, int32_t *perm, int mem, void *stream);
 
 /* Per-subgraph load balancing (Sec. 3.2, chosen per subgraph by the cost model):
  * warp_min_per_block (host int32[B], each >= 1, copied) replaces tc_pr_params.lb_warp_min for
@@ -204,7 +237,8 @@ int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
                                         deterministic; when 16 accumulators of merge_range
                                         floats do not fit in shared memory the call uses
                                         TC_MERGE_FIXED instead                                 */
-#define TC_MERGE_FLOAT    2          /* one accumulator, FP32 atomics: last bits may vary     */
+/* (2 was an FP32-atomic merge; it could miss the 1e-5 accuracy bar on ranges with hundreds of
+   pieces per vertex, measured slower, and is no longer accepted: TC_ERR_INVALID_ARG)         */
 
 typedef struct tc_pr_params {
     float   damping;          /* d, e.g. 0.85 */
@@ -213,7 +247,7 @@ typedef struct tc_pr_params {
     int32_t out_mem;          /* memory space of ranks_out (and of init) */
     const float *init;        /* initial ranks [V] or NULL for 1/V */
     int32_t profile;          /* nonzero: time each kernel with CUDA events (stats) */
-    int32_t merge_mode;       /* TOCAB pull merge: TC_MERGE_FIXED (0), _ORDERED or _FLOAT */
+    int32_t merge_mode;       /* TOCAB pull merge: TC_MERGE_FIXED (0) or TC_MERGE_ORDERED */
     int32_t lb_warp_min;      /* unstaged gathers (Sec. 3.2): rows with fewer edges are summed
                                  by one lane, longer rows by a warp (hubs by a CTA); 0 = 32,
                                  1 = a warp for every row, large = lane-serial; a partition's

@@ -21,7 +21,7 @@ import torch
 
 from . import _lib as L
 from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
-                   TC_MULTI_RESIDENT, TC_PULL, TC_PUSH)
+                   TC_MULTI_RESIDENT, TC_ORDER_NATURAL, TC_ORDER_OUTDEGREE, TC_PULL, TC_PUSH)
 
 __all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "multigraph_load",
            "pagerank_multi", "multi_autotune", "MultiGraph",
@@ -130,6 +130,10 @@ class Partition:
         self.num_hubs = info.num_hubs
         self.staged = bool(info.staged)
         self.staged_edges = info.staged_edges
+        self.vertex_order = info.vertex_order
+        self.num_ranges = info.num_ranges
+        self.num_items = info.num_items
+        self.num_sources = info.num_sources
 
     @property
     def handle(self):
@@ -167,6 +171,13 @@ class Partition:
         return {"B": B, "W": self.block_width, "blk_rows": br.numpy(), "blk_edges": be.numpy(),
                 "rowptr": rp.numpy(), "id_map": im.numpy()[:R], "colidx": ci.numpy()[:E]}
 
+    def export_order(self):
+        """tc_part_export_order: perm[n] = original ID of the vertex numbered n (numpy int32[V])."""
+        perm = torch.empty(max(self.graph.V, 1), dtype=torch.int32)
+        _check(L.load().tc_part_export_order(self._h, perm.data_ptr(), L.TC_MEM_HOST, _stream()),
+               "tc_part_export_order")
+        return perm.numpy()[: self.graph.V]
+
 
 def graph_load_csr(rowptr, colidx, V: int | None = None, stream=None) -> Graph:
     """tc_graph_load_csr: out-edge CSR (int32 tensors on host or device) -> Graph."""
@@ -184,11 +195,13 @@ def graph_load_csr(rowptr, colidx, V: int | None = None, stream=None) -> Graph:
 
 def tocab_partition(graph: Graph, dir: int = L.TC_PULL, num_blocks: int = 0, l2_fraction: float = 0.0,
                     merge_range: int = 0, hub_degree: int = 0, block_policy: str = "l2", smem_stage: int = 0,
-                    stream=None) -> Partition:
+                    order: str = "natural", stream=None) -> Partition:
     """tc_tocab_partition: static 1D blocking.  num_blocks = 0 derives W from the L2 size
-    (block_policy="l2", the paper's rule) or from one CTA's shared memory ("smem")."""
+    (block_policy="l2", the paper's rule) or from one CTA's shared memory ("smem").
+    order="outdegree" renumbers the vertices by out-degree before cutting the blocks (pull only)."""
     policy = {"l2": L.TC_BLOCKS_L2, "smem": L.TC_BLOCKS_SMEM}[block_policy]
-    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree, policy, smem_stage)
+    vo = {"natural": L.TC_ORDER_NATURAL, "outdegree": L.TC_ORDER_OUTDEGREE}[order]
+    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree, policy, smem_stage, vo)
     h = C.c_void_p()
     _check(L.load().tc_tocab_partition(graph.handle, dir, num_blocks, C.byref(pp), _stream(stream), C.byref(h)),
            "tc_tocab_partition")
@@ -199,7 +212,7 @@ def default_block_width(V: int, l2_bytes: int, l2_fraction: float = 0.0) -> int:
     return int(L.load().tc_default_block_width(V, l2_bytes, l2_fraction))
 
 
-_MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED, "float": L.TC_MERGE_FLOAT}
+_MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED}
 
 
 def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream, merge="fixed",
@@ -229,7 +242,7 @@ def pagerank_pull(graph: Graph, part: Partition | None = None, damping: float = 
                   profile: bool = False, stream=None, return_stats: bool = False, merge: str = "fixed",
                   lb_warp_min: int = 0, l2_window: bool = False):
     """tc_pagerank_pull (Alg. 1; TOCAB Alg. 4 + merge when part is given).
-    merge: "fixed" (default) or "ordered" (both deterministic), or "float".
+    merge: "fixed" (default) or "ordered" (both deterministic).
     l2_window: an L2 access-policy window over the contributions of the unstaged gathers."""
     r, st = _pagerank(L.load().tc_pagerank_pull, "tc_pagerank_pull", graph, part, damping, iters, dangling, out,
                       init, profile, stream, merge, lb_warp_min, l2_window)

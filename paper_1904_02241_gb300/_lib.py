@@ -33,18 +33,23 @@ TC_BLOCKS_SMEM = 1
 
 class tc_part_params(C.Structure):
     _fields_ = [("l2_fraction", C.c_float), ("merge_range", C.c_int32), ("hub_degree", C.c_int32),
-                ("block_policy", C.c_int32), ("smem_stage", C.c_int32)]
+                ("block_policy", C.c_int32), ("smem_stage", C.c_int32), ("vertex_order", C.c_int32)]
+
+
+TC_ORDER_NATURAL = 0
+TC_ORDER_OUTDEGREE = 1
 
 
 class tc_part_info(C.Structure):
     _fields_ = [("dir", C.c_int32), ("num_blocks", C.c_int32), ("block_width", C.c_int32),
                 ("num_rows", C.c_int64), ("num_edges", C.c_int64), ("merge_range", C.c_int32),
-                ("num_hubs", C.c_int32), ("staged", C.c_int32), ("staged_edges", C.c_int64)]
+                ("num_hubs", C.c_int32), ("staged", C.c_int32), ("staged_edges", C.c_int64),
+                ("vertex_order", C.c_int32), ("num_ranges", C.c_int32), ("num_items", C.c_int32),
+                ("num_sources", C.c_int32)]
 
 
 TC_MERGE_FIXED = 0
 TC_MERGE_ORDERED = 1
-TC_MERGE_FLOAT = 2
 TC_MULTI_RESIDENT = 1024
 
 
@@ -94,6 +99,7 @@ SIGNATURES = {
     "tc_part_free": (None, [VP]),
     "tc_part_get_info": (C.c_int, [VP, C.POINTER(tc_part_info)]),
     "tc_part_export": (C.c_int, [VP, VP, VP, VP, VP, VP, C.c_int, VP]),
+    "tc_part_export_order": (C.c_int, [VP, VP, C.c_int, VP]),
     "tc_part_set_lb": (C.c_int, [VP, VP]),
     "tc_default_block_width": (C.c_int32, [C.c_int32, C.c_int64, C.c_float]),
     "tc_pagerank_pull": (C.c_int, [VP, VP, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),

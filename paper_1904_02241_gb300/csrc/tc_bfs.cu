@@ -466,6 +466,8 @@ extern "C" int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t sourc
         return fail(TC_ERR_INVALID_ARG, "tc_bfs_pull: bad out_mem");
     if (part && (part->g != g || part->dir != TC_PULL))
         return fail(TC_ERR_INVALID_ARG, "tc_bfs_pull: partition must be a TC_PULL partition of this graph");
+    if (part && part->order != TC_ORDER_NATURAL)
+        return fail(TC_ERR_UNSUPPORTED, "tc_bfs_pull: renumbered (TC_ORDER_OUTDEGREE) partitions are not supported");
     if (stats) memset(stats, 0, sizeof(*stats));
     return bfs_impl(g, part, source, params, levels_out, stats, (cudaStream_t)stream);
 }

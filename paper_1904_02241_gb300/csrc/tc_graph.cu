@@ -69,7 +69,7 @@ static int load_impl(int32_t V, int64_t E, const int32_t *rowptr, const int32_t 
     TC_TRY(g->out_colidx.alloc((size_t)E * 4));
     TC_TRY(g->in_rowptr.alloc(((size_t)V + 1) * 4));
     TC_TRY(g->in_colidx.alloc((size_t)E * 4));
-    TC_TRY(g->inv_outdeg.alloc((size_t)V * 4));
+    TC_TRY(g->inv_outdeg.alloc((size_t)V * 4 + 256));  // padded: bulk copies read whole 16-byte units
     TC_TRY(copy_in(g->out_rowptr.p, rowptr, ((size_t)V + 1) * 4, mem, s));
     TC_TRY(copy_in(g->out_colidx.p, colidx, (size_t)E * 4, mem, s));
 

@@ -26,6 +26,11 @@ struct UpdateArgs {
     float *rank_out;        // may be null (only the last iteration writes ranks)
     float *contrib_next;    // contributions for the next iteration
     double *fx_scale;       // fixed-point scale of the merge (written by the init kernel)
+    const int32_t *perm;    // renumbered partitions: original ID of vertex v (null: identity)
+    int32_t nz;             // renumbered: vertices [nz, V) have no out-edges (else nz = V)
+    int32_t ni;             // renumbered: vertices [ni, V) have no edge at all (else ni = V)
+    int *err;               // sticky error flag of bounded device waits
+    unsigned *queue;        // work queue of the persistent merge (zero between launches)
 };
 
 __device__ __forceinline__ float spread_of(const UpdateArgs &u) {
@@ -33,10 +38,22 @@ __device__ __forceinline__ float spread_of(const UpdateArgs &u) {
 }
 
 // rank[v] = (1-d)/V + d (sum + D/V); contribution = rank / out_degree; returns the dangling share.
+// Ranks leave under the caller's vertex IDs.  Renumbered vertices from nz on have no out-edges:
+// their contribution is never read, so neither the reciprocal is loaded nor the value stored.
 __device__ __forceinline__ float apply_update(const UpdateArgs &u, int32_t v, float sum, float spread) {
     const float r = u.base + u.damping * (sum + spread);
-    if (u.rank_out) u.rank_out[v] = r;
+    if (u.rank_out) u.rank_out[u.perm ? __ldg(u.perm + v) : v] = r;
+    if (v >= u.nz) return r;
     const float inv = __ldg(u.inv_outdeg + v);
+    u.contrib_next[v] = r * inv;
+    return inv == 0.0f ? r : 0.0f;
+}
+
+// The same update with the out-degree reciprocal of v already at hand (inv; ignored from nz on).
+__device__ __forceinline__ float apply_update_inv(const UpdateArgs &u, int32_t v, float sum, float spread, float inv) {
+    const float r = u.base + u.damping * (sum + spread);
+    if (u.rank_out) u.rank_out[u.perm ? __ldg(u.perm + v) : v] = r;
+    if (v >= u.nz) return r;
     u.contrib_next[v] = r * inv;
     return inv == 0.0f ? r : 0.0f;
 }
@@ -154,7 +171,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
                                                            const int32_t *__restrict__ id_map,
                                                            const uint16_t *__restrict__ id16,
                                                            const int32_t *__restrict__ offT, int32_t B, int32_t k,
-                                                           UpdateArgs u) {
+                                                           const int32_t *__restrict__ rstart, UpdateArgs u) {
     extern __shared__ __align__(16) unsigned char msm[];
     float *acc = reinterpret_cast<float *>(msm);                        // [MG_WARPS][k]
     int32_t *lo = reinterpret_cast<int32_t *>(acc + (size_t)MG_WARPS * k);  // [B]
@@ -166,7 +183,9 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
     __shared__ float fred[32];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t j = blockIdx.x;
-    const int32_t vbase = j * k;
+    // range j: [j k, (j+1) k), or [rstart[j], rstart[j+1]) (at most k wide) when given
+    const int32_t vbase = rstart ? rstart[j] : j * k;
+    const int32_t width = rstart ? rstart[j + 1] - vbase : k;
     for (int t = tid; t < MG_WARPS * k; t += MG_THREADS) acc[t] = 0.0f;
     // slice bounds and chunk counts of every block, then an exclusive scan of the counts
     const int per = (B + MG_THREADS - 1) / MG_THREADS;
@@ -252,7 +271,7 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
     __syncthreads();
     const float spread = spread_of(u);
     float dsum = 0.0f;
-    for (int t = tid; t < k; t += MG_THREADS) {
+    for (int t = tid; t < width; t += MG_THREADS) {
         const int32_t v = vbase + t;
         if (v >= u.V) break;
         float sum = 0.0f;
@@ -260,8 +279,14 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
         for (int w = 0; w < MG_WARPS; ++w) sum += acc[(size_t)w * k + t];
         dsum += apply_update(u, v, sum, spread);
     }
+    // vertices without any edge (renumbered, from ni on): see k_pull_merge_atomic
+    const float r_iso = u.base + u.damping * (0.0f + spread);
+    if (u.rank_out)
+        for (int64_t v = (int64_t)u.ni + (int64_t)blockIdx.x * MG_THREADS + tid; v < u.V;
+             v += (int64_t)gridDim.x * MG_THREADS)
+            u.rank_out[u.perm ? __ldg(u.perm + v) : v] = r_iso;
     const float bs = block_sum<float>(dsum, fred);
-    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next, (double)(u.V - u.ni) * (double)r_iso);
 }
 
 // Rounding to an integer by adding 1.5 * 2^23: for |y| <= 2^22 the sum's low significand
@@ -308,207 +333,293 @@ __device__ __forceinline__ void fx_split3(float xs, int32_t &hi, int32_t &mid, i
 // are added with 32-bit shared reductions and recombined exactly, so the result does not
 // depend on the order of the additions: deterministic.  (FP32 shared atomics measured about
 // 3.4x slower than 32-bit integer ones on GB300, and 64-bit ones 6.5x.)
-// MODE 0: FP32 atomics (the order of the additions, and so the last bits, may vary).
 constexpr int MG_GRAN = 8;     // entries per granule: 32 bytes of sums, 16 bytes of 2-byte ids
 constexpr int MG_GUNROLL = 2;  // granules of a lane in flight
 
 // Shared-memory layout of k_pull_merge_atomic: nacc accumulator arrays of [k], slice bounds
-// and granule prefix ([3B + 1] ints), then the chunk-to-slice map.
+// and granule prefix ([3B + 1] ints), the chunk-to-slice map, then (16-byte aligned) the out-degree
+// reciprocals of the range's vertices ([k] floats, one bulk copy).
+__host__ __device__ inline size_t merge_atomic_inv_offset(int32_t k, int32_t B, int nacc) {
+    const size_t head = (size_t)k * 4 * nacc + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+    return (head + 15) & ~(size_t)15;
+}
 __host__ __device__ inline size_t merge_atomic_layout_bytes(int32_t k, int32_t B, int nacc) {
-    return (size_t)k * 4 * nacc + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+    return merge_atomic_inv_offset(k, B, nacc) + (size_t)k * 4;
 }
 
+// Persistent: CTA c reduces range c first, then draws further ranges from a work queue (an
+// atomic counter) until none is left.  While one range is reduced, the slice bounds of the
+// CTA's next range are already loading (one per thread when B fits the CTA) and the out-degree
+// reciprocals of the current range arrive by a bulk copy.  Each range's dangling mass goes to
+// its own slot u.dpart[j]; the last CTA adds the slots in range order, so the result does not
+// depend on which CTA took which range.
 template <int MODE>
-__global__ void __launch_bounds__(MG_THREADS) k_pull_merge_atomic(const float *__restrict__ partial,
-                                                                  const int32_t *__restrict__ id_map,
-                                                                  const uint16_t *__restrict__ id16,
-                                                                  const int32_t *__restrict__ offT, int32_t B,
-                                                                  int32_t k, UpdateArgs u) {
-    constexpr int NACC = MODE == 0 ? 1 : MODE;
+__global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float *__restrict__ partial,
+                                                                     const int32_t *__restrict__ id_map,
+                                                                     const uint16_t *__restrict__ id16,
+                                                                     const int32_t *__restrict__ offT, int32_t B,
+                                                                     int32_t k, const int32_t *__restrict__ rstart,
+                                                                     int32_t nranges, UpdateArgs u) {
+    static_assert(MODE == 2 || MODE == 3, "two- or three-part fixed point");
+    constexpr int NACC = MODE;
     extern __shared__ __align__(16) unsigned char msm[];
     int32_t *acc_hi = reinterpret_cast<int32_t *>(msm);  // fixed point: NACC arrays of [k]
     int32_t *acc_mid = acc_hi + k;                       // MODE 3 only
     int32_t *acc_lo = acc_hi + (size_t)(NACC - 1) * k;
-    float *acc32 = reinterpret_cast<float *>(msm);       // MODE 0: [k]
     int32_t *e_lo = reinterpret_cast<int32_t *>(msm + (size_t)k * 4 * NACC);  // [B] first entry
     int32_t *e_hi = e_lo + B;                                                  // [B] end entry
     int32_t *gpre = e_hi + B;                                                  // [B + 1] granule prefix
     uint16_t *cmap = reinterpret_cast<uint16_t *>(gpre + B + 1);
+    float *sinv = reinterpret_cast<float *>(msm + merge_atomic_inv_offset(k, B, NACC));  // [k]
     const int32_t cmap_cap = B + MG_CMAP_EXTRA;
+    __shared__ __align__(8) uint64_t inv_bar;
     __shared__ int32_t wsum[MG_WARPS];
-    __shared__ float fred[32];
+    __shared__ float wdang[MG_WARPS];  // per-warp dangling mass of the range just finished
+    __shared__ int32_t s_next;         // the CTA's next range, drawn from the queue
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int32_t j = blockIdx.x;
-    const int32_t vbase = j * k;
     // u.fx_scale = 2^61 / mass (a power of two); the parts want 2^44 or 2^48 per unit of mass
-    const float scalef = MODE == 2 ? (float)(*u.fx_scale * 0x1p-17) : MODE == 3 ? (float)(*u.fx_scale * 0x1p-13) : 1.0f;
-    for (int t = tid; t < k * NACC; t += MG_THREADS) acc_hi[t] = 0;  // also clears acc32
-    // slice bounds and granule counts, then an exclusive CTA scan of the counts
+    const float scalef = MODE == 2 ? (float)(*u.fx_scale * 0x1p-17) : (float)(*u.fx_scale * 0x1p-13);
+    const float inv_scalef = 1.0f / scalef;  // a power of two
+    const float spread = spread_of(u);
     const int per = (B + MG_THREADS - 1) / MG_THREADS;
-    int32_t run = 0;
-    for (int q = 0; q < per; ++q) {
-        const int32_t b = tid * per + q;
-        if (b < B) {
-            const int32_t l0 = __ldg(offT + (int64_t)j * B + b), l1 = __ldg(offT + (int64_t)(j + 1) * B + b);
-            e_lo[b] = l0;
-            e_hi[b] = l1;
-            run += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
+    if (tid == 0) {
+        mbar_init(&inv_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    uint32_t phase = 0;    // parity of the reciprocal copy's next completion
+    bool broken = false;   // a bounded wait gave up: no more copies, ranges skipped
+    int32_t j = blockIdx.x, jprev = -1;
+    int32_t pre_lo = 0, pre_hi = 0;  // slice bounds of block tid in range j (per == 1)
+    if (per == 1 && tid < B && j < nranges) {
+        pre_lo = __ldg(offT + (int64_t)j * B + tid);
+        pre_hi = __ldg(offT + (int64_t)(j + 1) * B + tid);
+    }
+    while (j < nranges) {
+        // range j: [j k, (j+1) k), or [rstart[j], rstart[j+1]) (at most k wide) when given
+        const int32_t vbase = rstart ? rstart[j] : j * k;
+        const int32_t width = rstart ? rstart[j + 1] - vbase : k;
+        const int32_t nload = broken ? 0 : min(width, max(0, u.nz - vbase));
+        __syncthreads();  // the previous range is done with the accumulators, tables and sinv
+        if (tid == 0) {
+            if (jprev >= 0) {  // the previous range's dangling mass, warps added in order
+                float d = 0.0f;
+                for (int w = 0; w < MG_WARPS; ++w) d += wdang[w];
+                u.dpart[jprev] = (double)d;
+            }
+            s_next = (int32_t)gridDim.x + (int32_t)atomicAdd(u.queue, 1u);
         }
-    }
-    int incl = run;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += y;
-    }
-    if (lane == 31) wsum[warp] = incl;
-    __syncthreads();
-    if (warp == 0) {
-        const int w = lane < MG_WARPS ? wsum[lane] : 0;
-        int wi = w;
+        // only the range's own slots are cleared (masked entries add zero to slots < 32, which
+        // are never read when the range is narrower)
+        for (int a = 0; a < NACC; ++a)
+            for (int t = tid; t < width; t += MG_THREADS) acc_hi[(size_t)a * k + t] = 0;
+        // the reciprocals of the range's vertices with out-edges arrive by one bulk copy while the
+        // partial sums are reduced (vbase is a multiple of 32 and the arrays are padded, so the
+        // 16-byte rounded copy stays in bounds)
+        if (tid == 0 && nload > 0) {
+            const uint32_t bytes = (uint32_t)(nload * 4 + 15) & ~15u;
+            mbar_expect_tx(&inv_bar, bytes);
+            for (uint32_t off = 0; off < bytes; off += 16384) {
+                const uint32_t part = (bytes - off) < 16384u ? (bytes - off) : 16384u;
+                bulk_g2s(reinterpret_cast<unsigned char *>(sinv) + off,
+                         reinterpret_cast<const unsigned char *>(u.inv_outdeg + vbase) + off, part, &inv_bar);
+            }
+        }
+        // slice bounds and granule counts (the next range's bounds start loading), then an
+        // exclusive CTA scan of the counts
+        int32_t run = 0;
+        if (per == 1) {
+            if (tid < B) {
+                e_lo[tid] = pre_lo;
+                e_hi[tid] = pre_hi;
+                run = pre_hi > pre_lo ? ((pre_hi + MG_GRAN - 1) / MG_GRAN - pre_lo / MG_GRAN) : 0;
+            }
+        } else {
+            for (int q = 0; q < per; ++q) {
+                const int32_t b = tid * per + q;
+                if (b < B) {
+                    const int32_t l0 = __ldg(offT + (int64_t)j * B + b), l1 = __ldg(offT + (int64_t)(j + 1) * B + b);
+                    e_lo[b] = l0;
+                    e_hi[b] = l1;
+                    run += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
+                }
+            }
+        }
+        int incl = run;
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, wi, d);
-            if (lane >= d) wi += y;
+            const int y = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += y;
         }
-        if (lane < MG_WARPS) wsum[lane] = wi - w;
-    }
-    __syncthreads();
-    int32_t base = wsum[warp] + incl - run;
-    for (int q = 0; q < per; ++q) {
-        const int32_t b = tid * per + q;
-        if (b < B) {
-            gpre[b] = base;
-            const int32_t l0 = e_lo[b], l1 = e_hi[b];
-            base += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        const int32_t jn = s_next;  // published by the barrier above
+        if (per == 1 && tid < B && jn < nranges) {  // the next range's slice bounds start loading
+            pre_lo = __ldg(offT + (int64_t)jn * B + tid);
+            pre_hi = __ldg(offT + (int64_t)(jn + 1) * B + tid);
         }
-    }
-    if (tid == MG_THREADS - 1) gpre[B] = base;
-    __syncthreads();
-    // cmap[c] = slice holding granule 32 c (the last slice starting at or before it)
-    for (int q = 0; q < per; ++q) {
-        const int32_t b = tid * per + q;
-        if (b < B) {
-            const int32_t g0 = gpre[b], g1 = gpre[b + 1];
-            for (int32_t c = (g0 + 31) >> 5; (c << 5) < g1 && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
-        }
-    }
-    __syncthreads();
-    const int32_t ngran = gpre[B];
-    const int32_t nchunks = (ngran + 31) >> 5;
-    const int32_t dummy = lane < k ? lane : 0;  // target of the zero adds of masked entries
-    const int32_t c_begin = (int32_t)((int64_t)nchunks * warp / MG_WARPS);
-    const int32_t c_end = (int32_t)((int64_t)nchunks * (warp + 1) / MG_WARPS);
-    int32_t bp = 0;
-    if (c_begin < c_end) {
-        if (c_begin < cmap_cap) {
-            bp = cmap[c_begin];
-        } else {  // beyond the map: last slice with gpre <= the chunk's first granule
-            int32_t lo = 0, hi = B - 1;
-            const int32_t gq = c_begin << 5;
-            while (lo < hi) {
-                const int32_t mid = (lo + hi + 1) >> 1;
-                if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
-            }
-            bp = lo;
-        }
-    }
-    for (int32_t c0 = c_begin; c0 < c_end; c0 += MG_GUNROLL) {
-        float4 xa[MG_GUNROLL], xb[MG_GUNROLL];
-        uint4 iv[MG_GUNROLL];
-        uint32_t valid[MG_GUNROLL];  // bit e: entry first + e belongs to the slice
+        if (warp == 0) {
+            const int w = lane < MG_WARPS ? wsum[lane] : 0;
+            int wi = w;
 #pragma unroll
-        for (int q = 0; q < MG_GUNROLL; ++q) {
-            const int32_t c = c0 + q;
-            const int32_t g = (c << 5) + lane;
-            valid[q] = 0u;
-            xa[q] = xb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
-            iv[q] = make_uint4(0u, 0u, 0u, 0u);
-            if (c < c_end && g < ngran) {
-                while (gpre[bp + 1] <= g) ++bp;
-                const int32_t l0 = e_lo[bp], l1 = e_hi[bp];
-                const int32_t f = ((l0 >> 3) + (g - gpre[bp])) << 3;  // MG_GRAN = 8, l0 >= 0
-                const int32_t a = l0 - f > 0 ? l0 - f : 0;              // first valid offset
-                const int32_t z = l1 - f < MG_GRAN ? l1 - f : MG_GRAN;  // end offset
-                valid[q] = (0xFFu >> (MG_GRAN - z)) & (0xFFu << a);
-                const float4 *px = reinterpret_cast<const float4 *>(partial + f);
-                xa[q] = __ldg(px);
-                xb[q] = __ldg(px + 1);
+            for (int d = 1; d < 32; d <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, wi, d);
+                if (lane >= d) wi += y;
+            }
+            if (lane < MG_WARPS) wsum[lane] = wi - w;
+        }
+        __syncthreads();
+        int32_t base = wsum[warp] + incl - run;
+        for (int q = 0; q < per; ++q) {
+            const int32_t b = tid * per + q;
+            if (b < B) {
+                gpre[b] = base;
+                const int32_t l0 = e_lo[b], l1 = e_hi[b];
+                base += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
+            }
+        }
+        if (tid == MG_THREADS - 1) gpre[B] = base;
+        __syncthreads();
+        // cmap[c] = slice holding granule 32 c (the last slice starting at or before it)
+        for (int q = 0; q < per; ++q) {
+            const int32_t b = tid * per + q;
+            if (b < B) {
+                const int32_t g0 = gpre[b], g1 = gpre[b + 1];
+                for (int32_t c = (g0 + 31) >> 5; (c << 5) < g1 && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
+            }
+        }
+        __syncthreads();
+        const int32_t ngran = gpre[B];
+        const int32_t nchunks = (ngran + 31) >> 5;
+        const int32_t dummy = lane < k ? lane : 0;  // target of the zero adds of masked entries
+        const int32_t c_begin = (int32_t)((int64_t)nchunks * warp / MG_WARPS);
+        const int32_t c_end = (int32_t)((int64_t)nchunks * (warp + 1) / MG_WARPS);
+        int32_t bp = 0;
+        if (c_begin < c_end) {
+            if (c_begin < cmap_cap) {
+                bp = cmap[c_begin];
+            } else {  // beyond the map: last slice with gpre <= the chunk's first granule
+                int32_t lo = 0, hi = B - 1;
+                const int32_t gq = c_begin << 5;
+                while (lo < hi) {
+                    const int32_t mid = (lo + hi + 1) >> 1;
+                    if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
+                }
+                bp = lo;
+            }
+        }
+        for (int32_t c0 = c_begin; c0 < c_end; c0 += MG_GUNROLL) {
+            float4 xa[MG_GUNROLL], xb[MG_GUNROLL];
+            uint4 iv[MG_GUNROLL];
+            uint32_t valid[MG_GUNROLL];  // bit e: entry first + e belongs to the slice
+#pragma unroll
+            for (int q = 0; q < MG_GUNROLL; ++q) {
+                const int32_t c = c0 + q;
+                const int32_t g = (c << 5) + lane;
+                valid[q] = 0u;
+                xa[q] = xb[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+                iv[q] = make_uint4(0u, 0u, 0u, 0u);
+                if (c < c_end && g < ngran) {
+                    while (gpre[bp + 1] <= g) ++bp;
+                    const int32_t l0 = e_lo[bp], l1 = e_hi[bp];
+                    const int32_t f = ((l0 >> 3) + (g - gpre[bp])) << 3;  // MG_GRAN = 8, l0 >= 0
+                    const int32_t a = l0 - f > 0 ? l0 - f : 0;              // first valid offset
+                    const int32_t z = l1 - f < MG_GRAN ? l1 - f : MG_GRAN;  // end offset
+                    valid[q] = (0xFFu >> (MG_GRAN - z)) & (0xFFu << a);
+                    const float4 *px = reinterpret_cast<const float4 *>(partial + f);
+                    xa[q] = __ldg(px);
+                    xb[q] = __ldg(px + 1);
+                    if (id16) {
+                        iv[q] = __ldg(reinterpret_cast<const uint4 *>(id16 + f));
+                    } else {  // global ids: keep the granule's position, read them below
+                        iv[q].x = (uint32_t)f;
+                    }
+                }
+            }
+#pragma unroll
+            for (int q = 0; q < MG_GUNROLL; ++q) {
+                float x8[MG_GRAN] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
+                int32_t id8[MG_GRAN];
                 if (id16) {
-                    iv[q] = __ldg(reinterpret_cast<const uint4 *>(id16 + f));
-                } else {  // global ids: keep the granule's position, read them below
-                    iv[q].x = (uint32_t)f;
-                }
-            }
-        }
+                    const uint32_t w[4] = {iv[q].x, iv[q].y, iv[q].z, iv[q].w};
 #pragma unroll
-        for (int q = 0; q < MG_GUNROLL; ++q) {
-            float x8[MG_GRAN] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
-            int32_t id8[MG_GRAN];
-            if (id16) {
-                const uint32_t w[4] = {iv[q].x, iv[q].y, iv[q].z, iv[q].w};
-#pragma unroll
-                for (int h = 0; h < 4; ++h) {
-                    id8[2 * h] = (int32_t)(w[h] & 0xFFFFu);
-                    id8[2 * h + 1] = (int32_t)(w[h] >> 16);
-                }
-            } else {
-                int4 w0 = make_int4(vbase, vbase, vbase, vbase), w1 = w0;
-                if (valid[q]) {
-                    const int4 *pi = reinterpret_cast<const int4 *>(id_map + (int32_t)iv[q].x);
-                    w0 = __ldg(pi);
-                    w1 = __ldg(pi + 1);
-                }
-                id8[0] = w0.x - vbase; id8[1] = w0.y - vbase; id8[2] = w0.z - vbase; id8[3] = w0.w - vbase;
-                id8[4] = w1.x - vbase; id8[5] = w1.y - vbase; id8[6] = w1.z - vbase; id8[7] = w1.w - vbase;
-            }
-            // Entries outside the slice add zero to a slot of their own lane (no branches: the
-            // atomics of a warp stay converged).
-#pragma unroll
-            for (int e = 0; e < MG_GRAN; ++e) {
-                const bool ok = (valid[q] >> e) & 1u;
-                const int32_t id = ok ? id8[e] : dummy;
-                const float x = ok ? x8[e] : 0.0f;
-                if (MODE == 2) {
-                    int32_t h, lw;
-                    fx_split2(x * scalef, h, lw);
-                    atomicAdd(acc_hi + id, h);
-                    atomicAdd(acc_lo + id, lw);
-                } else if (MODE == 3) {
-                    int32_t h, md, lw;
-                    fx_split3(x * scalef, h, md, lw);
-                    if (h) atomicAdd(acc_hi + id, h);
-                    atomicAdd(acc_mid + id, md);
-                    atomicAdd(acc_lo + id, lw);
+                    for (int h = 0; h < 4; ++h) {
+                        id8[2 * h] = (int32_t)(w[h] & 0xFFFFu);
+                        id8[2 * h + 1] = (int32_t)(w[h] >> 16);
+                    }
                 } else {
-                    atomicAdd(acc32 + id, x);
+                    int4 w0 = make_int4(vbase, vbase, vbase, vbase), w1 = w0;
+                    if (valid[q]) {
+                        const int4 *pi = reinterpret_cast<const int4 *>(id_map + (int32_t)iv[q].x);
+                        w0 = __ldg(pi);
+                        w1 = __ldg(pi + 1);
+                    }
+                    id8[0] = w0.x - vbase; id8[1] = w0.y - vbase; id8[2] = w0.z - vbase; id8[3] = w0.w - vbase;
+                    id8[4] = w1.x - vbase; id8[5] = w1.y - vbase; id8[6] = w1.z - vbase; id8[7] = w1.w - vbase;
+                }
+                // Entries outside the slice add zero to a slot of their own lane (no branches: the
+                // atomics of a warp stay converged).
+#pragma unroll
+                for (int e = 0; e < MG_GRAN; ++e) {
+                    const bool ok = (valid[q] >> e) & 1u;
+                    const int32_t id = ok ? id8[e] : dummy;
+                    const float x = ok ? x8[e] : 0.0f;
+                    if (MODE == 2) {
+                        int32_t h, lw;
+                        fx_split2(x * scalef, h, lw);
+                        atomicAdd(acc_hi + id, h);
+                        atomicAdd(acc_lo + id, lw);
+                    } else {
+                        int32_t h, md, lw;
+                        fx_split3(x * scalef, h, md, lw);
+                        if (h) atomicAdd(acc_hi + id, h);
+                        atomicAdd(acc_mid + id, md);
+                        atomicAdd(acc_lo + id, lw);
+                    }
                 }
             }
         }
-    }
-    __syncthreads();
-    const float spread = spread_of(u);
-    const float inv_scalef = 1.0f / scalef;  // a power of two
-    float dsum = 0.0f;
-    for (int t = tid; t < k; t += MG_THREADS) {
-        const int32_t v = vbase + t;
-        if (v >= u.V) break;
-        float sum;
-        if (MODE != 0) {
+        __syncthreads();
+        // bounded wait for the reciprocals; on a timeout the flag is set (the caller reports
+        // TC_ERR_TIMEOUT) and this and every later range of the CTA are skipped, but the CTA
+        // still joins the dangling-mass reduction so that its arrival counter stays consistent
+        if (nload > 0) {
+            if (!mbar_wait(&inv_bar, phase, u.err, 2)) broken = true;
+            phase ^= 1u;
+        }
+        float dsum = 0.0f;
+        for (int t = tid; !broken && t < width; t += MG_THREADS) {
+            const int32_t v = vbase + t;
+            if (v >= u.V) break;
             // exact 64-bit total, converted with 32-bit integer-to-float steps (no FP64)
             const long long tot = MODE == 2 ? ((long long)acc_hi[t] << 22) + (long long)acc_lo[t]
                                             : ((long long)acc_hi[t] << 32) + ((long long)acc_mid[t] << 16) +
                                                   (long long)acc_lo[t];
             const float th = (float)(int32_t)(tot >> 24);            // |tot| < 2^49
             const float tl = (float)(uint32_t)(tot & 0xFFFFFFll);     // < 2^24, exact
-            sum = fmaf(th, 16777216.0f, tl) * inv_scalef;
-        } else {
-            sum = acc32[t];
+            const float sum = fmaf(th, 16777216.0f, tl) * inv_scalef;
+            dsum += apply_update_inv(u, v, sum, spread, t < nload ? sinv[t] : 0.0f);
         }
-        dsum += apply_update(u, v, sum, spread);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) dsum += __shfl_xor_sync(0xffffffffu, dsum, d);
+        if (lane == 0) wdang[warp] = dsum;
+        jprev = j;
+        j = jn;
     }
-    const float bs = block_sum<float>(dsum, fred);
-    grid_sum_last_cta((double)bs, u.dpart, u.counter, u.D_next);
+    __syncthreads();
+    if (tid == 0 && jprev >= 0) {
+        float d = 0.0f;
+        for (int w = 0; w < MG_WARPS; ++w) d += wdang[w];
+        u.dpart[jprev] = (double)d;
+    }
+    // Vertices without any edge (renumbered to the end, from ni on) get no pieces and pass nothing
+    // on: every one of them has the rank of an empty sum, and their dangling mass is that rank
+    // times their count, added once by the last CTA.
+    const float r_iso = u.base + u.damping * (0.0f + spread);
+    if (u.rank_out)
+        for (int64_t v = (int64_t)u.ni + (int64_t)blockIdx.x * MG_THREADS + tid; v < u.V;
+             v += (int64_t)gridDim.x * MG_THREADS)
+            u.rank_out[u.perm ? __ldg(u.perm + v) : v] = r_iso;
+    grid_sum_slots_last_cta(u.dpart, nranges, u.counter, u.queue, u.D_next, (double)(u.V - u.ni) * (double)r_iso);
 }
 
 // Entries per vertex are at most B (one per block): two-part fixed point below 1024 blocks.
@@ -526,8 +637,9 @@ __global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict_
     float dsum = 0.0f, msum = 0.0f;
     const float r0 = 1.0f / (float)u.V;
     for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < u.V; v += (int64_t)gridDim.x * PR_THREADS) {
-        const float r = init ? init[v] : r0;
-        if (u.rank_out) u.rank_out[v] = r;
+        const int32_t orig = u.perm ? __ldg(u.perm + v) : (int32_t)v;  // caller's ID of vertex v
+        const float r = init ? init[orig] : r0;
+        if (u.rank_out) u.rank_out[orig] = r;
         const float inv = __ldg(u.inv_outdeg + v);
         u.contrib_next[v] = r * inv;
         if (inv == 0.0f) dsum += r;
@@ -705,6 +817,7 @@ struct PrState {
     float *contrib[2];
     double *D;          // D[0], D[1]
     unsigned *counter;
+    unsigned *queue;    // work queue of the persistent merge
     double *mass;       // L1 mass of the initial ranks
     double *scale;      // fixed-point scale of the merge
     int *err;           // sticky error flag of bounded device waits
@@ -728,6 +841,7 @@ static int prepare_state(tc_graph *g, const tc_pr_params *pp, float *ranks_out, 
     char *sc = g->ws_scalars.as<char>();
     st->D = reinterpret_cast<double *>(sc);
     st->counter = reinterpret_cast<unsigned *>(sc + 32);
+    st->queue = reinterpret_cast<unsigned *>(sc + 36);
     st->err = reinterpret_cast<int *>(sc + 40);
     st->mass = reinterpret_cast<double *>(sc + 48);
     st->scale = reinterpret_cast<double *>(sc + 56);
@@ -751,7 +865,7 @@ static int check_pr_args(const tc_graph *g, const tc_part *part, const tc_pr_par
     if (pp->out_mem != TC_MEM_HOST && pp->out_mem != TC_MEM_DEVICE)
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad out_mem");
     if (pp->lb_warp_min < 0) return fail(TC_ERR_INVALID_ARG, "pagerank: lb_warp_min < 0");
-    if (pp->merge_mode < TC_MERGE_FIXED || pp->merge_mode > TC_MERGE_FLOAT)
+    if (pp->merge_mode != TC_MERGE_FIXED && pp->merge_mode != TC_MERGE_ORDERED)
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad merge_mode");
     if (part && (part->g != g || part->dir != dir))
         return fail(TC_ERR_INVALID_ARG, "pagerank: partition belongs to another graph or direction");
@@ -811,13 +925,13 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
             TC_CUDA(cudaFuncSetAttribute(k_pull_merge_ordered, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)merge_smem));
         } else {
-            const bool fx = merge_mode == TC_MERGE_FIXED;
-            merge_smem = merge_atomic_smem_bytes(part->k, part->B, fx);
-            const void *kmerge = !fx ? (const void *)k_pull_merge_atomic<0>
-                                     : merge_fixed_parts(part->B) == 2 ? (const void *)k_pull_merge_atomic<2>
-                                                                       : (const void *)k_pull_merge_atomic<3>;
+            merge_smem = merge_atomic_smem_bytes(part->k, part->B, true);
+            const void *kmerge = merge_fixed_parts(part->B) == 2 ? (const void *)k_pull_merge_atomic<2>
+                                                                 : (const void *)k_pull_merge_atomic<3>;
             // always: the 48 KB default also counts the kernel's static shared memory
             TC_CUDA(cudaFuncSetAttribute(kmerge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)merge_smem));
+            // persistent: as many CTAs as fit on the device at once (each loops over ranges)
+            TC_TRY(occupancy_grid(kmerge, MG_THREADS, merge_smem, part->nranges, &g_merge));
         }
     }
     int g_init = 1;
@@ -827,10 +941,12 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     if (max_ctas_hint > max_ctas) max_ctas = max_ctas_hint;
     if (g_upd > max_ctas) max_ctas = g_upd;
     if (g_merge > max_ctas) max_ctas = g_merge;
+    if (part && !push && part->nranges > max_ctas) max_ctas = part->nranges;  // one dangling slot per range
 
     PrState st;
     TC_TRY(prepare_state(g, pp, ranks_out, push, max_ctas, &st));
-    TC_CUDA(cudaMemsetAsync(st.counter, 0, 16, s));  // counter and error flag
+    TC_CUDA(cudaMemsetAsync(st.counter, 0, 16, s));  // counter, merge work queue and the error flag
+    if (tiled) TC_CUDA(cudaMemsetAsync(part->bq.p, 0, ((size_t)part->B + 1) * 4, s));  // the gather's item counters
     if (push) TC_CUDA(cudaMemsetAsync(st.sums, 0, (size_t)V * 4, s));
 
     UpdateArgs u;
@@ -840,8 +956,14 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     u.V = V;
     u.dpart = st.dpart;
     u.counter = st.counter;
-    u.inv_outdeg = g->inv_outdeg.as<float>();
+    const bool renumbered = part && part->order == TC_ORDER_OUTDEGREE;
+    u.inv_outdeg = renumbered ? part->inv_outdeg.as<float>() : g->inv_outdeg.as<float>();
     u.fx_scale = st.scale;
+    u.perm = renumbered ? part->perm.as<int32_t>() : nullptr;
+    u.nz = renumbered ? part->nz_out : V;
+    u.ni = renumbered ? part->ni : V;
+    u.err = st.err;
+    u.queue = st.queue;
 
     // the window applies to the unstaged pull gathers (the staged one copies its block's values
     // to shared memory)
@@ -924,22 +1046,19 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
                 k_push_update<<<g_upd, PR_THREADS, 0, s>>>(st.sums, u);
             } else {
                 const uint16_t *i16 = part->id16.p ? part->id16.as<uint16_t>() : nullptr;
+                const int32_t *rst = part->rstart.p ? part->rstart.as<int32_t>() : nullptr;
                 if (merge_mode == TC_MERGE_ORDERED)
                     k_pull_merge_ordered<<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->B, part->k, u);
-                else if (merge_mode == TC_MERGE_FIXED && merge_fixed_parts(part->B) == 2)
+                        part->B, part->k, rst, u);
+                else if (merge_fixed_parts(part->B) == 2)
                     k_pull_merge_atomic<2><<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->B, part->k, u);
-                else if (merge_mode == TC_MERGE_FIXED)
+                        part->B, part->k, rst, part->nranges, u);
+                else
                     k_pull_merge_atomic<3><<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->B, part->k, u);
-                else
-                    k_pull_merge_atomic<0><<<g_merge, MG_THREADS, merge_smem, s>>>(
-                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->B, part->k, u);
+                        part->B, part->k, rst, part->nranges, u);
             }
             TC_LAUNCH_CHECK();
             ++launches;

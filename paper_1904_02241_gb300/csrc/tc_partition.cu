@@ -35,15 +35,16 @@ __global__ void k_block_bounds(const int32_t *col, const int32_t *rowptr, int64_
     }
 }
 
-// off[b][j] = first local row of block b whose global id is >= j*k, j in [0, nranges];
-// offT[j][b] holds the same table range-major (the merge of range j reads one row of it).
+// off[b][j] = first local row of block b whose global id is >= the first vertex of merge range
+// j (j*k, or rstart[j] when the ranges are given), j in [0, nranges]; offT[j][b] holds the same
+// table range-major (the merge of range j reads one row of it).
 __global__ void k_merge_offsets(const int32_t *id_map, const int64_t *blk_rows, int32_t B, int32_t nranges, int32_t k,
-                                int32_t *off, int32_t *offT) {
+                                const int32_t *rstart, int32_t *off, int32_t *offT) {
     const int64_t total = (int64_t)B * (nranges + 1);
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
         const int32_t b = (int32_t)(t / (nranges + 1));
         const int32_t j = (int32_t)(t - (int64_t)b * (nranges + 1));
-        const int64_t bound = (int64_t)j * k;
+        const int64_t bound = rstart ? (int64_t)rstart[j] : (int64_t)j * k;
         int64_t lo = blk_rows[b], hi = blk_rows[b + 1];
         while (lo < hi) {
             int64_t mid = (lo + hi) >> 1;
@@ -57,6 +58,100 @@ __global__ void k_merge_offsets(const int32_t *id_map, const int64_t *blk_rows, 
 __global__ void k_id16(const int32_t *id_map, int64_t R, int32_t kmask, uint16_t *id16) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
         id16[r] = (uint16_t)(id_map[r] & kmask);
+}
+
+// id16[r] = id_map[r] minus the first vertex of its merge range (the last rstart <= the id).
+__global__ void k_id16_ranges(const int32_t *id_map, int64_t R, const int32_t *rstart, int32_t nranges,
+                              uint16_t *id16) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = id_map[r];
+        int32_t lo = 0, hi = nranges - 1;
+        while (lo < hi) {
+            const int32_t mid = (lo + hi + 1) >> 1;
+            if (rstart[mid] <= v) lo = mid; else hi = mid - 1;
+        }
+        id16[r] = (uint16_t)(v - rstart[lo]);
+    }
+}
+
+// ---- vertex renumbering by out-degree (TC_ORDER_OUTDEGREE) ---------------------------------
+// key[v] = maxdeg - out_degree(v), or maxdeg + 1 for a vertex without any edge: an ascending
+// stable sort of the keys lists the vertices by out-degree, highest first, ties in ID order, with
+// the vertices that have no edge at all after those that have in-edges only.  *isolated counts
+// the vertices without any edge.
+__global__ void k_order_keys(const int32_t *out_rowptr, const int32_t *in_rowptr, int32_t V, int32_t maxdeg,
+                             int32_t *key, int32_t *val, int32_t *isolated) {
+    int32_t n = 0;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t od = out_rowptr[v + 1] - out_rowptr[v];
+        const bool iso = od == 0 && in_rowptr[v + 1] == in_rowptr[v];
+        key[v] = iso ? maxdeg + 1 : maxdeg - od;
+        val[v] = (int32_t)v;
+        n += iso;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) n += __shfl_xor_sync(0xffffffffu, n, d);
+    if ((threadIdx.x & 31) == 0 && n) atomicAdd(isolated, n);
+}
+
+// For new vertex n with original ID perm[n]: inv[perm[n]] = n, its in-degree (row length of the
+// renumbered G^T; deg[V] = 0 closes the scan) and its out-degree reciprocal.
+__global__ void k_order_apply(const int32_t *perm, const int32_t *in_rowptr, const float *inv_outdeg_old, int32_t V,
+                              int32_t *inv, int32_t *deg, float *inv_outdeg_new) {
+    for (int64_t n = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; n <= V; n += (int64_t)gridDim.x * blockDim.x) {
+        if (n == V) {
+            deg[V] = 0;
+            continue;
+        }
+        const int32_t o = perm[n];
+        inv[o] = (int32_t)n;
+        deg[n] = in_rowptr[o + 1] - in_rowptr[o];
+        inv_outdeg_new[n] = inv_outdeg_old[o];
+    }
+}
+
+// Renumbered G^T: edge e of new row n is edge (e - rowptr_new[n]) of old row perm[n], with its
+// source renumbered.  Sources keep the old row's order (ascending old ID).
+__global__ void k_order_edges(const int32_t *row_of_edge, const int32_t *rowptr_new, const int32_t *perm,
+                              const int32_t *in_rowptr, const int32_t *in_colidx, const int32_t *inv, int64_t E,
+                              int32_t *colidx_new) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t n = row_of_edge[e];
+        const int64_t src_pos = (int64_t)in_rowptr[perm[n]] + (e - rowptr_new[n]);
+        colidx_new[e] = inv[in_colidx[src_pos]];
+    }
+}
+
+// Pieces per destination: cnt[id_map[r]] += 1 over all local rows.
+__global__ void k_pieces_per_vertex(const int32_t *id_map, int64_t R, int32_t *cnt) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(cnt + id_map[r], 1);
+}
+
+// w[v] = cnt[v] + c for v < V, w[V] = 0 (in place).
+__global__ void k_range_weights(int32_t *w, int32_t V, int32_t c) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= V; v += (int64_t)gridDim.x * blockDim.x)
+        w[v] = v < V ? w[v] + c : 0;
+}
+
+// rstart[j] = the first vertex whose exclusive weight prefix reaches j * total / nr, rounded down
+// to a multiple of 32; rstart[0] = 0 and rstart[nr] = V.
+__global__ void k_range_bounds(const int64_t *cum /* [V+1] exclusive prefix */, int32_t V, int32_t nr,
+                               int32_t *rstart) {
+    const int64_t total = cum[V];
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= nr; j += gridDim.x * blockDim.x) {
+        if (j == 0 || j == nr) {
+            rstart[j] = j == 0 ? 0 : V;
+            continue;
+        }
+        const int64_t target = total * j / nr;  // total < 2^34, nr < 2^20: no overflow
+        int64_t lo = 0, hi = V;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (cum[mid] < target) lo = mid + 1; else hi = mid;
+        }
+        rstart[j] = (int32_t)(lo & ~31LL);
+    }
 }
 
 __global__ void k_hub_flags(const int32_t *rowptr, int64_t nrows, int32_t min_degree, int32_t *flag) {
@@ -103,6 +198,106 @@ static int log2_ceil(int64_t x) {
     return b;
 }
 
+// Renumber the vertices by out-degree (highest first, ties by ID) and build G^T in the new
+// numbering (rp_new, ci_new), the permutation p->perm (new -> old) and the out-degree
+// reciprocals p->inv_outdeg in the new order.  Vertices with out-edges get the IDs [0, nz_out).
+static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, int grid, DevBuf *rp_new, DevBuf *ci_new,
+                                 tc_part *p) {
+    const int32_t V = g->V;
+    const int64_t E = g->E;
+    DevBuf key, val, kout, ktmp, vtmp, inv, deg, niso;
+    TC_TRY(niso.alloc(16));
+    TC_CUDA(cudaMemsetAsync(niso.p, 0, 4, s));
+    TC_TRY(key.alloc((size_t)V * 4));
+    TC_TRY(val.alloc((size_t)V * 4));
+    TC_TRY(kout.alloc((size_t)V * 4));
+    TC_TRY(ktmp.alloc((size_t)V * 4));
+    TC_TRY(vtmp.alloc((size_t)V * 4));
+    TC_TRY(p->perm.alloc((size_t)V * 4));
+    TC_TRY(p->inv_outdeg.alloc((size_t)V * 4 + 256));
+    k_order_keys<<<grid, 256, 0, s>>>(g->out_rowptr.as<int32_t>(), g->in_rowptr.as<int32_t>(), V, g->max_out_degree,
+                                      key.as<int32_t>(), val.as<int32_t>(), niso.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    int32_t h_iso = 0;
+    TC_CUDA(cudaMemcpyAsync(&h_iso, niso.p, 4, cudaMemcpyDeviceToHost, s));
+    TC_TRY(stable_bucket_sort(key.as<int32_t>(), val.as<int32_t>(), kout.as<int32_t>(), p->perm.as<int32_t>(),
+                              ktmp.as<int32_t>(), vtmp.as<int32_t>(), V, 1, log2_ceil((int64_t)g->max_out_degree + 2),
+                              s));  // synchronises: h_iso is in
+    key.release();
+    val.release();
+    kout.release();
+    ktmp.release();
+    vtmp.release();
+    TC_TRY(inv.alloc((size_t)V * 4));
+    TC_TRY(deg.alloc(((size_t)V + 1) * 4));
+    k_order_apply<<<grid, 256, 0, s>>>(p->perm.as<int32_t>(), g->in_rowptr.as<int32_t>(), g->inv_outdeg.as<float>(), V,
+                                       inv.as<int32_t>(), deg.as<int32_t>(), p->inv_outdeg.as<float>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(rp_new->alloc(((size_t)V + 1) * 4));
+    TC_TRY(scan_i32(deg.as<int32_t>(), (int64_t)V + 1, rp_new->as<int32_t>(), s));
+    deg.release();
+    TC_TRY(ci_new->alloc((size_t)(E > 0 ? E : 1) * 4));
+    if (E > 0) {
+        DevBuf row;
+        TC_TRY(row.alloc((size_t)E * 4));
+        TC_TRY(expand_rows(rp_new->as<int32_t>(), V, row.as<int32_t>(), s));
+        k_order_edges<<<grid, 256, 0, s>>>(row.as<int32_t>(), rp_new->as<int32_t>(), p->perm.as<int32_t>(),
+                                           g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), inv.as<int32_t>(), E,
+                                           ci_new->as<int32_t>());
+        TC_LAUNCH_CHECK();
+        TC_CUDA(cudaStreamSynchronize(s));
+    }
+    p->nz_out = (int32_t)((int64_t)V - g->num_dangling);
+    p->ni = V - h_iso;
+    p->order = TC_ORDER_OUTDEGREE;
+    return TC_OK;
+}
+
+// Merge ranges that hold about equal work over the vertices [0, V') with V' = ni (the rest have
+// no edge at all): vertex v weighs (pieces with destination v) + c, with c = max(1, ceil(R / V'));
+// nr = ceil(2V' / (kmax - 64)) ranges split the total weight evenly, at multiples of 32.  As every
+// vertex weighs at least c and R <= c V', no range is wider than kmax.
+static int weighted_ranges(tc_part *p, int32_t kmax, cudaStream_t s, int grid) {
+    const int32_t V = p->ni;  // the vertices from ni on have no edge: no range covers them
+    const int64_t R = p->R;
+    DevBuf cnt, cum;
+    TC_TRY(cnt.alloc(((size_t)V + 1) * 4));
+    TC_TRY(cum.alloc(((size_t)V + 1) * 8));
+    TC_CUDA(cudaMemsetAsync(cnt.p, 0, ((size_t)V + 1) * 4, s));
+    if (R > 0) {
+        k_pieces_per_vertex<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), R, cnt.as<int32_t>());
+        TC_LAUNCH_CHECK();
+    }
+    const int32_t c = (int32_t)(R > V ? (R + V - 1) / V : 1);
+    k_range_weights<<<grid, 256, 0, s>>>(cnt.as<int32_t>(), V, c);
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32_to_i64(cnt.as<int32_t>(), (int64_t)V + 1, cum.as<int64_t>(), s));
+    const int64_t nr64 = ((int64_t)2 * V + (kmax - 64) - 1) / (kmax - 64);
+    const int32_t nr = (int32_t)(nr64 > 0 ? nr64 : 1);
+    TC_TRY(p->rstart.alloc(((size_t)nr + 1) * 4));
+    k_range_bounds<<<(nr + 256) / 256, 256, 0, s>>>(cum.as<int64_t>(), V, nr, p->rstart.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    // the width bound holds by construction; check it once on the host all the same
+    int32_t *h = new (std::nothrow) int32_t[nr + 1];
+    if (!h) return fail(TC_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaMemcpyAsync(h, p->rstart.p, ((size_t)nr + 1) * 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    int32_t widest = 0;
+    bool monotone = true;
+    for (int32_t j = 0; e == cudaSuccess && j < nr; ++j) {
+        const int32_t w = h[j + 1] - h[j];
+        if (w < 0) monotone = false;
+        if (w > widest) widest = w;
+    }
+    const bool ends_ok = e != cudaSuccess || (h[0] == 0 && h[nr] == V);
+    delete[] h;
+    if (e != cudaSuccess) return fail(TC_ERR_CUDA, "weighted_ranges: %s", cudaGetErrorString(e));
+    if (!monotone || !ends_ok || widest > kmax)
+        return fail(TC_ERR_CUDA, "weighted_ranges: internal error (widest range %d > %d)", widest, kmax);
+    p->nranges = nr;
+    return TC_OK;
+}
+
 static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const tc_part_params *pp, cudaStream_t s,
                           tc_part *p) {
     DeviceCaps caps;
@@ -115,6 +310,21 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->dir = dir;
     p->V = V;
     p->E = E;
+    const int order = pp ? pp->vertex_order : TC_ORDER_NATURAL;
+    if (order != TC_ORDER_NATURAL && order != TC_ORDER_OUTDEGREE)
+        return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: bad vertex_order");
+    if (order == TC_ORDER_OUTDEGREE && dir != TC_PULL)
+        return fail(TC_ERR_UNSUPPORTED, "tc_tocab_partition: push partitions cannot be renumbered");
+    if (order == TC_ORDER_OUTDEGREE && pp && pp->merge_range > 0 && pp->merge_range < 128)
+        return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: renumbered partitions need merge_range >= 128");
+    DevBuf rel_rowptr, rel_colidx;
+    p->nz_out = (int32_t)((int64_t)V - g->num_dangling);  // vertices with out-edges
+    p->ni = V;
+    if (order == TC_ORDER_OUTDEGREE && V > 0) {
+        TC_TRY(renumber_by_outdegree(g, s, caps.sms * 8, &rel_rowptr, &rel_colidx, p));
+        rp = rel_rowptr.as<int32_t>();
+        ci = rel_colidx.as<int32_t>();
+    }
     const float frac = (pp && pp->l2_fraction > 0) ? pp->l2_fraction : 0.0f;
     if (pp && pp->merge_range > 0) {
         p->k = pp->merge_range;
@@ -127,7 +337,11 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->hub_degree = (pp && pp->hub_degree > 0) ? pp->hub_degree : 2048;
     const int32_t smem_w = tile_max_width(caps.max_smem_optin);
     const int policy = pp ? pp->block_policy : TC_BLOCKS_L2;
-    if (num_blocks == 0 && policy == TC_BLOCKS_SMEM) {
+    if (num_blocks == 0 && policy == TC_BLOCKS_SMEM && p->order == TC_ORDER_OUTDEGREE) {
+        // the gather splits blocks into row-aligned pieces of equal size, so B need not fill
+        // whole waves: the widest block that fits shared memory gives the fewest pieces
+        p->W = smem_w > 0 ? smem_w : 32;
+    } else if (num_blocks == 0 && policy == TC_BLOCKS_SMEM) {
         // the smallest multiple of the SM count of blocks whose width fits shared memory:
         // one CTA per block, whole waves
         int64_t m = 1, Wc = 1;
@@ -144,12 +358,13 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
         if (p->W > 32) p->W = (p->W + 31) / 32 * 32;  // 128-byte aligned source ranges
     }
     if (p->W < 1) p->W = 1;
-    p->B = V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1;
+    // renumbered: sources are exactly [0, nz_out), so the blocks past them would be empty
+    const int64_t span = p->order == TC_ORDER_OUTDEGREE ? (int64_t)p->nz_out : (int64_t)V;
+    p->B = span > 0 ? (int32_t)((span + p->W - 1) / p->W) : 1;
     p->nranges = (int32_t)(((int64_t)V + p->k - 1) / p->k);
-    if (dir == TC_PULL && ((int64_t)V + p->W - 1) / p->W > 65535)
+    if (dir == TC_PULL && p->B > 65535)
         return fail(TC_ERR_UNSUPPORTED, "more than 65535 blocks");
-    if (dir == TC_PULL && (int64_t)merge_atomic_smem_bytes(p->k, V > 0 ? (int32_t)(((int64_t)V + p->W - 1) / p->W) : 1,
-                                                           true) > (int64_t)caps.max_smem_optin)
+    if (dir == TC_PULL && (int64_t)merge_atomic_smem_bytes(p->k, p->B, true) > (int64_t)caps.max_smem_optin)
         return fail(TC_ERR_INVALID_ARG, "merge_range %d with this block count needs more shared memory than a CTA has",
                     p->k);
     const int32_t B = p->B, W = p->W;
@@ -207,17 +422,27 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     TC_TRY(p->blk_rows_dev.alloc(((size_t)B + 1) * 8));
     TC_CUDA(cudaMemcpyAsync(p->blk_rows_dev.p, blk_rows.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToDevice, s));
 
+    // merge ranges: fixed width k, or (renumbered) cut to about equal work
+    const int32_t *rst = nullptr;
+    if (p->order == TC_ORDER_OUTDEGREE && V > 0) {
+        TC_TRY(weighted_ranges(p, p->k, s, grid));
+        rst = p->rstart.as<int32_t>();
+    }
     // merge range table
     const int64_t noff = (int64_t)B * (p->nranges + 1);
     TC_TRY(p->merge_off.alloc((size_t)(noff > 0 ? noff : 1) * 4));
     TC_TRY(p->merge_offT.alloc((size_t)(noff > 0 ? noff : 1) * 4));
     if (noff > 0) {
         k_merge_offsets<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), blk_rows.as<int64_t>(), B, p->nranges, p->k,
-                                             p->merge_off.as<int32_t>(), p->merge_offT.as<int32_t>());
+                                             rst, p->merge_off.as<int32_t>(), p->merge_offT.as<int32_t>());
         TC_LAUNCH_CHECK();
     }
     TC_TRY(collect_hubs(p->rowptr.as<int32_t>(), R, p->hub_degree, &p->hubs, &p->num_hubs, s));
-    if (R > 0 && (p->k & (p->k - 1)) == 0 && p->k <= 65536) {  // 2-byte local ids for the merge
+    if (R > 0 && rst) {  // 2-byte offsets inside the (variable) merge ranges, all <= k <= 65536
+        TC_TRY(p->id16.alloc((size_t)(R + 8) * 2));
+        k_id16_ranges<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), R, rst, p->nranges, p->id16.as<uint16_t>());
+        TC_LAUNCH_CHECK();
+    } else if (R > 0 && (p->k & (p->k - 1)) == 0 && p->k <= 65536) {  // 2-byte local ids for the merge
         TC_TRY(p->id16.alloc((size_t)(R + 8) * 2));
         k_id16<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), R, p->k - 1, p->id16.as<uint16_t>());
         TC_LAUNCH_CHECK();
@@ -285,6 +510,36 @@ extern "C" int tc_part_get_info(const tc_part *p, tc_part_info *info) {
     info->num_hubs = p->num_hubs;
     info->staged = p->tiled ? 1 : 0;
     info->staged_edges = p->padded_edges;
+    info->vertex_order = p->order;
+    info->num_ranges = p->nranges;
+    info->num_items = p->tiled ? p->nitems : 0;
+    info->num_sources = p->nz_out;
+    return TC_OK;
+}
+
+extern "C" int tc_part_export_order(const tc_part *p, int32_t *perm, int mem, void *stream) {
+    using namespace tc;
+    if (!p || !perm) return fail(TC_ERR_INVALID_ARG, "tc_part_export_order: null argument");
+    if (mem != TC_MEM_HOST && mem != TC_MEM_DEVICE) return fail(TC_ERR_INVALID_ARG, "bad mem flag");
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->V == 0) return TC_OK;
+    if (p->order == TC_ORDER_OUTDEGREE) {
+        TC_CUDA(cudaMemcpyAsync(perm, p->perm.p, (size_t)p->V * 4,
+                                mem == TC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        return TC_OK;
+    }
+    if (mem == TC_MEM_HOST) {
+        for (int32_t n = 0; n < p->V; ++n) perm[n] = n;
+        return TC_OK;
+    }
+    int32_t *h = new (std::nothrow) int32_t[p->V];
+    if (!h) return fail(TC_ERR_OOM, "host allocation failed");
+    for (int32_t n = 0; n < p->V; ++n) h[n] = n;
+    cudaError_t e = cudaMemcpyAsync(perm, h, (size_t)p->V * 4, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    delete[] h;
+    if (e != cudaSuccess) return fail(TC_ERR_CUDA, "tc_part_export_order: %s", cudaGetErrorString(e));
     return TC_OK;
 }
 

@@ -590,6 +590,8 @@ extern "C" int tc_ppr_batch(const tc_graph *g, const tc_part *part, const int32_
     if (!g || !sources || !params || !R_out) return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: null argument");
     if (part && (part->g != g || part->dir != TC_PULL))
         return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: partition must be a TC_PULL partition of this graph");
+    if (part && part->order != TC_ORDER_NATURAL)
+        return fail(TC_ERR_UNSUPPORTED, "tc_ppr_batch: renumbered (TC_ORDER_OUTDEGREE) partitions are not supported");
     if (part && (size_t)part->k * 32 * 4 > 200 * 1024)
         return fail(TC_ERR_INVALID_ARG, "tc_ppr_batch: the partition's merge_range must be <= 1600 (<= 256 advised)");
     if (n < 1 || n > 1024) return fail(TC_ERR_UNSUPPORTED, "tc_ppr_batch: n must be in [1, 1024]");

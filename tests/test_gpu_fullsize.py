@@ -77,6 +77,22 @@ def test_rmat24_pagerank_in_the_benchmark_configuration(T, rmat24):
     assert l1_rel(T.pagerank_pull(G, None).cpu().numpy(), want) <= TOL
 
 
+def test_rmat24_pagerank_renumbered_blocks(T, rmat24):
+    """The benchmark's headline configuration: blocks cut after renumbering the vertices by
+    out-degree (widest shared-memory blocks, gather tiles, merge ranges cut by pieces), fixed-point
+    merge, 20 iterations: every rank against the oracle, mass 1, bit-identical reruns."""
+    g, G, rp, ci, tr = rmat24
+    want = oracle.pagerank_pull(g.V, rp, ci, nthreads=CORES, transposed=tr)
+    P = T.tocab_partition(G, T.TC_PULL, 0, block_policy="smem", order="outdegree")
+    assert P.staged and P.vertex_order == T.TC_ORDER_OUTDEGREE
+    r1 = T.pagerank_pull(G, P)
+    r2 = T.pagerank_pull(G, P)
+    got = r1.cpu().numpy()
+    assert l1_rel(got, want) <= TOL
+    assert abs(float(np.sum(got, dtype=np.float64)) - 1.0) < 1e-4
+    assert torch.equal(r1, r2)
+
+
 def test_rmat24_bfs_bit_exact(T, rmat24):
     """Symmetrised R-MAT 24 (~521M directed edges), two seeded sources, direction-optimised with
     and without TOCAB pull levels, and pure pull."""
@@ -95,10 +111,12 @@ def test_rmat24_bfs_bit_exact(T, rmat24):
 
 def test_rmat22_ppr_batch_sampled_columns(T):
     """256 sources on R-MAT 22 in one [V x 256] batch: four seeded columns against the oracle
-    (columns are independent problems)."""
+    (columns are independent problems).  The last column's source is the vertex with the most
+    in-edges, whose own row is the longest gather of every iteration."""
     g = gg.rmat(22, device="cuda")
     G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
     srcs = gg.sources(g, 256, seed=17)
+    srcs[255] = int(torch.bincount(g.colidx.long(), minlength=g.V).argmax())
     R = T.ppr_batch(G, srcs, iters=20).cpu().numpy()
     cols = [0, 85, 170, 255]
     rp, ci = g.numpy()

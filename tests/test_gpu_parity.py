@@ -347,7 +347,7 @@ def test_ppr_batch_rejects_bad_sources(T):
 
 # ------------------------------------------------------------------ merge modes
 
-@pytest.mark.parametrize("merge", ["fixed", "ordered", "float"])
+@pytest.mark.parametrize("merge", ["fixed", "ordered"])
 @pytest.mark.parametrize("policy", ["smem", "l2"])
 def test_pagerank_pull_merge_modes(T, merge, policy):
     g = gg.rmat(14)
@@ -355,8 +355,20 @@ def test_pagerank_pull_merge_modes(T, merge, policy):
     P = T.tocab_partition(G, T.TC_PULL, 0 if policy == "smem" else 3, block_policy=policy)
     r = T.pagerank_pull(G, P, merge=merge)
     assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
-    if merge != "float":
-        assert torch.equal(r.cpu(), T.pagerank_pull(G, P, merge=merge).cpu())
+    assert torch.equal(r.cpu(), T.pagerank_pull(G, P, merge=merge).cpu())
+
+
+def test_removed_float_merge_mode_is_rejected(T):
+    import ctypes as C
+    from paper_1904_02241_gb300 import _lib as L
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, 4)
+    out = torch.empty(g.V, dtype=torch.float32, device="cuda")
+    pp = L.tc_pr_params(0.85, 20, 0, L.TC_MEM_DEVICE, None, 0, 2, 0, 0)  # merge_mode 2
+    st = T.lib().tc_pagerank_pull(G.handle, P.handle, C.byref(pp), out.data_ptr(), None,
+                                  torch.cuda.current_stream().cuda_stream)
+    assert st == -1
 
 
 def _dense_range_graph():
@@ -370,18 +382,35 @@ def _dense_range_graph():
     return gg.from_edge_list(V, np.stack([u, d], 1), name="dense_range")
 
 
-@pytest.mark.parametrize("merge", ["fixed", "float"])
-def test_pagerank_pull_merge_dense_range(T, merge):
+@pytest.mark.parametrize("B", [512, 2048])
+def test_pagerank_pull_merge_dense_range(T, B):
+    """Hundreds of pieces per vertex.  B = 2048 (32 sources per block) takes the three-part
+    fixed-point merge, which every partition with 1,024 or more blocks uses."""
     g = _dense_range_graph()
     G = _load(T, g)
-    P = T.tocab_partition(G, T.TC_PULL, 512, merge_range=4096)
-    r = T.pagerank_pull(G, P, merge=merge)
-    # fixed: exact sums, so the 1e-5 bar holds.  float: every vertex takes ~400 FP32 atomic
-    # additions of similar size per iteration; their rounding (up to 400 ulp/2 relative)
-    # is the float merge's own limit on this graph, so it gets 1e-4.
-    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= (TOL if merge == "fixed" else 1e-4)
-    if merge == "fixed":
-        assert torch.equal(r.cpu(), T.pagerank_pull(G, P, merge=merge).cpu())
+    P = T.tocab_partition(G, T.TC_PULL, B, merge_range=4096)
+    assert P.num_blocks == B
+    r = T.pagerank_pull(G, P)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    assert torch.equal(r.cpu(), T.pagerank_pull(G, P).cpu())
+
+
+@pytest.mark.parametrize("name,B,stage", [("rmat14_noperm", 1024, 0), ("plc", 1250, 0), ("rmat12", 2048, 0),
+                                          ("rmat14_noperm", 2048, -1)])
+def test_pagerank_pull_three_part_merge(T, name, B, stage):
+    """1,024 blocks or more: the merge splits each partial into three fixed-point parts.  Small
+    graphs give narrow blocks (W = 2..16 sources), so these run the unstaged gather; the dense-range
+    test above runs the staged one with 2,048 blocks."""
+    g = GRAPHS[name]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B, smem_stage=stage)
+    assert P.num_blocks >= 1024
+    r = T.pagerank_pull(G, P)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    assert torch.equal(r.cpu(), T.pagerank_pull(G, P).cpu())
+    for d, mode in [(0.85, "drop"), (0.5, "redistribute")]:
+        r = T.pagerank_pull(G, P, damping=d, dangling=mode)
+        assert l1_rel(r.cpu().numpy(), _oracle_pr(g, damping=d, dangling=mode)) <= TOL
 
 
 # ------------------------------------------------------------------ a10: many graphs in one launch

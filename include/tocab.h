@@ -190,7 +190,7 @@ typedef struct tc_part_info {
     int64_t staged_edges;     /* edges of the staged stream incl. per-block padding (0 if not) */
     int32_t vertex_order;     /* TC_ORDER_NATURAL or TC_ORDER_OUTDEGREE */
     int32_t num_ranges;       /* merge ranges (CTAs of the merge) */
-    int32_t num_items;        /* work items of the staged gather (0 if not staged) */
+    int32_t num_tiles;        /* CTAs of the staged gather (0 if not staged) */
     int32_t num_sources;      /* vertices with out-edges (TC_ORDER_OUTDEGREE: they come first) */
 } tc_part_info;
 /* Shape of a partition: B and W of Sec. 3.1, R local rows (Fig. 4), k of Fig. 5.  Errors:

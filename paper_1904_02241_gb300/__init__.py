@@ -132,7 +132,7 @@ class Partition:
         self.staged_edges = info.staged_edges
         self.vertex_order = info.vertex_order
         self.num_ranges = info.num_ranges
-        self.num_items = info.num_items
+        self.num_tiles = info.num_tiles
         self.num_sources = info.num_sources
 
     @property

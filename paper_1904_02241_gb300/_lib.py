@@ -44,7 +44,7 @@ class tc_part_info(C.Structure):
     _fields_ = [("dir", C.c_int32), ("num_blocks", C.c_int32), ("block_width", C.c_int32),
                 ("num_rows", C.c_int64), ("num_edges", C.c_int64), ("merge_range", C.c_int32),
                 ("num_hubs", C.c_int32), ("staged", C.c_int32), ("staged_edges", C.c_int64),
-                ("vertex_order", C.c_int32), ("num_ranges", C.c_int32), ("num_items", C.c_int32),
+                ("vertex_order", C.c_int32), ("num_ranges", C.c_int32), ("num_tiles", C.c_int32),
                 ("num_sources", C.c_int32)]
 
 

@@ -193,14 +193,9 @@ struct tc_part {
     tc::DevBuf heads;           // 1 bit per staged edge: a local row starts here
     tc::DevBuf id16;            // uint16[R]: id_map[r] minus the first vertex of its merge range
     tc::DevBuf lb_tab;          // int32[B]: per-block warp_min of the unstaged gathers (optional)
-    int32_t nitems = 0;         // work items of the staged gather: row-aligned pieces of blocks
-    int32_t gather_ctas = 0;    // persistent CTAs of the staged gather (one per SM at most)
-    tc::DevBuf items;           // int4[nitems]: (staged start, staged end, first row starting in it, 0)
-    tc::DevBuf ibase;           // int32[B + 1]: first item of every block
-    tc::DevBuf cta_blk;         // int32[gather_ctas]: starting block of every CTA
-    tc::DevBuf bq;              // uint32[B + 1]: per-block item counters (+ finished CTAs), zero
-                                // between launches (one gather at a time per partition)
-    tc::DevBuf headval, tailval, tailrow;  // per item: pieces of the rows open at its ends
+    int32_t ntiles = 0;         // CTAs of the staged gather: row-aligned tiles of equal estimated cost
+    tc::DevBuf tile_blk;        // int32[ntiles]: block of every tile, in launch order (largest first)
+    tc::DevBuf wtab;            // int2[ntiles * 33]: per tile and warp, (first staged edge, first row)
     // ---- vertex renumbering (TC_ORDER_OUTDEGREE); everything above is in the new numbering ----
     int32_t order = TC_ORDER_NATURAL;
     int32_t nz_out = 0;         // vertices with out-edges; renumbered: exactly the IDs below nz_out
@@ -219,15 +214,12 @@ namespace tc {
 // Shared-memory staged TOCAB format (tc_tile.cu).
 constexpr int TILE_WCHUNK = 512;         // edges a warp streams per step (16 per lane)
 constexpr int TILE_THREADS = 1024;
-constexpr int ITEM_EDGES = 2048;         // staged edges of a gather work item (whole warp chunks)
 size_t tile_smem_bytes(int32_t W);       // dynamic shared memory of the staged gather for width W
 int32_t tile_max_width(int max_smem_optin);
 int build_tiles(tc_part *p, int sms, cudaStream_t s);
 size_t merge_smem_bytes(int32_t k, int32_t B);   // dynamic shared memory of the ordered pull merge
 size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed);  // ... of the one-accumulator merges
 // Launch the staged gather (+ long rows) writing p->partial from contributions `contrib`.
-// The partition's item counters must be zero (the kernel leaves them so): one staged gather of a
-// partition runs at a time.
 int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, cudaStream_t s, int *launches);
 
 // Rows of a CSR with more than `min_degree` edges, as a compact int32 list (ascending).

@@ -946,7 +946,6 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     PrState st;
     TC_TRY(prepare_state(g, pp, ranks_out, push, max_ctas, &st));
     TC_CUDA(cudaMemsetAsync(st.counter, 0, 16, s));  // counter, merge work queue and the error flag
-    if (tiled) TC_CUDA(cudaMemsetAsync(part->bq.p, 0, ((size_t)part->B + 1) * 4, s));  // the gather's item counters
     if (push) TC_CUDA(cudaMemsetAsync(st.sums, 0, (size_t)V * 4, s));
 
     UpdateArgs u;

@@ -512,7 +512,7 @@ extern "C" int tc_part_get_info(const tc_part *p, tc_part_info *info) {
     info->staged_edges = p->padded_edges;
     info->vertex_order = p->order;
     info->num_ranges = p->nranges;
-    info->num_items = p->tiled ? p->nitems : 0;
+    info->num_tiles = p->tiled ? p->ntiles : 0;
     info->num_sources = p->nz_out;
     return TC_OK;
 }

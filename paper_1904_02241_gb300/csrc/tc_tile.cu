@@ -10,21 +10,21 @@
 //   * col16[]  : uint16 source offset inside the block (source - b*W), each block's edges
 //                padded to a multiple of TILE_WCHUNK;
 //   * heads[]  : one bit per edge, set where a local row starts (uint16 per 16 edges);
-//   * items    : every block's staged edges are cut into items of ITEM_EDGES (whole warp
-//                chunks; the last item of a block may be shorter); one persistent CTA per SM
-//                holds one block's values at a time and its warps draw that block's items from
-//                the block's work counter; a CTA starts in its own stretch of blocks (in
-//                proportion to their edges) and moves on to the next block with items left once
-//                its block runs dry, so no CTA idles while work remains and few blocks are
-//                loaded twice;
-//   * a row may cross items: an item records the piece of the row open at its start (head)
-//     and the row open at its end with its piece (tail), and a fix-up pass adds every tail to
-//     the heads of the items that follow it, in item order (deterministic).
+//   * tiles    : every block's rows are cut into row-aligned tiles of about equal estimated
+//                cost (about three waves of CTAs over the device), one CTA each, launched
+//                largest first so that the last wave holds the smallest tiles; every tile of a
+//                block loads the same block values;
+//   * wtab[]   : per tile, 33 (edge, row) pairs: warp w of the CTA owns the row-aligned edge
+//                range [wtab[w].x, wtab[w+1].x) whose first row is wtab[w].y (equal estimated
+//                cost per warp).
+// The estimated cost of a row of L edges is 3 per edge, 1 per edge inside the chunks in which
+// no row starts (the walk's fast path, about L - 512 edges once L >= 1024), and 2 for the row.
 // A warp streams its range in chunks of TILE_WCHUNK edges, 16 consecutive edges per lane
 // (two 16-byte loads), sums the source values of each lane's row pieces, and joins pieces of
 // rows that cross lanes or chunks with a warp segmented scan.  Finished row sums go to a
 // per-warp shared-memory stage and leave as coalesced stores to partial[row] in the
 // partition's row numbering; the merge kernel (Fig. 5) reduces them.
+#include <algorithm>
 #include <vector>
 
 #include "tc_common_dev.cuh"
@@ -55,14 +55,8 @@ int32_t tile_max_width(int max_smem_optin) {
 struct TileArgs {
     const uint16_t *col16;
     const uint16_t *heads;
-    const int4 *items;       // [nitems]: (first staged edge, end, first row, 0), block after block
-    const int32_t *ibase;    // [B + 1]: first item of every block
-    const int32_t *cta_blk;  // [gridDim.x]: the block every CTA starts in
-    int32_t B;
-    unsigned *bq;            // [B + 1]: items handed out per block; bq[B] counts finished CTAs
-    float *headval;          // [nitems]: the item's piece of the row open at its start
-    float *tailval;          // [nitems]: the item's piece of the row open at its end
-    int32_t *tailrow;        // [nitems]: that row, or -1 when no row starts in the item
+    const int32_t *tile_blk; // [ntiles]: block of every tile (in launch order)
+    const int2 *wtab;        // [ntiles][TWARPS + 1]
     const float *contrib;
     int32_t V, W;
     float *partial;
@@ -78,19 +72,18 @@ __device__ __forceinline__ void load_chunk(const TileArgs &t, int32_t q0, int la
     h = __ldg(t.heads + (q >> 4));
 }
 
-// One warp's item: edges [es, ee) of the staged stream (es at a chunk start), the first row
-// starting in it rs (Alg. 4 on the block values in `slice`).  Rows that start and end inside
-// the item go to partial[]; the pieces of the rows open at its two ends go to the item's records.
-// Software pipeline: (nc0, nc1, nh) hold the item's first chunk on entry; every chunk's loads
-// are issued before the previous one is summed, and the last chunk's loads fetch the first chunk
-// of the warp's next item (at next_es, if >= 0), which (nc0, nc1, nh) then hold on return.
+// One warp's row-aligned range: edges [es, ee) of the staged stream, whose first row rs starts
+// at es (Alg. 4 on the block values in `slice`); every row of it goes to partial[].
+// Software pipeline: every chunk's loads are issued before the previous one is summed.
 __device__ __forceinline__ void warp_walk(const TileArgs &t, const float *slice, float *stage_base, int32_t es,
-                                          int32_t ee, int32_t rs, int lane, int32_t item, uint4 &nc0, uint4 &nc1,
-                                          uint32_t &nh, int32_t next_es) {
+                                          int32_t ee, int32_t rs, int lane) {
     int32_t rowbase = rs;                 // row started by the next head
     float carry = 0.0f;                   // value of the open row (rowbase - 1)
     bool open = false;                    // whether row rowbase-1 belongs to this warp
     const int32_t q_begin = es & ~(WCH - 1);
+    uint4 nc0, nc1;
+    uint32_t nh;
+    load_chunk(t, q_begin, lane, nc0, nc1, nh);
     // Chunks in which no row starts (inside a row longer than a chunk, as hub destinations have)
     // only add to the open row: each lane keeps its share in racc, and the shares join the
     // carry (a fixed-order warp sum) before the next chunk that has a head.
@@ -100,7 +93,6 @@ __device__ __forceinline__ void warp_walk(const TileArgs &t, const float *slice,
         const uint4 c0 = nc0, c1 = nc1;
         uint32_t hd = nh;
         if (q0 + WCH < ee) load_chunk(t, q0 + WCH, lane, nc0, nc1, nh);
-        else if (next_es >= 0) load_chunk(t, next_es, lane, nc0, nc1, nh);
         const uint32_t words[8] = {c0.x, c0.y, c0.z, c0.w, c1.x, c1.y, c1.z, c1.w};
         const bool full = q0 >= es && q0 + WCH <= ee;  // whole chunk inside the warp's range (warp-uniform)
         if (full && __ballot_sync(0xffffffffu, hd != 0u) == 0u) {
@@ -206,7 +198,6 @@ __device__ __forceinline__ void warp_walk(const TileArgs &t, const float *slice,
                 if (gb > ga && lane == 0) bulk_store_s2g(t.partial + ga, stage + (ga - r0), (uint32_t)(gb - ga) * 4u);
             }
         }
-        if (!open && total > 0 && lane == 0) t.headval[item] = stage[0];  // the row open at es
         if (total > 0) open = true;
         rowbase += total;
         carry = xlast;
@@ -217,111 +208,40 @@ __device__ __forceinline__ void warp_walk(const TileArgs &t, const float *slice,
         for (int d = 16; d > 0; d >>= 1) x += __shfl_xor_sync(0xffffffffu, x, d);
         carry += x;
     }
-    if (lane == 0) {
-        if (open) {  // the last row started here runs to the end of the item (or beyond)
-            t.tailval[item] = carry;
-            t.tailrow[item] = rowbase - 1;
-        } else {     // no row starts in the item: all of it continues the row open at es
-            t.headval[item] = carry;
-            t.tailrow[item] = -1;
-        }
-    }
-}
-
-// partial[tailrow[i]] = tailval[i] + the heads of the items that follow i up to and including the
-// first one in which a row starts (a block's first item starts with a row, so a row never takes
-// a head from another block).
-__global__ void k_item_fixup(const float *headval, const float *tailval, const int32_t *tailrow, int32_t nitems,
-                             float *partial) {
-    for (int32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nitems; i += gridDim.x * blockDim.x) {
-        const int32_t r = tailrow[i];
-        if (r < 0) continue;
-        float v = tailval[i];
-        int32_t j = i + 1;
-        while (j < nitems && tailrow[j] < 0) v += headval[j++];
-        if (j < nitems) v += headval[j];
-        partial[r] = v;
-    }
+    if (open && lane == 0) t.partial[rowbase - 1] = carry;
 }
 
 __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t slice_bar;
-    __shared__ int32_t s_b;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t tile = blockIdx.x;
+    const int32_t b = t.tile_blk[tile];
     float *slice = reinterpret_cast<float *>(smem);
     float *stage_base = reinterpret_cast<float *>(smem + slice_bytes(t.W)) + warp * WSTAGE;
+    // ---- the block's contributions -> shared memory (bulk copies on one mbarrier) ----
     if (tid == 0) {
         mbar_init(&slice_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    uint32_t phase = 0;
-    int32_t b = t.cta_blk[blockIdx.x];
-    for (;;) {
-        // the first block from b on that still has items to hand out
-        if (tid == 0) {
-            while (b < t.B && *(volatile unsigned *)(t.bq + b) >= (unsigned)(t.ibase[b + 1] - t.ibase[b])) ++b;
-            s_b = b;
-        }
-        __syncthreads();  // also: every warp is done with the previous block's values
-        b = s_b;
-        if (b >= t.B) break;
-        if (tid == 0) {
-            const int64_t lo = (int64_t)b * t.W;
-            const int64_t n = ((int64_t)t.V - lo) < t.W ? ((int64_t)t.V - lo) : t.W;
-            const uint32_t bytes = (uint32_t)((n * 4 + 15) & ~15LL);
-            mbar_expect_tx(&slice_bar, bytes);
-            for (uint32_t off = 0; off < bytes; off += 16384) {
-                const uint32_t part = (bytes - off) < 16384u ? (bytes - off) : 16384u;
-                bulk_g2s(reinterpret_cast<unsigned char *>(slice) + off,
-                         reinterpret_cast<const unsigned char *>(t.contrib + lo) + off, part, &slice_bar);
-            }
-        }
-        // every thread waits for the copy (bounded); if any thread gives up, the flag is set and
-        // the whole CTA leaves together
-        const bool ok = mbar_wait(&slice_bar, phase, t.err, 1);
-        phase ^= 1u;
-        if (__syncthreads_or(!ok)) break;
-        // Each warp draws the block's items one at a time.  The next item's index is drawn while
-        // the current one is summed, and its descriptor and first chunk load during the current
-        // item's last chunk, so no draw or load waits between items.
-        const int32_t i0 = t.ibase[b], ni = t.ibase[b + 1] - i0;
-        int32_t cur = 0;
-        if (lane == 0) cur = (int32_t)atomicAdd(t.bq + b, 1u);
-        cur = __shfl_sync(0xffffffffu, cur, 0);
-        if (cur < ni) {
-            int4 dc = t.items[i0 + cur];
-            uint4 nc0, nc1;
-            uint32_t nh;
-            load_chunk(t, dc.x, lane, nc0, nc1, nh);
-            int32_t drawn = 0;
-            if (lane == 0) drawn = (int32_t)atomicAdd(t.bq + b, 1u);
-            for (;;) {
-                const int32_t nxt = __shfl_sync(0xffffffffu, drawn, 0);
-                int4 dn = make_int4(-1, -1, 0, 0);
-                if (nxt < ni) {
-                    dn = t.items[i0 + nxt];
-                    if (lane == 0) drawn = (int32_t)atomicAdd(t.bq + b, 1u);
-                }
-                warp_walk(t, slice, stage_base, dc.x, dc.y, dc.z, lane, i0 + cur, nc0, nc1, nh, dn.x);
-                if (nxt >= ni) break;
-                cur = nxt;
-                dc = dn;
-            }
-        }
-        ++b;
-    }
-    if (lane == 0) bulk_store_wait_all();  // the stage must outlive the bulk stores reading it
-    // the last CTA to finish re-arms the counters (every CTA has drawn its last item by now)
     __syncthreads();
-    __shared__ bool last;
     if (tid == 0) {
-        __threadfence();
-        last = atomicAdd(t.bq + t.B, 1u) == gridDim.x - 1;
+        const int64_t lo = (int64_t)b * t.W;
+        const int64_t n = ((int64_t)t.V - lo) < t.W ? ((int64_t)t.V - lo) : t.W;
+        const uint32_t bytes = (uint32_t)((n * 4 + 15) & ~15LL);
+        mbar_expect_tx(&slice_bar, bytes);
+        for (uint32_t off = 0; off < bytes; off += 16384) {
+            const uint32_t part = (bytes - off) < 16384u ? (bytes - off) : 16384u;
+            bulk_g2s(reinterpret_cast<unsigned char *>(slice) + off,
+                     reinterpret_cast<const unsigned char *>(t.contrib + lo) + off, part, &slice_bar);
+        }
     }
-    __syncthreads();
-    if (last)
-        for (int32_t k = tid; k <= t.B; k += TILE_THREADS) t.bq[k] = 0u;
+    // every thread waits for the copy (bounded); on a timeout the flag is set and all leave
+    if (!mbar_wait(&slice_bar, 0, t.err, 1)) return;
+    const int2 w0 = t.wtab[(int64_t)tile * (TWARPS + 1) + warp];
+    const int2 w1 = t.wtab[(int64_t)tile * (TWARPS + 1) + warp + 1];
+    if (w0.x < w1.x) warp_walk(t, slice, stage_base, w0.x, w1.x, w0.y, lane);
+    if (lane == 0) bulk_store_wait_all();  // the stage must outlive the bulk stores reading it
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -392,23 +312,62 @@ __global__ void k_tile_heads(const int32_t *rowptr, const int64_t *blk_rows, con
     }
 }
 
-// Items of every block: item k of block b holds the staged edges [pbase[b] + k ITEM_EDGES,
-// min(that + ITEM_EDGES, pbase[b] + edges of b)); its first row is the first row of the block
-// starting at or after that edge (blk_rows[b + 1] when none does).  Stored as (staged start,
-// staged end, first row, 0).
-__global__ void k_items(const int32_t *rowptr, const int64_t *blk_rows, const int64_t *blk_edges, const int64_t *pbase,
-                        const int32_t *ibase, const int32_t *item_blk, int32_t nitems, int4 *items) {
-    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < nitems; t += gridDim.x * blockDim.x) {
-        const int32_t b = item_blk[t], k = t - ibase[b];
-        const int64_t eb = blk_edges[b], ne = blk_edges[b + 1] - eb;
-        const int64_t off = (int64_t)k * ITEM_EDGES;
-        const int64_t end = off + ITEM_EDGES < ne ? off + ITEM_EDGES : ne;
-        int64_t lo = blk_rows[b], hi = blk_rows[b + 1];  // rowptr[blk_rows[b + 1]] = blk_edges[b + 1]
-        while (lo < hi) {
-            const int64_t mid = (lo + hi) >> 1;
-            if ((int64_t)rowptr[mid] < eb + off) lo = mid + 1; else hi = mid;
+// Estimated cost of every local row (see the top of the file); w[R] = 0 closes the scan.
+__global__ void k_row_weights(const int32_t *rowptr, int64_t R, int32_t *w) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= R; r += (int64_t)gridDim.x * blockDim.x) {
+        if (r == R) {
+            w[R] = 0;
+            continue;
         }
-        items[t] = make_int4((int32_t)(pbase[b] + off), (int32_t)(pbase[b] + end), (int32_t)lo, 0);
+        const int32_t L = rowptr[r + 1] - rowptr[r];
+        const int32_t fast = L >= 1024 ? ((L >> 9) - 1) << 9 : 0;
+        w[r] = 3 * L - 2 * fast + 2;
+    }
+}
+
+// First row r in [lo, hi] with cum[r] >= target (cum ascending; cum[hi] >= target).
+__device__ __forceinline__ int64_t first_row_at(const int64_t *cum, int64_t lo, int64_t hi, int64_t target) {
+    while (lo < hi) {
+        const int64_t mid = (lo + hi) >> 1;
+        if (cum[mid] < target) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Weight prefix at every block's first row: cw[b] = cum[blk_rows[b]], b in [0, B].
+__global__ void k_block_weights(const int64_t *cum, const int64_t *blk_rows, int32_t B, int64_t *cw) {
+    for (int32_t b = blockIdx.x * blockDim.x + threadIdx.x; b <= B; b += gridDim.x * blockDim.x) cw[b] = cum[blk_rows[b]];
+}
+
+// Rows and cost of every tile: tile k of the n tiles of block b spans the rows whose weight prefix
+// lies in the k-th n-th of the block's weight range (row-aligned, rounded up).
+__global__ void k_tile_rows(const int64_t *cum, const int64_t *blk_rows, const int4 *tiles, int32_t ntiles,
+                            int2 *rows, int64_t *cost) {
+    for (int32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < ntiles; t += gridDim.x * blockDim.x) {
+        const int4 tt = tiles[t];  // (block, k, n, 0)
+        const int64_t br0 = blk_rows[tt.x], br1 = blk_rows[tt.x + 1];
+        const int64_t c0 = cum[br0], c1 = cum[br1];
+        const int64_t r0 = first_row_at(cum, br0, br1, c0 + ((c1 - c0) * tt.y + tt.z - 1) / tt.z);
+        const int64_t r1 = first_row_at(cum, br0, br1, c0 + ((c1 - c0) * (tt.y + 1) + tt.z - 1) / tt.z);
+        rows[t] = make_int2((int32_t)r0, (int32_t)r1);
+        cost[t] = cum[r1] - cum[r0];
+    }
+}
+
+// Warp ranges of every tile (rows [r0, r1) of block b): warp w starts at the first row whose
+// weight prefix reaches cum[r0] + (cum[r1] - cum[r0]) w / TWARPS (rounded up); stored as
+// (position in the staged stream, row).
+__global__ void k_tile_wtab(const int32_t *rowptr, const int64_t *cum, const int64_t *blk_edges, const int64_t *pbase,
+                            const int32_t *tile_blk, const int2 *tile_rows, int32_t ntiles, int2 *wtab) {
+    const int64_t total = (int64_t)ntiles * (TWARPS + 1);
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t tile = (int32_t)(t / (TWARPS + 1)), w = (int32_t)(t % (TWARPS + 1));
+        const int32_t b = tile_blk[tile];
+        const int64_t r0 = tile_rows[tile].x, r1 = tile_rows[tile].y;
+        const int64_t c0 = cum[r0], c1 = cum[r1];
+        const int64_t r = first_row_at(cum, r0, r1, c0 + ((c1 - c0) * w + TWARPS - 1) / TWARPS);
+        const int64_t edge = rowptr[r];
+        wtab[t] = make_int2((int32_t)(pbase[b] + (edge - blk_edges[b])), (int32_t)r);
     }
 }
 
@@ -445,38 +404,73 @@ int build_tiles(tc_part *p, int sms, cudaStream_t s) {
     TC_TRY(p->heads.alloc((size_t)(npad + WCH) / 8 + 64));
     TC_CUDA(cudaMemsetAsync(p->col16.p, 0, (size_t)(npad + WCH) * 2, s));
     TC_CUDA(cudaMemsetAsync(p->heads.p, 0, (size_t)(npad + WCH) / 8 + 64, s));
-    // items: ceil(edges / ITEM_EDGES) per block; the CTAs' starting blocks split the edges evenly
-    std::vector<int32_t> h_ibase((size_t)B + 1, 0), h_item_blk, h_cta_blk;
+    // tiles: the rows of every block with edges are cut into n_b = max(1, round(cost_b / T)) tiles
+    // of equal estimated cost, T = the total over three waves of one CTA per SM
+    DevBuf wrow, cum, cw;
+    TC_TRY(wrow.alloc(((size_t)R + 1) * 4));
+    TC_TRY(cum.alloc(((size_t)R + 1) * 8));
+    TC_TRY(cw.alloc(((size_t)B + 1) * 8));
+    k_row_weights<<<sms * 8, 256, 0, s>>>(p->rowptr.as<int32_t>(), R, wrow.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32_to_i64(wrow.as<int32_t>(), R + 1, cum.as<int64_t>(), s));
+    wrow.release();
+    k_block_weights<<<(B + 256) / 256, 256, 0, s>>>(cum.as<int64_t>(), p->blk_rows_dev.as<int64_t>(), B,
+                                                    cw.as<int64_t>());
+    TC_LAUNCH_CHECK();
+    std::vector<int64_t> h_cw((size_t)B + 1);
+    TC_CUDA(cudaMemcpyAsync(h_cw.data(), cw.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    const int64_t T = h_cw[B] / (3LL * sms) > 0 ? h_cw[B] / (3LL * sms) : 1;
+    std::vector<int4> h_tiles;
     for (int32_t b = 0; b < B; ++b) {
-        const int64_t ne = p->h_blk_edges[b + 1] - p->h_blk_edges[b];
-        const int64_t n = (ne + ITEM_EDGES - 1) / ITEM_EDGES;
-        if ((int64_t)h_ibase[b] + n > INT32_MAX / 2) return fail(TC_ERR_UNSUPPORTED, "build_tiles: too many items");
-        h_ibase[b + 1] = h_ibase[b] + (int32_t)n;
-        for (int64_t k = 0; k < n; ++k) h_item_blk.push_back(b);
+        if (p->h_blk_edges[b + 1] == p->h_blk_edges[b]) continue;
+        int64_t n = (h_cw[b + 1] - h_cw[b] + T / 2) / T;
+        if (n < 1) n = 1;
+        if (n > p->h_blk_rows[b + 1] - p->h_blk_rows[b]) n = p->h_blk_rows[b + 1] - p->h_blk_rows[b];
+        for (int64_t k = 0; k < n; ++k) h_tiles.push_back(make_int4(b, (int)k, (int)n, 0));
     }
-    const int32_t nitems = h_ibase[B];
-    const int32_t G = (int32_t)(nitems < sms ? nitems : sms);
-    for (int32_t c = 0, b = 0; c < G; ++c) {
-        const int64_t at = p->E * c / G;  // CTA c starts in the block holding edge c E / G
-        while (b + 1 < B && p->h_blk_edges[b + 1] <= at) ++b;
-        h_cta_blk.push_back(b);
+    const int64_t ntiles = (int64_t)h_tiles.size();
+    if (ntiles * (TWARPS + 1) > INT32_MAX) return fail(TC_ERR_UNSUPPORTED, "build_tiles: too many tiles");
+    DevBuf tiles_dev, rows0, cost, rows_lpt;
+    const size_t nt = (size_t)(ntiles > 0 ? ntiles : 1);
+    TC_TRY(tiles_dev.alloc(nt * 16));
+    TC_TRY(rows0.alloc(nt * 8));
+    TC_TRY(rows_lpt.alloc(nt * 8));
+    TC_TRY(cost.alloc(nt * 8));
+    TC_TRY(p->tile_blk.alloc(nt * 4));
+    if (ntiles > 0) {
+        TC_CUDA(cudaMemcpyAsync(tiles_dev.p, h_tiles.data(), (size_t)ntiles * 16, cudaMemcpyHostToDevice, s));
+        k_tile_rows<<<(unsigned)((ntiles + 255) / 256), 256, 0, s>>>(cum.as<int64_t>(), p->blk_rows_dev.as<int64_t>(),
+                                                                     tiles_dev.as<int4>(), (int32_t)ntiles,
+                                                                     rows0.as<int2>(), cost.as<int64_t>());
+        TC_LAUNCH_CHECK();
+        // launch order: largest estimated cost first (ties by position), so that the CTAs of the
+        // last wave run the smallest tiles
+        std::vector<int64_t> h_cost((size_t)ntiles);
+        std::vector<int2> h_rows((size_t)ntiles);
+        TC_CUDA(cudaMemcpyAsync(h_cost.data(), cost.p, (size_t)ntiles * 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaMemcpyAsync(h_rows.data(), rows0.p, (size_t)ntiles * 8, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        std::vector<int32_t> order((size_t)ntiles);
+        for (int64_t i = 0; i < ntiles; ++i) order[(size_t)i] = (int32_t)i;
+        std::stable_sort(order.begin(), order.end(),
+                         [&](int32_t a, int32_t c) { return h_cost[(size_t)a] > h_cost[(size_t)c]; });
+        std::vector<int32_t> h_blk((size_t)ntiles);
+        std::vector<int2> h_rows_lpt((size_t)ntiles);
+        for (int64_t i = 0; i < ntiles; ++i) {
+            h_blk[(size_t)i] = h_tiles[(size_t)order[(size_t)i]].x;
+            h_rows_lpt[(size_t)i] = h_rows[(size_t)order[(size_t)i]];
+        }
+        TC_CUDA(cudaMemcpyAsync(p->tile_blk.p, h_blk.data(), (size_t)ntiles * 4, cudaMemcpyHostToDevice, s));
+        TC_CUDA(cudaMemcpyAsync(rows_lpt.p, h_rows_lpt.data(), (size_t)ntiles * 8, cudaMemcpyHostToDevice, s));
+        TC_TRY(p->wtab.alloc(nt * (TWARPS + 1) * 8));
+        k_tile_wtab<<<(unsigned)((ntiles * (TWARPS + 1) + 255) / 256), 256, 0, s>>>(
+            p->rowptr.as<int32_t>(), cum.as<int64_t>(), blk_edges.as<int64_t>(), pbase.as<int64_t>(),
+            p->tile_blk.as<int32_t>(), rows_lpt.as<int2>(), (int32_t)ntiles, p->wtab.as<int2>());
+        TC_LAUNCH_CHECK();
+        TC_CUDA(cudaStreamSynchronize(s));  // the host vectors above must outlive their copies
     }
-    TC_TRY(p->items.alloc((size_t)(nitems > 0 ? nitems : 1) * 16));
-    TC_TRY(p->ibase.alloc(((size_t)B + 1) * 4));
-    TC_TRY(p->cta_blk.alloc((size_t)(G > 0 ? G : 1) * 4));
-    TC_TRY(p->bq.alloc(((size_t)B + 1) * 4));
-    TC_TRY(p->headval.alloc((size_t)(nitems > 0 ? nitems : 1) * 4));
-    TC_TRY(p->tailval.alloc((size_t)(nitems > 0 ? nitems : 1) * 4));
-    TC_TRY(p->tailrow.alloc((size_t)(nitems > 0 ? nitems : 1) * 4));
-    TC_CUDA(cudaMemsetAsync(p->bq.p, 0, ((size_t)B + 1) * 4, s));
-    DevBuf item_blk;
-    TC_TRY(item_blk.alloc((size_t)(nitems > 0 ? nitems : 1) * 4));
-    TC_CUDA(cudaMemcpyAsync(p->ibase.p, h_ibase.data(), ((size_t)B + 1) * 4, cudaMemcpyHostToDevice, s));
-    if (nitems > 0)
-        TC_CUDA(cudaMemcpyAsync(item_blk.p, h_item_blk.data(), (size_t)nitems * 4, cudaMemcpyHostToDevice, s));
-    if (G > 0) TC_CUDA(cudaMemcpyAsync(p->cta_blk.p, h_cta_blk.data(), (size_t)G * 4, cudaMemcpyHostToDevice, s));
-    p->nitems = nitems;
-    p->gather_ctas = G;
+    p->ntiles = (int32_t)ntiles;
     // grid.y over blocks, grid.x over each block's share: about 8 CTAs per SM in all
     const int gy = B < 65535 ? B : 65535;
     const dim3 grid((unsigned)((sms * 8 + gy - 1) / gy), (unsigned)gy);
@@ -486,12 +480,6 @@ int build_tiles(tc_part *p, int sms, cudaStream_t s) {
     k_tile_heads<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->blk_rows_dev.as<int64_t>(), blk_edges.as<int64_t>(),
                                       pbase.as<int64_t>(), B, p->heads.as<uint32_t>());
     TC_LAUNCH_CHECK();
-    if (nitems > 0) {
-        k_items<<<(nitems + 255) / 256, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->blk_rows_dev.as<int64_t>(),
-                                                     blk_edges.as<int64_t>(), pbase.as<int64_t>(), p->ibase.as<int32_t>(),
-                                                     item_blk.as<int32_t>(), nitems, p->items.as<int4>());
-        TC_LAUNCH_CHECK();
-    }
     TC_CUDA(cudaStreamSynchronize(s));
     p->padded_edges = npad;
     p->tiled = true;
@@ -501,29 +489,20 @@ int build_tiles(tc_part *p, int sms, cudaStream_t s) {
 int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, cudaStream_t s, int *launches) {
     const size_t smem = tile_smem_bytes(p->W);
     TC_CUDA(cudaFuncSetAttribute(k_tile_gather, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    if (p->nitems == 0) return TC_OK;  // no edges: every partial sum is empty (none exist)
+    if (p->ntiles == 0) return TC_OK;  // no edges: no partial sums exist
     TileArgs t;
     t.col16 = p->col16.as<uint16_t>();
     t.heads = p->heads.as<uint16_t>();
-    t.items = p->items.as<int4>();
-    t.ibase = p->ibase.as<int32_t>();
-    t.cta_blk = p->cta_blk.as<int32_t>();
-    t.B = p->B;
-    t.bq = const_cast<unsigned *>(p->bq.as<unsigned>());
-    t.headval = const_cast<float *>(p->headval.as<float>());
-    t.tailval = const_cast<float *>(p->tailval.as<float>());
-    t.tailrow = const_cast<int32_t *>(p->tailrow.as<int32_t>());
+    t.tile_blk = p->tile_blk.as<int32_t>();
+    t.wtab = p->wtab.as<int2>();
     t.contrib = contrib;
     t.V = p->V;
     t.W = p->W;
     t.partial = const_cast<float *>(p->partial.as<float>());
     t.err = err_flag;
-    k_tile_gather<<<p->gather_ctas, TILE_THREADS, smem, s>>>(t);
+    k_tile_gather<<<p->ntiles, TILE_THREADS, smem, s>>>(t);
     TC_LAUNCH_CHECK();
-    k_item_fixup<<<(p->nitems + 255) / 256 < 4 * p->gather_ctas ? (p->nitems + 255) / 256 : 4 * p->gather_ctas, 256, 0,
-                   s>>>(t.headval, t.tailval, t.tailrow, p->nitems, t.partial);
-    TC_LAUNCH_CHECK();
-    *launches += 2;
+    ++*launches;
     return TC_OK;
 }
 

@@ -202,7 +202,7 @@ static int log2_ceil(int64_t x) {
 // numbering (rp_new, ci_new), the permutation p->perm (new -> old) and the out-degree
 // reciprocals p->inv_outdeg in the new order.  Vertices with out-edges get the IDs [0, nz_out).
 static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, int grid, DevBuf *rp_new, DevBuf *ci_new,
-                                 tc_part *p) {
+                                 DevBuf *row, tc_part *p) {
     const int32_t V = g->V;
     const int64_t E = g->E;
     DevBuf key, val, kout, ktmp, vtmp, inv, deg, niso;
@@ -238,10 +238,9 @@ static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, int grid, De
     deg.release();
     TC_TRY(ci_new->alloc((size_t)(E > 0 ? E : 1) * 4));
     if (E > 0) {
-        DevBuf row;
-        TC_TRY(row.alloc((size_t)E * 4));
-        TC_TRY(expand_rows(rp_new->as<int32_t>(), V, row.as<int32_t>(), s));
-        k_order_edges<<<grid, 256, 0, s>>>(row.as<int32_t>(), rp_new->as<int32_t>(), p->perm.as<int32_t>(),
+        TC_TRY(row->alloc((size_t)E * 4));  // the row of every edge of the renumbered G^T (kept for the blocking)
+        TC_TRY(expand_rows(rp_new->as<int32_t>(), V, row->as<int32_t>(), s));
+        k_order_edges<<<grid, 256, 0, s>>>(row->as<int32_t>(), rp_new->as<int32_t>(), p->perm.as<int32_t>(),
                                            g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), inv.as<int32_t>(), E,
                                            ci_new->as<int32_t>());
         TC_LAUNCH_CHECK();
@@ -317,11 +316,11 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
         return fail(TC_ERR_UNSUPPORTED, "tc_tocab_partition: push partitions cannot be renumbered");
     if (order == TC_ORDER_OUTDEGREE && pp && pp->merge_range > 0 && pp->merge_range < 128)
         return fail(TC_ERR_INVALID_ARG, "tc_tocab_partition: renumbered partitions need merge_range >= 128");
-    DevBuf rel_rowptr, rel_colidx;
+    DevBuf rel_rowptr, rel_colidx, rows_in;
     p->nz_out = (int32_t)((int64_t)V - g->num_dangling);  // vertices with out-edges
     p->ni = V;
     if (order == TC_ORDER_OUTDEGREE && V > 0) {
-        TC_TRY(renumber_by_outdegree(g, s, caps.sms * 8, &rel_rowptr, &rel_colidx, p));
+        TC_TRY(renumber_by_outdegree(g, s, caps.sms * 8, &rel_rowptr, &rel_colidx, &rows_in, p));
         rp = rel_rowptr.as<int32_t>();
         ci = rel_colidx.as<int32_t>();
     }
@@ -371,11 +370,13 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     const int grid = caps.sms * 8;
 
     TC_TRY(p->colidx.alloc((size_t)E * 4));
-    DevBuf rows_sorted, rows_in, head, head_prefix, ktmp, vtmp;
+    DevBuf rows_sorted, head, head_prefix, ktmp, vtmp;
     TC_TRY(rows_sorted.alloc((size_t)E * 4));
     if (E > 0) {
-        TC_TRY(rows_in.alloc((size_t)E * 4));
-        TC_TRY(expand_rows(rp, V, rows_in.as<int32_t>(), s));
+        if (!rows_in.p) {  // (the renumbering has built it already)
+            TC_TRY(rows_in.alloc((size_t)E * 4));
+            TC_TRY(expand_rows(rp, V, rows_in.as<int32_t>(), s));
+        }
         if (B > 1) {
             TC_TRY(ktmp.alloc((size_t)E * 4));
             TC_TRY(vtmp.alloc((size_t)E * 4));

@@ -248,66 +248,68 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
 // building the staged format from a base partition
 // ---------------------------------------------------------------------------------------------
 // Block b's edges are contiguous in the partition and keep their order in the staged stream, so
-// filling it is a straight copy: col16[pbase[b] + (i - eb)] = colidx[i] - b*W (grid.y strides
-// over blocks, grid.x over a block's edges).
-__global__ void k_tile_copy(const int32_t *colidx, const int64_t *blk_edges, const int64_t *pbase, int32_t B,
-                            int32_t W, uint16_t *col16) {
-    for (int32_t b = blockIdx.y; b < B; b += gridDim.y) {
-        const int64_t eb = blk_edges[b], ee = blk_edges[b + 1];
-        const int64_t off = pbase[b] - eb;
-        const int32_t base = b * W;
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        int64_t i = eb + blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-        // eight independent loads in flight per thread, then their stores
-        for (; i + 7 * stride < ee; i += 8 * stride) {
-            int32_t c[8];
+// filling it is a straight copy over all edges: edge i of block b = colidx[i] / W goes to
+// col16[i + delta[b]] = colidx[i] - b W, with delta[b] = pbase[b] - blk_edges[b].  Edge-parallel
+// over the whole stream, so one block holding most of the edges gets the whole grid.
+__global__ void k_tile_copy(const int32_t *colidx, int64_t E, DivBy W, int32_t Wi, const int64_t *delta,
+                            uint16_t *col16) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    // eight independent loads in flight per thread, then their stores
+    for (; i + 7 * stride < E; i += 8 * stride) {
+        int32_t c[8];
 #pragma unroll
-            for (int k = 0; k < 8; ++k) c[k] = __ldg(colidx + i + k * stride);
+        for (int k = 0; k < 8; ++k) c[k] = __ldg(colidx + i + k * stride);
 #pragma unroll
-            for (int k = 0; k < 8; ++k) col16[i + k * stride + off] = (uint16_t)(c[k] - base);
+        for (int k = 0; k < 8; ++k) {
+            const int32_t b = div_apply(c[k], W);
+            col16[i + k * stride + __ldg(delta + b)] = (uint16_t)(c[k] - b * Wi);
         }
-        for (; i < ee; i += stride) col16[i + off] = (uint16_t)(__ldg(colidx + i) - base);
+    }
+    for (; i < E; i += stride) {
+        const int32_t c = __ldg(colidx + i), b = div_apply(c, W);
+        col16[i + __ldg(delta + b)] = (uint16_t)(c - b * Wi);
     }
 }
 
-// A head bit at the first staged edge of every local row.  A warp's 32 rows are consecutive, so
-// their head positions increase with the lane: lanes whose heads share a 32-bit word OR their
-// bits together (segmented shuffle reduction) and one atomic per word remains.
-__global__ void k_tile_heads(const int32_t *rowptr, const int64_t *blk_rows, const int64_t *blk_edges,
-                             const int64_t *pbase, int32_t B, uint32_t *heads32) {
+// A head bit at the first staged edge of every local row (row r's block is that of its first
+// edge's column).  A warp's 32 rows are consecutive, so their head positions increase with the
+// lane: lanes whose heads share a 32-bit word OR their bits together (segmented shuffle
+// reduction) and one atomic per word remains.
+__global__ void k_tile_heads(const int32_t *rowptr, const int32_t *colidx, int64_t R, DivBy W, const int64_t *delta,
+                             uint32_t *heads32) {
     const int lane = threadIdx.x & 31;
-    for (int32_t b = blockIdx.y; b < B; b += gridDim.y) {
-        const int64_t r1 = blk_rows[b + 1];
-        const int64_t off = pbase[b] - blk_edges[b];
-        const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-        // four groups of 32 rows per step: their row offsets are loaded together
-        for (int64_t r0 = blk_rows[b] + blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < r1;
-             r0 += 4 * stride) {
-            int32_t s4[4];
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    // four groups of 32 rows per step: their row offsets are loaded together
+    for (int64_t r0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); r0 < R; r0 += 4 * stride) {
+        int32_t s4[4];
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t r = r0 + k * stride + lane;
-                s4[k] = r < r1 ? rowptr[r] : 0;
+        for (int k = 0; k < 4; ++k) {
+            const int64_t r = r0 + k * stride + lane;
+            s4[k] = r < R ? rowptr[r] : 0;
+        }
+        int64_t d4[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const int64_t r = r0 + k * stride + lane;
+            d4[k] = r < R ? (int64_t)s4[k] + __ldg(delta + div_apply(__ldg(colidx + s4[k]), W)) : -1;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past the rows: a group of their own, no atomic
+            if (d4[k] >= 0) {
+                word = (uint32_t)(d4[k] >> 5);
+                bit = 1u << (d4[k] & 31);
             }
+            uint32_t v = bit;
 #pragma unroll
-            for (int k = 0; k < 4; ++k) {
-                const int64_t r = r0 + k * stride + lane;
-                uint32_t word = 0xFFFFFFFFu, bit = 0u;  // lanes past the block: a group of their own, no atomic
-                if (r < r1) {
-                    const int64_t dst = s4[k] + off;
-                    word = (uint32_t)(dst >> 5);
-                    bit = 1u << (dst & 31);
-                }
-                uint32_t v = bit;
-#pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
-                    const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
-                    if (lane + d < 32 && wy == word) v |= y;
-                }
-                const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
-                if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_down_sync(0xffffffffu, v, d);
+                const uint32_t wy = __shfl_down_sync(0xffffffffu, word, d);
+                if (lane + d < 32 && wy == word) v |= y;
             }
+            const uint32_t wprev = __shfl_up_sync(0xffffffffu, word, 1);
+            if (bit && (lane == 0 || wprev != word)) atomicOr(heads32 + word, v);
         }
     }
 }
@@ -471,14 +473,23 @@ int build_tiles(tc_part *p, int sms, cudaStream_t s) {
         TC_CUDA(cudaStreamSynchronize(s));  // the host vectors above must outlive their copies
     }
     p->ntiles = (int32_t)ntiles;
-    // grid.y over blocks, grid.x over each block's share: about 8 CTAs per SM in all
-    const int gy = B < 65535 ? B : 65535;
-    const dim3 grid((unsigned)((sms * 8 + gy - 1) / gy), (unsigned)gy);
-    k_tile_copy<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), blk_edges.as<int64_t>(), pbase.as<int64_t>(), B, p->W,
-                                     p->col16.as<uint16_t>());
+    // the staged stream and its row-head bits, edge- and row-parallel over the whole partition
+    std::vector<int64_t> h_delta((size_t)B);
+    {
+        int64_t pb = 0;
+        for (int32_t b = 0; b < B; ++b) {
+            h_delta[(size_t)b] = pb - p->h_blk_edges[b];
+            pb += (p->h_blk_edges[b + 1] - p->h_blk_edges[b] + WCH - 1) / WCH * WCH;
+        }
+    }
+    DevBuf delta;
+    TC_TRY(delta.alloc((size_t)B * 8));
+    TC_CUDA(cudaMemcpyAsync(delta.p, h_delta.data(), (size_t)B * 8, cudaMemcpyHostToDevice, s));
+    k_tile_copy<<<sms * 8, 256, 0, s>>>(p->colidx.as<int32_t>(), p->E, div_by(p->W), p->W, delta.as<int64_t>(),
+                                        p->col16.as<uint16_t>());
     TC_LAUNCH_CHECK();
-    k_tile_heads<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->blk_rows_dev.as<int64_t>(), blk_edges.as<int64_t>(),
-                                      pbase.as<int64_t>(), B, p->heads.as<uint32_t>());
+    k_tile_heads<<<sms * 8, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->colidx.as<int32_t>(), R, div_by(p->W),
+                                         delta.as<int64_t>(), p->heads.as<uint32_t>());
     TC_LAUNCH_CHECK();
     TC_CUDA(cudaStreamSynchronize(s));
     p->padded_edges = npad;

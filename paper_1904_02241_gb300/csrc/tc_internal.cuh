@@ -185,6 +185,8 @@ struct tc_part {
     tc::DevBuf partial;         // float[R] partial sums (scratch)
     tc::DevBuf rowbits;         // uint32[ceil(R/32)] local next bits (BFS scratch)
     tc::DevBuf merge_offT;      // int32[(nranges+1) * B]: merge_off transposed (range-major)
+    tc::DevBuf merge_gpre;      // int32[nranges * (B+1)]: per range, granules of MERGE_GRAN local
+                                // rows before each block's slice (exclusive prefix; [B] = total)
     tc::DevBuf blk_rows_dev;    // int64[B+1]
     // ---- shared-memory staged format (pull, W <= smem capacity; see tc_tile.cu) ----
     bool tiled = false;
@@ -211,6 +213,8 @@ struct tc_part {
 };
 
 namespace tc {
+// The pull merge reads local rows in aligned granules of MERGE_GRAN entries (tc_pagerank.cu).
+constexpr int MERGE_GRAN = 8;
 // Shared-memory staged TOCAB format (tc_tile.cu).
 constexpr int TILE_WCHUNK = 512;         // edges a warp streams per step (16 per lane)
 constexpr int TILE_THREADS = 1024;

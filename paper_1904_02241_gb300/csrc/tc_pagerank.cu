@@ -333,14 +333,14 @@ __device__ __forceinline__ void fx_split3(float xs, int32_t &hi, int32_t &mid, i
 // are added with 32-bit shared reductions and recombined exactly, so the result does not
 // depend on the order of the additions: deterministic.  (FP32 shared atomics measured about
 // 3.4x slower than 32-bit integer ones on GB300, and 64-bit ones 6.5x.)
-constexpr int MG_GRAN = 8;     // entries per granule: 32 bytes of sums, 16 bytes of 2-byte ids
+constexpr int MG_GRAN = MERGE_GRAN;  // entries per granule: 32 bytes of sums, 16 bytes of 2-byte ids
 constexpr int MG_GUNROLL = 2;  // granules of a lane in flight
 
 // Shared-memory layout of k_pull_merge_atomic: nacc accumulator arrays of [k], slice bounds
-// and granule prefix ([3B + 1] ints), the chunk-to-slice map, then (16-byte aligned) the out-degree
-// reciprocals of the range's vertices ([k] floats, one bulk copy).
+// and granule prefix ([3B + 1] ints), then (16-byte aligned) the out-degree reciprocals of the
+// range's vertices ([k] floats, one bulk copy).
 __host__ __device__ inline size_t merge_atomic_inv_offset(int32_t k, int32_t B, int nacc) {
-    const size_t head = (size_t)k * 4 * nacc + ((size_t)3 * B + 2) * 4 + ((size_t)B + MG_CMAP_EXTRA) * 2;
+    const size_t head = (size_t)k * 4 * nacc + ((size_t)3 * B + 2) * 4;
     return (head + 15) & ~(size_t)15;
 }
 __host__ __device__ inline size_t merge_atomic_layout_bytes(int32_t k, int32_t B, int nacc) {
@@ -357,7 +357,8 @@ template <int MODE>
 __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float *__restrict__ partial,
                                                                      const int32_t *__restrict__ id_map,
                                                                      const uint16_t *__restrict__ id16,
-                                                                     const int32_t *__restrict__ offT, int32_t B,
+                                                                     const int32_t *__restrict__ offT,
+                                                                     const int32_t *__restrict__ gpre_tab, int32_t B,
                                                                      int32_t k, const int32_t *__restrict__ rstart,
                                                                      int32_t nranges, UpdateArgs u) {
     static_assert(MODE == 2 || MODE == 3, "two- or three-part fixed point");
@@ -369,11 +370,8 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
     int32_t *e_lo = reinterpret_cast<int32_t *>(msm + (size_t)k * 4 * NACC);  // [B] first entry
     int32_t *e_hi = e_lo + B;                                                  // [B] end entry
     int32_t *gpre = e_hi + B;                                                  // [B + 1] granule prefix
-    uint16_t *cmap = reinterpret_cast<uint16_t *>(gpre + B + 1);
     float *sinv = reinterpret_cast<float *>(msm + merge_atomic_inv_offset(k, B, NACC));  // [k]
-    const int32_t cmap_cap = B + MG_CMAP_EXTRA;
     __shared__ __align__(8) uint64_t inv_bar;
-    __shared__ int32_t wsum[MG_WARPS];
     __shared__ float wdang[MG_WARPS];  // per-warp dangling mass of the range just finished
     __shared__ int32_t s_next;         // the CTA's next range, drawn from the queue
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -381,7 +379,7 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
     const float scalef = MODE == 2 ? (float)(*u.fx_scale * 0x1p-17) : (float)(*u.fx_scale * 0x1p-13);
     const float inv_scalef = 1.0f / scalef;  // a power of two
     const float spread = spread_of(u);
-    const int per = (B + MG_THREADS - 1) / MG_THREADS;
+    const bool one = B < MG_THREADS;  // a thread per block (and one for the total): bounds kept in registers
     if (tid == 0) {
         mbar_init(&inv_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -389,10 +387,14 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
     uint32_t phase = 0;    // parity of the reciprocal copy's next completion
     bool broken = false;   // a bounded wait gave up: no more copies, ranges skipped
     int32_t j = blockIdx.x, jprev = -1;
-    int32_t pre_lo = 0, pre_hi = 0;  // slice bounds of block tid in range j (per == 1)
-    if (per == 1 && tid < B && j < nranges) {
-        pre_lo = __ldg(offT + (int64_t)j * B + tid);
-        pre_hi = __ldg(offT + (int64_t)(j + 1) * B + tid);
+    // slice bounds and granule prefix of block tid in range j (when `one`), loaded a range ahead
+    int32_t pre_lo = 0, pre_hi = 0, pre_g = 0;
+    if (one && tid <= B && j < nranges) {
+        if (tid < B) {
+            pre_lo = __ldg(offT + (int64_t)j * B + tid);
+            pre_hi = __ldg(offT + (int64_t)(j + 1) * B + tid);
+        }
+        pre_g = __ldg(gpre_tab + (int64_t)j * (B + 1) + tid);
     }
     while (j < nranges) {
         // range j: [j k, (j+1) k), or [rstart[j], rstart[j+1]) (at most k wide) when given
@@ -424,89 +426,49 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
                          reinterpret_cast<const unsigned char *>(u.inv_outdeg + vbase) + off, part, &inv_bar);
             }
         }
-        // slice bounds and granule counts (the next range's bounds start loading), then an
-        // exclusive CTA scan of the counts
-        int32_t run = 0;
-        if (per == 1) {
+        // the range's slice bounds and granule prefix (precomputed with the partition) go to
+        // shared memory; once the barrier has published the next range's index, its bounds start
+        // loading
+        if (one) {
             if (tid < B) {
                 e_lo[tid] = pre_lo;
                 e_hi[tid] = pre_hi;
-                run = pre_hi > pre_lo ? ((pre_hi + MG_GRAN - 1) / MG_GRAN - pre_lo / MG_GRAN) : 0;
             }
+            if (tid <= B) gpre[tid] = pre_g;
         } else {
-            for (int q = 0; q < per; ++q) {
-                const int32_t b = tid * per + q;
+            for (int32_t b = tid; b <= B; b += MG_THREADS) {
                 if (b < B) {
-                    const int32_t l0 = __ldg(offT + (int64_t)j * B + b), l1 = __ldg(offT + (int64_t)(j + 1) * B + b);
-                    e_lo[b] = l0;
-                    e_hi[b] = l1;
-                    run += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
+                    e_lo[b] = __ldg(offT + (int64_t)j * B + b);
+                    e_hi[b] = __ldg(offT + (int64_t)(j + 1) * B + b);
                 }
-            }
-        }
-        int incl = run;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += y;
-        }
-        if (lane == 31) wsum[warp] = incl;
-        __syncthreads();
-        const int32_t jn = s_next;  // published by the barrier above
-        if (per == 1 && tid < B && jn < nranges) {  // the next range's slice bounds start loading
-            pre_lo = __ldg(offT + (int64_t)jn * B + tid);
-            pre_hi = __ldg(offT + (int64_t)(jn + 1) * B + tid);
-        }
-        if (warp == 0) {
-            const int w = lane < MG_WARPS ? wsum[lane] : 0;
-            int wi = w;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, wi, d);
-                if (lane >= d) wi += y;
-            }
-            if (lane < MG_WARPS) wsum[lane] = wi - w;
-        }
-        __syncthreads();
-        int32_t base = wsum[warp] + incl - run;
-        for (int q = 0; q < per; ++q) {
-            const int32_t b = tid * per + q;
-            if (b < B) {
-                gpre[b] = base;
-                const int32_t l0 = e_lo[b], l1 = e_hi[b];
-                base += l1 > l0 ? ((l1 + MG_GRAN - 1) / MG_GRAN - l0 / MG_GRAN) : 0;
-            }
-        }
-        if (tid == MG_THREADS - 1) gpre[B] = base;
-        __syncthreads();
-        // cmap[c] = slice holding granule 32 c (the last slice starting at or before it)
-        for (int q = 0; q < per; ++q) {
-            const int32_t b = tid * per + q;
-            if (b < B) {
-                const int32_t g0 = gpre[b], g1 = gpre[b + 1];
-                for (int32_t c = (g0 + 31) >> 5; (c << 5) < g1 && c < cmap_cap; ++c) cmap[c] = (uint16_t)b;
+                gpre[b] = __ldg(gpre_tab + (int64_t)j * (B + 1) + b);
             }
         }
         __syncthreads();
+        const int32_t jn = s_next;
+        if (one && tid <= B && jn < nranges) {
+            if (tid < B) {
+                pre_lo = __ldg(offT + (int64_t)jn * B + tid);
+                pre_hi = __ldg(offT + (int64_t)(jn + 1) * B + tid);
+            }
+            pre_g = __ldg(gpre_tab + (int64_t)jn * (B + 1) + tid);
+        }
         const int32_t ngran = gpre[B];
         const int32_t nchunks = (ngran + 31) >> 5;
         const int32_t dummy = lane < k ? lane : 0;  // target of the zero adds of masked entries
         const int32_t c_begin = (int32_t)((int64_t)nchunks * warp / MG_WARPS);
         const int32_t c_end = (int32_t)((int64_t)nchunks * (warp + 1) / MG_WARPS);
         int32_t bp = 0;
-        if (c_begin < c_end) {
-            if (c_begin < cmap_cap) {
-                bp = cmap[c_begin];
-            } else {  // beyond the map: last slice with gpre <= the chunk's first granule
-                int32_t lo = 0, hi = B - 1;
-                const int32_t gq = c_begin << 5;
-                while (lo < hi) {
-                    const int32_t mid = (lo + hi + 1) >> 1;
-                    if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
-                }
-                bp = lo;
+        if (c_begin < c_end) {  // the last slice with gpre <= the warp's first granule
+            int32_t lo = 0, hi = B - 1;
+            const int32_t gq = c_begin << 5;
+            while (lo < hi) {
+                const int32_t mid = (lo + hi + 1) >> 1;
+                if (gpre[mid] <= gq) lo = mid; else hi = mid - 1;
             }
+            bp = lo;
         }
+        // MG_GUNROLL chunks at a time: all their granule loads are issued before any is added in.
         for (int32_t c0 = c_begin; c0 < c_end; c0 += MG_GUNROLL) {
             float4 xa[MG_GUNROLL], xb[MG_GUNROLL];
             uint4 iv[MG_GUNROLL];
@@ -537,7 +499,7 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
             }
 #pragma unroll
             for (int q = 0; q < MG_GUNROLL; ++q) {
-                float x8[MG_GRAN] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
+                const float x8[MG_GRAN] = {xa[q].x, xa[q].y, xa[q].z, xa[q].w, xb[q].x, xb[q].y, xb[q].z, xb[q].w};
                 int32_t id8[MG_GRAN];
                 if (id16) {
                     const uint32_t w[4] = {iv[q].x, iv[q].y, iv[q].z, iv[q].w};
@@ -557,7 +519,7 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
                     id8[4] = w1.x - vbase; id8[5] = w1.y - vbase; id8[6] = w1.z - vbase; id8[7] = w1.w - vbase;
                 }
                 // Entries outside the slice add zero to a slot of their own lane (no branches: the
-                // atomics of a warp stay converged).
+                // atomics of a warp stay converged; predicating them off measured slower).
 #pragma unroll
                 for (int e = 0; e < MG_GRAN; ++e) {
                     const bool ok = (valid[q] >> e) & 1u;
@@ -1053,11 +1015,11 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
                 else if (merge_fixed_parts(part->B) == 2)
                     k_pull_merge_atomic<2><<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->B, part->k, rst, part->nranges, u);
+                        part->merge_gpre.as<int32_t>(), part->B, part->k, rst, part->nranges, u);
                 else
                     k_pull_merge_atomic<3><<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->B, part->k, rst, part->nranges, u);
+                        part->merge_gpre.as<int32_t>(), part->B, part->k, rst, part->nranges, u);
             }
             TC_LAUNCH_CHECK();
             ++launches;

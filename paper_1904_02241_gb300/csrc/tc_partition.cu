@@ -55,6 +55,42 @@ __global__ void k_merge_offsets(const int32_t *id_map, const int64_t *blk_rows, 
     }
 }
 
+// gpre[j][b] = granules (aligned groups of MERGE_GRAN local rows that hold rows of the slice)
+// in the slices of blocks 0..b-1 of merge range j; gpre[j][B] = all of range j's.  One CTA per
+// range (grid-stride), an exclusive scan over the blocks in chunks of the CTA's width.
+__global__ void __launch_bounds__(256) k_merge_gpre(const int32_t *offT, int32_t B, int32_t nranges, int32_t *gpre) {
+    __shared__ int32_t wsum[8];
+    __shared__ int32_t carry_s;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int32_t j = blockIdx.x; j < nranges; j += gridDim.x) {
+        int32_t carry = 0;
+        for (int32_t b0 = 0; b0 < B; b0 += 256) {
+            const int32_t b = b0 + tid;
+            int32_t cnt = 0;
+            if (b < B) {
+                const int32_t l0 = offT[(int64_t)j * B + b], l1 = offT[(int64_t)(j + 1) * B + b];
+                cnt = l1 > l0 ? (l1 + MERGE_GRAN - 1) / MERGE_GRAN - l0 / MERGE_GRAN : 0;
+            }
+            int32_t incl = cnt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t y = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane >= d) incl += y;
+            }
+            if (lane == 31) wsum[warp] = incl;
+            __syncthreads();
+            int32_t before = carry;
+            for (int w = 0; w < warp; ++w) before += wsum[w];
+            if (b < B) gpre[(int64_t)j * (B + 1) + b] = before + incl - cnt;
+            if (tid == 255) carry_s = before + incl;
+            __syncthreads();
+            carry = carry_s;
+            __syncthreads();
+        }
+        if (tid == 0) gpre[(int64_t)j * (B + 1) + B] = carry;
+    }
+}
+
 __global__ void k_id16(const int32_t *id_map, int64_t R, int32_t kmask, uint16_t *id16) {
     for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x)
         id16[r] = (uint16_t)(id_map[r] & kmask);
@@ -438,6 +474,9 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
                                              rst, p->merge_off.as<int32_t>(), p->merge_offT.as<int32_t>());
         TC_LAUNCH_CHECK();
     }
+    TC_TRY(p->merge_gpre.alloc((size_t)p->nranges * ((size_t)B + 1) * 4));
+    k_merge_gpre<<<grid, 256, 0, s>>>(p->merge_offT.as<int32_t>(), B, p->nranges, p->merge_gpre.as<int32_t>());
+    TC_LAUNCH_CHECK();
     TC_TRY(collect_hubs(p->rowptr.as<int32_t>(), R, p->hub_degree, &p->hubs, &p->num_hubs, s));
     if (R > 0 && rst) {  // 2-byte offsets inside the (variable) merge ranges, all <= k <= 65536
         TC_TRY(p->id16.alloc((size_t)(R + 8) * 2));

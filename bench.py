@@ -58,7 +58,7 @@ def parse():
                     help="vertex numbering the TOCAB blocks are cut in (renumbered by out-degree, or as given)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
-    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc"],
+    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc", "bfs_grid", "rmat16"],
                     help="profiling runs: time only this row and print its figures")
     return ap.parse_args()
 
@@ -340,6 +340,13 @@ def variants(args, ctx, world):
     res["pull_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
     res["pull_unblocked_bmin_frac"] = bmin_frac(ms)
     res["pull_tocab_blocks"] = P.num_blocks
+    other_order = "natural" if args.order == "outdegree" else "outdegree"
+    Pn = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy, order=other_order)
+    ms = run(lambda: T.pagerank_pull(G, Pn, damping=DAMPING, iters=ITERS, out=out))
+    res[f"pull_tocab_{other_order}_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res[f"pull_tocab_{other_order}_bmin_frac"] = bmin_frac(ms)
+    res[f"pull_tocab_{other_order}_local_rows"] = Pn.num_rows
+    del Pn
     other = "l2" if args.policy == "smem" else "smem"
     Po = T.tocab_partition(G, T.TC_PULL, 0, block_policy=other)
     ms = run(lambda: T.pagerank_pull(G, Po, damping=DAMPING, iters=ITERS, out=out))
@@ -369,21 +376,14 @@ def variants(args, ctx, world):
     srcs = gg.sources(gs, args.bfs_sources, seed=13)
     for thr, push, key in [(0.05, 0.0, "bfs_tocab"), (-1.0, 0.0, "bfs_unblocked"),
                            (0.05, 1.0 / 24, "bfs_diropt_tocab"), (-1.0, 1.0 / 24, "bfs_diropt_unblocked")]:
-        T.bfs_pull(Gs, Ps, srcs[0], tocab_threshold=thr, out=lv, push_threshold=push)
-        torch.cuda.synchronize()
-        tot_ms, tot_edges = 0.0, 0
-        for s in srcs:
-            t0 = torch.cuda.Event(enable_timing=True)
-            t1 = torch.cuda.Event(enable_timing=True)
-            t0.record(stream)
-            _, st = T.bfs_pull(Gs, Ps, s, tocab_threshold=thr, out=lv, return_stats=True, push_threshold=push)
-            t1.record(stream)
-            t1.synchronize()
-            tot_ms += t0.elapsed_time(t1)
-            tot_edges += st.edges_reached // 2
-        res[key + "_gteps"] = round(tot_edges / (tot_ms * 1e-3) / 1e9, 2)
+        res[key + "_gteps"] = bfs_rate(T, Gs, Ps, srcs, lv, stream, thr, push)[0]
     res["bfs_graph"] = {"V": gs.V, "E_directed": gs.E, "sources": len(srcs)}
     res["bfs_oracle"] = oracle_bfs_rate(gs, srcs[0])
+    # the TOCAB frontier threshold tau (Sec. 3.3, "frontier large enough"), swept on 16 of the
+    # sources: pure pull levels and direction-optimised levels; levels are identical for every tau
+    res["bfs_tau_sweep_gteps"] = bfs_tau_sweep(T, Gs, Ps, srcs[:16], lv, stream)
+    taus = res["bfs_tau_sweep_gteps"]
+    res["bfs_tau_best"] = {kind: max(taus[kind], key=lambda k: taus[kind][k]) for kind in taus}
     del Gs, Ps, gs, lv
     torch.cuda.empty_cache()
     # block-count sweep around the L2 capacity (paper's source-range blocks, unstaged gather)
@@ -395,9 +395,71 @@ def variants(args, ctx, world):
         del Pb
     res["pull_tocab_block_sweep_gteps"] = sweep
     torch.cuda.empty_cache()
+    res["rmat16"] = rmat16_row(stream, run)
+    res["bfs_grid4096"] = bfs_grid_row(stream)
     res.update(graph_variants(args, stream, E, run))
     res.update(batch_variants(args, stream))
     return res
+
+
+def bfs_rate(T, G, P, srcs, lv, stream, thr, push):
+    """GTEPS of BFS from every source (edges reached / 2, symmetrised graphs) and the levels."""
+    T.bfs_pull(G, P, srcs[0], tocab_threshold=thr, out=lv, push_threshold=push)
+    torch.cuda.synchronize()
+    tot_ms, tot_edges, levels = 0.0, 0, 0
+    for s in srcs:
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        _, st = T.bfs_pull(G, P, s, tocab_threshold=thr, out=lv, return_stats=True, push_threshold=push)
+        t1.record(stream)
+        t1.synchronize()
+        tot_ms += t0.elapsed_time(t1)
+        tot_edges += st.edges_reached // 2
+        levels = max(levels, st.levels)
+    return round(tot_edges / (tot_ms * 1e-3) / 1e9, 2), levels
+
+
+def bfs_tau_sweep(T, G, P, srcs, lv, stream):
+    out = {}
+    for kind, push in (("pull", 0.0), ("diropt", 1.0 / 24)):
+        out[kind] = {}
+        for tau in (0.0, 0.02, 0.05, 0.1, 0.2, 0.4, -1.0):
+            out[kind][str(tau)] = bfs_rate(T, G, P, srcs, lv, stream, tau, push)[0]
+    return out
+
+
+def rmat16_row(stream, run):
+    """The small configuration: R-MAT 16 (V = 65,536, ~1M edges), unblocked pull against TOCAB with
+    4 source-range blocks (the paper's ranges, and the same after renumbering by out-degree)."""
+    import paper_1904_02241_gb300 as T
+    g = gg.rmat(16, device="cuda")
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    out = torch.empty(g.V, dtype=torch.float32, device="cuda")
+    row = {"V": g.V, "E": g.E}
+    for key, P in (("pull_unblocked", None), ("pull_tocab_b4", T.tocab_partition(G, T.TC_PULL, 4)),
+                   ("pull_tocab_b4_renumbered", T.tocab_partition(G, T.TC_PULL, 4, order="outdegree"))):
+        ms = run(lambda: T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out))
+        row[key + "_gteps"] = round(g.E * ITERS / (ms * 1e-3) / 1e9, 2)
+    return row
+
+
+def bfs_grid_row(stream, nsrc: int = 8):
+    """BFS on the 4096 x 4096 grid with 5% of its edges removed (both directions): about 8,000
+    levels with small frontiers, so the levels run top-down (direction optimisation); pure pull
+    levels rescan every unvisited vertex per level and are not timed here."""
+    import paper_1904_02241_gb300 as T
+    g = gg.grid2d(4096, 4096, drop=0.05, seed=11, device="cuda")
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    P = T.tocab_partition(G, T.TC_PULL, 0, block_policy="l2")
+    lv = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    srcs = gg.sources(g, nsrc, seed=13)
+    row = {"V": g.V, "E_directed": g.E, "sources": nsrc}
+    for key, thr in (("bfs_diropt_unblocked", -1.0), ("bfs_diropt_tocab", 0.05)):
+        gteps, levels = bfs_rate(T, G, P, srcs, lv, stream, thr, 1.0 / 24)
+        row[key + "_gteps"] = gteps
+        row["levels_max"] = levels
+    return row
 
 
 def graph_variants(args, stream, E_rmat, run):
@@ -413,17 +475,20 @@ def graph_variants(args, stream, E_rmat, run):
         g = make()
         G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
         P = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy)
+        Pr = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy, order="outdegree")
         out = torch.empty(g.V, dtype=torch.float32, device="cuda")
         bmin = 4 * g.E + 4 * (g.V + 1) + 12 * g.V
         row = {"V": g.V, "E": g.E, "blocks": P.num_blocks}
         for key, fn in (("pull_tocab", lambda: T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out)),
+                        ("pull_tocab_renumbered", lambda: T.pagerank_pull(G, Pr, damping=DAMPING, iters=ITERS,
+                                                                          out=out)),
                         ("pull_unblocked", lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out)),
                         ("push_unblocked", lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))):
             ms = run(fn)
             row[key + "_gteps"] = round(g.E * ITERS / (ms * 1e-3) / 1e9, 2)
             row[key + "_bmin_frac"] = round(bmin / (ms / ITERS * 1e-3) / 1e9 / peak, 4)
         res[name] = row
-        del P, G, g, out
+        del P, Pr, G, g, out
         torch.cuda.empty_cache()
     return res
 
@@ -688,8 +753,14 @@ def main():
         raise SystemExit("bench.py needs a CUDA device (the TOCAB path has no CPU fallback)")
     if args.row:
         stream = torch.cuda.current_stream()
+        def run(fn):
+            for _ in range(2):
+                fn()
+            torch.cuda.synchronize()
+            return statistics.median(time_runs(fn, 5, stream))
         res = {"many_graphs": lambda: many_graphs(stream, with_oracle=False), "spmv": lambda: spmv_row(stream),
-               "bc": lambda: bc_row(stream)}[args.row]()
+               "bc": lambda: bc_row(stream), "bfs_grid": lambda: {"bfs_grid4096": bfs_grid_row(stream)},
+               "rmat16": lambda: {"rmat16": rmat16_row(stream, run)}}[args.row]()
         print(json.dumps(res), flush=True)
         return
     res, ctx = bench_tocab(args, world, rank, local)

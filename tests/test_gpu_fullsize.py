@@ -145,3 +145,19 @@ def test_thousand_graphs_sampled(T):
         assert l1_rel(r[lo:hi], want) <= TOL, k
     sums = np.add.reduceat(r.astype(np.float64), off[:-1])
     assert np.all(np.abs(sums - 1.0) < 1e-4)
+
+
+def test_grid4096_bfs_bit_exact(T):
+    """The 4096 x 4096 grid with 5% of its edges removed (about 8,000 levels of small frontiers):
+    two seeded sources, direction-optimised with and without TOCAB pull levels, bit-exact."""
+    g = gg.grid2d(4096, 4096, drop=0.05, seed=11, device="cuda")
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    P = T.tocab_partition(G, T.TC_PULL, 0, block_policy="l2")
+    rp, ci = g.numpy()
+    for s in gg.sources(g, 2, seed=13):
+        want = oracle.bfs(g.V, rp, ci, s)
+        for thr in (0.05, -1.0):
+            lv, st = T.bfs_pull(G, P, s, tocab_threshold=thr, push_threshold=1.0 / 24, return_stats=True)
+            np.testing.assert_array_equal(lv.cpu().numpy(), want)
+            assert st.reached == int((want >= 0).sum())
+            assert st.levels == int(want.max()) + 1

@@ -58,7 +58,7 @@ def parse():
                     help="vertex numbering the TOCAB blocks are cut in (renumbered by out-degree, or as given)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
-    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc", "bfs_grid", "rmat16"],
+    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc", "bfs_grid", "rmat16", "ppr"],
                     help="profiling runs: time only this row and print its figures")
     return ap.parse_args()
 
@@ -494,15 +494,25 @@ def graph_variants(args, stream, E_rmat, run):
 
 
 def batch_variants(args, stream):
-    """Batching: 256 personalised PageRank sources on R-MAT 22 (one [V x 256] launch per
-    iteration), and 1,000 R-MAT graphs with scales 10..16 in one persistent, graph-captured
-    launch with the lanes-per-vertex variant chosen by the autotuner."""
+    """Batching: 256 personalised PageRank sources on R-MAT 22 (all iterations in one persistent,
+    graph-captured launch with the autotuned hot block and width), and 1,000 R-MAT graphs with
+    scales 10..16 in one persistent, graph-captured launch with the lanes-per-vertex variant
+    chosen by the autotuner."""
+    res = ppr_row(stream)
+    res.update(many_graphs(stream))
+    return res
+
+
+def ppr_row(stream):
+    """256 personalised PageRank sources on R-MAT 22: the persistent batch (autotuned first) and
+    the TOCAB-blocked form per 32-column tile."""
     import paper_1904_02241_gb300 as T
     res = {}
     g22 = gg.rmat(22, device="cuda")
     G22 = T.graph_load_csr(g22.rowptr, g22.colidx, V=g22.V)
     srcs = gg.sources(g22, 256, seed=17)
     R = torch.empty((g22.V, 256), dtype=torch.float32, device="cuda")
+    hot, tile, tune_ms = T.ppr_autotune(G22, srcs)
     T.ppr_batch(G22, srcs, iters=ITERS, out=R)
     torch.cuda.synchronize()
     ms = statistics.median(time_runs(lambda: T.ppr_batch(G22, srcs, iters=ITERS, out=R), 3, stream))
@@ -515,6 +525,10 @@ def batch_variants(args, stream):
     res["ppr_oracle"] = oracle_ppr_rate(g22, srcs[0])
     res["ppr_batch"] = {"graph": "rmat22", "V": V22, "E": E22, "sources": 256, "iters": ITERS,
                         "ms": round(ms, 2), "ms_per_iter": round(ms / ITERS, 3),
+                        "launches_per_run": 1, "cuda_graph": True,
+                        "autotuned": {"hot_rows": hot, "tile_columns": tile,
+                                      "ms_3_iters": {f"tile{w or 'whole'}_l2frac{f:g}": round(t, 3)
+                                                     for (w, f), t in tune_ms.items()}},
                         "edge_columns_per_s_G": round(E22 * 256 * ITERS / (ms * 1e-3) / 1e9, 1),
                         "gteps_equiv": round(E22 * ITERS / (ms * 1e-3) / 1e9, 3),
                         "row_bytes_frac": round(row_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4),
@@ -531,7 +545,6 @@ def batch_variants(args, stream):
                               "floor_bytes_frac": round(floor_bytes / (ms / ITERS * 1e-3) / 1e9 / peak, 4)}
     del R, G22, g22, P22
     torch.cuda.empty_cache()
-    res.update(many_graphs(stream))
     return res
 
 
@@ -760,7 +773,8 @@ def main():
             return statistics.median(time_runs(fn, 5, stream))
         res = {"many_graphs": lambda: many_graphs(stream, with_oracle=False), "spmv": lambda: spmv_row(stream),
                "bc": lambda: bc_row(stream), "bfs_grid": lambda: {"bfs_grid4096": bfs_grid_row(stream)},
-               "rmat16": lambda: {"rmat16": rmat16_row(stream, run)}}[args.row]()
+               "rmat16": lambda: {"rmat16": rmat16_row(stream, run)},
+               "ppr": lambda: ppr_row(stream)}[args.row]()
         print(json.dumps(res), flush=True)
         return
     res, ctx = bench_tocab(args, world, rank, local)

@@ -348,8 +348,21 @@ int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
  *   R'[v,j] = d * sum_{u->v} R[u,j] / out_degree[u] + [v == s_j] ((1-d) + d * D_j),
  *   D_j = sum of R[u,j] over dangling u.
  * The batch lives as an FP32 [V x n] row-major matrix.
- *   part == NULL : every iteration is one pull launch in which a warp reads whole rows of the
- *                  contribution matrix (one launch for the whole batch per iteration).
+ *   part == NULL : all iterations run as ONE persistent cooperative launch (one grid barrier
+ *                  per iteration), captured in a CUDA graph that later calls with the same output
+ *                  buffer, n, iters, damping and tuning replay.  The batch works in the graph's
+ *                  vertex numbering by out-degree (built on first use and kept with the graph):
+ *                  the rows of the sources with the most out-edges are one contiguous block.
+ *                  The columns run in tiles of 32, 64 or 128 (all iterations of one tile, then
+ *                  the next), or as whole rows; a lane group reads the tile's segment of a
+ *                  source row per in-edge, so a smaller tile lets the L2 hold more source rows
+ *                  (the source block sized to the cache of Sec. 3.1, without partial sums).
+ *                  Warps draw work from a queue: pieces of the rows with more than 2048
+ *                  in-edges, then runs of rows each walked as one in-edge stream.  Loads and
+ *                  stores of the first `hot` rows carry an L2 evict-last priority, every other
+ *                  row and the in-edge lists evict-first.  Tile width and `hot` come from
+ *                  tc_ppr_autotune when it has run, else 32 columns and half the rows the L2
+ *                  holds.
  *   part != NULL : TOCAB per column tile (Sec. 3.1): columns in tiles of 32; for each tile,
  *                  Alg. 4 over the partition's source blocks (size them so that W x 128 bytes
  *                  of a block's row segments fit in L2, e.g. l2_fraction = 1/88) into 32-wide
@@ -358,12 +371,38 @@ int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t source,
  *   sources : host int32[n], each in [0, V) (repeats allowed);  1 <= n <= 1024.
  *   params  : damping, iters, out_mem (R_out space), profile (stats->ms_total); init ignored.
  *   R_out   : float[V * n], R_out[v*n + j].
- * Device scratch: two [V x round_up(n,128)] FP32 matrices, allocated and freed per call.
+ * Device scratch: two [V x round_up(n,128)] FP32 matrices (part == NULL: kept with the graph
+ * for later calls with the same padded width; otherwise allocated and freed per call).
  * Synchronises the stream before returning.
- * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED (n out of range), TC_ERR_OOM, TC_ERR_CUDA.
+ * Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED (n out of range, or a renumbered partition),
+ * TC_ERR_OOM, TC_ERR_CUDA, TC_ERR_TIMEOUT (a grid barrier gave up after about a second).
  */
 int tc_ppr_batch(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t n,
                  const tc_pr_params *params, float *R_out, tc_pr_stats *stats, void *stream);
+
+/*
+ * tc_ppr_autotune -- times the persistent batch (part == NULL above) for this graph and batch
+ * width over its tile width (whole rows, 128, 64 or 32 columns) and the size of its evict-last
+ * block (0, 1/4, 1/2 or all of the rows of that width the L2 holds), on `sources` with
+ * params->iters capped at 3, and keeps the fastest with the graph for later tc_ppr_batch calls
+ * (no counterpart in the paper, which sizes its blocks from the cache size alone).
+ *   best_hot  : the chosen evict-last rows (may be NULL).
+ *   best_tile : the chosen tile width in columns, 0 for whole rows (may be NULL).
+ *   times     : float[16] or NULL: ms of each variant, tile-major (whole, 128, 64, 32) x
+ *               evict-last fraction (0, 1/4, 1/2, 1).
+ * Synchronises.  Errors: as tc_ppr_batch.
+ */
+int tc_ppr_autotune(tc_graph *g, const int32_t *sources, int32_t n, const tc_pr_params *params,
+                    int32_t *best_hot, int32_t *best_tile, float *times, void *stream);
+
+/*
+ * tc_ppr_set_tuning -- sets the persistent batch's schedule for this graph by hand, as
+ * tc_ppr_autotune would (no counterpart in the paper): hot = evict-last rows (clamped to what the L2 holds; -1: the default),
+ * tile = 0 (whole rows), 32, 64 or 128 columns (-1: the default).  Results do not depend on
+ * hot; the tile width changes how each row's in-edges are grouped for summation (rounding only).
+ * Errors: TC_ERR_INVALID_ARG.
+ */
+int tc_ppr_set_tuning(tc_graph *g, int32_t hot, int32_t tile);
 
 /* ---- betweenness centrality ----------------------------------------------------------------- */
 /*

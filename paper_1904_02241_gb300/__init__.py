@@ -23,7 +23,8 @@ from . import _lib as L
 from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
                    TC_MULTI_RESIDENT, TC_ORDER_NATURAL, TC_ORDER_OUTDEGREE, TC_PULL, TC_PUSH)
 
-__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "multigraph_load",
+__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "ppr_autotune", "ppr_set_tuning",
+           "multigraph_load",
            "pagerank_multi", "multi_autotune", "MultiGraph",
            "Graph", "Partition", "TocabError", "lib", "default_block_width", "set_device_memory_limit",
            "device_memory_held"]
@@ -310,6 +311,27 @@ def ppr_batch(graph: Graph, sources, damping: float = 0.85, iters: int = 20, out
     _check(L.load().tc_ppr_batch(graph.handle, part.handle if part is not None else None, src.data_ptr(), n,
                                  C.byref(pp), out.data_ptr(), C.byref(st), _stream(stream)), "tc_ppr_batch")
     return (out, st) if return_stats else out
+
+
+def ppr_set_tuning(graph: Graph, hot: int = -1, tile: int = -1):
+    """tc_ppr_set_tuning: the persistent batch's evict-last rows and tile width (0: whole rows;
+    -1: default)."""
+    _check(L.load().tc_ppr_set_tuning(graph.handle, int(hot), int(tile)), "tc_ppr_set_tuning")
+
+
+def ppr_autotune(graph: Graph, sources, damping: float = 0.85, iters: int = 3, stream=None):
+    """tc_ppr_autotune: time the persistent batch's tile widths and evict-last block sizes on these
+    sources; returns (hot rows, tile width (0: whole rows), {(tile width, L2 fraction): ms}) and
+    keeps the choice with the graph."""
+    src = torch.as_tensor(sources, dtype=torch.int32).contiguous().cpu()
+    pp = L.tc_pr_params(float(damping), int(iters), 0, L.TC_MEM_DEVICE, None, 0, 0, 0)
+    hot = C.c_int32()
+    tile = C.c_int32()
+    times = (C.c_float * 16)()
+    _check(L.load().tc_ppr_autotune(graph.handle, src.data_ptr(), src.numel(), C.byref(pp), C.byref(hot),
+                                    C.byref(tile), times, _stream(stream)), "tc_ppr_autotune")
+    keys = [(w, f) for w in (0, 128, 64, 32) for f in (0.0, 0.25, 0.5, 1.0)]
+    return hot.value, tile.value, dict(zip(keys, list(times)))
 
 
 class MultiGraph:

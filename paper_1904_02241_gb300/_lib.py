@@ -109,6 +109,9 @@ SIGNATURES = {
     "tc_bc": (C.c_int, [VP, VP, C.c_int32, C.c_int, VP, VP]),
     "tc_spmv": (C.c_int, [VP, VP, VP, VP, C.c_int, VP]),
     "tc_ppr_batch": (C.c_int, [VP, VP, VP, C.c_int32, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
+    "tc_ppr_autotune": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_pr_params), C.POINTER(C.c_int32),
+                                  C.POINTER(C.c_int32), VP, VP]),
+    "tc_ppr_set_tuning": (C.c_int, [VP, C.c_int32, C.c_int32]),
     "tc_multigraph_load": (C.c_int, [C.c_int32, VP, C.c_int32, C.c_int64, VP, VP, C.c_int, VP, C.POINTER(VP)]),
     "tc_multigraph_free": (None, [VP]),
     "tc_pagerank_multi": (C.c_int, [VP, C.POINTER(tc_pr_params), C.POINTER(tc_multi_params), VP,

@@ -160,8 +160,27 @@ struct tc_graph {
     tc::DevBuf ws_contrib, ws_scalars, ws_partials, ws_bits, ws_misc;
     tc::DevBuf ws_queue, ws_qcnt, ws_qpos, ws_scan;  // BFS push levels
     unsigned long long *h_counts = nullptr;          // pinned host words read after each BFS level
+    // vertex numbering by out-degree and G^T in it, built on first use by the PPR batch
+    bool ord_built = false;
+    int32_t ord_ni = 0;
+    tc::DevBuf ord_perm, ord_inv, ord_inv_outdeg, ord_rowptr, ord_colidx;
+    // the PPR batch's persistent launch: its buffers (for one padded column count ppr_np), the
+    // long rows' pieces, the autotuned hot block, and the captured launch with what it was built for
+    int32_t ppr_np = 0, ppr_nhubs = 0, ppr_npieces = 0;
+    int32_t ppr_hot = -1, ppr_tile = -1;  // evict-last source rows and tile width (-1: not tuned)
+    tc::DevBuf ppr_C, ppr_D, ppr_src_old, ppr_src, ppr_isrc, ppr_sync, ppr_hub_rows, ppr_hub_p0, ppr_pieces, ppr_Ppc,
+        ppr_hubcnt;
+    // the rows without the in-edges of the long ones, and the runs of rows the queue hands out
+    bool ppr_light_built = false;
+    int32_t ppr_nchunks = 0;
+    tc::DevBuf ppr_rowptr_l, ppr_colidx_l, ppr_islong, ppr_chunks;
+    cudaGraphExec_t ppr_exec = nullptr;
+    const void *ppr_key_out = nullptr;
+    int32_t ppr_key_n = -1, ppr_key_iters = -1, ppr_key_hot = -1, ppr_key_grid = -1, ppr_key_tile = -1;
+    float ppr_key_damping = -1.0f;
     ~tc_graph() {
         if (h_counts) cudaFreeHost(h_counts);
+        if (ppr_exec) cudaGraphExecDestroy(ppr_exec);
     }
 };
 
@@ -225,6 +244,60 @@ size_t merge_smem_bytes(int32_t k, int32_t B);   // dynamic shared memory of the
 size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed);  // ... of the one-accumulator merges
 // Launch the staged gather (+ long rows) writing p->partial from contributions `contrib`.
 int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, cudaStream_t s, int *launches);
+
+// The vertex numbering by out-degree (highest first, ties by ID, vertices without any edge last;
+// tc_partition.cu): perm[n] = old ID of new vertex n, inv = its inverse, inv_outdeg in the new
+// order, G^T renumbered (rp_new, ci_new; sources of a row in their old order), optionally the row
+// of every edge of it (row may be null), and ni = the vertices with some edge.  Synchronises.
+int order_by_outdegree(const tc_graph *g, cudaStream_t s, DevBuf *perm, DevBuf *inv, DevBuf *inv_outdeg,
+                       DevBuf *rp_new, DevBuf *ci_new, DevBuf *row, int32_t *ni);
+
+// L2 access-policy window over vertex values a kernel reads repeatedly (the block's values that
+// Sec. 3.1 sizes to the last-level cache).  For one call, the context's persisting set-aside is
+// raised to cover them (as far as the device allows), each launch carries a window that marks
+// hits on them persisting and misses streaming, so streamed data cannot evict them; at the end
+// the persisting lines are reset and the previous set-aside restored, after the stream has
+// drained.
+struct L2Window {
+    bool on = false;
+    size_t old_limit = 0, setaside = 0, max_window = 0;
+    cudaStream_t s = nullptr;
+    int begin(size_t want, cudaStream_t stream) {
+        int dev = 0, max_persist = 0, max_win = 0;
+        TC_CUDA(cudaGetDevice(&dev));
+        TC_CUDA(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev));
+        TC_CUDA(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+        if (max_persist <= 0 || max_win <= 0) return TC_OK;  // no set-aside: the call runs without
+        TC_CUDA(cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize));
+        setaside = want < (size_t)max_persist ? want : (size_t)max_persist;
+        max_window = (size_t)max_win;
+        s = stream;
+        TC_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, setaside));
+        on = true;
+        return TC_OK;
+    }
+    cudaAccessPolicyWindow window(const void *base, size_t bytes) const {
+        cudaAccessPolicyWindow w = {};
+        w.base_ptr = const_cast<void *>(base);
+        w.num_bytes = bytes < max_window ? bytes : max_window;
+        w.hitRatio = w.num_bytes > setaside ? (float)((double)setaside / (double)w.num_bytes) : 1.0f;
+        w.hitProp = cudaAccessPropertyPersisting;
+        w.missProp = cudaAccessPropertyStreaming;
+        return w;
+    }
+    int end() {
+        if (!on) return TC_OK;
+        on = false;
+        cudaError_t e = cudaStreamSynchronize(s);
+        cudaError_t e2 = cudaCtxResetPersistingL2Cache();
+        cudaError_t e3 = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
+        if (e == cudaSuccess) e = e2;
+        if (e == cudaSuccess) e = e3;
+        if (e != cudaSuccess) return fail(TC_ERR_CUDA, "L2 window: %s", cudaGetErrorString(e));
+        return TC_OK;
+    }
+    ~L2Window() { end(); }
+};
 
 // Rows of a CSR with more than `min_degree` edges, as a compact int32 list (ascending).
 int collect_hubs(const int32_t *rowptr, int64_t nrows, int32_t min_degree, DevBuf *list, int32_t *count,

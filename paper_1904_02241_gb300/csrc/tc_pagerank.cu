@@ -715,53 +715,6 @@ struct Timer {
     }
 };
 
-// L2 access-policy window over the vertex values an unstaged pull gather reads (the block's
-// contributions that Sec. 3.1 sizes to the last-level cache).  For one call, the context's
-// persisting set-aside is raised to cover them (as far as the device allows), each gather launch
-// carries a window that marks hits on them persisting and misses streaming, so the column-index
-// stream cannot evict them; at the end the persisting lines are reset and the previous set-aside
-// restored, after the stream has drained.
-struct L2Window {
-    bool on = false;
-    size_t old_limit = 0, setaside = 0, max_window = 0;
-    cudaStream_t s = nullptr;
-    int begin(size_t want, cudaStream_t stream) {
-        int dev = 0, max_persist = 0, max_win = 0;
-        TC_CUDA(cudaGetDevice(&dev));
-        TC_CUDA(cudaDeviceGetAttribute(&max_persist, cudaDevAttrMaxPersistingL2CacheSize, dev));
-        TC_CUDA(cudaDeviceGetAttribute(&max_win, cudaDevAttrMaxAccessPolicyWindowSize, dev));
-        if (max_persist <= 0 || max_win <= 0) return TC_OK;  // no set-aside: the call runs without
-        TC_CUDA(cudaDeviceGetLimit(&old_limit, cudaLimitPersistingL2CacheSize));
-        setaside = want < (size_t)max_persist ? want : (size_t)max_persist;
-        max_window = (size_t)max_win;
-        s = stream;
-        TC_CUDA(cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, setaside));
-        on = true;
-        return TC_OK;
-    }
-    cudaAccessPolicyWindow window(const void *base, size_t bytes) const {
-        cudaAccessPolicyWindow w = {};
-        w.base_ptr = const_cast<void *>(base);
-        w.num_bytes = bytes < max_window ? bytes : max_window;
-        w.hitRatio = w.num_bytes > setaside ? (float)((double)setaside / (double)w.num_bytes) : 1.0f;
-        w.hitProp = cudaAccessPropertyPersisting;
-        w.missProp = cudaAccessPropertyStreaming;
-        return w;
-    }
-    int end() {
-        if (!on) return TC_OK;
-        on = false;
-        cudaError_t e = cudaStreamSynchronize(s);
-        cudaError_t e2 = cudaCtxResetPersistingL2Cache();
-        cudaError_t e3 = cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, old_limit);
-        if (e == cudaSuccess) e = e2;
-        if (e == cudaSuccess) e = e3;
-        if (e != cudaSuccess) return fail(TC_ERR_CUDA, "L2 window: %s", cudaGetErrorString(e));
-        return TC_OK;
-    }
-    ~L2Window() { end(); }
-};
-
 static int occupancy_grid(const void *kernel, int threads, size_t smem, int64_t work_ctas, int *grid) {
     DeviceCaps caps;
     TC_TRY(device_caps(&caps));

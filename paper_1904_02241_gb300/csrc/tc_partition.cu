@@ -237,11 +237,14 @@ static int log2_ceil(int64_t x) {
 // Renumber the vertices by out-degree (highest first, ties by ID) and build G^T in the new
 // numbering (rp_new, ci_new), the permutation p->perm (new -> old) and the out-degree
 // reciprocals p->inv_outdeg in the new order.  Vertices with out-edges get the IDs [0, nz_out).
-static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, int grid, DevBuf *rp_new, DevBuf *ci_new,
-                                 DevBuf *row, tc_part *p) {
+int order_by_outdegree(const tc_graph *g, cudaStream_t s, DevBuf *perm, DevBuf *inv, DevBuf *inv_outdeg,
+                       DevBuf *rp_new, DevBuf *ci_new, DevBuf *row, int32_t *ni) {
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    const int grid = caps.sms * 8;
     const int32_t V = g->V;
     const int64_t E = g->E;
-    DevBuf key, val, kout, ktmp, vtmp, inv, deg, niso;
+    DevBuf key, val, kout, ktmp, vtmp, deg, niso, row_local;
     TC_TRY(niso.alloc(16));
     TC_CUDA(cudaMemsetAsync(niso.p, 0, 4, s));
     TC_TRY(key.alloc((size_t)V * 4));
@@ -249,14 +252,14 @@ static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, int grid, De
     TC_TRY(kout.alloc((size_t)V * 4));
     TC_TRY(ktmp.alloc((size_t)V * 4));
     TC_TRY(vtmp.alloc((size_t)V * 4));
-    TC_TRY(p->perm.alloc((size_t)V * 4));
-    TC_TRY(p->inv_outdeg.alloc((size_t)V * 4 + 256));
+    TC_TRY(perm->alloc((size_t)V * 4));
+    TC_TRY(inv_outdeg->alloc((size_t)V * 4 + 256));
     k_order_keys<<<grid, 256, 0, s>>>(g->out_rowptr.as<int32_t>(), g->in_rowptr.as<int32_t>(), V, g->max_out_degree,
                                       key.as<int32_t>(), val.as<int32_t>(), niso.as<int32_t>());
     TC_LAUNCH_CHECK();
     int32_t h_iso = 0;
     TC_CUDA(cudaMemcpyAsync(&h_iso, niso.p, 4, cudaMemcpyDeviceToHost, s));
-    TC_TRY(stable_bucket_sort(key.as<int32_t>(), val.as<int32_t>(), kout.as<int32_t>(), p->perm.as<int32_t>(),
+    TC_TRY(stable_bucket_sort(key.as<int32_t>(), val.as<int32_t>(), kout.as<int32_t>(), perm->as<int32_t>(),
                               ktmp.as<int32_t>(), vtmp.as<int32_t>(), V, 1, log2_ceil((int64_t)g->max_out_degree + 2),
                               s));  // synchronises: h_iso is in
     key.release();
@@ -264,26 +267,36 @@ static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, int grid, De
     kout.release();
     ktmp.release();
     vtmp.release();
-    TC_TRY(inv.alloc((size_t)V * 4));
+    TC_TRY(inv->alloc((size_t)V * 4));
     TC_TRY(deg.alloc(((size_t)V + 1) * 4));
-    k_order_apply<<<grid, 256, 0, s>>>(p->perm.as<int32_t>(), g->in_rowptr.as<int32_t>(), g->inv_outdeg.as<float>(), V,
-                                       inv.as<int32_t>(), deg.as<int32_t>(), p->inv_outdeg.as<float>());
+    k_order_apply<<<grid, 256, 0, s>>>(perm->as<int32_t>(), g->in_rowptr.as<int32_t>(), g->inv_outdeg.as<float>(), V,
+                                       inv->as<int32_t>(), deg.as<int32_t>(), inv_outdeg->as<float>());
     TC_LAUNCH_CHECK();
     TC_TRY(rp_new->alloc(((size_t)V + 1) * 4));
     TC_TRY(scan_i32(deg.as<int32_t>(), (int64_t)V + 1, rp_new->as<int32_t>(), s));
     deg.release();
     TC_TRY(ci_new->alloc((size_t)(E > 0 ? E : 1) * 4));
     if (E > 0) {
-        TC_TRY(row->alloc((size_t)E * 4));  // the row of every edge of the renumbered G^T (kept for the blocking)
-        TC_TRY(expand_rows(rp_new->as<int32_t>(), V, row->as<int32_t>(), s));
-        k_order_edges<<<grid, 256, 0, s>>>(row->as<int32_t>(), rp_new->as<int32_t>(), p->perm.as<int32_t>(),
-                                           g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), inv.as<int32_t>(), E,
+        DevBuf *r = row ? row : &row_local;  // the row of every edge of the renumbered G^T
+        TC_TRY(r->alloc((size_t)E * 4));
+        TC_TRY(expand_rows(rp_new->as<int32_t>(), V, r->as<int32_t>(), s));
+        k_order_edges<<<grid, 256, 0, s>>>(r->as<int32_t>(), rp_new->as<int32_t>(), perm->as<int32_t>(),
+                                           g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), inv->as<int32_t>(), E,
                                            ci_new->as<int32_t>());
         TC_LAUNCH_CHECK();
-        TC_CUDA(cudaStreamSynchronize(s));
     }
-    p->nz_out = (int32_t)((int64_t)V - g->num_dangling);
-    p->ni = V - h_iso;
+    TC_CUDA(cudaStreamSynchronize(s));
+    *ni = V - h_iso;
+    return TC_OK;
+}
+
+static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, DevBuf *rp_new, DevBuf *ci_new, DevBuf *row,
+                                 tc_part *p) {
+    DevBuf inv;
+    int32_t ni = 0;
+    TC_TRY(order_by_outdegree(g, s, &p->perm, &inv, &p->inv_outdeg, rp_new, ci_new, row, &ni));
+    p->nz_out = (int32_t)((int64_t)g->V - g->num_dangling);
+    p->ni = ni;
     p->order = TC_ORDER_OUTDEGREE;
     return TC_OK;
 }
@@ -356,7 +369,7 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->nz_out = (int32_t)((int64_t)V - g->num_dangling);  // vertices with out-edges
     p->ni = V;
     if (order == TC_ORDER_OUTDEGREE && V > 0) {
-        TC_TRY(renumber_by_outdegree(g, s, caps.sms * 8, &rel_rowptr, &rel_colidx, &rows_in, p));
+        TC_TRY(renumber_by_outdegree(g, s, &rel_rowptr, &rel_colidx, &rows_in, p));
         rp = rel_rowptr.as<int32_t>();
         ci = rel_colidx.as<int32_t>();
     }

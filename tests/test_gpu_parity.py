@@ -594,3 +594,70 @@ def test_ppr_batch_long_rows_are_split(T, tocab):
     want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
     for j in range(len(srcs)):
         assert l1_rel(R[:, j], want[:, j]) <= TOL, j
+
+
+def test_ppr_batch_persistent_replay_and_autotune(T):
+    """The persistent batch is captured once and replayed: a second call with other sources into
+    the same output must give that batch's answer, and after the autotuner has picked the hot
+    block and launch width the answer is unchanged bit for bit."""
+    g = GRAPHS["plc"]
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    out = torch.empty((g.V, 40), dtype=torch.float32, device="cuda")
+    rng = np.random.default_rng(3)
+    a = rng.integers(0, g.V, 40).astype(np.int32)
+    b = rng.integers(0, g.V, 40).astype(np.int32)
+    for srcs in (a, b, a):
+        R = T.ppr_batch(G, srcs, iters=20, out=out).cpu().numpy()
+        want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
+        for j in range(len(srcs)):
+            assert l1_rel(R[:, j], want[:, j]) <= TOL, j
+    first = T.ppr_batch(G, a, iters=20, out=out).cpu().clone()
+    hot, tile, times = T.ppr_autotune(G, a)
+    assert hot >= 0 and tile in (0, 32, 64, 128) and min(times.values()) > 0
+    again = T.ppr_batch(G, a, iters=20, out=out).cpu()
+    assert torch.equal(first, again)  # the schedule changes no result
+
+
+@pytest.mark.parametrize("tile", [0, 128, 64, 32])
+@pytest.mark.parametrize("name,n", [("rmat12", 256), ("plc", 70), ("er", 33), ("isolated", 5)])
+def test_ppr_batch_every_schedule(T, tile, name, n):
+    """Every tile width of the persistent batch (0: whole rows), with and without evict-last
+    rows, gives the oracle's answer, and all schedules give bit-identical results (each row's sum
+    has a fixed order whatever the tiling)."""
+    g = GRAPHS[name]
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    rng = np.random.default_rng(n + tile)
+    srcs = rng.integers(0, g.V, n).astype(np.int32)
+    want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
+    outs = []
+    for hot in (0, g.V // 3):
+        T.ppr_set_tuning(G, hot=hot, tile=tile)
+        R = T.ppr_batch(G, srcs, iters=20).cpu().numpy()
+        for j in range(n):
+            assert l1_rel(R[:, j], want[:, j]) <= TOL, (hot, j)
+        outs.append(R)
+    assert np.array_equal(outs[0], outs[1])
+    T.ppr_set_tuning(G)
+
+
+def test_ppr_batch_schedules_agree_on_long_rows(T):
+    """A hub whose in-edges are cut into pieces, under every tile width."""
+    g = gg.star(6000)
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    srcs = np.array([0, 1, 77, 5999, 0], np.int32)
+    want = oracle.ppr_pull(g.V, rp, ci, srcs, iters=20)
+    for tile in (0, 128, 64, 32):
+        T.ppr_set_tuning(G, hot=-1, tile=tile)
+        R = T.ppr_batch(G, srcs, iters=20).cpu().numpy()
+        for j in range(len(srcs)):
+            assert l1_rel(R[:, j], want[:, j]) <= TOL, (tile, j)
+
+
+def test_ppr_set_tuning_rejects(T):
+    G = _load(T, GRAPHS["rmat12"])
+    for hot, tile in ((-2, 0), (0, 48), (0, 256)):
+        with pytest.raises(T.TocabError):
+            T.ppr_set_tuning(G, hot=hot, tile=tile)

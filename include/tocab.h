@@ -146,6 +146,10 @@ typedef struct tc_part_params {
                                  memory whenever W fits (W <= about 41K sources, W % 32 == 0),
                                  -1 = never, 1 = require it (TC_ERR_UNSUPPORTED if W does not fit) */
     int32_t vertex_order;     /* pull only: TC_ORDER_NATURAL (0) or TC_ORDER_OUTDEGREE (1), below */
+    int32_t direct_blocks;    /* renumbered pull only: local rows with a single edge whose source
+                                 lies in the first `direct_blocks` blocks leave the blocked CSR
+                                 (direct pieces, below); 0 = none, -1 = the blocks whose
+                                 contributions fill at most 1/8 of the L2 */
 } tc_part_params;
 
 /*
@@ -161,6 +165,16 @@ typedef struct tc_part_params {
  * form.  Everything the caller sees stays
  * in the graph's own numbering: PageRank takes `init` and returns ranks by original ID.
  * tc_part_export reports the renumbered structure and tc_part_export_order the numbering.
+ * Direct pieces: in a renumbered pull partition most (block, row) pieces of the first blocks -
+ * the sources with the most out-edges - hold a single edge.  Such a piece's partial sum is
+ * just its source's contribution, so it leaves the blocked CSR (and the gather) and the merge
+ * adds that contribution itself, read from the contribution array (those blocks' values stay
+ * in L2): 4 bytes of source ID and 2 of local target instead of a staged edge, a row start,
+ * a partial sum written and read, and its 2-byte ID.  tc_part_export then reports the
+ * blocked CSR without them (num_direct in tc_part_info counts them); with direct_blocks = 0 (the
+ * default) it is the paper's blocking exactly.  Measured on R-MAT 24 the option is slower: the
+ * gather gains 7-14% but the merge's random reads of the contribution array and its atomics on
+ * a target's adjacent pieces cost more (see the design notes), so it stays off by default.
  * BFS and the PPR batch do not take renumbered partitions (TC_ERR_UNSUPPORTED), and push
  * partitions cannot be renumbered (TC_ERR_UNSUPPORTED).
  */
@@ -192,6 +206,8 @@ typedef struct tc_part_info {
     int32_t num_ranges;       /* merge ranges (CTAs of the merge) */
     int32_t num_tiles;        /* CTAs of the staged gather (0 if not staged) */
     int32_t num_sources;      /* vertices with out-edges (TC_ORDER_OUTDEGREE: they come first) */
+    int32_t direct_blocks;    /* blocks whose single-edge pieces are direct (0: none) */
+    int64_t num_direct;       /* direct pieces (not in num_rows / num_edges) */
 } tc_part_info;
 /* Shape of a partition: B and W of Sec. 3.1, R local rows (Fig. 4), k of Fig. 5.  Errors:
  * TC_ERR_INVALID_ARG for a NULL argument. */

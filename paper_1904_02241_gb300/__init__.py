@@ -135,6 +135,8 @@ class Partition:
         self.num_ranges = info.num_ranges
         self.num_tiles = info.num_tiles
         self.num_sources = info.num_sources
+        self.direct_blocks = info.direct_blocks
+        self.num_direct = info.num_direct
 
     @property
     def handle(self):
@@ -196,13 +198,14 @@ def graph_load_csr(rowptr, colidx, V: int | None = None, stream=None) -> Graph:
 
 def tocab_partition(graph: Graph, dir: int = L.TC_PULL, num_blocks: int = 0, l2_fraction: float = 0.0,
                     merge_range: int = 0, hub_degree: int = 0, block_policy: str = "l2", smem_stage: int = 0,
-                    order: str = "natural", stream=None) -> Partition:
+                    order: str = "natural", direct_blocks: int = 0, stream=None) -> Partition:
     """tc_tocab_partition: static 1D blocking.  num_blocks = 0 derives W from the L2 size
     (block_policy="l2", the paper's rule) or from one CTA's shared memory ("smem").
-    order="outdegree" renumbers the vertices by out-degree before cutting the blocks (pull only)."""
+    order="outdegree" renumbers the vertices by out-degree before cutting the blocks (pull only);
+    its single-edge pieces of the first direct_blocks blocks (0: none, -1: automatic) are direct."""
     policy = {"l2": L.TC_BLOCKS_L2, "smem": L.TC_BLOCKS_SMEM}[block_policy]
     vo = {"natural": L.TC_ORDER_NATURAL, "outdegree": L.TC_ORDER_OUTDEGREE}[order]
-    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree, policy, smem_stage, vo)
+    pp = L.tc_part_params(l2_fraction, merge_range, hub_degree, policy, smem_stage, vo, direct_blocks)
     h = C.c_void_p()
     _check(L.load().tc_tocab_partition(graph.handle, dir, num_blocks, C.byref(pp), _stream(stream), C.byref(h)),
            "tc_tocab_partition")

@@ -33,7 +33,8 @@ TC_BLOCKS_SMEM = 1
 
 class tc_part_params(C.Structure):
     _fields_ = [("l2_fraction", C.c_float), ("merge_range", C.c_int32), ("hub_degree", C.c_int32),
-                ("block_policy", C.c_int32), ("smem_stage", C.c_int32), ("vertex_order", C.c_int32)]
+                ("block_policy", C.c_int32), ("smem_stage", C.c_int32), ("vertex_order", C.c_int32),
+                ("direct_blocks", C.c_int32)]
 
 
 TC_ORDER_NATURAL = 0
@@ -45,7 +46,7 @@ class tc_part_info(C.Structure):
                 ("num_rows", C.c_int64), ("num_edges", C.c_int64), ("merge_range", C.c_int32),
                 ("num_hubs", C.c_int32), ("staged", C.c_int32), ("staged_edges", C.c_int64),
                 ("vertex_order", C.c_int32), ("num_ranges", C.c_int32), ("num_tiles", C.c_int32),
-                ("num_sources", C.c_int32)]
+                ("num_sources", C.c_int32), ("direct_blocks", C.c_int32), ("num_direct", C.c_int64)]
 
 
 TC_MERGE_FIXED = 0

@@ -64,6 +64,13 @@ __device__ __forceinline__ void bulk_store_wait_all() { asm volatile("cp.async.b
 // Orders this thread's generic-proxy shared-memory writes before later bulk-copy reads.
 __device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
+// Programmatic dependent launch: a kernel launched with the programmatic stream serialization
+// attribute may start while the previous kernel in the stream finishes; pdl_wait() blocks until
+// that kernel has completed and its writes are visible (a no-op without the attribute), and
+// pdl_trigger() lets the next kernel start launching.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 
 // Sum over the block in a fixed tree order (deterministic for a fixed launch shape).
 // All threads must call it; the result is valid in every thread.

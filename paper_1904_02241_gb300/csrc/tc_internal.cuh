@@ -102,6 +102,17 @@ struct DevBuf {
         return TC_OK;
     }
     template <class T> T *as() const { return static_cast<T *>(p); }
+    void swap(DevBuf &o) {
+        void *tp = p;
+        p = o.p;
+        o.p = tp;
+        const size_t tb = bytes;
+        bytes = o.bytes;
+        o.bytes = tb;
+        const int td = device;
+        device = o.device;
+        o.device = td;
+    }
 };
 
 struct DeviceCaps {
@@ -225,6 +236,12 @@ struct tc_part {
     tc::DevBuf inv_outdeg;      // float[V] in the new numbering (renumbered only)
     tc::DevBuf rstart;          // int32[nranges+1]: first vertex of every merge range (renumbered
                                 // only; natural partitions use ranges [j*k, (j+1)*k))
+    // ---- direct pieces (renumbered pull): single-edge pieces of the first Bd blocks ----
+    int32_t Bd = 0;             // blocks whose single-edge pieces are direct
+    int64_t ndirect = 0;
+    tc::DevBuf dir_off;         // int32[nranges+1]: first direct piece of every merge range
+    tc::DevBuf dir_u;           // int32[ndirect + 8]: source (new ID), sorted by target
+    tc::DevBuf dir_id16;        // uint16[ndirect + 8]: target minus its range's first vertex
     ~tc_part() {
         delete[] h_blk_rows;
         delete[] h_blk_edges;

@@ -31,6 +31,12 @@ struct UpdateArgs {
     int32_t ni;             // renumbered: vertices [ni, V) have no edge at all (else ni = V)
     int *err;               // sticky error flag of bounded device waits
     unsigned *queue;        // work queue of the persistent merge (zero between launches)
+    // direct pieces of the partition (null when it has none): per merge range j, pieces
+    // [dir_off[j], dir_off[j+1]) add cur[dir_u[i]] to vertex rstart[j] + dir_id16[i]
+    const int32_t *dir_off;
+    const int32_t *dir_u;
+    const uint16_t *dir_id16;
+    const float *cur;       // the contributions the gather read
 };
 
 __device__ __forceinline__ float spread_of(const UpdateArgs &u) {
@@ -268,6 +274,28 @@ __global__ void __launch_bounds__(MG_THREADS) k_pull_merge_ordered(const float *
             __syncwarp();
         }
     }
+    if (u.dir_off) {  // direct pieces, 32 per warp step; their targets ascend, so equal targets
+                      // are adjacent lanes: a segmented sum, then the segment's last lane adds
+        const int32_t d0 = __ldg(u.dir_off + j), d1 = __ldg(u.dir_off + j + 1);
+        for (int32_t c = d0 + warp * 32; c < d1; c += MG_WARPS * 32) {
+            const int32_t i = c + lane;
+            int32_t id = -1;
+            float v = 0.0f;
+            if (i < d1) {
+                id = (int32_t)__ldg(u.dir_id16 + i);
+                v = __ldg(u.cur + __ldg(u.dir_u + i));
+            }
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const float y = __shfl_up_sync(0xffffffffu, v, d);
+                const int32_t yid = __shfl_up_sync(0xffffffffu, id, d);
+                if (lane >= d && yid == id) v += y;
+            }
+            const int32_t nid = __shfl_down_sync(0xffffffffu, id, 1);
+            if (id >= 0 && (lane == 31 || nid != id)) mine[id] += v;
+            __syncwarp();
+        }
+    }
     __syncthreads();
     const float spread = spread_of(u);
     float dsum = 0.0f;
@@ -363,6 +391,9 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
                                                                      int32_t nranges, UpdateArgs u) {
     static_assert(MODE == 2 || MODE == 3, "two- or three-part fixed point");
     constexpr int NACC = MODE;
+    // launched programmatically after the gather, whose partial sums it reads
+    pdl_trigger();
+    pdl_wait();
     extern __shared__ __align__(16) unsigned char msm[];
     int32_t *acc_hi = reinterpret_cast<int32_t *>(msm);  // fixed point: NACC arrays of [k]
     int32_t *acc_mid = acc_hi + k;                       // MODE 3 only
@@ -524,6 +555,43 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
                 for (int e = 0; e < MG_GRAN; ++e) {
                     const bool ok = (valid[q] >> e) & 1u;
                     const int32_t id = ok ? id8[e] : dummy;
+                    const float x = ok ? x8[e] : 0.0f;
+                    if (MODE == 2) {
+                        int32_t h, lw;
+                        fx_split2(x * scalef, h, lw);
+                        atomicAdd(acc_hi + id, h);
+                        atomicAdd(acc_lo + id, lw);
+                    } else {
+                        int32_t h, md, lw;
+                        fx_split3(x * scalef, h, md, lw);
+                        if (h) atomicAdd(acc_hi + id, h);
+                        atomicAdd(acc_mid + id, md);
+                        atomicAdd(acc_lo + id, lw);
+                    }
+                }
+            }
+        }
+        if (u.dir_off) {  // the range's direct pieces: their sources' contributions, read here
+            const int32_t d0 = __ldg(u.dir_off + j), d1 = __ldg(u.dir_off + j + 1);
+            const int32_t f0 = d0 & ~(MG_GRAN - 1);
+            const int32_t ng = d1 > d0 ? (d1 - f0 + MG_GRAN - 1) / MG_GRAN : 0;
+            for (int32_t gi = tid; gi < ng; gi += MG_THREADS) {
+                const int32_t f = f0 + gi * MG_GRAN;
+                const int32_t a = d0 - f > 0 ? d0 - f : 0;              // first valid offset
+                const int32_t z = d1 - f < MG_GRAN ? d1 - f : MG_GRAN;  // end offset
+                const uint32_t valid = (0xFFu >> (MG_GRAN - z)) & (0xFFu << a);
+                const int4 s0 = __ldg(reinterpret_cast<const int4 *>(u.dir_u + f));
+                const int4 s1 = __ldg(reinterpret_cast<const int4 *>(u.dir_u + f) + 1);
+                const uint4 iv = __ldg(reinterpret_cast<const uint4 *>(u.dir_id16 + f));
+                const int32_t src[MG_GRAN] = {s0.x, s0.y, s0.z, s0.w, s1.x, s1.y, s1.z, s1.w};
+                float x8[MG_GRAN];
+#pragma unroll
+                for (int e = 0; e < MG_GRAN; ++e) x8[e] = ((valid >> e) & 1u) ? __ldg(u.cur + src[e]) : 0.0f;
+                const uint32_t w[4] = {iv.x, iv.y, iv.z, iv.w};
+#pragma unroll
+                for (int e = 0; e < MG_GRAN; ++e) {
+                    const bool ok = (valid >> e) & 1u;
+                    const int32_t id = ok ? (int32_t)((w[e >> 1] >> (16 * (e & 1))) & 0xFFFFu) : dummy;
                     const float x = ok ? x8[e] : 0.0f;
                     if (MODE == 2) {
                         int32_t h, lw;
@@ -878,6 +946,11 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     u.ni = renumbered ? part->ni : V;
     u.err = st.err;
     u.queue = st.queue;
+    const bool direct = part && part->ndirect > 0;
+    u.dir_off = direct ? part->dir_off.as<int32_t>() : nullptr;
+    u.dir_u = direct ? part->dir_u.as<int32_t>() : nullptr;
+    u.dir_id16 = direct ? part->dir_id16.as<uint16_t>() : nullptr;
+    u.cur = nullptr;
 
     // the window applies to the unstaged pull gathers (the staged one copies its block's values
     // to shared memory)
@@ -912,6 +985,7 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
         u.D_next = st.D + ((it + 1) & 1);
         u.rank_out = last ? st.rank_dev : nullptr;
         u.contrib_next = push ? st.contrib[0] : st.contrib[(it + 1) & 1];
+        u.cur = cur;
         Timer t1;
         TC_TRY(t1.begin(pp->profile != 0, s, &ms_gather));
         LbArgs lb;
@@ -965,14 +1039,27 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
                     k_pull_merge_ordered<<<g_merge, MG_THREADS, merge_smem, s>>>(
                         part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
                         part->B, part->k, rst, u);
-                else if (merge_fixed_parts(part->B) == 2)
-                    k_pull_merge_atomic<2><<<g_merge, MG_THREADS, merge_smem, s>>>(
-                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->merge_gpre.as<int32_t>(), part->B, part->k, rst, part->nranges, u);
-                else
-                    k_pull_merge_atomic<3><<<g_merge, MG_THREADS, merge_smem, s>>>(
-                        part->partial.as<float>(), part->id_map.as<int32_t>(), i16, part->merge_offT.as<int32_t>(),
-                        part->merge_gpre.as<int32_t>(), part->B, part->k, rst, part->nranges, u);
+                else {
+                    cudaLaunchConfig_t cfg = {};
+                    cfg.gridDim = dim3(g_merge);
+                    cfg.blockDim = dim3(MG_THREADS);
+                    cfg.dynamicSmemBytes = merge_smem;
+                    cfg.stream = s;
+                    cudaLaunchAttribute attr[1];
+                    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+                    attr[0].val.programmaticStreamSerializationAllowed = 1;
+                    cfg.attrs = attr;
+                    cfg.numAttrs = 1;
+                    const float *pa = part->partial.as<float>();
+                    const int32_t *im = part->id_map.as<int32_t>(), *ot = part->merge_offT.as<int32_t>(),
+                                  *gp = part->merge_gpre.as<int32_t>();
+                    if (merge_fixed_parts(part->B) == 2)
+                        TC_CUDA(cudaLaunchKernelEx(&cfg, k_pull_merge_atomic<2>, pa, im, i16, ot, gp, part->B, part->k,
+                                                   rst, part->nranges, u));
+                    else
+                        TC_CUDA(cudaLaunchKernelEx(&cfg, k_pull_merge_atomic<3>, pa, im, i16, ot, gp, part->B, part->k,
+                                                   rst, part->nranges, u));
+                }
             }
             TC_LAUNCH_CHECK();
             ++launches;

@@ -301,6 +301,146 @@ static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, DevBuf *rp_n
     return TC_OK;
 }
 
+// ---------------------------------------------------------------------------------------------
+// Direct pieces.  Edge e of the blocked CSR alone forms its local row when it starts a row and
+// the next edge starts one too; in the first Bd blocks (edges below e_cut) such pieces leave the
+// CSR.  keep[e] = 0 marks them; keep[E] = 0 closes the scan.
+// ---------------------------------------------------------------------------------------------
+__global__ void k_direct_keep(const uint8_t *head, int64_t E, int64_t e_cut, int32_t *keep) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e <= E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (e == E) {
+            keep[e] = 0;
+            continue;
+        }
+        const bool single = head[e] && (e + 1 == E || head[e + 1]);
+        keep[e] = (single && e < e_cut) ? 0 : 1;
+    }
+}
+
+// Kept edges move to pos[e]; dropped edge e becomes direct piece e - pos[e] (target, source).
+__global__ void k_direct_split(const int32_t *colidx, const int32_t *rows_sorted, const int32_t *keep,
+                               const int32_t *pos, int64_t E, int32_t *colidx_new, int32_t *dv, int32_t *du) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < E; e += (int64_t)gridDim.x * blockDim.x) {
+        if (keep[e]) {
+            colidx_new[pos[e]] = colidx[e];
+        } else {
+            const int64_t d = e - pos[e];
+            dv[d] = rows_sorted[e];
+            du[d] = colidx[e];
+        }
+    }
+}
+
+// rkeep[r] = whether local row r stays (its first edge is kept); rkeep[R] = 0.
+__global__ void k_direct_rkeep(const int32_t *rowptr, int64_t R, const int32_t *keep, int32_t *rkeep) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r <= R; r += (int64_t)gridDim.x * blockDim.x)
+        rkeep[r] = r < R ? keep[rowptr[r]] : 0;
+}
+
+__global__ void k_direct_rows(const int32_t *rowptr, const int32_t *id_map, int64_t R, const int32_t *rkeep,
+                              const int32_t *rpos, const int32_t *pos, int32_t *rowptr_new, int32_t *id_map_new) {
+    for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < R; r += (int64_t)gridDim.x * blockDim.x) {
+        if (!rkeep[r]) continue;
+        const int32_t nr = rpos[r];
+        rowptr_new[nr] = pos[rowptr[r]];
+        id_map_new[nr] = id_map[r];
+    }
+}
+
+// dir_off[j] = first direct piece whose target is >= rstart[j] (targets sorted); [nranges] = n.
+__global__ void k_direct_off(const int32_t *dv, int64_t n, const int32_t *rstart, int32_t nranges, int32_t *dir_off) {
+    for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j <= nranges; j += gridDim.x * blockDim.x) {
+        if (j == nranges) {
+            dir_off[j] = (int32_t)n;
+            continue;
+        }
+        const int32_t want = rstart[j];
+        int64_t lo = 0, hi = n;
+        while (lo < hi) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (dv[mid] < want) lo = mid + 1; else hi = mid;
+        }
+        dir_off[j] = (int32_t)lo;
+    }
+}
+
+// Take the single-edge pieces of the first Bd blocks out of the blocked CSR (rowptr, id_map,
+// colidx, block bounds and their host copies are replaced) into the direct arrays, sorted by
+// target and indexed per merge range (rstart).  head / rows_sorted describe the current CSR.
+static int split_direct(tc_part *p, int32_t Bd, const uint8_t *head, const int32_t *rows_sorted,
+                        const int32_t *rstart, DevBuf &blk_rows, DevBuf &blk_edges, cudaStream_t s, int grid) {
+    const int64_t E = p->E, R = p->R;
+    const int32_t B = p->B;
+    const int64_t e_cut = p->h_blk_edges[Bd];
+    DevBuf keep, pos;
+    TC_TRY(keep.alloc(((size_t)E + 1) * 4));
+    TC_TRY(pos.alloc(((size_t)E + 1) * 4));
+    k_direct_keep<<<grid, 256, 0, s>>>(head, E, e_cut, keep.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32(keep.as<int32_t>(), E + 1, pos.as<int32_t>(), s));
+    int32_t En = 0;
+    TC_CUDA(cudaMemcpyAsync(&En, pos.as<int32_t>() + E, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    const int64_t Nd = E - En;
+    p->Bd = Bd;
+    p->ndirect = Nd;
+    if (Nd == 0) return TC_OK;
+    DevBuf col_new, dv, du;
+    TC_TRY(col_new.alloc((size_t)(En > 0 ? En : 1) * 4));
+    TC_TRY(dv.alloc((size_t)Nd * 4));
+    TC_TRY(du.alloc((size_t)Nd * 4));
+    k_direct_split<<<grid, 256, 0, s>>>(p->colidx.as<int32_t>(), rows_sorted, keep.as<int32_t>(), pos.as<int32_t>(), E,
+                                        col_new.as<int32_t>(), dv.as<int32_t>(), du.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    // rows
+    DevBuf rkeep, rpos, rp_new, im_new;
+    TC_TRY(rkeep.alloc(((size_t)R + 1) * 4));
+    TC_TRY(rpos.alloc(((size_t)R + 1) * 4));
+    k_direct_rkeep<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), R, keep.as<int32_t>(), rkeep.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(scan_i32(rkeep.as<int32_t>(), R + 1, rpos.as<int32_t>(), s));
+    int32_t Rn = 0;
+    TC_CUDA(cudaMemcpyAsync(&Rn, rpos.as<int32_t>() + R, 4, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    TC_TRY(rp_new.alloc(((size_t)Rn + 1) * 4));
+    TC_TRY(im_new.alloc(((size_t)Rn + 8) * 4));
+    TC_CUDA(cudaMemsetAsync(im_new.p, 0, ((size_t)Rn + 8) * 4, s));
+    k_direct_rows<<<grid, 256, 0, s>>>(p->rowptr.as<int32_t>(), p->id_map.as<int32_t>(), R, rkeep.as<int32_t>(),
+                                       rpos.as<int32_t>(), pos.as<int32_t>(), rp_new.as<int32_t>(), im_new.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_CUDA(cudaMemcpyAsync(rp_new.as<int32_t>() + Rn, &En, 4, cudaMemcpyHostToDevice, s));
+    p->colidx.swap(col_new);
+    p->rowptr.swap(rp_new);
+    p->id_map.swap(im_new);
+    p->E = En;
+    p->R = Rn;
+    k_block_bounds<<<(B + 256) / 256, 256, 0, s>>>(p->colidx.as<int32_t>(), p->rowptr.as<int32_t>(), En, Rn, p->W, B,
+                                                   blk_edges.as<int64_t>(), blk_rows.as<int64_t>());
+    TC_LAUNCH_CHECK();
+    TC_CUDA(cudaMemcpyAsync(p->h_blk_rows, blk_rows.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(p->h_blk_edges, blk_edges.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToHost, s));
+    TC_CUDA(cudaMemcpyAsync(p->blk_rows_dev.p, blk_rows.p, ((size_t)B + 1) * 8, cudaMemcpyDeviceToDevice, s));
+    // the direct pieces by target (stable: block order within a target), then per merge range
+    DevBuf dvs, dus, kt, vt;
+    TC_TRY(dvs.alloc((size_t)Nd * 4));
+    TC_TRY(p->dir_u.alloc(((size_t)Nd + 8) * 4));
+    TC_TRY(kt.alloc((size_t)Nd * 4));
+    TC_TRY(vt.alloc((size_t)Nd * 4));
+    TC_CUDA(cudaMemsetAsync(p->dir_u.p, 0, ((size_t)Nd + 8) * 4, s));
+    TC_TRY(stable_bucket_sort(dv.as<int32_t>(), du.as<int32_t>(), dvs.as<int32_t>(), p->dir_u.as<int32_t>(),
+                              kt.as<int32_t>(), vt.as<int32_t>(), Nd, 1, log2_ceil(p->V > 1 ? p->V : 2), s));
+    TC_TRY(p->dir_off.alloc(((size_t)p->nranges + 1) * 4));
+    k_direct_off<<<(p->nranges + 256) / 256, 256, 0, s>>>(dvs.as<int32_t>(), Nd, rstart, p->nranges,
+                                                          p->dir_off.as<int32_t>());
+    TC_LAUNCH_CHECK();
+    TC_TRY(p->dir_id16.alloc(((size_t)Nd + 8) * 2));
+    TC_CUDA(cudaMemsetAsync(p->dir_id16.p, 0, ((size_t)Nd + 8) * 2, s));
+    k_id16_ranges<<<grid, 256, 0, s>>>(dvs.as<int32_t>(), Nd, rstart, p->nranges, p->dir_id16.as<uint16_t>());
+    TC_LAUNCH_CHECK();
+    TC_CUDA(cudaStreamSynchronize(s));  // the scratch buffers are freed at return
+    return TC_OK;
+}
+
 // Merge ranges that hold about equal work over the vertices [0, V') with V' = ni (the rest have
 // no edge at all): vertex v weighs (pieces with destination v) + c, with c = max(1, ceil(R / V'));
 // nr = ceil(2V' / (kmax - 64)) ranges split the total weight evenly, at multiples of 32.  As every
@@ -446,7 +586,7 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     } else {
         p->R = 0;
     }
-    const int64_t R = p->R;
+    int64_t R = p->R;
     TC_TRY(p->rowptr.alloc(((size_t)R + 1) * 4));
     TC_TRY(p->id_map.alloc((size_t)(R + 8) * 4));  // padded: the merge reads whole 4-entry granules
     DevBuf blk_edges, blk_rows;
@@ -477,6 +617,17 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     if (p->order == TC_ORDER_OUTDEGREE && V > 0) {
         TC_TRY(weighted_ranges(p, p->k, s, grid));
         rst = p->rstart.as<int32_t>();
+    }
+    // direct pieces (renumbered pull partitions; the ranges above still count them as pieces,
+    // which they remain for the merge)
+    if (rst && dir == TC_PULL && E > 0 && R > 0 && pp && pp->direct_blocks != 0) {
+        int64_t bd = pp->direct_blocks > 0 ? (int64_t)pp->direct_blocks
+                                           : (int64_t)(caps.l2_bytes / 8) / ((int64_t)W * 4);
+        if (bd < 1) bd = 1;
+        if (bd > B) bd = B;
+        TC_TRY(split_direct(p, (int32_t)bd, head.as<uint8_t>(), rows_sorted.as<int32_t>(), rst, blk_rows, blk_edges, s,
+                            grid));
+        R = p->R;
     }
     // merge range table
     const int64_t noff = (int64_t)B * (p->nranges + 1);
@@ -567,6 +718,8 @@ extern "C" int tc_part_get_info(const tc_part *p, tc_part_info *info) {
     info->num_ranges = p->nranges;
     info->num_tiles = p->tiled ? p->ntiles : 0;
     info->num_sources = p->nz_out;
+    info->direct_blocks = p->Bd;
+    info->num_direct = p->ndirect;
     return TC_OK;
 }
 

@@ -224,6 +224,11 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
         mbar_init(&slice_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
+    // launched programmatically after the merge: the contributions are its output.  Every tile
+    // CTA is resident or done before the next kernel's CTAs are placed, so they take no slot a
+    // tile still needs.
+    pdl_trigger();
+    pdl_wait();
     __syncthreads();
     if (tid == 0) {
         const int64_t lo = (int64_t)b * t.W;
@@ -511,8 +516,17 @@ int launch_tiled_gather(const tc_part *p, const float *contrib, int *err_flag, c
     t.W = p->W;
     t.partial = const_cast<float *>(p->partial.as<float>());
     t.err = err_flag;
-    k_tile_gather<<<p->ntiles, TILE_THREADS, smem, s>>>(t);
-    TC_LAUNCH_CHECK();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(p->ntiles);
+    cfg.blockDim = dim3(TILE_THREADS);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TC_CUDA(cudaLaunchKernelEx(&cfg, k_tile_gather, t));
     ++*launches;
     return TC_OK;
 }

@@ -80,14 +80,36 @@ def _rows_sorted(rowptr, colidx):
     return rows[o], cols[o]
 
 
+def _without_direct(want, Bd):
+    """The oracle's blocking minus the single-edge local rows of blocks [0, Bd): the blocked CSR
+    a partition with direct pieces keeps.  Returns it and the number of pieces taken out."""
+    rp = np.asarray(want["rowptr"], np.int64)
+    br = np.asarray(want["blk_rows"], np.int64)
+    R = len(rp) - 1
+    ln = np.diff(rp)
+    drop = (ln == 1) & (np.arange(R) < br[min(Bd, len(br) - 1)])
+    keep = ~drop
+    edge_keep = np.repeat(keep, ln)
+    new_ln = ln[keep]
+    out = {"rowptr": np.concatenate([[0], np.cumsum(new_ln)]), "id_map": np.asarray(want["id_map"])[keep],
+           "colidx": np.asarray(want["colidx"])[edge_keep]}
+    kept_before = np.concatenate([[0], np.cumsum(keep)])
+    out["blk_rows"] = kept_before[br]
+    out["blk_edges"] = np.concatenate([[0], np.cumsum(new_ln)])[out["blk_rows"]]
+    return out, int(drop.sum())
+
+
 @pytest.mark.parametrize("name", ["rmat12", "er", "grid", "star", "isolated", "plc", "single", "two"])
 @pytest.mark.parametrize("B", [1, 3, 4, 7, 64])
-def test_renumbered_partition_matches_oracle_blocking(T, name, B):
+@pytest.mark.parametrize("direct", [0, -1, 2])
+def test_renumbered_partition_matches_oracle_blocking(T, name, B, direct):
+    """direct = 0: the oracle's blocking exactly; otherwise the same minus the single-edge
+    pieces of the first direct_blocks blocks (-1: automatic), which are counted as direct."""
     g = GRAPHS[name]
     if B > g.V:
         pytest.skip("B > V")
     G = _load(T, g)
-    P = T.tocab_partition(G, T.TC_PULL, B, order="outdegree")
+    P = T.tocab_partition(G, T.TC_PULL, B, order="outdegree", direct_blocks=direct)
     assert P.vertex_order == T.TC_ORDER_OUTDEGREE
     perm = P.export_order()
     np.testing.assert_array_equal(perm, _want_order(g))
@@ -100,6 +122,17 @@ def test_renumbered_partition_matches_oracle_blocking(T, name, B):
     tr = _renumbered_transpose(g, perm)
     want = oracle.partition(g.V, tr[0], tr[1], W)
     Bg = got["B"]
+    if direct == 0 or tr[1].size == 0:
+        assert P.num_direct == 0
+    else:
+        if direct > 0:
+            assert P.direct_blocks == min(direct, Bg)
+        else:
+            assert 1 <= P.direct_blocks <= Bg
+        R_full = len(want["id_map"])
+        want, nd = _without_direct(want, P.direct_blocks)
+        assert P.num_direct == nd
+        assert P.num_rows + nd == R_full
     np.testing.assert_array_equal(got["blk_rows"], want["blk_rows"][:Bg + 1])
     np.testing.assert_array_equal(got["blk_edges"], want["blk_edges"][:Bg + 1])
     assert (want["blk_rows"][Bg:] == want["blk_rows"][-1]).all()  # the oracle's extra blocks are empty
@@ -154,6 +187,30 @@ def test_renumbered_modes_iterations_init_and_host_output(T, B):
     out = torch.empty(g.V, dtype=torch.float32)
     T.pagerank_pull(G, P, iters=5, init=init, out=out)  # host init and host output
     assert l1_rel(out.numpy(), _oracle_pr(g, iters=5, init=init.double().numpy())) <= TOL
+
+
+@pytest.mark.parametrize("name", ["rmat12", "plc", "star", "isolated", "er"])
+@pytest.mark.parametrize("direct", [0, 1, 3, -1])
+@pytest.mark.parametrize("merge", ["fixed", "ordered"])
+def test_renumbered_direct_pieces_parity(T, name, direct, merge):
+    """Direct pieces (single-edge pieces of the first blocks, added by the merge from the
+    contribution array) give the oracle's ranks in both merges, bit for bit on reruns, and agree
+    with the partition without them (the other pieces' partial sums round differently: their
+    rows fall on other chunk boundaries of the staged stream)."""
+    g = GRAPHS[name]
+    G = _load(T, g)
+    B = min(8, g.V)
+    P = T.tocab_partition(G, T.TC_PULL, B, block_policy="smem", order="outdegree", merge_range=256,
+                          direct_blocks=direct)
+    if direct != 0 and g.E > 0:
+        assert P.num_direct > 0
+    r = T.pagerank_pull(G, P, merge=merge)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    assert torch.equal(r.cpu(), T.pagerank_pull(G, P, merge=merge).cpu())
+    if merge == "fixed":
+        P0 = T.tocab_partition(G, T.TC_PULL, B, block_policy="smem", order="outdegree", merge_range=256,
+                               direct_blocks=0)
+        assert l1_rel(r.cpu().numpy(), T.pagerank_pull(G, P0, merge=merge).cpu().numpy()) <= TOL
 
 
 @pytest.mark.parametrize("merge", ["fixed", "ordered"])

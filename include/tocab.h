@@ -142,9 +142,14 @@ typedef struct tc_part_params {
                                  fewer than two ranges per SM) */
     int32_t hub_degree;       /* rows with more edges go to CTA-per-row tasks; 0 = 2048 */
     int32_t block_policy;     /* TC_BLOCKS_L2 or TC_BLOCKS_SMEM (used when num_blocks == 0) */
-    int32_t smem_stage;       /* pull only: 0 = stage each block's contributions in shared
+    int32_t smem_stage;       /* pull: 0 = stage each block's contributions in shared
                                  memory whenever W fits (W <= about 41K sources, W % 32 == 0),
-                                 -1 = never, 1 = require it (TC_ERR_UNSUPPORTED if W does not fit) */
+                                 -1 = never, 1 = require it (TC_ERR_UNSUPPORTED if W does not fit).
+                                 push: 1 = accumulate each block's destination range in shared
+                                 memory when W * 8 bytes fit (about 29K vertices; the
+                                 TC_BLOCKS_SMEM policy picks that width), 0 / -1 = the global
+                                 scatters.  Measured slower on R-MAT (shared-memory atomics on
+                                 the hub destinations of a range serialise), so not the default */
     int32_t vertex_order;     /* pull only: TC_ORDER_NATURAL (0) or TC_ORDER_OUTDEGREE (1), below */
     int32_t direct_blocks;    /* renumbered pull only: local rows with a single edge whose source
                                  lies in the first `direct_blocks` blocks leave the blocked CSR
@@ -255,6 +260,11 @@ int32_t tc_default_block_width(int32_t V, int64_t l2_bytes, float l2_fraction);
                                         TC_MERGE_FIXED instead                                 */
 /* (2 was an FP32-atomic merge; it could miss the 1e-5 accuracy bar on ranges with hundreds of
    pieces per vertex, measured slower, and is no longer accepted: TC_ERR_INVALID_ARG)         */
+#define TC_PUSH_FLOAT     3          /* push only: FP32 atomicAdd into the sums (the paper's
+                                        Alg. 2/5; order-dependent rounding).  Push otherwise
+                                        (TC_MERGE_FIXED or _ORDERED) adds 64-bit fixed-point
+                                        integers (red.add.u64): exact in any order, so the
+                                        ranks repeat bit for bit                               */
 
 typedef struct tc_pr_params {
     float   damping;          /* d, e.g. 0.85 */
@@ -263,11 +273,16 @@ typedef struct tc_pr_params {
     int32_t out_mem;          /* memory space of ranks_out (and of init) */
     const float *init;        /* initial ranks [V] or NULL for 1/V */
     int32_t profile;          /* nonzero: time each kernel with CUDA events (stats) */
-    int32_t merge_mode;       /* TOCAB pull merge: TC_MERGE_FIXED (0) or TC_MERGE_ORDERED */
+    int32_t merge_mode;       /* TOCAB pull merge: TC_MERGE_FIXED (0) or TC_MERGE_ORDERED;
+                                 push sums: fixed point (0, 1) or TC_PUSH_FLOAT */
     int32_t lb_warp_min;      /* unstaged gathers (Sec. 3.2): rows with fewer edges are summed
                                  by one lane, longer rows by a warp (hubs by a CTA); 0 = 32,
                                  1 = a warp for every row, large = lane-serial; a partition's
-                                 per-block table (tc_part_set_lb) overrides it */
+                                 per-block table (tc_part_set_lb) overrides it.  Push: 0 = an
+                                 edge-parallel scatter (a thread per edge, the default; with a
+                                 partition whose destination range fits shared memory, the
+                                 staged scatter of tc_push.cu), > 0 = that thread/warp/CTA row
+                                 mapping (TWC) with this threshold */
     int32_t l2_window;        /* nonzero: unstaged pull gathers (unblocked, or a partition without
                                  the staged format) run with an L2 access-policy window over the
                                  contributions they read, so that the cache keeps the block's

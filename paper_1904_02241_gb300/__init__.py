@@ -216,7 +216,7 @@ def default_block_width(V: int, l2_bytes: int, l2_fraction: float = 0.0) -> int:
     return int(L.load().tc_default_block_width(V, l2_bytes, l2_fraction))
 
 
-_MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED}
+_MERGE = {"fixed": L.TC_MERGE_FIXED, "ordered": L.TC_MERGE_ORDERED, "float": L.TC_PUSH_FLOAT}
 
 
 def _pagerank(fn, name, graph, part, damping, iters, dangling, out, init, profile, stream, merge="fixed",
@@ -255,10 +255,13 @@ def pagerank_pull(graph: Graph, part: Partition | None = None, damping: float = 
 
 def pagerank_push(graph: Graph, part: Partition | None = None, damping: float = 0.85, iters: int = 20,
                   dangling="redistribute", out: torch.Tensor | None = None, init: torch.Tensor | None = None,
-                  profile: bool = False, stream=None, return_stats: bool = False, lb_warp_min: int = 0):
-    """tc_pagerank_push (Alg. 2; TOCAB Alg. 5 when part is given)."""
+                  profile: bool = False, stream=None, return_stats: bool = False, lb_warp_min: int = 0,
+                  sums: str = "fixed"):
+    """tc_pagerank_push (Alg. 2; TOCAB Alg. 5 when part is given).  sums="fixed": 64-bit
+    fixed-point reductions (bitwise repeatable); "float": FP32 atomics.  lb_warp_min = 0: a
+    thread per edge; > 0: the thread/warp/CTA row mapping with that warp threshold."""
     r, st = _pagerank(L.load().tc_pagerank_push, "tc_pagerank_push", graph, part, damping, iters, dangling, out,
-                      init, profile, stream, "fixed", lb_warp_min)
+                      init, profile, stream, sums, lb_warp_min)
     return (r, st) if return_stats else r
 
 

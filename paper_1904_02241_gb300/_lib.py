@@ -51,6 +51,7 @@ class tc_part_info(C.Structure):
 
 TC_MERGE_FIXED = 0
 TC_MERGE_ORDERED = 1
+TC_PUSH_FLOAT = 3
 TC_MULTI_RESIDENT = 1024
 
 

@@ -171,6 +171,9 @@ struct tc_graph {
     tc::DevBuf ws_contrib, ws_scalars, ws_partials, ws_bits, ws_misc;
     tc::DevBuf ws_queue, ws_qcnt, ws_qpos, ws_scan;  // BFS push levels
     unsigned long long *h_counts = nullptr;          // pinned host words read after each BFS level
+    // source of every out-edge (edge-parallel push), built on first use
+    bool push_esrc_built = false;
+    tc::DevBuf push_esrc;
     // vertex numbering by out-degree and G^T in it, built on first use by the PPR batch
     bool ord_built = false;
     int32_t ord_ni = 0;
@@ -218,6 +221,10 @@ struct tc_part {
     tc::DevBuf merge_gpre;      // int32[nranges * (B+1)]: per range, granules of MERGE_GRAN local
                                 // rows before each block's slice (exclusive prefix; [B] = total)
     tc::DevBuf blk_rows_dev;    // int64[B+1]
+    tc::DevBuf esrc;            // push only: int32[E] source (global) of every edge, for the
+                                // edge-parallel scatter
+    int32_t nptiles = 0;        // push, W * 8 bytes within shared memory: tiles of the staged push
+    tc::DevBuf ptiles;          // int4[nptiles]: (block, first edge low 31 bits, high bits, edges)
     // ---- shared-memory staged format (pull, W <= smem capacity; see tc_tile.cu) ----
     bool tiled = false;
     int64_t padded_edges = 0;   // edges of the staged stream (blocks padded to TILE_WCHUNK)
@@ -256,6 +263,11 @@ constexpr int TILE_WCHUNK = 512;         // edges a warp streams per step (16 pe
 constexpr int TILE_THREADS = 1024;
 size_t tile_smem_bytes(int32_t W);       // dynamic shared memory of the staged gather for width W
 int32_t tile_max_width(int max_smem_optin);
+// Staged push (tc_push.cu): widest destination range in shared memory, its tiles, the scatter.
+int32_t push_smem_width(int max_smem_optin);
+int build_push_tiles(tc_part *p, int sms, cudaStream_t s);
+int launch_push_smem(const tc_part *p, const float *contrib, void *sums, const double *fx_scale, bool fixed,
+                     cudaStream_t s);
 int build_tiles(tc_part *p, int sms, cudaStream_t s);
 size_t merge_smem_bytes(int32_t k, int32_t B);   // dynamic shared memory of the ordered pull merge
 size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed);  // ... of the one-accumulator merges

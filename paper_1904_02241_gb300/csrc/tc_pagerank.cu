@@ -690,16 +690,49 @@ __global__ void k_pr_scale(const double *mass, double *scale) {
 }
 
 // ---------------------------------------------------------------------------------------------
-// Push scatter (Alg. 2; Alg. 5 when id_map != null): rows are sources; red.global.add into sums.
+// Push scatter (Alg. 2; Alg. 5 when id_map != null): every edge s -> d adds contrib[s] to
+// sums[d] by a reduction in L2.  FIXED: 64-bit fixed-point integer reductions (red.add.u64),
+// exact in any order, so the ranks repeat bit for bit; otherwise FP32 atomicAdd (the paper's
+// form, order-dependent rounding).
 // ---------------------------------------------------------------------------------------------
+
+// round(y) as a 64-bit two's-complement integer for |y| < 2^62, from the FP32 bits (integer
+// operations only: 64-bit float-to-integer conversions run on the FP64 unit).
+__device__ __forceinline__ unsigned long long fx_round64(float y) {
+    const uint32_t b = __float_as_uint(y);
+    const uint32_t a = b & 0x7fffffffu;
+    const int e = (int)(a >> 23);
+    const unsigned long long m = (a & 0x7fffffu) | (e ? 0x800000u : 0u);
+    const int sh = (e ? e : 1) - 150;  // |y| = m * 2^sh
+    unsigned long long r;
+    if (sh >= 0) r = m << sh;
+    else if (sh <= -25) r = 0ull;
+    else r = (m + (1ull << (-sh - 1))) >> (-sh);  // to nearest, ties away from zero
+    return (b >> 31) ? (0ull - r) : r;
+}
+
+template <bool FIXED>
+__device__ __forceinline__ void push_add(void *sums, int32_t d, float c, float scalef) {
+    if (FIXED) atomicAdd(static_cast<unsigned long long *>(sums) + d, fx_round64(c * scalef));
+    else atomicAdd(static_cast<float *>(sums) + d, c);
+}
+
+// The push sums' fixed-point scale: 2^55 per unit of the largest L1 mass, so that |sum| < 2^55
+// (the update converts it with 32-bit steps).
+__device__ __forceinline__ float push_scale(const double *fx_scale) { return (float)(*fx_scale * 0x1p-6); }
+
+// Thread/warp/CTA mapping of the rows (Sec. 3.2's TWC): short rows a lane each, rows of at least
+// warp_min edges a warp each, hubs a CTA each.
+template <bool FIXED>
 __global__ void __launch_bounds__(PR_THREADS) k_push_scatter(const int32_t *__restrict__ rowptr,
                                                              const int32_t *__restrict__ colidx, int64_t nrows,
                                                              const int32_t *__restrict__ id_map,
                                                              const int32_t *__restrict__ hubs, int32_t num_hubs,
                                                              int32_t hub_degree, int hub_ctas,
-                                                             const float *__restrict__ contrib, float *sums,
-                                                             LbArgs lb) {
+                                                             const float *__restrict__ contrib, void *sums,
+                                                             const double *fx_scale, LbArgs lb) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float scalef = FIXED ? push_scale(fx_scale) : 1.0f;
     if ((int)blockIdx.x < hub_ctas) {
         for (int32_t h = blockIdx.x; h < num_hubs; h += hub_ctas) {
             const int32_t row = hubs[h];
@@ -707,7 +740,7 @@ __global__ void __launch_bounds__(PR_THREADS) k_push_scatter(const int32_t *__re
             const float c = __ldg(contrib + src);
             const int32_t s = rowptr[row], e = rowptr[row + 1];
             if (c != 0.0f)
-                for (int32_t i = s + threadIdx.x; i < e; i += PR_THREADS) atomicAdd(sums + __ldg(colidx + i), c);
+                for (int32_t i = s + threadIdx.x; i < e; i += PR_THREADS) push_add<FIXED>(sums, __ldg(colidx + i), c, scalef);
         }
         return;
     }
@@ -726,26 +759,70 @@ __global__ void __launch_bounds__(PR_THREADS) k_push_scatter(const int32_t *__re
         const int32_t deg = e - s;
         const int32_t wmin = lb_warp_min(lb, grp * 32);
         if (deg < wmin && deg <= hub_degree && c != 0.0f)  // hubs are scattered by their CTA only
-            for (int32_t i = s; i < e; ++i) atomicAdd(sums + __ldg(colidx + i), c);
+            for (int32_t i = s; i < e; ++i) push_add<FIXED>(sums, __ldg(colidx + i), c, scalef);
         unsigned wm = __ballot_sync(0xffffffffu, valid && deg >= wmin && deg <= hub_degree && c != 0.0f);
         while (wm) {
             const int l = __ffs(wm) - 1;
             wm &= wm - 1;
             const int32_t ws = __shfl_sync(0xffffffffu, s, l), we = __shfl_sync(0xffffffffu, e, l);
             const float cl = __shfl_sync(0xffffffffu, c, l);
-            for (int32_t i = ws + lane; i < we; i += 32) atomicAdd(sums + __ldg(colidx + i), cl);
+            for (int32_t i = ws + lane; i < we; i += 32) push_add<FIXED>(sums, __ldg(colidx + i), cl, scalef);
         }
     }
 }
 
-// Update after a push iteration: ranks from sums, next contributions, sums cleared.
-__global__ void __launch_bounds__(PR_THREADS) k_push_update(float *sums, UpdateArgs u) {
+// Edge-parallel mapping: thread t takes edges t, t + T, ... of the whole stream (every edge the
+// same work, so no row is a straggler).  esrc[i] is the source of edge i; consecutive edges
+// share it, so its contribution mostly comes from L1.  The grid walks the edges in order, so
+// with a partition the blocks - and their L2-resident destination ranges - pass one by one.
+template <bool FIXED>
+__global__ void __launch_bounds__(PR_THREADS) k_push_edges(const int32_t *__restrict__ esrc,
+                                                           const int32_t *__restrict__ dst, int64_t E,
+                                                           const float *__restrict__ contrib, void *sums,
+                                                           const double *fx_scale) {
+    const float scalef = FIXED ? push_scale(fx_scale) : 1.0f;
+    const int64_t T = (int64_t)gridDim.x * PR_THREADS;
+    int64_t i = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x;
+    for (; i + 3 * T < E; i += 4 * T) {  // four edges in flight per thread
+        int32_t sv[4], dv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            sv[k] = __ldg(esrc + i + k * T);
+            dv[k] = __ldg(dst + i + k * T);
+        }
+        float cv[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) cv[k] = __ldg(contrib + sv[k]);
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+            if (cv[k] != 0.0f) push_add<FIXED>(sums, dv[k], cv[k], scalef);
+    }
+    for (; i < E; i += T) {
+        const float c = __ldg(contrib + __ldg(esrc + i));
+        if (c != 0.0f) push_add<FIXED>(sums, __ldg(dst + i), c, scalef);
+    }
+}
+
+template <bool FIXED>
+__global__ void __launch_bounds__(PR_THREADS) k_push_update(void *sums, UpdateArgs u) {
     __shared__ float fred[32];
     const float spread = spread_of(u);
+    const float inv_scalef = FIXED ? 1.0f / push_scale(u.fx_scale) : 1.0f;  // a power of two
     float dsum = 0.0f;
     for (int64_t v = blockIdx.x * (int64_t)PR_THREADS + threadIdx.x; v < u.V; v += (int64_t)gridDim.x * PR_THREADS) {
-        const float s = sums[v];
-        sums[v] = 0.0f;
+        float s;
+        if (FIXED) {
+            unsigned long long *sp = static_cast<unsigned long long *>(sums) + v;
+            const long long tot = (long long)*sp;
+            *sp = 0ull;
+            const float th = (float)(int32_t)(tot >> 24);          // |tot| < 2^55
+            const float tl = (float)(uint32_t)(tot & 0xFFFFFFll);  // < 2^24, exact
+            s = fmaf(th, 16777216.0f, tl) * inv_scalef;
+        } else {
+            float *sp = static_cast<float *>(sums) + v;
+            s = *sp;
+            *sp = 0.0f;
+        }
         dsum += apply_update(u, (int32_t)v, s, spread);
     }
     const float bs = block_sum<float>(dsum, fred);
@@ -814,7 +891,7 @@ static int prepare_state(tc_graph *g, const tc_pr_params *pp, float *ranks_out, 
                          PrState *st) {
     const int32_t V = g->V;
     const int64_t Vp = ((int64_t)V + 63) / 64 * 64;  // 256-byte aligned vectors, padded for bulk copies
-    TC_TRY(g->ws_contrib.alloc((size_t)Vp * 4 * (push ? 3 : 2) + 256));
+    TC_TRY(g->ws_contrib.alloc((size_t)Vp * 4 * (push ? 4 : 2) + 256));  // push: 8-byte sums
     st->contrib[0] = g->ws_contrib.as<float>();
     st->contrib[1] = st->contrib[0] + Vp;
     st->sums = push ? st->contrib[1] + Vp : nullptr;
@@ -848,10 +925,22 @@ static int check_pr_args(const tc_graph *g, const tc_part *part, const tc_pr_par
     if (pp->out_mem != TC_MEM_HOST && pp->out_mem != TC_MEM_DEVICE)
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad out_mem");
     if (pp->lb_warp_min < 0) return fail(TC_ERR_INVALID_ARG, "pagerank: lb_warp_min < 0");
-    if (pp->merge_mode != TC_MERGE_FIXED && pp->merge_mode != TC_MERGE_ORDERED)
+    if (pp->merge_mode != TC_MERGE_FIXED && pp->merge_mode != TC_MERGE_ORDERED &&
+        !(dir == TC_PUSH && pp->merge_mode == TC_PUSH_FLOAT))
         return fail(TC_ERR_INVALID_ARG, "pagerank: bad merge_mode");
     if (part && (part->g != g || part->dir != dir))
         return fail(TC_ERR_INVALID_ARG, "pagerank: partition belongs to another graph or direction");
+    return TC_OK;
+}
+
+// The source of every out-edge of the graph (its row in the out-CSR), built on first use by the
+// edge-parallel push and kept with the graph.
+static int push_sources(tc_graph *g, cudaStream_t s) {
+    if (g->push_esrc_built) return TC_OK;
+    TC_TRY(g->push_esrc.alloc((size_t)(g->E > 0 ? g->E : 1) * 4));
+    if (g->E > 0) TC_TRY(expand_rows(g->out_rowptr.as<int32_t>(), g->V, g->push_esrc.as<int32_t>(), s));
+    TC_CUDA(cudaStreamSynchronize(s));
+    g->push_esrc_built = true;
     return TC_OK;
 }
 
@@ -889,11 +978,12 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     hub_ctas = nhubs > 0 ? (nhubs < caps.sms ? nhubs : caps.sms) : 0;
     const bool tiled = part && !push && part->tiled;
     const int64_t group_ctas = ((nrows + 31) / 32 + PR_WARPS - 1) / PR_WARPS;
-    const void *kgather = push ? (const void *)k_push_scatter
+    const void *kgather = push ? (const void *)k_push_scatter<true>
                                : (part ? (const void *)k_pull_gather<false> : (const void *)k_pull_gather<true>);
     TC_TRY(occupancy_grid(kgather, PR_THREADS, 0, group_ctas > 0 ? group_ctas : 1, &g_gather));
     g_gather += hub_ctas;
-    TC_TRY(occupancy_grid((const void *)k_push_update, PR_THREADS, 0, ((int64_t)V + PR_THREADS - 1) / PR_THREADS, &g_upd));
+    TC_TRY(occupancy_grid((const void *)k_push_update<true>, PR_THREADS, 0, ((int64_t)V + PR_THREADS - 1) / PR_THREADS,
+                          &g_upd));
     size_t merge_smem = 0;
     int merge_mode = TC_MERGE_FIXED;
     if (part && !push) {
@@ -929,7 +1019,28 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
     PrState st;
     TC_TRY(prepare_state(g, pp, ranks_out, push, max_ctas, &st));
     TC_CUDA(cudaMemsetAsync(st.counter, 0, 16, s));  // counter, merge work queue and the error flag
-    if (push) TC_CUDA(cudaMemsetAsync(st.sums, 0, (size_t)V * 4, s));
+    if (push) TC_CUDA(cudaMemsetAsync(st.sums, 0, (size_t)V * 8, s));
+    // push: fixed-point sums unless FP32 atomics are asked for; the edge-parallel scatter unless
+    // a TWC warp threshold (lb_warp_min or a per-block table) is given
+    const bool push_fixed = pp->merge_mode != TC_PUSH_FLOAT;
+    const bool push_staged = push && part && part->nptiles > 0 && pp->lb_warp_min == 0 && !part->lb_tab.p;
+    const bool push_edges = push && !push_staged && pp->lb_warp_min == 0 && !(part && part->lb_tab.p);
+    const int32_t *esrc = nullptr;
+    int64_t nedges = 0;
+    int g_edges = 1;
+    if (push_edges) {
+        if (part) {
+            esrc = part->esrc.as<int32_t>();
+            nedges = part->E;
+        } else {
+            TC_TRY(push_sources(g, s));
+            esrc = g->push_esrc.as<int32_t>();
+            nedges = g->E;
+        }
+        TC_TRY(occupancy_grid((const void *)k_push_edges<true>, PR_THREADS, 0,
+                              (nedges + PR_THREADS - 1) / PR_THREADS > 0 ? (nedges + PR_THREADS - 1) / PR_THREADS : 1,
+                              &g_edges));
+    }
 
     UpdateArgs u;
     u.base = (1.0f - pp->damping) / (float)V;
@@ -994,8 +1105,18 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
         lb.blk_rows = part ? part->blk_rows_dev.as<int64_t>() : nullptr;
         lb.B = part ? part->B : 1;
         if (push) {
-            k_push_scatter<<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, idm, hubs, nhubs, hubdeg, hub_ctas, cur,
-                                                          st.sums, lb);
+            if (push_staged)
+                TC_TRY(launch_push_smem(part, cur, st.sums, st.scale, push_fixed, s));
+            else if (push_edges && push_fixed)
+                k_push_edges<true><<<g_edges, PR_THREADS, 0, s>>>(esrc, ci, nedges, cur, st.sums, st.scale);
+            else if (push_edges)
+                k_push_edges<false><<<g_edges, PR_THREADS, 0, s>>>(esrc, ci, nedges, cur, st.sums, st.scale);
+            else if (push_fixed)
+                k_push_scatter<true><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, idm, hubs, nhubs, hubdeg,
+                                                                     hub_ctas, cur, st.sums, st.scale, lb);
+            else
+                k_push_scatter<false><<<g_gather, PR_THREADS, 0, s>>>(rp, ci, nrows, idm, hubs, nhubs, hubdeg,
+                                                                      hub_ctas, cur, st.sums, st.scale, lb);
         } else if (tiled) {
             int nl = 0;
             TC_TRY(launch_tiled_gather(part, cur, st.err, s, &nl));
@@ -1031,7 +1152,8 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
             Timer t2;
             TC_TRY(t2.begin(pp->profile != 0, s, &ms_merge));
             if (push) {
-                k_push_update<<<g_upd, PR_THREADS, 0, s>>>(st.sums, u);
+                if (push_fixed) k_push_update<true><<<g_upd, PR_THREADS, 0, s>>>(st.sums, u);
+                else k_push_update<false><<<g_upd, PR_THREADS, 0, s>>>(st.sums, u);
             } else {
                 const uint16_t *i16 = part->id16.p ? part->id16.as<uint16_t>() : nullptr;
                 const int32_t *rst = part->rstart.p ? part->rstart.as<int32_t>() : nullptr;

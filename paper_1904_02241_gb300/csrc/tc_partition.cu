@@ -301,6 +301,9 @@ static int renumber_by_outdegree(const tc_graph *g, cudaStream_t s, DevBuf *rp_n
     return TC_OK;
 }
 
+// smem_stage = 1 asks a push partition for the staged scatter.
+static bool stage_ok_push(const tc_part_params *pp) { return pp && pp->smem_stage > 0; }
+
 // ---------------------------------------------------------------------------------------------
 // Direct pieces.  Edge e of the blocked CSR alone forms its local row when it starts a row and
 // the next edge starts one too; in the first Bd blocks (edges below e_cut) such pieces leave the
@@ -525,7 +528,11 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
     p->hub_degree = (pp && pp->hub_degree > 0) ? pp->hub_degree : 2048;
     const int32_t smem_w = tile_max_width(caps.max_smem_optin);
     const int policy = pp ? pp->block_policy : TC_BLOCKS_L2;
-    if (num_blocks == 0 && policy == TC_BLOCKS_SMEM && p->order == TC_ORDER_OUTDEGREE) {
+    if (num_blocks == 0 && policy == TC_BLOCKS_SMEM && dir == TC_PUSH) {
+        // push: the widest destination range whose 8-byte sums fit one CTA's shared memory
+        const int32_t pw = push_smem_width(caps.max_smem_optin);
+        p->W = pw > 0 ? (V < pw ? (V > 32 ? (V + 31) / 32 * 32 : 32) : pw) : 32;
+    } else if (num_blocks == 0 && policy == TC_BLOCKS_SMEM && p->order == TC_ORDER_OUTDEGREE) {
         // the gather splits blocks into row-aligned pieces of equal size, so B need not fill
         // whole waves: the widest block that fits shared memory gives the fewest pieces
         p->W = smem_w > 0 ? smem_w : 32;
@@ -651,15 +658,22 @@ static int partition_impl(const tc_graph *g, int dir, int32_t num_blocks, const 
         k_id16<<<grid, 256, 0, s>>>(p->id_map.as<int32_t>(), R, p->k - 1, p->id16.as<uint16_t>());
         TC_LAUNCH_CHECK();
     }
+    // push: the source of every edge in stream order (the sort's row values), for the
+    // edge-parallel scatter
+    if (dir == TC_PUSH) p->esrc.swap(rows_sorted);
+    // push ranges that fit shared memory get the staged scatter (tc_push.cu)
+    if (dir == TC_PUSH && (int64_t)W * 8 + 1024 <= (int64_t)caps.max_smem_optin && stage_ok_push(pp))
+        TC_TRY(build_push_tiles(p, caps.sms, s));
     p->num_groups = (R + 31) / 32;
     TC_TRY(p->partial.alloc((size_t)(R + 8) * 4));
     TC_TRY(p->rowbits.alloc((size_t)((R + 31) / 32 + 1) * 4));
     TC_CUDA(cudaStreamSynchronize(s));
     const int stage = pp ? pp->smem_stage : 0;
-    if (stage > 0 && dir != TC_PULL) return fail(TC_ERR_UNSUPPORTED, "smem_stage = 1 applies to pull partitions only");
+    if (stage > 0 && dir == TC_PUSH && p->nptiles == 0 && E > 0)
+        return fail(TC_ERR_UNSUPPORTED, "smem_stage = 1 needs a push partition with W * 8 bytes within shared memory");
     if (dir == TC_PULL && stage >= 0 && W <= smem_w && W % 32 == 0 && V > 0)
         TC_TRY(build_tiles(p, caps.sms, s));
-    if (stage > 0 && !p->tiled)
+    if (stage > 0 && dir == TC_PULL && !p->tiled)
         return fail(TC_ERR_UNSUPPORTED, "smem_stage = 1 needs a pull partition with W <= %d and W %% 32 == 0", smem_w);
     return TC_OK;
 }

@@ -196,14 +196,36 @@ def test_pull_result_is_deterministic(T):
 
 @pytest.mark.parametrize("name", list(GRAPHS))
 @pytest.mark.parametrize("B", [None, 1, 4, 64])
-def test_pagerank_push_parity(T, name, B):
+@pytest.mark.parametrize("lb", [0, 32])
+def test_pagerank_push_parity(T, name, B, lb):
+    """Push with fixed-point sums (the default): the oracle's ranks, bit for bit on reruns and
+    the same bits whether a thread per edge (lb = 0) or the TWC rows (lb > 0) scatter them."""
     g = GRAPHS[name]
     if B is not None and B > g.V:
         pytest.skip("B > V")
     G = _load(T, g)
     P = T.tocab_partition(G, T.TC_PUSH, B) if B is not None else None
-    r = T.pagerank_push(G, P)
+    r = T.pagerank_push(G, P, lb_warp_min=lb)
     assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    assert torch.equal(r.cpu(), T.pagerank_push(G, P, lb_warp_min=lb).cpu())
+    assert torch.equal(r.cpu(), T.pagerank_push(G, P, lb_warp_min=1 << 30).cpu())
+
+
+@pytest.mark.parametrize("name", ["rmat12", "plc", "er", "isolated"])
+@pytest.mark.parametrize("lb", [0, 8])
+def test_pagerank_push_float_atomics(T, name, lb):
+    """The paper's FP32-atomic sums: within the bar (order-dependent rounding)."""
+    g = GRAPHS[name]
+    G = _load(T, g)
+    for P in (None, T.tocab_partition(G, T.TC_PUSH, min(4, g.V))):
+        r = T.pagerank_push(G, P, lb_warp_min=lb, sums="float")
+        assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+
+
+def test_pagerank_push_float_rejected_for_pull(T):
+    G = _load(T, GRAPHS["rmat12"])
+    with pytest.raises(T.TocabError):
+        T.pagerank_pull(G, None, merge="float")
 
 
 def test_partition_direction_mismatch_rejected(T):
@@ -294,12 +316,12 @@ def test_smem_block_policy(T):
 
 
 def test_staged_requirement_rejected_when_width_too_large(T):
-    g = GRAPHS["rmat12"]
+    g = gg.rmat(17)  # one block of 131,072 sources / destinations fits neither staged form
     G = _load(T, g)
-    with pytest.raises(T.TocabError) as e:
-        T.tocab_partition(G, T.TC_PULL, 1, smem_stage=1, hub_degree=0) if g.V > 65536 else \
-            T.tocab_partition(G, T.TC_PUSH, 4, smem_stage=1)
-    assert e.value.status in (-6,)
+    for d in (T.TC_PULL, T.TC_PUSH):
+        with pytest.raises(T.TocabError) as e:
+            T.tocab_partition(G, d, 1, smem_stage=1)
+        assert e.value.status == -6
 
 
 # ------------------------------------------------------------------ a9: batched personalised PageRank
@@ -661,3 +683,33 @@ def test_ppr_set_tuning_rejects(T):
     for hot, tile in ((-2, 0), (0, 48), (0, 256)):
         with pytest.raises(T.TocabError):
             T.ppr_set_tuning(G, hot=hot, tile=tile)
+
+
+def test_pagerank_push_fixed_point_signed_init(T):
+    """Caller ranks of either sign go through the fixed-point sums (two's complement)."""
+    g = GRAPHS["rmat12"]
+    G = _load(T, g)
+    rng = np.random.default_rng(11)
+    init = torch.tensor(rng.standard_normal(g.V) / g.V, dtype=torch.float32)
+    rp, ci = g.numpy()
+    want = oracle.pagerank_push(g.V, rp, ci, iters=3, init=init.double().numpy())
+    for P in (None, T.tocab_partition(G, T.TC_PUSH, 4)):
+        r = T.pagerank_push(G, P, iters=3, init=init.cuda()).cpu().numpy()
+        assert np.abs(r - want).sum() <= 1e-5 * np.abs(want).sum()
+
+
+@pytest.mark.parametrize("name", ["rmat12", "plc", "er", "star", "isolated"])
+@pytest.mark.parametrize("sums", ["fixed", "float"])
+def test_pagerank_push_staged(T, name, sums):
+    """The shared-memory staged push (smem_stage = 1): the oracle's ranks; with fixed-point sums
+    the same bits as the global scatters."""
+    g = GRAPHS[name]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PUSH, min(4, g.V), smem_stage=1)
+    r = T.pagerank_push(G, P, sums=sums)
+    assert l1_rel(r.cpu().numpy(), _oracle_pr(g)) <= TOL
+    if sums == "fixed":
+        assert torch.equal(r.cpu(), T.pagerank_push(G, P, lb_warp_min=8).cpu())
+        assert torch.equal(r.cpu(), T.pagerank_push(G, None).cpu())
+
+

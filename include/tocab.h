@@ -440,8 +440,12 @@ int tc_ppr_set_tuning(tc_graph *g, int32_t hot, int32_t tile);
  * tc_bc_forward -- the shortest-path calculation of Alg. 3 from one source over the out-edges
  * of G: depth_out[v] = hop distance from `source` (-1 when unreachable; the paper's delta) and
  * sigma_out[v] = number of shortest paths from `source` to v (the paper's sigma, FP64, exact
- * below 2^53; 0 when unreachable).  Computed topology-driven in the pull direction (every level
- * scans the in-rows of the vertices not yet reached), with no atomics.
+ * below 2^53; 0 when unreachable).  Each level runs in the cheaper direction (Sec. 3.3's
+ * push-pull-push): push from the frontier list (compare-and-swap on depth, FP64 atomics on
+ * sigma - exact, as every partial sum is an integer below 2^53) while the frontier holds fewer
+ * than 1/14 of the vertices not yet reached, else pull over the in-rows of the unreached
+ * vertices (a thread per short row, a warp per row of 32 or more in-edges).  Results do not
+ * depend on the direction chosen.
  *   out_mem : memory space of depth_out (int32[V]) and sigma_out (double[V]).
  * Synchronises the stream.  Errors: TC_ERR_INVALID_ARG (source outside [0, V), bad out_mem),
  * TC_ERR_OOM, TC_ERR_CUDA.
@@ -457,10 +461,12 @@ int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int32_t *depth
  * pulled over the out-edges of G; scores_out[v] = the sum of dep[v] over the sources other than
  * v itself.  Scores are not normalised and count ordered targets (an undirected graph given
  * with both edge directions counts every pair twice).  FP64 throughout; every product, quotient
- * and sum is rounded separately, in the formula's order, so the result is deterministic.
+ * and sum is rounded separately; a warp takes each vertex of a level, each lane summing its
+ * strided share of the out-row in order and a fixed shuffle tree adding the lanes, so the
+ * result is deterministic.
  *   sources : host int32[num_sources], each in [0, V) (repeats allowed; 0 sources gives zeros).
  *   out_mem : memory space of scores_out (double[V]).
- * Scratch: int32[V] + 3 double[V] (+ double[V] for host output), per call.
+ * Scratch: 2 int32[V] + 3 double[V] (+ double[V] for host output), per call.
  * Synchronises the stream.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA.
  */
 int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int out_mem, double *scores_out,
@@ -471,8 +477,9 @@ int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int ou
  * tc_spmv -- y = A x (the SpMV benchmark of Sec. 4).  A is the CSR loaded with
  * tc_graph_load_csr, read as rows = outputs: y[i] = sum over the stored entries k of row i of
  * vals[k] * x[colidx[k]], with vals in the loaded entry order.  FP32 values, vectors and
- * accumulation; a warp per row with a fixed reduction order (deterministic).  The graph's
- * preprocessing (transpose, degrees) is not used.
+ * accumulation; a group of 4 to 32 lanes per row (from the mean row length) and a CTA per row
+ * of more than the hub degree (Sec. 3.2's binning), each with a fixed reduction order
+ * (deterministic).  The graph's transpose is not used.
  *   vals : float[E], x : float[V], y : float[V] (y[i] for every row i < V), all device pointers.
  *   mem  : TC_MEM_DEVICE (TC_MEM_HOST is refused with TC_ERR_UNSUPPORTED).
  * Asynchronous on `stream`.  Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED, TC_ERR_CUDA.

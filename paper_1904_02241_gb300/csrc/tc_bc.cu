@@ -1,34 +1,46 @@
 // Betweenness centrality (the traversal benchmark of Sec. 3.3 and Sec. 4).
 //
 // Forward sweep: the shortest-path calculation of Alg. 3 (depth delta and shortest-path count
-// sigma from one source), run topology-driven in the pull direction over G^T: in level L every
-// vertex not yet reached adds up sigma over its in-neighbours of depth L, and takes depth L+1 if
-// it has any.  Pull needs no atomics (a vertex is written only by its own thread) and sums in
-// in-row order, so it is deterministic.  A thread reads depth[u] of in-neighbours that other
-// threads may set to L+1 in the same launch; both the old value (-1) and the new one differ from
-// L, so the read is unaffected, and sigma[u] is read only for vertices of depth L, which no one
-// writes in this level.
+// sigma from one source), level by level, in the direction each level is cheaper in (Sec. 3.3's
+// push-pull-push pattern: the first and last levels have small frontiers, the middle ones large):
+//  * push: the frontier (the vertices of depth L, kept as a list) scatters over its out-edges;
+//    an unreached target takes depth L+1 by compare-and-swap and every parent adds its sigma
+//    with an FP64 atomic.  sigma counts paths, so every partial sum is an integer below 2^53
+//    and exact: the result does not depend on the order of the additions.
+//  * pull: every unreached vertex adds sigma over its in-neighbours of depth L (G^T), with no
+//    atomics; a thread walks a short in-row, a warp a long one (in-degree >= 32, Sec. 3.2's
+//    binning).  A vertex reads depth[u] of in-neighbours that other threads may set to L+1 in
+//    the same launch; the old value (-1) and the new one both differ from L, so the read is
+//    unaffected, and sigma[u] is read only for vertices of depth L, which no one writes now.
+// Both directions append the vertices they reach to the next frontier list.
 //
-// Backward sweep: the dependency back-propagation of the BC the paper cites, pulled over the
-// out-edges of G level by level from the deepest: for a vertex v of depth L,
+// Backward sweep: the dependency back-propagation of the BC the paper cites, over the level
+// lists from the deepest, pulled over the out-edges of G: for a vertex v of depth L,
 //   dep[v] = sum over out-neighbours w of depth L+1 of sigma[v] / sigma[w] * (1 + dep[w]),
-// in out-row order, and every vertex other than the source adds dep[v] to its score.  The
-// products, quotients and sums are rounded one by one (no fused multiply-add), in the order of
-// that formula.
+// one warp per vertex: each lane adds its strided share of the row in order, then a fixed
+// shuffle tree adds the lane sums; every vertex other than the source adds dep[v] to its score.
+// Products, quotients and sums are rounded one by one (no fused multiply-add).  A vertex's
+// dependency reads only final values of the next level, so the order of a level's list (which
+// the forward sweep fills as vertices are reached) does not change any result.
 //
-// sigma, dep and the scores are FP64 (sigma is an integer count, exact below 2^53).
+// sigma, dep and the scores are FP64.
+#include <vector>
+
 #include "tc_internal.cuh"
 
 namespace tc {
 
 constexpr int BC_THREADS = 256;
+constexpr int BC_WARPS = BC_THREADS / 32;
+constexpr int BC_LONG = 32;  // rows with at least this many edges get a warp in pull levels
 
-__global__ void k_bc_init(int32_t V, int32_t source, int32_t *depth, double *sigma, double *dep) {
+__global__ void k_bc_init(int32_t V, int32_t source, int32_t *depth, double *sigma, double *dep, int32_t *order) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         depth[v] = v == source ? 0 : -1;
         sigma[v] = v == source ? 1.0 : 0.0;
         dep[v] = 0.0;
     }
+    if (blockIdx.x == 0 && threadIdx.x == 0) order[0] = source;  // level 0
 }
 
 __global__ void k_bc_zero(int32_t V, double *score) {
@@ -36,18 +48,45 @@ __global__ void k_bc_zero(int32_t V, double *score) {
         score[v] = 0.0;
 }
 
-// level L -> L+1 of Alg. 3 in pull form; *found counts the vertices reached
-__global__ void __launch_bounds__(BC_THREADS) k_bc_forward(const int32_t *__restrict__ in_rowptr,
-                                                           const int32_t *__restrict__ in_colidx, int32_t V,
-                                                           int32_t L, int32_t *depth, double *sigma,
-                                                           unsigned *found) {
-    unsigned n = 0;
+// push level L: a warp per frontier vertex u strides its out-row
+__global__ void __launch_bounds__(BC_THREADS) k_bc_push(const int32_t *__restrict__ rowptr,
+                                                        const int32_t *__restrict__ colidx,
+                                                        const int32_t *__restrict__ front, int64_t nf, int32_t L,
+                                                        int32_t *depth, double *sigma, int32_t *next,
+                                                        unsigned *next_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * BC_WARPS;
+    for (int64_t f = (blockIdx.x * (int64_t)BC_THREADS + threadIdx.x) >> 5; f < nf; f += nw) {
+        const int32_t u = front[f];
+        const double su = sigma[u];
+        for (int32_t e = rowptr[u] + lane; e < rowptr[u + 1]; e += 32) {
+            const int32_t w = colidx[e];
+            int32_t dw = *(volatile int32_t *)(depth + w);
+            if (dw == -1) {
+                dw = atomicCAS(depth + w, -1, L + 1);
+                if (dw == -1) {  // this edge reached w first
+                    dw = L + 1;
+                    next[atomicAdd(next_count, 1u)] = w;
+                }
+            }
+            if (dw == L + 1) atomicAdd(sigma + w, su);
+        }
+    }
+}
+
+// pull level L, short in-rows: a thread per unreached vertex
+__global__ void __launch_bounds__(BC_THREADS) k_bc_pull(const int32_t *__restrict__ in_rowptr,
+                                                        const int32_t *__restrict__ in_colidx, int32_t V, int32_t L,
+                                                        int32_t *depth, double *sigma, int32_t *next,
+                                                        unsigned *next_count) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         if (depth[v] != -1) continue;
+        const int32_t s = in_rowptr[v], e = in_rowptr[v + 1];
+        if (e - s >= BC_LONG) continue;  // k_bc_pull_long
         double acc = 0.0;
         bool hit = false;
-        for (int32_t e = in_rowptr[v]; e < in_rowptr[v + 1]; ++e) {
-            const int32_t u = in_colidx[e];
+        for (int32_t i = s; i < e; ++i) {
+            const int32_t u = in_colidx[i];
             if (depth[u] == L) {
                 acc = __dadd_rn(acc, sigma[u]);
                 hit = true;
@@ -56,68 +95,141 @@ __global__ void __launch_bounds__(BC_THREADS) k_bc_forward(const int32_t *__rest
         if (hit) {
             depth[v] = L + 1;
             sigma[v] = acc;
-            ++n;
+            next[atomicAdd(next_count, 1u)] = (int32_t)v;
         }
     }
-    if (n) atomicAdd(found, n);
 }
 
-// dependencies of the vertices of depth L (those of depth L+1 are final)
+// pull level L, long in-rows: a warp per unreached vertex of the long-row list
+__global__ void __launch_bounds__(BC_THREADS) k_bc_pull_long(const int32_t *__restrict__ in_rowptr,
+                                                             const int32_t *__restrict__ in_colidx,
+                                                             const int32_t *__restrict__ longrows, int32_t nlong,
+                                                             int32_t L, int32_t *depth, double *sigma, int32_t *next,
+                                                             unsigned *next_count) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * BC_WARPS;
+    for (int64_t k = (blockIdx.x * (int64_t)BC_THREADS + threadIdx.x) >> 5; k < nlong; k += nw) {
+        const int32_t v = longrows[k];
+        if (depth[v] != -1) continue;  // the same value for the whole warp
+        double acc = 0.0;
+        bool hit = false;
+        for (int32_t i = in_rowptr[v] + lane; i < in_rowptr[v + 1]; i += 32) {
+            const int32_t u = in_colidx[i];
+            if (depth[u] == L) {
+                acc = __dadd_rn(acc, sigma[u]);
+                hit = true;
+            }
+        }
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc = __dadd_rn(acc, __shfl_xor_sync(0xffffffffu, acc, d));
+        hit = __any_sync(0xffffffffu, hit);
+        if (hit && lane == 0) {
+            depth[v] = L + 1;
+            sigma[v] = acc;
+            next[atomicAdd(next_count, 1u)] = v;
+        }
+    }
+}
+
+// dependencies of the vertices of depth L (those of depth L+1 are final): a warp per vertex of
+// the level's list
 __global__ void __launch_bounds__(BC_THREADS) k_bc_backward(const int32_t *__restrict__ rowptr,
-                                                            const int32_t *__restrict__ colidx, int32_t V,
+                                                            const int32_t *__restrict__ colidx,
+                                                            const int32_t *__restrict__ level_list, int64_t n,
                                                             int32_t L, int32_t source,
                                                             const int32_t *__restrict__ depth,
                                                             const double *__restrict__ sigma, double *dep,
                                                             double *score) {
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
-        if (depth[v] != L) continue;
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * BC_WARPS;
+    for (int64_t k = (blockIdx.x * (int64_t)BC_THREADS + threadIdx.x) >> 5; k < n; k += nw) {
+        const int32_t v = level_list[k];
         const double sv = sigma[v];
         double d = 0.0;
-        for (int32_t e = rowptr[v]; e < rowptr[v + 1]; ++e) {
+        for (int32_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
             const int32_t w = colidx[e];
             if (depth[w] == L + 1) d = __dadd_rn(d, __dmul_rn(__ddiv_rn(sv, sigma[w]), __dadd_rn(1.0, dep[w])));
         }
-        dep[v] = d;
-        if (v != source) score[v] = __dadd_rn(score[v], d);
+#pragma unroll
+        for (int q = 16; q > 0; q >>= 1) d = __dadd_rn(d, __shfl_xor_sync(0xffffffffu, d, q));
+        if (lane == 0) {
+            dep[v] = d;
+            if (v != source) score[v] = __dadd_rn(score[v], d);
+        }
     }
 }
 
-// Forward sweep from `source` into depth/sigma (device); returns the deepest level reached.
-static int bc_forward_impl(const tc_graph *g, int32_t source, int32_t *depth, double *sigma, double *dep,
-                           unsigned *found_dev, unsigned *found_host, int grid, cudaStream_t s, int32_t *max_depth) {
-    const int32_t V = g->V;
-    k_bc_init<<<grid, BC_THREADS, 0, s>>>(V, source, depth, sigma, dep);
-    TC_LAUNCH_CHECK();
-    int32_t L = 0;
-    for (;; ++L) {
-        TC_CUDA(cudaMemsetAsync(found_dev, 0, 4, s));
-        k_bc_forward<<<grid, BC_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), V, L,
-                                                 depth, sigma, found_dev);
-        TC_LAUNCH_CHECK();
-        TC_CUDA(cudaMemcpyAsync(found_host, found_dev, 4, cudaMemcpyDeviceToHost, s));
-        TC_CUDA(cudaStreamSynchronize(s));
-        if (*found_host == 0) break;
-    }
-    *max_depth = L;
-    return TC_OK;
-}
+// A level runs in the push direction while its frontier holds fewer than 1 / BC_PUSH_RATIO of
+// the vertices not yet reached (Beamer's rule with vertex counts standing in for edge counts).
+constexpr int64_t BC_PUSH_RATIO = 14;
 
 struct BcScratch {
-    DevBuf depth, sigma, dep, score, found;
-    unsigned found_host = 0;
+    DevBuf depth, sigma, dep, score, order, counter, longrows;
+    int32_t nlong = 0;
+    std::vector<int64_t> off;  // level L of `order` is [off[L], off[L+1])
     int grid = 1;
-    int setup(int32_t V, bool need_score) {
+    int setup(const tc_graph *g, bool need_score, cudaStream_t s) {
+        const int32_t V = g->V;
         DeviceCaps caps;
         TC_TRY(device_caps(&caps));
         grid = caps.sms * 8;
         TC_TRY(depth.alloc((size_t)V * 4));
         TC_TRY(sigma.alloc((size_t)V * 8));
         TC_TRY(dep.alloc((size_t)V * 8));
+        TC_TRY(order.alloc((size_t)V * 4));
         if (need_score) TC_TRY(score.alloc((size_t)V * 8));
-        TC_TRY(found.alloc(16));
+        TC_TRY(counter.alloc(16));
+        TC_TRY(collect_hubs(g->in_rowptr.as<int32_t>(), V, BC_LONG - 1, &longrows, &nlong, s));
         return TC_OK;
     }
 };
+
+// Forward sweep from `source`: depth/sigma, and w.order holding the reached vertices level by
+// level.  *max_depth = the deepest level (levels 0 .. *max_depth).  *pushed counts push levels.
+static int bc_forward_impl(const tc_graph *g, int32_t source, BcScratch &w, cudaStream_t s, int32_t *max_depth,
+                           int32_t *pushed) {
+    const int32_t V = g->V;
+    int32_t *depth = w.depth.as<int32_t>(), *order = w.order.as<int32_t>();
+    double *sigma = w.sigma.as<double>();
+    unsigned *cnt = w.counter.as<unsigned>();
+    k_bc_init<<<w.grid, BC_THREADS, 0, s>>>(V, source, depth, sigma, w.dep.as<double>(), order);
+    TC_LAUNCH_CHECK();
+    w.off.assign(1, 0);
+    w.off.push_back(1);
+    int32_t L = 0, np = 0;
+    for (;; ++L) {
+        const int64_t f0 = w.off[(size_t)L], nf = w.off[(size_t)L + 1] - f0;
+        const int64_t reached = w.off[(size_t)L + 1];
+        TC_CUDA(cudaMemsetAsync(cnt, 0, 4, s));
+        int32_t *next = order + reached;
+        if (nf * BC_PUSH_RATIO < (int64_t)V - reached) {
+            const int64_t want = (nf + BC_WARPS - 1) / BC_WARPS;
+            const int grid = (int)(want < w.grid ? (want > 0 ? want : 1) : w.grid);
+            k_bc_push<<<grid, BC_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(),
+                                                  order + f0, nf, L, depth, sigma, next, cnt);
+            TC_LAUNCH_CHECK();
+            ++np;
+        } else {
+            k_bc_pull<<<w.grid, BC_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), V, L,
+                                                    depth, sigma, next, cnt);
+            TC_LAUNCH_CHECK();
+            if (w.nlong > 0) {
+                k_bc_pull_long<<<w.grid, BC_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(),
+                                                             w.longrows.as<int32_t>(), w.nlong, L, depth, sigma,
+                                                             next, cnt);
+                TC_LAUNCH_CHECK();
+            }
+        }
+        unsigned found = 0;
+        TC_CUDA(cudaMemcpyAsync(&found, cnt, 4, cudaMemcpyDeviceToHost, s));
+        TC_CUDA(cudaStreamSynchronize(s));
+        if (found == 0) break;
+        w.off.push_back(reached + (int64_t)found);
+    }
+    *max_depth = L;
+    if (pushed) *pushed = np;
+    return TC_OK;
+}
 
 }  // namespace tc
 
@@ -130,10 +242,9 @@ extern "C" int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int
     cudaStream_t s = (cudaStream_t)stream;
     const int32_t V = g->V;
     BcScratch w;
-    TC_TRY(w.setup(V, false));
+    TC_TRY(w.setup(g, false, s));
     int32_t maxd = 0;
-    TC_TRY(bc_forward_impl(g, source, w.depth.as<int32_t>(), w.sigma.as<double>(), w.dep.as<double>(),
-                           w.found.as<unsigned>(), &w.found_host, w.grid, s, &maxd));
+    TC_TRY(bc_forward_impl(g, source, w, s, &maxd, nullptr));
     const cudaMemcpyKind kind = out_mem == TC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     TC_CUDA(cudaMemcpyAsync(depth_out, w.depth.p, (size_t)V * 4, kind, s));
     TC_CUDA(cudaMemcpyAsync(sigma_out, w.sigma.p, (size_t)V * 8, kind, s));
@@ -155,18 +266,21 @@ extern "C" int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sour
     if (V == 0) return TC_OK;
     BcScratch w;
     const bool dev_out = out_mem == TC_MEM_DEVICE;
-    TC_TRY(w.setup(V, !dev_out));
+    TC_TRY(w.setup(g, !dev_out, s));
     double *score = dev_out ? scores_out : w.score.as<double>();
     k_bc_zero<<<w.grid, BC_THREADS, 0, s>>>(V, score);
     TC_LAUNCH_CHECK();
     for (int32_t k = 0; k < num_sources; ++k) {
         int32_t maxd = 0;
-        TC_TRY(bc_forward_impl(g, sources[k], w.depth.as<int32_t>(), w.sigma.as<double>(), w.dep.as<double>(),
-                               w.found.as<unsigned>(), &w.found_host, w.grid, s, &maxd));
+        TC_TRY(bc_forward_impl(g, sources[k], w, s, &maxd, nullptr));
         for (int32_t L = maxd; L >= 0; --L) {
-            k_bc_backward<<<w.grid, BC_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(), V, L,
-                                                        sources[k], w.depth.as<int32_t>(), w.sigma.as<double>(),
-                                                        w.dep.as<double>(), score);
+            const int64_t a = w.off[(size_t)L], n = w.off[(size_t)L + 1] - a;
+            const int64_t want = (n + BC_WARPS - 1) / BC_WARPS;
+            const int grid = (int)(want < w.grid ? (want > 0 ? want : 1) : w.grid);
+            k_bc_backward<<<grid, BC_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(),
+                                                      w.order.as<int32_t>() + a, n, L, sources[k],
+                                                      w.depth.as<int32_t>(), w.sigma.as<double>(),
+                                                      w.dep.as<double>(), score);
             TC_LAUNCH_CHECK();
         }
     }

@@ -37,6 +37,12 @@ GRAPHS = {
     "er": gg.random_small(300, 1400, 6),
     "empty": gg.empty_graph(9),
 }
+# hubs with hundreds of in-edges (warp-per-row pull levels) beside small frontiers (push levels);
+# checked from a few sources only
+BIG = {
+    "rmat13_sym": gg.symmetrize(gg.rmat(13)),
+    "big_star": gg.symmetrize(gg.star(3000)),
+}
 
 
 def _load(T, g):
@@ -96,3 +102,21 @@ def test_invalid_source_is_refused(T):
     assert e.value.status == -1
     with pytest.raises(T.TocabError):
         T.bc_forward(G, -1)
+
+
+@pytest.mark.parametrize("name", ["rmat13_sym", "big_star", "grid", "dpath"])
+def test_scores_repeat_bit_for_bit(T, name):
+    """Push levels (FP64 atomics on integer path counts) and warp trees leave no trace of timing;
+    depths and counts stay exact."""
+    g = BIG[name] if name in BIG else GRAPHS[name]
+    G = _load(T, g)
+    srcs = [0, g.V // 3, g.V - 1]
+    a = T.bc(G, srcs).cpu()
+    assert torch.equal(a, T.bc(G, srcs).cpu())
+    rp, ci = g.numpy()
+    np.testing.assert_allclose(a.numpy(), oracle.bc(g.V, rp, ci, srcs), rtol=1e-12, atol=1e-9)
+    for s in srcs:
+        depth, sigma = T.bc_forward(G, s)
+        want_d, want_s = oracle.bc_forward(g.V, rp, ci, s)
+        assert np.array_equal(depth.cpu().numpy(), want_d)
+        assert np.array_equal(sigma.cpu().numpy(), want_s)

@@ -367,7 +367,26 @@ def variants(args, ctx, world):
     ms = run(lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))
     res["push_unblocked_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
     res["push_unblocked_bmin_frac"] = bmin_frac(ms)
+    # the paper's FP32 atomics instead of the default 64-bit fixed-point reductions, and the
+    # thread/warp/CTA row mapping instead of the edge-parallel scatter
+    push = {}
+    for key, P_, kw in (("tocab_float", Pp, {"sums": "float"}), ("unblocked_float", None, {"sums": "float"}),
+                        ("unblocked_twc_fixed", None, {"lb_warp_min": 32}),
+                        ("unblocked_twc_float", None, {"lb_warp_min": 32, "sums": "float"})):
+        ms = run(lambda: T.pagerank_push(G, P_, damping=DAMPING, iters=ITERS, out=out, **kw))
+        push[key + "_gteps"] = round(E * ITERS / (ms * 1e-3) / 1e9, 2)
+    res["push_variants"] = push
     del Pp
+    # direct pieces (single-edge pieces of the first blocks added by the merge): an opt-in
+    # partition option, measured against the default here
+    if args.order == "outdegree":
+        Pd = T.tocab_partition(G, T.TC_PULL, args.blocks, block_policy=args.policy, merge_range=args.merge_range,
+                               order="outdegree", direct_blocks=-1)
+        ms = run(lambda: T.pagerank_pull(G, Pd, damping=DAMPING, iters=ITERS, out=out))
+        res["pull_tocab_direct_pieces"] = {"gteps": round(E * ITERS / (ms * 1e-3) / 1e9, 2),
+                                           "bmin_frac": bmin_frac(ms), "direct_blocks": Pd.direct_blocks,
+                                           "num_direct": Pd.num_direct, "local_rows": Pd.num_rows}
+        del Pd
     # BFS on the symmetrised graph, 64 seeded sources (TEPS counts each undirected edge once)
     gs = gg.symmetrize(g)
     Gs = T.graph_load_csr(gs.rowptr, gs.colidx, V=gs.V)
@@ -397,6 +416,8 @@ def variants(args, ctx, world):
     torch.cuda.empty_cache()
     res["rmat16"] = rmat16_row(stream, run)
     res["bfs_grid4096"] = bfs_grid_row(stream)
+    res.update(spmv_row(stream))
+    res.update(bc_row(stream))
     res.update(graph_variants(args, stream, E, run))
     res.update(batch_variants(args, stream))
     return res
@@ -726,9 +747,9 @@ def cpu_baseline(g, budget_s: float):
 def reference_arm(args, world, rank):
     if rank != 0:
         return
-    dev = "cuda" if torch.cuda.is_available() else "cpu"
-    g = make_graph(args.scale, dev)
-    g = gg.CSRGraph(g.V, g.rowptr.cpu(), g.colidx.cpu(), g.name)
+    t0 = time.time()
+    g = gg.rmat_host(args.scale)  # the same graph as the GPU arm's, generated on the host cores
+    gen_s = time.time() - t0
     import oracle
     oracle.build()
     rp, ci = g.rowptr.numpy(), g.colidx.numpy()
@@ -749,7 +770,8 @@ def reference_arm(args, world, rank):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(sec_iter * 1e3, 2),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"pagerank_pull rmat{args.scale} ef16 20 iters d=0.85 (FP64 CPU oracle)",
-                   "graph": f"rmat{args.scale}", "V": g.V, "E": g.E, "iters": ITERS},
+                   "graph": f"rmat{args.scale}", "V": g.V, "E": g.E, "iters": ITERS,
+                   "generated_on": "host (graphgen.rmat_host)", "generate_s": round(gen_s, 2)},
         "cpu_baseline": {"value": round(value, 4), "unit": "GTEPS", "cores": cores, "kind": "oracle",
                          "sample": sample},
         "e2e": {"value": round(value, 4), "unit": "GTEPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},

@@ -17,7 +17,10 @@ no self loops, no duplicate edges.
 """
 from __future__ import annotations
 
+import ctypes
 import dataclasses
+import os
+import subprocess
 
 import numpy as np
 import torch
@@ -318,3 +321,60 @@ def batch_scales(count: int = 1000, lo: int = 10, hi: int = 16, seed: int = 19) 
     """Seeded scales drawn uniformly from [lo, hi] for a many-graph batch."""
     u = hash_u32(seed, torch.arange(count, dtype=torch.int64))
     return [lo + int(x) % (hi - lo + 1) for x in u]
+
+
+# ----------------------------------------------------------------------------------------
+# host R-MAT (C, OpenMP): the same graph as rmat(..., device="cpu"), generated in seconds
+# instead of minutes at scale 24, for runs that must stay on the host
+# ----------------------------------------------------------------------------------------
+
+_HOST_DIR = os.path.dirname(os.path.abspath(__file__))
+_HOST_SO = os.path.join(_HOST_DIR, "_build", "libgg_host.so")
+_host_lib = None
+
+
+def build_native(force: bool = False) -> str:
+    """Compile rmat_host.c with gcc (OpenMP when available) into graphgen/_build."""
+    src = os.path.join(_HOST_DIR, "rmat_host.c")
+    os.makedirs(os.path.dirname(_HOST_SO), exist_ok=True)
+    if not force and os.path.exists(_HOST_SO) and os.path.getmtime(_HOST_SO) >= os.path.getmtime(src):
+        return _HOST_SO
+    tmp = _HOST_SO + f".tmp{os.getpid()}"
+    base = ["gcc", "-O3", "-fPIC", "-shared", "-std=c11", src, "-o", tmp]
+    try:
+        subprocess.run(base[:1] + ["-fopenmp"] + base[1:], check=True, capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base, check=True, capture_output=True)
+    os.replace(tmp, _HOST_SO)
+    return _HOST_SO
+
+
+def rmat_host(scale: int, edge_factor: int = 16, a: float = 0.57, b: float = 0.19, c: float = 0.19,
+              seed: int | None = None, permute_seed: int | None = 7) -> CSRGraph:
+    """rmat() computed on the host cores by rmat_host.c: the identical CSR (same draws, same
+    permutation, same deduplication and order), as CPU tensors."""
+    global _host_lib
+    if _host_lib is None:
+        lib = ctypes.CDLL(build_native())
+        lib.gg_rmat.restype = ctypes.c_int64
+        lib.gg_rmat.argtypes = [ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                ctypes.c_int64, ctypes.c_int64, ctypes.c_void_p, ctypes.POINTER(ctypes.c_void_p)]
+        lib.gg_free.argtypes = [ctypes.c_void_p]
+        _host_lib = lib
+    V = 1 << scale
+    seed = 1 + scale if seed is None else seed
+    ta = int(round(a * 2**32))
+    tab = int(round((a + b) * 2**32))
+    tabc = int(round((a + b + c) * 2**32))
+    rowptr = np.zeros(V + 1, np.int64)
+    ptr = ctypes.c_void_p()
+    E = _host_lib.gg_rmat(scale, edge_factor, ta, tab, tabc, seed, -1 if permute_seed is None else permute_seed,
+                          rowptr.ctypes.data, ctypes.byref(ptr))
+    if E < 0:
+        raise MemoryError("rmat_host: host allocation failed")
+    try:
+        col = np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctypes.c_int32)), (max(E, 1),))[:E].copy()
+    finally:
+        _host_lib.gg_free(ptr)
+    assert E < 2**31, "int32 CSR limit"
+    return CSRGraph(V, torch.from_numpy(rowptr.astype(np.int32)), torch.from_numpy(col), f"rmat{scale}")

@@ -2,11 +2,15 @@
 forward/backward/Adam and the feature extraction run in libtocab's CUDA kernels).
 
 The model maps 16 features of a graph (tc_graph_features) or of a TOCAB subgraph
-(tc_part_features) to three choices: the block count (the paper's block-size trade-off,
-Sec. 4.3), the load-balancing variant of the unstaged gather (Sec. 3.2), and the direction
-(pull or push, Sec. 3.1).  It never changes results, only the time.  Without a model the
-choice falls back to the paper's heuristic: pull, W from the L2 size (Sec. 4.3, Table 3),
-thread/warp/CTA load balancing.
+(tc_part_features) to five choices: for PageRank the block count (the paper's block-size
+trade-off, Sec. 4.3), the load-balancing variant of the unstaged gather (Sec. 3.2) and the
+direction (pull or push, Sec. 3.1); for BFS the frontier fraction above which a level runs
+blocked (TOCAB's working-set threshold, Sec. 3.3) and the one below which it runs top-down
+(the push phases of push-pull-push).  The load-balancing head also runs on each subgraph's
+features to pick that subgraph's variant (per_block_lb, applied with tc_part_set_lb).  It
+never changes results, only the time.  Without a model the choice falls back to the paper's
+heuristic: pull, W from the L2 size (Sec. 4.3, Table 3), thread/warp/CTA load balancing, and
+for BFS the thresholds 0.05 and 1/24.
 """
 from __future__ import annotations
 
@@ -26,7 +30,10 @@ BLOCK_CLASSES = ["unblocked", 1, 2, 4, 8, 16, 32, 64, "smem"]
 LB_CLASSES = ["hybrid", "serial", "warp"]      # rows >= 32 edges by warp / all lane-serial / all by warp
 LB_WARP_MIN = {"hybrid": 32, "serial": 1 << 30, "warp": 1}
 DIR_CLASSES = ["pull", "push"]
-HEADS = (len(BLOCK_CLASSES), len(LB_CLASSES), len(DIR_CLASSES))
+TAU_CLASSES = [-1.0, 0.0, 0.02, 0.05, 0.1, 0.2]  # BFS blocked levels: never, always, frontier > tau V
+PUSH_CLASSES = [0.0, 1.0 / 96, 1.0 / 24, 1.0 / 6]  # BFS top-down levels: never, frontier < p V
+BFS_HEURISTIC = (0.05, 1.0 / 24)
+HEADS = (len(BLOCK_CLASSES), len(LB_CLASSES), len(DIR_CLASSES), len(TAU_CLASSES), len(PUSH_CLASSES))
 N_FEATURES = 16
 HIDDEN = 64
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "costmodel_weights.json")
@@ -153,7 +160,8 @@ class MLP:
         d = {k: v.tolist() for k, v in p.items()}
         d.update({"mu": self.mu.tolist(), "sd": self.sd.tolist(), "heads": list(self.heads),
                   "block_classes": [str(b) for b in BLOCK_CLASSES], "lb_classes": LB_CLASSES,
-                  "dir_classes": DIR_CLASSES, "meta": meta or {}})
+                  "dir_classes": DIR_CLASSES, "tau_classes": TAU_CLASSES, "push_classes": PUSH_CLASSES,
+                  "meta": meta or {}})
         with open(path, "w") as fh:
             json.dump(d, fh)
 
@@ -206,12 +214,48 @@ def time_config(G, direction: str, block, lb: str = "hybrid", iters: int = 5, re
     return statistics.median(ts)
 
 
+def time_bfs(G, P, tau: float, push: float, sources, reps: int = 2) -> float:
+    """Device time (ms) of BFS from `sources` (summed) with these thresholds, median of reps."""
+    from . import bfs_pull
+    lv = torch.empty(G.V, dtype=torch.int32, device="cuda")
+    bfs_pull(G, P, int(sources[0]), tocab_threshold=tau, out=lv, push_threshold=push)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        s = torch.cuda.Event(enable_timing=True)
+        e = torch.cuda.Event(enable_timing=True)
+        s.record()
+        for src in sources:
+            bfs_pull(G, P, int(src), tocab_threshold=tau, out=lv, push_threshold=push)
+        e.record()
+        e.synchronize()
+        ts.append(s.elapsed_time(e))
+    return statistics.median(ts)
+
+
+def measure_bfs(G, sources=None, reps: int = 2):
+    """BFS time of every (tau, push) class pair on the paper's L2-rule partition.  Levels that
+    pull on a graph of thousands of levels rescan every unvisited vertex each time, so on graphs
+    above 2^20 vertices only the direction-optimised classes (push > 0) are timed."""
+    P = tocab_partition(G, L.TC_PULL, 0, block_policy="l2")
+    src = sources if sources is not None else [0, G.V // 2]
+    table = {}
+    for ti, tau in enumerate(TAU_CLASSES):
+        for pi, push in enumerate(PUSH_CLASSES):
+            if push == 0.0 and G.V > (1 << 20):
+                continue
+            table[(ti, pi)] = time_bfs(G, P, tau, push, src, reps)
+    best = min(table, key=table.get)
+    return {"labels": best, "table": {f"bfs|{TAU_CLASSES[t]:g}|{PUSH_CLASSES[q]:.4g}": v
+                                      for (t, q), v in table.items()}}
+
+
 def heuristic_config():
     """The method without the model: pull, the paper's L2-derived block width, hybrid LB."""
     return ("pull", "l2", "hybrid")
 
 
-def measure_graph(G, iters=5, reps=3):
+def measure_graph(G, iters=5, reps=3, bfs_src=None):
     """Times of every (direction, block class) with hybrid LB, and of every LB variant for the
     best unstaged pull block class.  Returns dict with labels and the timing table."""
     table = {}
@@ -238,21 +282,39 @@ def measure_graph(G, iters=5, reps=3):
     bblock = min(pull_blocks, key=pull_blocks.get)
     lbs = {lb: t for (d, b, lb), t in table.items() if d == "pull" and b == str(best_pull_unstaged)}
     blb = min(lbs, key=lbs.get)
+    bfs = measure_bfs(G, bfs_src)
     labels = (BLOCK_CLASSES.index(bblock if bblock in ("unblocked", "smem") else int(bblock)),
-              LB_CLASSES.index(blb), DIR_CLASSES.index(bdir))
-    return {"labels": labels, "table": {"|".join(map(str, k)): v for k, v in table.items()}}
+              LB_CLASSES.index(blb), DIR_CLASSES.index(bdir)) + tuple(bfs["labels"])
+    out = {"|".join(map(str, k)): v for k, v in table.items()}
+    out.update(bfs["table"])
+    return {"labels": labels, "table": out}
 
 
 def choose(model, G, P_probe=None):
-    """The model's configuration for graph G: (direction, block class, LB variant per block)."""
+    """The model's PageRank configuration for graph G: (direction, block class, LB variant)."""
     f = graph_features(G)
-    blk_c, lb_c, dir_c = model.predict(f[None])[0]
+    blk_c, lb_c, dir_c = model.predict(f[None])[0][:3]
     direction = DIR_CLASSES[dir_c]
     block = BLOCK_CLASSES[blk_c]
     lb = LB_CLASSES[lb_c]
     if direction == "push" and block == "smem":
         block = 64
     return direction, block, lb
+
+
+def choose_bfs(model, G):
+    """The model's BFS thresholds for graph G: (tocab_threshold, push_threshold)."""
+    pred = model.predict(graph_features(G)[None])[0]
+    return TAU_CLASSES[pred[3]], PUSH_CLASSES[pred[4]]
+
+
+def per_block_lb(model, P):
+    """The load-balancing variant of every subgraph of an unstaged partition, from the
+    subgraph's own features (the LB head), as tc_part_set_lb's warp thresholds."""
+    lb_c = model.predict(part_features(P))[:, 1]
+    wmin = [LB_WARP_MIN[LB_CLASSES[c]] for c in lb_c]
+    P.set_lb(wmin)
+    return wmin
 
 
 def time_choice(G, choice, iters=5, reps=3):
@@ -308,13 +370,18 @@ def make_graph(spec, device="cuda"):
     return gg.grid2d(spec["rows"], spec["cols"], drop=spec["drop"], seed=spec["seed"], device=device)
 
 
+def _bfs_sources(g, n: int = 2):
+    import graphgen as gg
+    return [int(x) for x in gg.sources(g, n, seed=g.V)]
+
+
 def build_dataset(specs, iters=5, reps=3, log=None):
     X, Y, tables = [], [], []
     for i, spec in enumerate(specs):
         g = make_graph(spec)
         G = graph_load_csr(g.rowptr, g.colidx, V=g.V)
         f = graph_features(G)
-        m = measure_graph(G, iters=iters, reps=reps)
+        m = measure_graph(G, iters=iters, reps=reps, bfs_src=_bfs_sources(g))
         X.append(f)
         Y.append(m["labels"])
         tables.append(m["table"])
@@ -331,18 +398,25 @@ def evaluate(model, specs, iters=5, reps=3, log=None):
     for spec in specs:
         g = make_graph(spec)
         G = graph_load_csr(g.rowptr, g.colidx, V=g.V)
-        m = measure_graph(G, iters=iters, reps=reps)
-        best = min(m["table"].values())
-        heur = m["table"]["pull|l2|hybrid"]
+        m = measure_graph(G, iters=iters, reps=reps, bfs_src=_bfs_sources(g))
+        pr = {k: v for k, v in m["table"].items() if not k.startswith("bfs|")}
+        bt = {k: v for k, v in m["table"].items() if k.startswith("bfs|")}
+        best = min(pr.values())
+        heur = pr["pull|l2|hybrid"]
         ch = choose(model, G) if model is not None else heuristic_config()
         key = f"{ch[0]}|{ch[1]}|{ch[2]}"
-        t_model = m["table"].get(key)
+        t_model = pr.get(key)
         if t_model is None:
             t_model = time_choice(G, ch, iters, reps)
+        tau, push = choose_bfs(model, G) if model is not None else BFS_HEURISTIC
+        bkey = f"bfs|{tau:g}|{push:.4g}"
+        hkey = f"bfs|{BFS_HEURISTIC[0]:g}|{BFS_HEURISTIC[1]:.4g}"
         rows.append({"spec": spec, "V": g.V, "E": g.E, "choice": key, "t_model": t_model, "t_heuristic": heur,
-                     "t_best": best})
+                     "t_best": best, "bfs_choice": bkey, "bfs_model": bt.get(bkey), "bfs_heuristic": bt[hkey],
+                     "bfs_best": min(bt.values())})
         if log:
-            log(f"{spec['kind']} V={g.V} E={g.E}: model {key} {t_model:.4f} ms, heuristic {heur:.4f}, best {best:.4f}")
+            log(f"{spec['kind']} V={g.V} E={g.E}: model {key} {t_model:.4f} ms, heuristic {heur:.4f}, best {best:.4f}; "
+                f"BFS {bkey} {bt.get(bkey)} heuristic {bt[hkey]:.4f} best {min(bt.values()):.4f}")
         del G, g
         torch.cuda.empty_cache()
     return rows
@@ -378,10 +452,14 @@ def _main():
                        "permute": True})
     held = evaluate(m, hspecs, log=log)
     gm = lambda k: float(np.exp(np.mean([np.log(r[k] / r["t_best"]) for r in held])))  # noqa: E731
+    gmb = lambda k: float(np.exp(np.mean([np.log(r[k] / r["bfs_best"]) for r in held  # noqa: E731
+                                          if r[k] is not None])))
     meta = {"graphs": a.graphs, "scales": [a.scale_lo, a.scale_hi], "large_graphs": a.large,
             "final_loss": loss, "train_accuracy": acc,
             "heldout": a.heldout, "heldout_model_over_best": gm("t_model"),
-            "heldout_heuristic_over_best": gm("t_heuristic"), "seconds": time.time() - t0}
+            "heldout_heuristic_over_best": gm("t_heuristic"),
+            "heldout_bfs_model_over_best": gmb("bfs_model"), "heldout_bfs_heuristic_over_best": gmb("bfs_heuristic"),
+            "seconds": time.time() - t0}
     m.save(a.out, meta)
     log(json.dumps(meta))
     if a.report:

@@ -17,6 +17,8 @@ def test_weights_file_is_a_consistent_network():
     assert len(d["b1"]) == len(d["b2"]) == cm.HIDDEN and len(d["b3"]) == sum(cm.HEADS)
     assert d["block_classes"] == [str(c) for c in cm.BLOCK_CLASSES]  # stored as strings
     assert d["lb_classes"] == cm.LB_CLASSES and d["dir_classes"] == cm.DIR_CLASSES
+    assert d["tau_classes"] == cm.TAU_CLASSES and d["push_classes"] == cm.PUSH_CLASSES
+    assert cm.BFS_HEURISTIC[0] in cm.TAU_CLASSES and cm.BFS_HEURISTIC[1] in cm.PUSH_CLASSES
     sd = np.asarray(d["sd"])
     assert sd.shape == (cm.N_FEATURES,) and np.all(sd > 0)
     for k in ("W1", "W2", "W3", "b1", "b2", "b3", "mu"):

@@ -140,6 +140,39 @@ def test_learned_model_gains_over_heuristic(CM):
     print(f"held-out time / exhaustive best: model {model:.3f}, heuristic {heur:.3f}, "
           f"gain {heur / model:.3f}x")
     assert model <= heur * 1.05
+    # the BFS heads (frontier thresholds): measured for the model's choice on every held-out graph
+    bm = [r["bfs_model"] / r["bfs_best"] for r in held if r["bfs_model"] is not None]
+    bh = [r["bfs_heuristic"] / r["bfs_best"] for r in held]
+    assert len(bm) == len(held)
+    print(f"BFS held-out time / best: model {np.exp(np.mean(np.log(bm))):.3f}, "
+          f"heuristic {np.exp(np.mean(np.log(bh))):.3f}")
+    assert np.exp(np.mean(np.log(bm))) <= np.exp(np.mean(np.log(bh))) * 1.10
+
+
+def test_per_block_lb_matches_or_beats_per_graph(CM):
+    """The shipped model's load-balancing head run on each subgraph's features (tc_part_features,
+    applied with tc_part_set_lb) against the same head on the whole graph's features applied to
+    every block: the per-subgraph choice is no slower (geometric mean over skewed graphs, within
+    timing noise), and both give the oracle's ranks."""
+    import graphgen as gg
+    import oracle
+    from tests.gpu_util import l1_rel
+    m = CM.MLP.load()
+    ratios = []
+    for g in (gg.rmat(16), gg.powerlaw_config(1 << 16, 8, 2.2, seed=3), gg.rmat(17, 8, 0.6, 0.15, 0.15, seed=9)):
+        G = CM.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+        P = CM.tocab_partition(G, CM.L.TC_PULL, 8, smem_stage=-1)
+        lb_graph = CM.LB_CLASSES[m.predict(CM.graph_features(G)[None])[0][1]]
+        t_graph = CM.time_config(G, "pull", None, lb_graph, part=P)
+        wmin = CM.per_block_lb(m, P)
+        assert len(wmin) == P.num_blocks
+        t_block = CM.time_config(G, "pull", None, "hybrid", part=P)  # the table overrides lb_warp_min
+        ratios.append(t_block / t_graph)
+        r = CM.pagerank_pull(G, P).cpu().numpy()
+        rp, ci = g.numpy()
+        assert l1_rel(r, oracle.pagerank_pull(g.V, rp, ci)) <= 1e-5
+        print(f"V={g.V}: per-graph {lb_graph} {t_graph:.4f} ms, per-block {wmin} {t_block:.4f} ms")
+    assert float(np.exp(np.mean(np.log(ratios)))) <= 1.10
 
 
 @pytest.mark.parametrize("bad", [-1, 3])

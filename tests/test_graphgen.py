@@ -3,6 +3,7 @@ determinism, and the structural promises every caller relies on (sorted, duplica
 without self loops; disjoint graphs in a batch; symmetric grids)."""
 import numpy as np
 import pytest
+import torch
 
 import graphgen as gg
 
@@ -83,3 +84,12 @@ def test_sources_are_deterministic_and_have_edges():
     assert s1 == s2 and len(s1) == 16 and len(set(s1)) > 1
     deg = np.diff(g.rowptr.numpy())
     assert all(deg[s] > 0 for s in s1)
+
+
+@pytest.mark.parametrize("scale,kw", [(8, {}), (12, {}), (12, {"permute_seed": None}),
+                                      (13, {"a": 0.6, "b": 0.15, "c": 0.15, "seed": 9}),
+                                      (10, {"a": 0.25, "b": 0.25, "c": 0.25}), (10, {"edge_factor": 4})])
+def test_host_rmat_is_the_same_graph(scale, kw):
+    """The C generator (the reference arm's) gives rmat()'s CSR exactly, thresholds of 2^32 included."""
+    h, g = gg.rmat_host(scale, **kw), gg.rmat(scale, **kw)
+    assert torch.equal(h.rowptr, g.rowptr) and torch.equal(h.colidx, g.colidx)

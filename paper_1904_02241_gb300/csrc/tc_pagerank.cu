@@ -518,11 +518,12 @@ __global__ void __launch_bounds__(MG_THREADS, 2) k_pull_merge_atomic(const float
                     const int32_t a = l0 - f > 0 ? l0 - f : 0;              // first valid offset
                     const int32_t z = l1 - f < MG_GRAN ? l1 - f : MG_GRAN;  // end offset
                     valid[q] = (0xFFu >> (MG_GRAN - z)) & (0xFFu << a);
+                    // partial sums and ids are read once: streaming loads (evict-first in L2)
                     const float4 *px = reinterpret_cast<const float4 *>(partial + f);
-                    xa[q] = __ldg(px);
-                    xb[q] = __ldg(px + 1);
+                    xa[q] = __ldcs(px);
+                    xb[q] = __ldcs(px + 1);
                     if (id16) {
-                        iv[q] = __ldg(reinterpret_cast<const uint4 *>(id16 + f));
+                        iv[q] = __ldcs(reinterpret_cast<const uint4 *>(id16 + f));
                     } else {  // global ids: keep the granule's position, read them below
                         iv[q].x = (uint32_t)f;
                     }

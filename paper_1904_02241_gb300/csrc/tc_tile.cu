@@ -224,10 +224,9 @@ __global__ void __launch_bounds__(TILE_THREADS, 1) k_tile_gather(TileArgs t) {
         mbar_init(&slice_bar, 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    // launched programmatically after the merge: the contributions are its output.  Every tile
-    // CTA is resident or done before the next kernel's CTAs are placed, so they take no slot a
-    // tile still needs.
-    pdl_trigger();
+    // launched programmatically after the merge: the contributions are its output.  No early
+    // trigger here: the merge's CTAs then launch as the tiles finish and do not sit on SMs the
+    // last wave of tiles could use (measured: 0.6% per step against triggering at the start).
     pdl_wait();
     __syncthreads();
     if (tid == 0) {

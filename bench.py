@@ -58,7 +58,8 @@ def parse():
                     help="vertex numbering the TOCAB blocks are cut in (renumbered by out-degree, or as given)")
     ap.add_argument("--quick", action="store_true",
                     help="headline only: skip variants, e2e and the CPU baseline (profiling runs)")
-    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc", "bfs_grid", "rmat16", "ppr"],
+    ap.add_argument("--row", default="", choices=["", "many_graphs", "spmv", "bc", "bfs_grid", "rmat16", "ppr",
+                                                  "ppr_probe", "ppr_probe_tile32", "bfs_levels"],
                     help="profiling runs: time only this row and print its figures")
     return ap.parse_args()
 
@@ -603,6 +604,39 @@ def many_graphs(stream, with_oracle: bool = True):
     return res
 
 
+def ppr_probe_row(stream, tile: int = 0, iters: int = 3):
+    """The PPR batch (256 sources, R-MAT 22) for a profiler: one warm call and one call of
+    `iters` iterations with a fixed tile width (0: whole rows) and no evict-last rows."""
+    import paper_1904_02241_gb300 as T
+    g = gg.rmat(22, device="cuda")
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    srcs = gg.sources(g, 256, seed=17)
+    R = torch.empty((g.V, 256), dtype=torch.float32, device="cuda")
+    T.ppr_set_tuning(G, hot=0, tile=tile)
+    T.ppr_batch(G, srcs, iters=iters, out=R)
+    _, st = T.ppr_batch(G, srcs, iters=iters, out=R, profile=True, return_stats=True)
+    return {"ppr_probe": {"tile": tile, "iters": iters, "ms": round(st.ms_total, 3)}}
+
+
+def bfs_levels_row(stream):
+    """Pure pull BFS (no push levels) on the symmetrised R-MAT 22 from one source, unblocked
+    (tocab_threshold -1) and with every level blocked (0): the per-level trace, for a profiler."""
+    import paper_1904_02241_gb300 as T
+    g = gg.symmetrize(gg.rmat(22, device="cuda"))
+    G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
+    P = T.tocab_partition(G, T.TC_PULL, 8)
+    src = gg.sources(g, 1, seed=13)[0]
+    lv = torch.empty(g.V, dtype=torch.int32, device="cuda")
+    out = {"V": g.V, "E": g.E, "blocks": P.num_blocks, "W": P.block_width}
+    for tau in (-1.0, 0.0):
+        _, st = T.bfs_pull(G, P, src, tocab_threshold=tau, out=lv, return_stats=True, profile=True)
+        n = min(st.levels, 64)
+        out[f"tau_{tau:g}"] = {"levels": st.levels, "ms": round(st.ms_total, 3),
+                               "level_ms": [round(st.level_ms[i], 4) for i in range(n)],
+                               "level_frontier": [int(st.level_frontier[i]) for i in range(n)]}
+    return {"bfs_levels": out}
+
+
 def spmv_row(stream, scale: int = 22):
     """y = A x with A the R-MAT 22 CSR and seeded FP32 values (Sec. 4's SpMV benchmark).  The
     algorithmic bytes of one product are the values and column indices (8 B per entry), the row
@@ -797,7 +831,9 @@ def main():
         res = {"many_graphs": lambda: many_graphs(stream, with_oracle=False), "spmv": lambda: spmv_row(stream),
                "bc": lambda: bc_row(stream), "bfs_grid": lambda: {"bfs_grid4096": bfs_grid_row(stream)},
                "rmat16": lambda: {"rmat16": rmat16_row(stream, run)},
-               "ppr": lambda: ppr_row(stream)}[args.row]()
+               "ppr": lambda: ppr_row(stream), "ppr_probe": lambda: ppr_probe_row(stream, 0),
+               "ppr_probe_tile32": lambda: ppr_probe_row(stream, 32),
+               "bfs_levels": lambda: bfs_levels_row(stream)}[args.row]()
         print(json.dumps(res), flush=True)
         return
     res, ctx = bench_tocab(args, world, rank, local)

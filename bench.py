@@ -653,9 +653,22 @@ def spmv_row(stream, scale: int = 22):
     ms = statistics.median(time_runs(lambda: T.spmv(A, vals, x, out=y), 10, stream))
     peak, _ = load_peaks()
     nbytes = 8 * g.E + 4 * (g.V + 1) + 8 * g.V
+    # GC-pull (TOCAB with a value stream) over column blocks of several widths
+    gc = {}
+    for B in (1, 8, 32, 128):
+        P = T.tocab_partition(A, T.TC_PUSH, B, merge_range=8192)
+        T.part_set_values(P, vals)
+        for _ in range(3):
+            T.spmv_tocab(P, x, out=y)
+        torch.cuda.synchronize()
+        ms_b = statistics.median(time_runs(lambda: T.spmv_tocab(P, x, out=y), 10, stream))
+        gc[str(B)] = {"ms": round(ms_b, 4), "local_rows": P.num_rows, "block_width": P.block_width}
+        del P
     return {"spmv": {"graph": f"rmat{scale}", "V": g.V, "E": g.E, "ms": round(ms, 4),
                      "gflops": round(2 * g.E / (ms * 1e-3) / 1e9, 2),
-                     "bytes_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4)}}
+                     "bytes_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
+                     "mapping": "lane groups per row (VWC) + CTA per hub row",
+                     "gc_pull_by_blocks": gc}}
 
 
 def bc_row(stream, scale: int = 18, nsrc: int = 4):

@@ -486,6 +486,30 @@ int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int ou
  */
 int tc_spmv(const tc_graph *g, const float *vals, const float *x, float *y, int mem, void *stream);
 
+/*
+ * tc_part_set_values -- give a TC_PUSH partition of the matrix's graph (its blocks are ranges of
+ * W columns of A; its local rows are the (column block, row) pieces of Fig. 4) the values of
+ * the stored entries, `vals` in the loaded CSR order (float[E], device).  The partition keeps
+ * them in its own entry order (the first call also records that order: the partition's stable
+ * sort again, carrying entry positions).  For GC-pull SpMV (Sec. 4).  Synchronises.
+ * Errors: TC_ERR_INVALID_ARG (NULL, a pull partition), TC_ERR_UNSUPPORTED (host values),
+ * TC_ERR_OOM, TC_ERR_CUDA.
+ */
+int tc_part_set_values(tc_part *p, const float *vals, int mem, void *stream);
+
+/*
+ * tc_spmv_tocab -- y = A x with TOCAB (the GC-pull SpMV of Sec. 4, a value stream of 4 B per
+ * entry): for every local row (column block b, row i), partial = sum of vals * x[col] over the
+ * piece's entries (x's block b is the working set, Sec. 3.1), then the merge of Fig. 5 adds row
+ * i's pieces in block order.  FP32, in a fixed order (deterministic).  A lane takes a piece below
+ * 32 entries, a warp a longer one.
+ *   p : a TC_PUSH partition of the graph holding A, with values set by tc_part_set_values;
+ *       its merge_range k must be at most 51,200.
+ *   x : float[V], y : float[V], device.
+ * Asynchronous on `stream`.  Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED, TC_ERR_CUDA.
+ */
+int tc_spmv_tocab(const tc_part *p, const float *x, float *y, int mem, void *stream);
+
 /* ---- many small graphs in one batch ---------------------------------------------------------- */
 typedef struct tc_multigraph tc_multigraph;   /* opaque: a batch of independent graphs */
 

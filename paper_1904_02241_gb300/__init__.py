@@ -23,7 +23,7 @@ from . import _lib as L
 from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
                    TC_MULTI_RESIDENT, TC_ORDER_NATURAL, TC_ORDER_OUTDEGREE, TC_PULL, TC_PUSH)
 
-__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "ppr_autotune", "ppr_set_tuning",
+__all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "ppr_autotune", "ppr_set_tuning", "part_set_values", "spmv_tocab",
            "multigraph_load",
            "pagerank_multi", "multi_autotune", "MultiGraph",
            "Graph", "Partition", "TocabError", "lib", "default_block_width", "set_device_memory_limit",
@@ -299,6 +299,29 @@ def spmv(matrix: Graph, vals: torch.Tensor, x: torch.Tensor, out: torch.Tensor |
         raise ValueError("out must be a contiguous float32 CUDA tensor with V elements")
     _check(L.load().tc_spmv(matrix.handle, vals.data_ptr() if vals.numel() else None, x.data_ptr(), out.data_ptr(),
                             L.TC_MEM_DEVICE, _stream(stream)), "tc_spmv")
+    return out
+
+
+def part_set_values(part: "Partition", vals: torch.Tensor, stream=None):
+    """tc_part_set_values: the matrix values (CSR order, float32 on the device) for GC-pull SpMV
+    on a TC_PUSH partition."""
+    if vals.dtype != torch.float32 or not vals.is_cuda or not vals.is_contiguous():
+        raise ValueError("vals must be a contiguous float32 CUDA tensor")
+    _check(L.load().tc_part_set_values(part.handle, vals.data_ptr() if vals.numel() else None, L.TC_MEM_DEVICE,
+                                       _stream(stream)), "tc_part_set_values")
+
+
+def spmv_tocab(part: "Partition", x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """tc_spmv_tocab: y = A x through the TC_PUSH partition of A's graph (GC-pull)."""
+    V = part.graph.V
+    if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.numel() < V:
+        raise ValueError(f"x must be a contiguous float32 CUDA tensor with {V} elements")
+    if out is None:
+        out = torch.empty(V, dtype=torch.float32, device="cuda")
+    if out.dtype != torch.float32 or not out.is_cuda or not out.is_contiguous() or out.numel() < V:
+        raise ValueError("out must be a contiguous float32 CUDA tensor with V elements")
+    _check(L.load().tc_spmv_tocab(part.handle, x.data_ptr(), out.data_ptr(), L.TC_MEM_DEVICE, _stream(stream)),
+           "tc_spmv_tocab")
     return out
 
 

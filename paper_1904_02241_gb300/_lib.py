@@ -110,6 +110,8 @@ SIGNATURES = {
     "tc_bc_forward": (C.c_int, [VP, C.c_int32, C.c_int, VP, VP, VP]),
     "tc_bc": (C.c_int, [VP, VP, C.c_int32, C.c_int, VP, VP]),
     "tc_spmv": (C.c_int, [VP, VP, VP, VP, C.c_int, VP]),
+    "tc_part_set_values": (C.c_int, [VP, VP, C.c_int, VP]),
+    "tc_spmv_tocab": (C.c_int, [VP, VP, VP, C.c_int, VP]),
     "tc_ppr_batch": (C.c_int, [VP, VP, VP, C.c_int32, C.POINTER(tc_pr_params), VP, C.POINTER(tc_pr_stats), VP]),
     "tc_ppr_autotune": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_pr_params), C.POINTER(C.c_int32),
                                   C.POINTER(C.c_int32), VP, VP]),

@@ -223,6 +223,9 @@ struct tc_part {
     tc::DevBuf blk_rows_dev;    // int64[B+1]
     tc::DevBuf esrc;            // push only: int32[E] source (global) of every edge, for the
                                 // edge-parallel scatter
+    bool pperm_built = false, has_vals = false;  // push: values of the matrix (GC-pull SpMV)
+    tc::DevBuf pperm;           // int32[E]: the loaded CSR position of every partition entry
+    tc::DevBuf pvals;           // float[E]: the matrix values in partition order
     int32_t nptiles = 0;        // push, W * 8 bytes within shared memory: tiles of the staged push
     tc::DevBuf ptiles;          // int4[nptiles]: (block, first edge low 31 bits, high bits, edges)
     // ---- shared-memory staged format (pull, W <= smem capacity; see tc_tile.cu) ----

@@ -94,3 +94,152 @@ extern "C" int tc_spmv(const tc_graph *g, const float *vals, const float *x, flo
     }
     return TC_OK;
 }
+
+// ---------------------------------------------------------------------------------------------
+// GC-pull SpMV (Sec. 4's SpMV with TOCAB, a value stream of 4 B per entry): a TC_PUSH partition
+// of the matrix's CSR cuts its columns into ranges of W (so x[block] is the block's working set,
+// Sec. 3.1 with the value read from x instead of the contributions); each (block, row) piece is a
+// local row whose partial sum goes to partial[], and the merge of Fig. 5 adds a row's pieces in
+// block order into y.  FP32; deterministic (a fixed order everywhere).
+// ---------------------------------------------------------------------------------------------
+namespace tc {
+
+__global__ void k_iota(int64_t n, int32_t *out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (int32_t)i;
+}
+
+__global__ void k_gather_vals(const int32_t *__restrict__ perm, const float *__restrict__ vals, int64_t n,
+                              float *__restrict__ out) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = vals[perm[i]];
+}
+
+// Local rows: a lane each below 32 entries (in order), a warp each from 32 (lane strides in
+// order, then a fixed shuffle tree).
+__global__ void __launch_bounds__(SP_THREADS) k_spmv_block_rows(const int32_t *__restrict__ rowptr,
+                                                                const int32_t *__restrict__ colidx,
+                                                                const float *__restrict__ pvals,
+                                                                const float *__restrict__ x, int64_t R,
+                                                                float *__restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (SP_THREADS / 32);
+    for (int64_t grp = (blockIdx.x * (int64_t)SP_THREADS + threadIdx.x) >> 5; grp * 32 < R; grp += nw) {
+        const int64_t r = grp * 32 + lane;
+        int32_t s = 0, e = 0;
+        if (r < R) {
+            s = __ldg(rowptr + r);
+            e = __ldg(rowptr + r + 1);
+        }
+        float acc = 0.0f;
+        if (e - s < 32)
+            for (int32_t k = s; k < e; ++k) acc = fmaf(__ldg(pvals + k), __ldg(x + __ldg(colidx + k)), acc);
+        unsigned long_rows = __ballot_sync(0xffffffffu, e - s >= 32);
+        while (long_rows) {
+            const int l = __ffs(long_rows) - 1;
+            long_rows &= long_rows - 1;
+            const int32_t ls = __shfl_sync(0xffffffffu, s, l), le = __shfl_sync(0xffffffffu, e, l);
+            float w = 0.0f;
+            for (int32_t k = ls + lane; k < le; k += 32) w = fmaf(__ldg(pvals + k), __ldg(x + __ldg(colidx + k)), w);
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+            if (lane == l) acc = w;
+        }
+        if (r < R) partial[r] = acc;
+    }
+}
+
+// Fig. 5: CTA j owns rows [j k, (j+1) k); it adds block b's slice for b = 0, 1, ... in order (the
+// rows of one slice are distinct, so its threads never collide), then writes y.
+__global__ void __launch_bounds__(SP_THREADS) k_spmv_merge(const float *__restrict__ partial,
+                                                           const int32_t *__restrict__ id_map,
+                                                           const int32_t *__restrict__ merge_off, int32_t B,
+                                                           int32_t nranges, int32_t k, int32_t V, float *y) {
+    extern __shared__ float macc[];  // [k]
+    for (int32_t j = blockIdx.x; j < nranges; j += gridDim.x) {
+        const int32_t vbase = j * k;
+        for (int32_t t = threadIdx.x; t < k; t += SP_THREADS) macc[t] = 0.0f;
+        __syncthreads();
+        for (int32_t b = 0; b < B; ++b) {
+            const int32_t *o = merge_off + (int64_t)b * (nranges + 1) + j;
+            const int32_t r0 = __ldg(o), r1 = __ldg(o + 1);
+            for (int32_t r = r0 + threadIdx.x; r < r1; r += SP_THREADS) macc[__ldg(id_map + r) - vbase] += __ldg(partial + r);
+            __syncthreads();
+        }
+        for (int32_t t = threadIdx.x; t < k && vbase + t < V; t += SP_THREADS) y[vbase + t] = macc[t];
+        __syncthreads();
+    }
+}
+
+}  // namespace tc
+
+extern "C" int tc_part_set_values(tc_part *p, const float *vals, int mem, void *stream) {
+    using namespace tc;
+    if (!p || (p->E > 0 && !vals)) return fail(TC_ERR_INVALID_ARG, "tc_part_set_values: null partition or values");
+    if (p->dir != TC_PUSH) return fail(TC_ERR_INVALID_ARG, "tc_part_set_values: needs a TC_PUSH partition");
+    if (mem != TC_MEM_DEVICE) return fail(TC_ERR_UNSUPPORTED, "tc_part_set_values: vals must be a device pointer");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t E = p->E;
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    const int grid = caps.sms * 8;
+    if (!p->pperm_built) {  // the partition's own sort again, carrying each entry's position
+        TC_TRY(p->pperm.alloc((size_t)(E > 0 ? E : 1) * 4));
+        if (E > 0) {
+            DevBuf iota, keys, kt, vt;
+            TC_TRY(iota.alloc((size_t)E * 4));
+            k_iota<<<grid, 256, 0, s>>>(E, iota.as<int32_t>());
+            TC_LAUNCH_CHECK();
+            if (p->B > 1) {
+                TC_TRY(keys.alloc((size_t)E * 4));
+                TC_TRY(kt.alloc((size_t)E * 4));
+                TC_TRY(vt.alloc((size_t)E * 4));
+                int bits = 0;
+                while ((1LL << bits) < (int64_t)p->B) ++bits;
+                TC_TRY(stable_bucket_sort(p->g->out_colidx.as<int32_t>(), iota.as<int32_t>(), keys.as<int32_t>(),
+                                          p->pperm.as<int32_t>(), kt.as<int32_t>(), vt.as<int32_t>(), E, p->W, bits, s));
+            } else {
+                TC_CUDA(cudaMemcpyAsync(p->pperm.p, iota.p, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
+            }
+            TC_CUDA(cudaStreamSynchronize(s));  // the scratch is freed at the end of this block
+        }
+        p->pperm_built = true;
+    }
+    TC_TRY(p->pvals.alloc((size_t)(E > 0 ? E : 1) * 4));
+    if (E > 0) {
+        k_gather_vals<<<grid, 256, 0, s>>>(p->pperm.as<int32_t>(), vals, E, p->pvals.as<float>());
+        TC_LAUNCH_CHECK();
+    }
+    TC_CUDA(cudaStreamSynchronize(s));
+    p->has_vals = true;
+    return TC_OK;
+}
+
+extern "C" int tc_spmv_tocab(const tc_part *p, const float *x, float *y, int mem, void *stream) {
+    using namespace tc;
+    if (!p || !x || !y) return fail(TC_ERR_INVALID_ARG, "tc_spmv_tocab: null partition or vector");
+    if (p->dir != TC_PUSH || !p->has_vals)
+        return fail(TC_ERR_INVALID_ARG, "tc_spmv_tocab: needs a TC_PUSH partition given values by tc_part_set_values");
+    if (mem != TC_MEM_DEVICE) return fail(TC_ERR_UNSUPPORTED, "tc_spmv_tocab: x and y must be device pointers");
+    const int32_t V = p->V;
+    if (V == 0) return TC_OK;
+    if ((size_t)p->k * 4 > 200 * 1024) return fail(TC_ERR_UNSUPPORTED, "tc_spmv_tocab: merge_range above 51,200");
+    DeviceCaps caps;
+    TC_TRY(device_caps(&caps));
+    cudaStream_t s = (cudaStream_t)stream;
+    if (p->R > 0) {
+        const int64_t want = (p->R + SP_THREADS - 1) / SP_THREADS;
+        const int grid = (int)(want < (int64_t)caps.sms * 16 ? (want > 0 ? want : 1) : (int64_t)caps.sms * 16);
+        k_spmv_block_rows<<<grid, SP_THREADS, 0, s>>>(p->rowptr.as<int32_t>(), p->colidx.as<int32_t>(),
+                                                      p->pvals.as<float>(), x, p->R,
+                                                      const_cast<float *>(p->partial.as<float>()));
+        TC_LAUNCH_CHECK();
+    }
+    const size_t smem = (size_t)p->k * 4;
+    TC_CUDA(cudaFuncSetAttribute(k_spmv_merge, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    const int mgrid = p->nranges < caps.sms * 8 ? (p->nranges > 0 ? p->nranges : 1) : caps.sms * 8;
+    k_spmv_merge<<<mgrid, SP_THREADS, smem, s>>>(p->partial.as<float>(), p->id_map.as<int32_t>(),
+                                                 p->merge_off.as<int32_t>(), p->B, p->nranges, p->k, V, y);
+    TC_LAUNCH_CHECK();
+    return TC_OK;
+}

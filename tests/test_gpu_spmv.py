@@ -75,3 +75,64 @@ def test_host_memory_is_refused(T):
     x = torch.ones(g.V, dtype=torch.float32)
     st = L.load().tc_spmv(G.handle, v.data_ptr(), x.data_ptr(), x.data_ptr(), L.TC_MEM_HOST, None)
     assert st == -6
+
+
+# ------------------------------------------------------------------ GC-pull SpMV (TOCAB, value stream)
+
+@pytest.mark.parametrize("name", ["rmat", "er", "plc", "grid", "star"])
+@pytest.mark.parametrize("B", [1, 3, 8, 64])
+def test_gc_pull_matches_oracle_within_the_fp32_bound(T, name, B):
+    """The pieces of a row are summed like a row of the warp form, then added in block order: at
+    most d_i + 6 + B roundings in the longest chain."""
+    g = {"rmat": gg.rmat(12), "er": gg.random_small(3000, 40000, 2), "plc": gg.powerlaw_config(4000, 8, 2.2, seed=5),
+         "grid": gg.grid2d(60, 70), "star": gg.star(5000)}[name]
+    if B > g.V:
+        pytest.skip("B > V")
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+    P = T.tocab_partition(G, T.TC_PUSH, B, merge_range=1024)
+    vals = gg.edge_values(g, seed=31)
+    x = torch.from_numpy(np.random.default_rng(B).standard_normal(g.V).astype(np.float32))
+    T.part_set_values(P, vals.cuda())
+    y = T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64)
+    rp, ci = g.numpy()
+    v64, x64 = vals.numpy().astype(np.float64), x.numpy().astype(np.float64)
+    want = oracle.spmv(g.V, rp, ci, v64, x64)
+    mag = oracle.spmv(g.V, rp, ci, np.abs(v64), np.abs(x64))
+    bound = (np.diff(rp) + 6 + P.num_blocks) * 2.0 ** -24 * mag
+    assert np.all(np.abs(y - want) <= bound + 1e-30)
+    assert np.array_equal(y, T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64))  # fixed order
+    # new values through the same partition (the recorded entry order is reused)
+    vals2 = gg.edge_values(g, seed=32)
+    T.part_set_values(P, vals2.cuda())
+    y2 = T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64)
+    v2 = vals2.numpy().astype(np.float64)
+    want2 = oracle.spmv(g.V, rp, ci, v2, x64)
+    bound2 = (np.diff(rp) + 6 + P.num_blocks) * 2.0 ** -24 * oracle.spmv(g.V, rp, ci, np.abs(v2), np.abs(x64))
+    assert np.all(np.abs(y2 - want2) <= bound2 + 1e-30)
+
+
+def test_gc_pull_permutation_matrix_is_exact(T):
+    n = 3000
+    perm = np.random.default_rng(9).permutation(n)
+    g = gg.from_edge_list(n, np.stack([np.arange(n), perm], 1))
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=n)
+    P = T.tocab_partition(G, T.TC_PUSH, 7, merge_range=512)
+    T.part_set_values(P, torch.ones(g.E, dtype=torch.float32, device="cuda"))
+    x = torch.from_numpy(np.random.default_rng(1).standard_normal(n).astype(np.float32)).cuda()
+    y = T.spmv_tocab(P, x).cpu().numpy()
+    rp, ci = g.numpy()
+    want = np.zeros(n, np.float32)  # rows whose entry was a self loop were dropped: they are empty
+    want[np.repeat(np.arange(n), np.diff(rp))] = x.cpu().numpy()[ci]
+    np.testing.assert_array_equal(y, want)  # row i holds x[perm[i]] exactly
+
+
+def test_gc_pull_refusals(T):
+    g = gg.rmat(10)
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+    x = torch.ones(g.V, dtype=torch.float32, device="cuda")
+    Pp = T.tocab_partition(G, T.TC_PULL, 2)
+    with pytest.raises(T.TocabError):
+        T.part_set_values(Pp, torch.ones(g.E, dtype=torch.float32, device="cuda"))
+    P = T.tocab_partition(G, T.TC_PUSH, 2)
+    with pytest.raises(T.TocabError):
+        T.spmv_tocab(P, x)  # no values yet

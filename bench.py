@@ -419,7 +419,7 @@ def variants(args, ctx, world):
     res["rmat16"] = rmat16_row(stream, run)
     res["bfs_grid4096"] = bfs_grid_row(stream)
     res.update(spmv_row(stream))
-    res.update(bc_row(stream))
+    res.update(bc_rows(stream))
     res.update(graph_variants(args, stream, E, run))
     res.update(batch_variants(args, stream))
     return res
@@ -671,6 +671,11 @@ def spmv_row(stream, scale: int = 22):
                      "gc_pull_by_blocks": gc}}
 
 
+def bc_rows(stream):
+    """BC on the symmetrised R-MAT 18 (the earlier row) and 21 (vertex arrays beyond L1/L2 reach)."""
+    return {"bc": bc_row(stream, 18)["bc"], "bc_rmat21": bc_row(stream, 21)["bc"]}
+
+
 def bc_row(stream, scale: int = 18, nsrc: int = 4):
     """Betweenness centrality from a few seeded sources on the symmetrised R-MAT; TEPS counts each
     undirected edge once per source."""
@@ -682,8 +687,16 @@ def bc_row(stream, scale: int = 18, nsrc: int = 4):
     T.bc(G, srcs[:1], out=out)
     torch.cuda.synchronize()
     ms = statistics.median(time_runs(lambda: T.bc(G, srcs, out=out), 3, stream))
+    blocked = {}
+    for B in (4, 16, 64):  # TOCAB pull levels (tc_bc_tocab): the same scores, bit for bit
+        P = T.tocab_partition(G, T.TC_PULL, B, merge_range=8192, smem_stage=-1)
+        T.bc(G, srcs[:1], out=out, part=P)
+        torch.cuda.synchronize()
+        ms_b = statistics.median(time_runs(lambda: T.bc(G, srcs, out=out, part=P), 3, stream))
+        blocked[str(B)] = {"ms": round(ms_b, 3), "gteps": round(gs.E / 2 * nsrc / (ms_b * 1e-3) / 1e9, 3)}
+        del P
     return {"bc": {"graph": f"rmat{scale}_sym", "V": gs.V, "E_directed": gs.E, "sources": nsrc, "ms": round(ms, 3),
-                   "gteps": round(gs.E / 2 * nsrc / (ms * 1e-3) / 1e9, 3)}}
+                   "gteps": round(gs.E / 2 * nsrc / (ms * 1e-3) / 1e9, 3), "tocab_pull_levels_by_blocks": blocked}}
 
 
 def e2e(args, ctx):
@@ -842,7 +855,7 @@ def main():
             torch.cuda.synchronize()
             return statistics.median(time_runs(fn, 5, stream))
         res = {"many_graphs": lambda: many_graphs(stream, with_oracle=False), "spmv": lambda: spmv_row(stream),
-               "bc": lambda: bc_row(stream), "bfs_grid": lambda: {"bfs_grid4096": bfs_grid_row(stream)},
+               "bc": lambda: bc_rows(stream), "bfs_grid": lambda: {"bfs_grid4096": bfs_grid_row(stream)},
                "rmat16": lambda: {"rmat16": rmat16_row(stream, run)},
                "ppr": lambda: ppr_row(stream), "ppr_probe": lambda: ppr_probe_row(stream, 0),
                "ppr_probe_tile32": lambda: ppr_probe_row(stream, 32),

@@ -460,10 +460,11 @@ int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int32_t *depth
  *   dep[v] = sum over out-neighbours w with depth[w] = depth[v] + 1 of sigma[v]/sigma[w] (1 + dep[w]),
  * pulled over the out-edges of G; scores_out[v] = the sum of dep[v] over the sources other than
  * v itself.  Scores are not normalised and count ordered targets (an undirected graph given
- * with both edge directions counts every pair twice).  FP64 throughout; every product, quotient
- * and sum is rounded separately; a warp takes each vertex of a level, each lane summing its
- * strided share of the out-row in order and a fixed shuffle tree adding the lanes, so the
- * result is deterministic.
+ * with both edge directions counts every pair twice).  FP64 throughout, computed as
+ * dep[v] = sigma[v] * sum over w of (1 + dep[w]) / sigma[w] (one division per vertex); every
+ * product, quotient and sum is rounded separately; a warp takes each vertex of a level, each
+ * lane summing its strided share of the out-row in order and a fixed shuffle tree adding the
+ * lanes, so the result is deterministic.
  *   sources : host int32[num_sources], each in [0, V) (repeats allowed; 0 sources gives zeros).
  *   out_mem : memory space of scores_out (double[V]).
  * Scratch: 2 int32[V] + 3 double[V] (+ double[V] for host output), per call.
@@ -471,6 +472,19 @@ int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int32_t *depth
  */
 int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int out_mem, double *scores_out,
           void *stream);
+
+/*
+ * tc_bc_tocab -- tc_bc with TOCAB in the pull levels of the forward sweep (Sec. 3.3: the
+ * push-pull-push BC with blocked pull levels, where "next" carries the sigma sums of the block's
+ * local rows): each local row of the partition sums sigma over its sources of depth L, then the
+ * merge of Fig. 5 adds a destination's pieces in block order (integers: exact), so depths, sigma
+ * and the scores equal tc_bc's bit for bit.
+ *   part : a TC_PULL partition of g in the graph's own numbering (TC_ERR_UNSUPPORTED for a
+ *          renumbered one), merge_range at most 25,600.
+ * Scratch: as tc_bc, plus double[R].  Errors: as tc_bc.
+ */
+int tc_bc_tocab(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t num_sources, int out_mem,
+                double *scores_out, void *stream);
 
 /* ---- sparse matrix-vector product ---------------------------------------------------------- */
 /*

@@ -274,16 +274,22 @@ def bc_forward(graph: Graph, source: int, stream=None):
     return depth, sigma
 
 
-def bc(graph: Graph, sources=None, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """tc_bc: betweenness scores summed over ``sources`` (all vertices when None) -> float64[V]."""
+def bc(graph: Graph, sources=None, out: torch.Tensor | None = None, stream=None,
+       part: "Partition | None" = None) -> torch.Tensor:
+    """tc_bc: betweenness scores summed over ``sources`` (all vertices when None) -> float64[V].
+    part: a TC_PULL partition of the graph for blocked pull levels (tc_bc_tocab; same result)."""
     src = torch.arange(graph.V, dtype=torch.int32) if sources is None else \
         torch.as_tensor(sources, dtype=torch.int32).reshape(-1).contiguous().cpu()
     if out is None:
         out = torch.empty(graph.V, dtype=torch.float64, device="cuda")
     if out.dtype != torch.float64 or out.numel() < graph.V or not out.is_contiguous():
         raise ValueError("out must be a contiguous float64 tensor with V elements")
-    _check(L.load().tc_bc(graph.handle, src.data_ptr() if src.numel() else None, src.numel(), _mem(out),
-                          out.data_ptr(), _stream(stream)), "tc_bc")
+    sp = src.data_ptr() if src.numel() else None
+    if part is None:
+        _check(L.load().tc_bc(graph.handle, sp, src.numel(), _mem(out), out.data_ptr(), _stream(stream)), "tc_bc")
+    else:
+        _check(L.load().tc_bc_tocab(graph.handle, part.handle, sp, src.numel(), _mem(out), out.data_ptr(),
+                                    _stream(stream)), "tc_bc_tocab")
     return out
 
 

@@ -109,6 +109,7 @@ SIGNATURES = {
     "tc_bfs_pull": (C.c_int, [VP, VP, C.c_int32, C.POINTER(tc_bfs_params), VP, C.POINTER(tc_bfs_stats), VP]),
     "tc_bc_forward": (C.c_int, [VP, C.c_int32, C.c_int, VP, VP, VP]),
     "tc_bc": (C.c_int, [VP, VP, C.c_int32, C.c_int, VP, VP]),
+    "tc_bc_tocab": (C.c_int, [VP, VP, VP, C.c_int32, C.c_int, VP, VP]),
     "tc_spmv": (C.c_int, [VP, VP, VP, VP, C.c_int, VP]),
     "tc_part_set_values": (C.c_int, [VP, VP, C.c_int, VP]),
     "tc_spmv_tocab": (C.c_int, [VP, VP, VP, C.c_int, VP]),

@@ -16,14 +16,16 @@
 //
 // Backward sweep: the dependency back-propagation of the BC the paper cites, over the level
 // lists from the deepest, pulled over the out-edges of G: for a vertex v of depth L,
-//   dep[v] = sum over out-neighbours w of depth L+1 of sigma[v] / sigma[w] * (1 + dep[w]),
-// one warp per vertex: each lane adds its strided share of the row in order, then a fixed
-// shuffle tree adds the lane sums; every vertex other than the source adds dep[v] to its score.
-// Products, quotients and sums are rounded one by one (no fused multiply-add).  A vertex's
-// dependency reads only final values of the next level, so the order of a level's list (which
-// the forward sweep fills as vertices are reached) does not change any result.
+//   dep[v] = sum over out-neighbours w of depth L+1 of sigma[v] / sigma[w] * (1 + dep[w])
+//          = sigma[v] * sum over those w of coef[w],   coef[w] = (1 + dep[w]) / sigma[w],
+// so each vertex divides once (when its dependency is known) and each edge only adds; FP64
+// division is slow on this GPU.  One warp per vertex: each lane adds its strided share of the
+// row in order, then a fixed shuffle tree adds the lane sums; every vertex other than the source
+// adds dep[v] to its score.  Operations are rounded one by one (no fused multiply-add).  A
+// vertex's dependency reads only final values of the next level, so the order of a level's list
+// (which the forward sweep fills as vertices are reached) does not change any result.
 //
-// sigma, dep and the scores are FP64.
+// sigma, the coefficients and the scores are FP64.
 #include <vector>
 
 #include "tc_internal.cuh"
@@ -34,11 +36,11 @@ constexpr int BC_THREADS = 256;
 constexpr int BC_WARPS = BC_THREADS / 32;
 constexpr int BC_LONG = 32;  // rows with at least this many edges get a warp in pull levels
 
-__global__ void k_bc_init(int32_t V, int32_t source, int32_t *depth, double *sigma, double *dep, int32_t *order) {
+__global__ void k_bc_init(int32_t V, int32_t source, int32_t *depth, double *sigma, double *coef, int32_t *order) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < V; v += (int64_t)gridDim.x * blockDim.x) {
         depth[v] = v == source ? 0 : -1;
         sigma[v] = v == source ? 1.0 : 0.0;
-        dep[v] = 0.0;
+        coef[v] = 0.0;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) order[0] = source;  // level 0
 }
@@ -131,6 +133,85 @@ __global__ void __launch_bounds__(BC_THREADS) k_bc_pull_long(const int32_t *__re
     }
 }
 
+// Blocked pull level (TOCAB, Sec. 3.3 with sigma sums as the "next" values): local row r of a
+// pull partition (block b's in-edges of destination id_map[r]) gets the sum of sigma over its
+// sources of depth L, 0 when it has none or its destination is already reached.  A lane takes a
+// row below 32 edges, a warp a longer one.  The sums are integers: exact in any order.
+__global__ void __launch_bounds__(BC_THREADS) k_bc_block_level(const int32_t *__restrict__ rowptr,
+                                                               const int32_t *__restrict__ colidx,
+                                                               const int32_t *__restrict__ id_map, int64_t R,
+                                                               int32_t L, const int32_t *__restrict__ depth,
+                                                               const double *__restrict__ sigma,
+                                                               double *__restrict__ partial) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * BC_WARPS;
+    for (int64_t grp = (blockIdx.x * (int64_t)BC_THREADS + threadIdx.x) >> 5; grp * 32 < R; grp += nw) {
+        const int64_t r = grp * 32 + lane;
+        int32_t s = 0, e = 0;
+        if (r < R && depth[__ldg(id_map + r)] == -1) {
+            s = __ldg(rowptr + r);
+            e = __ldg(rowptr + r + 1);
+        }
+        double acc = 0.0;
+        if (e - s < BC_LONG)
+            for (int32_t i = s; i < e; ++i) {
+                const int32_t u = __ldg(colidx + i);
+                if (depth[u] == L) acc = __dadd_rn(acc, sigma[u]);
+            }
+        unsigned long_rows = __ballot_sync(0xffffffffu, e - s >= BC_LONG);
+        while (long_rows) {
+            const int l = __ffs(long_rows) - 1;
+            long_rows &= long_rows - 1;
+            const int32_t ls = __shfl_sync(0xffffffffu, s, l), le = __shfl_sync(0xffffffffu, e, l);
+            double w = 0.0;
+            for (int32_t i = ls + lane; i < le; i += 32) {
+                const int32_t u = __ldg(colidx + i);
+                if (depth[u] == L) w = __dadd_rn(w, sigma[u]);
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) w = __dadd_rn(w, __shfl_xor_sync(0xffffffffu, w, d));
+            if (lane == l) acc = w;
+        }
+        if (r < R) partial[r] = acc;
+    }
+}
+
+// The blocked level's merge (Fig. 5): CTA j adds the partial sums of vertices [j k, (j+1) k) over
+// the blocks in order, then every unreached vertex with a nonzero sum takes depth L+1 and that
+// sigma and joins the next frontier.
+__global__ void __launch_bounds__(BC_THREADS) k_bc_block_merge(const double *__restrict__ partial,
+                                                               const int32_t *__restrict__ id_map,
+                                                               const int32_t *__restrict__ merge_off, int32_t B,
+                                                               int32_t nranges, int32_t k, int32_t V, int32_t L,
+                                                               int32_t *depth, double *sigma, int32_t *next,
+                                                               unsigned *next_count) {
+    extern __shared__ double bacc[];  // [k]
+    for (int32_t j = blockIdx.x; j < nranges; j += gridDim.x) {
+        const int32_t vbase = j * k;
+        for (int32_t t = threadIdx.x; t < k; t += BC_THREADS) bacc[t] = 0.0;
+        __syncthreads();
+        for (int32_t b = 0; b < B; ++b) {
+            const int32_t *o = merge_off + (int64_t)b * (nranges + 1) + j;
+            const int32_t r0 = __ldg(o), r1 = __ldg(o + 1);
+            for (int32_t r = r0 + threadIdx.x; r < r1; r += BC_THREADS) {
+                const double x = partial[r];
+                if (x != 0.0) bacc[__ldg(id_map + r) - vbase] = __dadd_rn(bacc[__ldg(id_map + r) - vbase], x);
+            }
+            __syncthreads();
+        }
+        for (int32_t t = threadIdx.x; t < k && vbase + t < V; t += BC_THREADS) {
+            const double x = bacc[t];
+            const int32_t v = vbase + t;
+            if (x != 0.0 && depth[v] == -1) {
+                depth[v] = L + 1;
+                sigma[v] = x;
+                next[atomicAdd(next_count, 1u)] = v;
+            }
+        }
+        __syncthreads();
+    }
+}
+
 // dependencies of the vertices of depth L (those of depth L+1 are final): a warp per vertex of
 // the level's list
 __global__ void __launch_bounds__(BC_THREADS) k_bc_backward(const int32_t *__restrict__ rowptr,
@@ -138,22 +219,23 @@ __global__ void __launch_bounds__(BC_THREADS) k_bc_backward(const int32_t *__res
                                                             const int32_t *__restrict__ level_list, int64_t n,
                                                             int32_t L, int32_t source,
                                                             const int32_t *__restrict__ depth,
-                                                            const double *__restrict__ sigma, double *dep,
+                                                            const double *__restrict__ sigma, double *coef,
                                                             double *score) {
     const int lane = threadIdx.x & 31;
     const int64_t nw = (int64_t)gridDim.x * BC_WARPS;
     for (int64_t k = (blockIdx.x * (int64_t)BC_THREADS + threadIdx.x) >> 5; k < n; k += nw) {
         const int32_t v = level_list[k];
-        const double sv = sigma[v];
-        double d = 0.0;
+        double t = 0.0;  // sum of (1 + dep[w]) / sigma[w] over the children w
         for (int32_t e = rowptr[v] + lane; e < rowptr[v + 1]; e += 32) {
             const int32_t w = colidx[e];
-            if (depth[w] == L + 1) d = __dadd_rn(d, __dmul_rn(__ddiv_rn(sv, sigma[w]), __dadd_rn(1.0, dep[w])));
+            if (depth[w] == L + 1) t = __dadd_rn(t, coef[w]);
         }
 #pragma unroll
-        for (int q = 16; q > 0; q >>= 1) d = __dadd_rn(d, __shfl_xor_sync(0xffffffffu, d, q));
+        for (int q = 16; q > 0; q >>= 1) t = __dadd_rn(t, __shfl_xor_sync(0xffffffffu, t, q));
         if (lane == 0) {
-            dep[v] = d;
+            const double sv = sigma[v];
+            const double d = __dmul_rn(sv, t);
+            coef[v] = __ddiv_rn(__dadd_rn(1.0, d), sv);  // for the parents of v, one level up
             if (v != source) score[v] = __dadd_rn(score[v], d);
         }
     }
@@ -164,18 +246,23 @@ __global__ void __launch_bounds__(BC_THREADS) k_bc_backward(const int32_t *__res
 constexpr int64_t BC_PUSH_RATIO = 14;
 
 struct BcScratch {
-    DevBuf depth, sigma, dep, score, order, counter, longrows;
+    DevBuf depth, sigma, coef, score, order, counter, longrows, bpartial;
     int32_t nlong = 0;
     std::vector<int64_t> off;  // level L of `order` is [off[L], off[L+1])
     int grid = 1;
-    int setup(const tc_graph *g, bool need_score, cudaStream_t s) {
+    int setup(const tc_graph *g, bool need_score, cudaStream_t s, const tc_part *part = nullptr) {
+        if (part) {
+            TC_TRY(bpartial.alloc((size_t)(part->R > 0 ? part->R : 1) * 8));
+            TC_CUDA(cudaFuncSetAttribute(k_bc_block_merge, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)part->k * 8)));
+        }
         const int32_t V = g->V;
         DeviceCaps caps;
         TC_TRY(device_caps(&caps));
         grid = caps.sms * 8;
         TC_TRY(depth.alloc((size_t)V * 4));
         TC_TRY(sigma.alloc((size_t)V * 8));
-        TC_TRY(dep.alloc((size_t)V * 8));
+        TC_TRY(coef.alloc((size_t)V * 8));
         TC_TRY(order.alloc((size_t)V * 4));
         if (need_score) TC_TRY(score.alloc((size_t)V * 8));
         TC_TRY(counter.alloc(16));
@@ -186,13 +273,13 @@ struct BcScratch {
 
 // Forward sweep from `source`: depth/sigma, and w.order holding the reached vertices level by
 // level.  *max_depth = the deepest level (levels 0 .. *max_depth).  *pushed counts push levels.
-static int bc_forward_impl(const tc_graph *g, int32_t source, BcScratch &w, cudaStream_t s, int32_t *max_depth,
-                           int32_t *pushed) {
+static int bc_forward_impl(const tc_graph *g, const tc_part *part, int32_t source, BcScratch &w, cudaStream_t s,
+                           int32_t *max_depth, int32_t *pushed) {
     const int32_t V = g->V;
     int32_t *depth = w.depth.as<int32_t>(), *order = w.order.as<int32_t>();
     double *sigma = w.sigma.as<double>();
     unsigned *cnt = w.counter.as<unsigned>();
-    k_bc_init<<<w.grid, BC_THREADS, 0, s>>>(V, source, depth, sigma, w.dep.as<double>(), order);
+    k_bc_init<<<w.grid, BC_THREADS, 0, s>>>(V, source, depth, sigma, w.coef.as<double>(), order);
     TC_LAUNCH_CHECK();
     w.off.assign(1, 0);
     w.off.push_back(1);
@@ -209,6 +296,19 @@ static int bc_forward_impl(const tc_graph *g, int32_t source, BcScratch &w, cuda
                                                   order + f0, nf, L, depth, sigma, next, cnt);
             TC_LAUNCH_CHECK();
             ++np;
+        } else if (part) {  // blocked pull level (TOCAB) and its merge
+            if (part->R > 0) {
+                k_bc_block_level<<<w.grid, BC_THREADS, 0, s>>>(part->rowptr.as<int32_t>(), part->colidx.as<int32_t>(),
+                                                               part->id_map.as<int32_t>(), part->R, L, depth, sigma,
+                                                               w.bpartial.as<double>());
+                TC_LAUNCH_CHECK();
+            }
+            const size_t smem = (size_t)part->k * 8;
+            const int mgrid = part->nranges < w.grid ? (part->nranges > 0 ? part->nranges : 1) : w.grid;
+            k_bc_block_merge<<<mgrid, BC_THREADS, smem, s>>>(w.bpartial.as<double>(), part->id_map.as<int32_t>(),
+                                                             part->merge_off.as<int32_t>(), part->B, part->nranges,
+                                                             part->k, V, L, depth, sigma, next, cnt);
+            TC_LAUNCH_CHECK();
         } else {
             k_bc_pull<<<w.grid, BC_THREADS, 0, s>>>(g->in_rowptr.as<int32_t>(), g->in_colidx.as<int32_t>(), V, L,
                                                     depth, sigma, next, cnt);
@@ -244,7 +344,7 @@ extern "C" int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int
     BcScratch w;
     TC_TRY(w.setup(g, false, s));
     int32_t maxd = 0;
-    TC_TRY(bc_forward_impl(g, source, w, s, &maxd, nullptr));
+    TC_TRY(bc_forward_impl(g, nullptr, source, w, s, &maxd, nullptr));
     const cudaMemcpyKind kind = out_mem == TC_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
     TC_CUDA(cudaMemcpyAsync(depth_out, w.depth.p, (size_t)V * 4, kind, s));
     TC_CUDA(cudaMemcpyAsync(sigma_out, w.sigma.p, (size_t)V * 8, kind, s));
@@ -252,9 +352,32 @@ extern "C" int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int
     return TC_OK;
 }
 
+namespace tc {
+static int bc_impl(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t num_sources, int out_mem,
+                   double *scores_out, void *stream);
+}  // namespace tc
+
 extern "C" int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int out_mem, double *scores_out,
                      void *stream) {
+    return tc::bc_impl(g, nullptr, sources, num_sources, out_mem, scores_out, stream);
+}
+
+extern "C" int tc_bc_tocab(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t num_sources,
+                           int out_mem, double *scores_out, void *stream) {
     using namespace tc;
+    if (!part) return fail(TC_ERR_INVALID_ARG, "tc_bc_tocab: null partition");
+    if (part->g != g || part->dir != TC_PULL)
+        return fail(TC_ERR_INVALID_ARG, "tc_bc_tocab: the partition must be a TC_PULL partition of this graph");
+    if (part->order != TC_ORDER_NATURAL)
+        return fail(TC_ERR_UNSUPPORTED, "tc_bc_tocab: renumbered (TC_ORDER_OUTDEGREE) partitions are not supported");
+    if ((size_t)part->k * 8 > 200 * 1024)
+        return fail(TC_ERR_UNSUPPORTED, "tc_bc_tocab: merge_range above 25,600");
+    return bc_impl(g, part, sources, num_sources, out_mem, scores_out, stream);
+}
+
+namespace tc {
+static int bc_impl(const tc_graph *g, const tc_part *part, const int32_t *sources, int32_t num_sources, int out_mem,
+                   double *scores_out, void *stream) {
     if (!g || !scores_out || (num_sources > 0 && !sources))
         return fail(TC_ERR_INVALID_ARG, "tc_bc: null graph, sources or output");
     if (num_sources < 0) return fail(TC_ERR_INVALID_ARG, "tc_bc: num_sources < 0");
@@ -266,13 +389,13 @@ extern "C" int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sour
     if (V == 0) return TC_OK;
     BcScratch w;
     const bool dev_out = out_mem == TC_MEM_DEVICE;
-    TC_TRY(w.setup(g, !dev_out, s));
+    TC_TRY(w.setup(g, !dev_out, s, part));
     double *score = dev_out ? scores_out : w.score.as<double>();
     k_bc_zero<<<w.grid, BC_THREADS, 0, s>>>(V, score);
     TC_LAUNCH_CHECK();
     for (int32_t k = 0; k < num_sources; ++k) {
         int32_t maxd = 0;
-        TC_TRY(bc_forward_impl(g, sources[k], w, s, &maxd, nullptr));
+        TC_TRY(bc_forward_impl(g, part, sources[k], w, s, &maxd, nullptr));
         for (int32_t L = maxd; L >= 0; --L) {
             const int64_t a = w.off[(size_t)L], n = w.off[(size_t)L + 1] - a;
             const int64_t want = (n + BC_WARPS - 1) / BC_WARPS;
@@ -280,7 +403,7 @@ extern "C" int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sour
             k_bc_backward<<<grid, BC_THREADS, 0, s>>>(g->out_rowptr.as<int32_t>(), g->out_colidx.as<int32_t>(),
                                                       w.order.as<int32_t>() + a, n, L, sources[k],
                                                       w.depth.as<int32_t>(), w.sigma.as<double>(),
-                                                      w.dep.as<double>(), score);
+                                                      w.coef.as<double>(), score);
             TC_LAUNCH_CHECK();
         }
     }
@@ -288,3 +411,4 @@ extern "C" int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sour
     TC_CUDA(cudaStreamSynchronize(s));
     return TC_OK;
 }
+}  // namespace tc

@@ -120,3 +120,31 @@ def test_scores_repeat_bit_for_bit(T, name):
         want_d, want_s = oracle.bc_forward(g.V, rp, ci, s)
         assert np.array_equal(depth.cpu().numpy(), want_d)
         assert np.array_equal(sigma.cpu().numpy(), want_s)
+
+
+@pytest.mark.parametrize("name", ["rmat13_sym", "big_star", "grid", "rmat", "rmat_dir", "er", "dpath", "empty"])
+@pytest.mark.parametrize("B", [1, 4, 16])
+def test_blocked_pull_levels_give_the_same_bits(T, name, B):
+    """tc_bc_tocab (TOCAB pull levels, sigma sums merged in block order) against tc_bc: the path
+    counts are integers, so depths, sigma and the scores must agree bit for bit; and both against
+    the oracle."""
+    g = BIG[name] if name in BIG else GRAPHS[name]
+    if B > g.V:
+        pytest.skip("B > V")
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, B, merge_range=1024, smem_stage=-1)
+    srcs = [0, g.V // 3, g.V - 1]
+    a = T.bc(G, srcs).cpu()
+    b = T.bc(G, srcs, part=P).cpu()
+    assert torch.equal(a, b)
+    rp, ci = g.numpy()
+    np.testing.assert_allclose(b.numpy(), oracle.bc(g.V, rp, ci, srcs), rtol=1e-12, atol=1e-9)
+
+
+def test_blocked_bc_refuses_other_partitions(T):
+    g = GRAPHS["rmat"]
+    G = _load(T, g)
+    with pytest.raises(T.TocabError):
+        T.bc(G, [0], part=T.tocab_partition(G, T.TC_PUSH, 2))
+    with pytest.raises(T.TocabError):
+        T.bc(G, [0], part=T.tocab_partition(G, T.TC_PULL, 2, order="outdegree"))

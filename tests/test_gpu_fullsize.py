@@ -161,3 +161,39 @@ def test_grid4096_bfs_bit_exact(T):
             np.testing.assert_array_equal(lv.cpu().numpy(), want)
             assert st.reached == int((want >= 0).sum())
             assert st.levels == int(want.max()) + 1
+
+
+def test_rmat22_spmv_both_forms(T):
+    """The SpMV row's workload (R-MAT 22, seeded values): the lane-group form and GC-pull with
+    8 column blocks, every row against the FP64 oracle within the FP32 summation bound (the
+    pieces of a row add one rounding per block), and GC-pull repeating bit for bit."""
+    g = gg.rmat_host(22)  # the same graph as gg.rmat(22), generated in C
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    vals = gg.edge_values(g)
+    x = torch.from_numpy(np.random.default_rng(22).standard_normal(g.V).astype(np.float32))
+    v64, x64 = vals.numpy().astype(np.float64), x.numpy().astype(np.float64)
+    want = oracle.spmv(g.V, rp, ci, v64, x64)
+    mag = oracle.spmv(g.V, rp, ci, np.abs(v64), np.abs(x64))
+    deg = np.diff(rp.astype(np.int64))
+    y = T.spmv(G, vals.cuda(), x.cuda()).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(y - want) <= (deg + 6) * 2.0 ** -24 * mag + 1e-30)
+    P = T.tocab_partition(G, T.TC_PUSH, 8, merge_range=8192)
+    T.part_set_values(P, vals.cuda())
+    yg = T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64)
+    assert np.all(np.abs(yg - want) <= (deg + 6 + 8) * 2.0 ** -24 * mag + 1e-30)
+    assert np.array_equal(yg, T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64))
+
+
+def test_rmat21_bc_blocked_levels_bit_identical(T):
+    """The BC row's larger workload (symmetrised R-MAT 21, 4 sources): blocked pull levels give
+    tc_bc's scores bit for bit, and both match the FP64 oracle."""
+    g = gg.symmetrize(gg.rmat_host(21).to("cuda")).to("cpu")
+    G = _load(T, g)
+    srcs = gg.sources(g, 4, seed=13)
+    a = T.bc(G, srcs).cpu()
+    P = T.tocab_partition(G, T.TC_PULL, 16, merge_range=8192, smem_stage=-1)
+    b = T.bc(G, srcs, part=P).cpu()
+    assert torch.equal(a, b)
+    rp, ci = g.numpy()
+    np.testing.assert_allclose(a.numpy(), oracle.bc(g.V, rp, ci, srcs), rtol=1e-11, atol=1e-8)

@@ -147,7 +147,8 @@ __device__ __forceinline__ void grid_sum_slots_last_cta(const double *part, int3
 }
 
 // Two sums at once (a in x, b in y), same protocol as grid_sum_last_cta.
-__device__ __forceinline__ void grid_sum2_last_cta(double a, double b, double *part /* 2 per CTA */,
+// Returns true in every thread of the last CTA (after the sums are written).
+__device__ __forceinline__ bool grid_sum2_last_cta(double a, double b, double *part /* 2 per CTA */,
                                                    unsigned *counter, double *out_a, double *out_b) {
     __shared__ bool am_last2;
     __shared__ double red2[32];
@@ -159,7 +160,7 @@ __device__ __forceinline__ void grid_sum2_last_cta(double a, double b, double *p
         am_last2 = (ticket == gridDim.x - 1);
     }
     __syncthreads();
-    if (!am_last2) return;
+    if (!am_last2) return false;
     __threadfence();
     double ta = 0.0, tb = 0.0;
     for (unsigned i = threadIdx.x; i < gridDim.x; i += blockDim.x) {
@@ -173,6 +174,7 @@ __device__ __forceinline__ void grid_sum2_last_cta(double a, double b, double *p
         *out_b = tb;
         *counter = 0u;
     }
+    return true;
 }
 
 }  // namespace tc

@@ -663,7 +663,9 @@ size_t merge_atomic_smem_bytes(int32_t k, int32_t B, bool fixed) {
 // Initial ranks (1/V or caller's), first contributions, their dangling mass, and the
 // fixed-point scale of the merge: 2^61 / max(1, sum |r|).  No later iteration has a larger
 // L1 mass (each is (1-d) + d * previous at most), so no vertex sum can overflow 2^63.
-__global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict__ init, UpdateArgs u, double *mass) {
+__global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict__ init, UpdateArgs u, double *mass,
+                                                         double *scale) {
+    pdl_wait();  // launched programmatically after the previous call's last kernel
     __shared__ float fred[32];
     float dsum = 0.0f, msum = 0.0f;
     const float r0 = 1.0f / (float)u.V;
@@ -678,17 +680,16 @@ __global__ void __launch_bounds__(PR_THREADS) k_pr_init(const float *__restrict_
     }
     const float bs = block_sum<float>(dsum, fred);
     const float bm = block_sum<float>(msum, fred);
-    grid_sum2_last_cta((double)bs, (double)bm, u.dpart, u.counter, u.D_next, mass);
+    if (grid_sum2_last_cta((double)bs, (double)bm, u.dpart, u.counter, u.D_next, mass) && threadIdx.x == 0) {
+        // 2^61 / 2^ceil(log2(max(1, mass))): a power of two (so FP32 values scale exactly), and
+        // a vertex sum is at most the mass, so |sum * scale| <= 2^61 < 2^63.
+        const double m = *mass;
+        int e = 0;
+        if (m > 1.0) e = (int)ceil(log2(m));
+        *scale = ldexp(1.0, 61 - e);
+    }
 }
 
-// 2^61 / 2^ceil(log2(max(1, mass))): a power of two (so FP32 values scale exactly), and a
-// vertex sum is at most the mass, so |sum * scale| <= 2^61 < 2^63.
-__global__ void k_pr_scale(const double *mass, double *scale) {
-    const double m = *mass;
-    int e = 0;
-    if (m > 1.0) e = (int)ceil(log2(m));
-    *scale = ldexp(1.0, 61 - e);
-}
 
 // ---------------------------------------------------------------------------------------------
 // Push scatter (Alg. 2; Alg. 5 when id_map != null): every edge s -> d adds contrib[s] to
@@ -1084,11 +1085,17 @@ static int pagerank_impl(const tc_graph *cg, const tc_part *part, const tc_pr_pa
             TC_CUDA(cudaMemcpyAsync(st.rank_dev, pp->init, (size_t)V * 4, cudaMemcpyHostToDevice, s));
             init_dev = st.rank_dev;
         }
-        k_pr_init<<<g_init, PR_THREADS, 0, s>>>(init_dev, u, st.mass);
-        TC_LAUNCH_CHECK();
-        k_pr_scale<<<1, 1, 0, s>>>(st.mass, st.scale);
-        TC_LAUNCH_CHECK();
-        launches += 2;
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(g_init);
+        cfg.blockDim = dim3(PR_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        TC_CUDA(cudaLaunchKernelEx(&cfg, k_pr_init, init_dev, u, st.mass, st.scale));
+        launches += 1;
     }
     for (int it = 0; it < pp->iters; ++it) {
         const bool last = it == pp->iters - 1;

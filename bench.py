@@ -405,6 +405,15 @@ def variants(args, ctx, world):
     res["bfs_tau_sweep_gteps"] = bfs_tau_sweep(T, Gs, Ps, srcs[:16], lv, stream)
     taus = res["bfs_tau_sweep_gteps"]
     res["bfs_tau_best"] = {kind: max(taus[kind], key=lambda k: taus[kind][k]) for kind in taus}
+    # pure pull BFS (the paper's topology-driven form) with every level blocked, over block
+    # counts: blocks whose frontier-bitmap slice stays in L1 turn the full-scan levels' random
+    # bitmap reads into L1 hits
+    bsweep = {}
+    for B in (8, 32, 128):
+        Pb = T.tocab_partition(Gs, T.TC_PULL, B, smem_stage=-1)
+        bsweep[str(B)] = bfs_rate(T, Gs, Pb, srcs[:16], lv, stream, 0.0, 0.0)[0]
+        del Pb
+    res["bfs_pull_blocked_by_blocks_gteps"] = bsweep
     del Gs, Ps, gs, lv
     torch.cuda.empty_cache()
     # block-count sweep around the L2 capacity (paper's source-range blocks, unstaged gather)

@@ -716,19 +716,26 @@ def e2e(args, ctx):
     rp_h = g.rowptr.cpu().pin_memory()
     ci_h = g.colidx.cpu().pin_memory()
     out_h = torch.empty(g.V, dtype=torch.float32).pin_memory()
+
+    def job():  # the headline's configuration, from host buffers to host ranks
+        G2 = T.graph_load_csr(rp_h, ci_h, V=g.V)
+        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks, block_policy=args.policy, merge_range=args.merge_range,
+                               order=args.order)
+        T.pagerank_pull(G2, P2, damping=DAMPING, iters=ITERS, out=out_h, merge=args.merge)
+        del P2, G2
+
+    for _ in range(max(args.warmup, 1)):  # untimed, like the headline's warm-up steps
+        job()
     times = []
     for i in range(3):
         torch.cuda.synchronize()
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        G2 = T.graph_load_csr(rp_h, ci_h, V=g.V)
-        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks, block_policy=args.policy)
-        T.pagerank_pull(G2, P2, damping=DAMPING, iters=ITERS, out=out_h)
+        job()
         t1.record(stream)
         t1.synchronize()
         times.append(t0.elapsed_time(t1))
-        del P2, G2
     ms = statistics.median(times)
     # the one-time preprocessing on its own (inputs already on the device)
     tl, tp = [], []
@@ -738,7 +745,8 @@ def e2e(args, ctx):
         G2 = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
         torch.cuda.synchronize()
         t1 = time.perf_counter()
-        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks, block_policy=args.policy)
+        P2 = T.tocab_partition(G2, T.TC_PULL, args.blocks, block_policy=args.policy, merge_range=args.merge_range,
+                               order=args.order)
         torch.cuda.synchronize()
         t2 = time.perf_counter()
         tl.append((t1 - t0) * 1e3)
@@ -748,7 +756,8 @@ def e2e(args, ctx):
             "load_transpose_ms": round(statistics.median(tl), 2), "partition_ms": round(statistics.median(tp), 2),
             "h2d_bytes_per_step": int(rp_h.numel() * 4 + ci_h.numel() * 4),
             "d2h_bytes_per_step": int(out_h.numel() * 4), "ms_per_step": round(ms, 3),
-            "includes": "H2D CSR + load/transpose + partition + 20 iters + D2H ranks"}
+            "includes": "H2D CSR + load/transpose + renumbering and partition + 20 iters + D2H ranks",
+            "warmup": max(args.warmup, 1)}
 
 
 # ---- the FP64 oracle timed beside the variant rows (bounded samples, single thread) ----------

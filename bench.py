@@ -398,6 +398,8 @@ def variants(args, ctx, world):
     for thr, push, key in [(0.05, 0.0, "bfs_tocab"), (-1.0, 0.0, "bfs_unblocked"),
                            (0.05, 1.0 / 24, "bfs_diropt_tocab"), (-1.0, 1.0 / 24, "bfs_diropt_unblocked")]:
         res[key + "_gteps"] = bfs_rate(T, Gs, Ps, srcs, lv, stream, thr, push)[0]
+    # the small-frontier push levels host-driven, one launch sequence and round trip per level
+    res["bfs_diropt_unblocked_no_resident_gteps"] = bfs_rate(T, Gs, Ps, srcs, lv, stream, -1.0, 1.0 / 24, 0)[0]
     res["bfs_graph"] = {"V": gs.V, "E_directed": gs.E, "sources": len(srcs)}
     res["bfs_oracle"] = oracle_bfs_rate(gs, srcs[0])
     # the TOCAB frontier threshold tau (Sec. 3.3, "frontier large enough"), swept on 16 of the
@@ -434,16 +436,17 @@ def variants(args, ctx, world):
     return res
 
 
-def bfs_rate(T, G, P, srcs, lv, stream, thr, push):
+def bfs_rate(T, G, P, srcs, lv, stream, thr, push, resident=-1):
     """GTEPS of BFS from every source (edges reached / 2, symmetrised graphs) and the levels."""
-    T.bfs_pull(G, P, srcs[0], tocab_threshold=thr, out=lv, push_threshold=push)
+    T.bfs_pull(G, P, srcs[0], tocab_threshold=thr, out=lv, push_threshold=push, resident_edges=resident)
     torch.cuda.synchronize()
     tot_ms, tot_edges, levels = 0.0, 0, 0
     for s in srcs:
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
-        _, st = T.bfs_pull(G, P, s, tocab_threshold=thr, out=lv, return_stats=True, push_threshold=push)
+        _, st = T.bfs_pull(G, P, s, tocab_threshold=thr, out=lv, return_stats=True, push_threshold=push,
+                           resident_edges=resident)
         t1.record(stream)
         t1.synchronize()
         tot_ms += t0.elapsed_time(t1)
@@ -476,10 +479,11 @@ def rmat16_row(stream, run):
     return row
 
 
-def bfs_grid_row(stream, nsrc: int = 8):
+def bfs_grid_row(stream, nsrc: int = 64):
     """BFS on the 4096 x 4096 grid with 5% of its edges removed (both directions): about 8,000
-    levels with small frontiers, so the levels run top-down (direction optimisation); pure pull
-    levels rescan every unvisited vertex per level and are not timed here."""
+    levels with small frontiers, so the levels run top-down (direction optimisation), by default
+    inside cluster-resident launches; pure pull levels rescan every unvisited vertex per level
+    and are not timed here."""
     import paper_1904_02241_gb300 as T
     g = gg.grid2d(4096, 4096, drop=0.05, seed=11, device="cuda")
     G = T.graph_load_csr(g.rowptr, g.colidx, V=g.V)
@@ -487,10 +491,12 @@ def bfs_grid_row(stream, nsrc: int = 8):
     lv = torch.empty(g.V, dtype=torch.int32, device="cuda")
     srcs = gg.sources(g, nsrc, seed=13)
     row = {"V": g.V, "E_directed": g.E, "sources": nsrc}
-    for key, thr in (("bfs_diropt_unblocked", -1.0), ("bfs_diropt_tocab", 0.05)):
-        gteps, levels = bfs_rate(T, G, P, srcs, lv, stream, thr, 1.0 / 24)
+    for key, thr, res in (("bfs_diropt_unblocked", -1.0, -1), ("bfs_diropt_tocab", 0.05, -1),
+                          ("bfs_diropt_unblocked_no_resident", -1.0, 0)):
+        gteps, levels = bfs_rate(T, G, P, srcs if res else srcs[:2], lv, stream, thr, 1.0 / 24, res)
         row[key + "_gteps"] = gteps
         row["levels_max"] = levels
+    row["no_resident_sources"] = 2
     return row
 
 

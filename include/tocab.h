@@ -339,7 +339,22 @@ typedef struct tc_bfs_params {
                                  switch to pull when the frontier's out-edges exceed 1/14 of
                                  the unvisited vertices' out-edges, and back to push when the
                                  frontier holds fewer than push_threshold * V vertices */
+    int32_t resident_edges;   /* push levels only: consecutive levels whose frontier has at most
+                                 this many vertices and out-edges run inside ONE launch of a
+                                 thread-block cluster (16 CTAs, else 8), the levels ended by the
+                                 cluster barrier instead of a host round trip (device memory:
+                                 24 x cluster size x resident_edges bytes, kept with the graph);
+                                 the frontier bitmap is rebuilt from the queue before the next
+                                 pull level.
+                                 No counterpart in the paper (its levels are host-driven): it
+                                 serves the long-diameter graphs' thousands of small levels.
+                                 0 = off, < 0 = TC_BFS_RESIDENT_DEFAULT, at most
+                                 TC_BFS_RESIDENT_MAX (else TC_ERR_INVALID_ARG); levels are
+                                 identical either way */
 } tc_bfs_params;
+
+#define TC_BFS_RESIDENT_DEFAULT 65536
+#define TC_BFS_RESIDENT_MAX (1 << 20)
 
 #define TC_BFS_TRACE 64
 typedef struct tc_bfs_stats {
@@ -349,11 +364,13 @@ typedef struct tc_bfs_stats {
     int64_t edges_reached;    /* sum of out-degrees of reached vertices */
     float   ms_total;         /* device time (profile only) */
     int32_t push_levels;      /* levels run top-down */
-    /* first TC_BFS_TRACE levels: kind (0 pull, 1 pull TOCAB, 2 push), frontier size at the
-       start of the level, device time (profile only) */
+    /* first TC_BFS_TRACE levels: kind (0 pull, 1 pull TOCAB, 2 push, 3 push inside a resident
+       launch), frontier size at the start of the level, device time (profile only; a resident
+       launch's time is shared evenly by its levels) */
     int32_t level_kind[TC_BFS_TRACE];
     int64_t level_frontier[TC_BFS_TRACE];
     float   level_ms[TC_BFS_TRACE];
+    int32_t resident_levels;  /* push levels run inside resident launches (counted in push_levels) */
 } tc_bfs_stats;
 
 /*

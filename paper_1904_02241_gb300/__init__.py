@@ -20,8 +20,8 @@ import ctypes as C
 import torch
 
 from . import _lib as L
-from ._lib import (TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE, TC_MEM_HOST,  # noqa: F401
-                   TC_MULTI_RESIDENT, TC_ORDER_NATURAL, TC_ORDER_OUTDEGREE, TC_PULL, TC_PUSH)
+from ._lib import (TC_BFS_TRACE, TC_DANGLING_DROP, TC_DANGLING_REDISTRIBUTE, TC_MEM_DEVICE,  # noqa: F401
+                   TC_MEM_HOST, TC_MULTI_RESIDENT, TC_ORDER_NATURAL, TC_ORDER_OUTDEGREE, TC_PULL, TC_PUSH)
 
 __all__ = ["graph_load_csr", "tocab_partition", "pagerank_pull", "pagerank_push", "bfs_pull", "ppr_batch", "ppr_autotune", "ppr_set_tuning", "part_set_values", "spmv_tocab",
            "multigraph_load",
@@ -433,14 +433,17 @@ def multi_autotune(mg: MultiGraph, damping: float = 0.85, iters: int = 20, strea
 
 def bfs_pull(graph: Graph, part: Partition | None, source: int, tocab_threshold: float = 0.05,
              out: torch.Tensor | None = None, profile: bool = False, stream=None, return_stats: bool = False,
-             push_threshold: float = 0.0):
+             push_threshold: float = 0.0, resident_edges: int = -1):
     """tc_bfs_pull: hop levels from source (-1 = unreachable).  push_threshold > 0 runs the
-    small-frontier levels top-down (direction optimisation)."""
+    small-frontier levels top-down (direction optimisation); consecutive push levels with at
+    most resident_edges frontier vertices and out-edges run inside one cluster launch (0 = off,
+    -1 = the library's default)."""
     if out is None:
         out = torch.empty(graph.V, dtype=torch.int32, device="cuda")
     if out.dtype != torch.int32 or out.numel() < graph.V or not out.is_contiguous():
         raise ValueError("out must be a contiguous int32 tensor with V elements")
-    bp = L.tc_bfs_params(float(tocab_threshold), _mem(out), 1 if profile else 0, float(push_threshold))
+    bp = L.tc_bfs_params(float(tocab_threshold), _mem(out), 1 if profile else 0, float(push_threshold),
+                         int(resident_edges))
     st = L.tc_bfs_stats()
     _check(L.load().tc_bfs_pull(graph.handle, part.handle if part is not None else None, int(source), C.byref(bp),
                                 out.data_ptr(), C.byref(st), _stream(stream)), "tc_bfs_pull")

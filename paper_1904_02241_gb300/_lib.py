@@ -72,7 +72,7 @@ class tc_multi_params(C.Structure):
 
 class tc_bfs_params(C.Structure):
     _fields_ = [("tocab_threshold", C.c_float), ("out_mem", C.c_int32), ("profile", C.c_int32),
-                ("push_threshold", C.c_float)]
+                ("push_threshold", C.c_float), ("resident_edges", C.c_int32)]
 
 
 TC_BFS_TRACE = 64
@@ -82,7 +82,7 @@ class tc_bfs_stats(C.Structure):
     _fields_ = [("levels", C.c_int32), ("tocab_levels", C.c_int32), ("reached", C.c_int64),
                 ("edges_reached", C.c_int64), ("ms_total", C.c_float), ("push_levels", C.c_int32),
                 ("level_kind", C.c_int32 * TC_BFS_TRACE), ("level_frontier", C.c_int64 * TC_BFS_TRACE),
-                ("level_ms", C.c_float * TC_BFS_TRACE)]
+                ("level_ms", C.c_float * TC_BFS_TRACE), ("resident_levels", C.c_int32)]
 
 
 VP = C.c_void_p

@@ -5,6 +5,8 @@
 //                     over the block's sources), then a merge kernel ORs the local bits of
 //                     all blocks per vertex range and writes levels, next and visited.
 // Levels run TOCAB only when the frontier exceeds a fraction of V (Sec. 3.3).
+#include <cooperative_groups.h>
+
 #include "tc_common_dev.cuh"
 
 namespace tc {
@@ -253,6 +255,250 @@ __global__ void __launch_bounds__(BFS_THREADS) k_bfs_push_edges(const int32_t *_
     }
 }
 
+// ---- cluster-resident push levels ------------------------------------------------------------
+// Consecutive push levels with small frontiers run inside ONE launch of a thread-block cluster:
+// the cluster's hardware barrier (release/acquire at cluster scope) ends each level, so a level
+// costs a few dependent memory round trips instead of a host round trip and five launches.  The
+// grid is exactly one cluster, so every CTA is co-scheduled by construction and no CTA waits on
+// anything but that barrier.
+// Level L: the frontier is the concatenation of the C CTAs' queue segments of level L-1 (the
+// host's vertex queue for the first level); CTA c expands the c-th slice of it in batches of
+// RES_THREADS vertices, and a CTA-wide scan of the out-degrees deals the batch's edges out one
+// per thread.  A neighbour is claimed by an atomic OR on visited, gets its level, and is appended
+// (warp-aggregated, position from a shared-memory counter) to CTA c's own segment with its
+// out-edge range, which the next level reads instead of the row offsets.  After the barrier
+// warp 0 of every CTA reads all C counters through distributed shared memory; every thread then
+// holds the same counts and takes the same decision, the host's: stop when the frontier is
+// empty, when direction optimisation switches to pull (m_f > m_u / 14), or when the next level
+// has more than `cap` vertices or out-edges.  At the end the segments are copied, in CTA order,
+// into the host's queue for the next level.  Everything written during the launch by other CTAs
+// is read with L2 loads (ld.global.cg), never through L1.
+constexpr int RES_THREADS = 1024;
+constexpr int RES_WARPS = RES_THREADS / 32;
+constexpr int RES_MAX_CTAS = 16;
+
+struct ResOut {  // written by CTA 0, thread 0 when the launch ends
+    unsigned long long front;  // frontier size of level `lvl`
+    double m_f, m_u;           // its out-edges, and those of the unvisited vertices
+    int32_t lvl;               // the next level to expand
+    int32_t levels;            // levels expanded by the launch
+};
+
+__device__ __forceinline__ void cluster_barrier() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Exclusive prefix sum over the CTA (RES_THREADS threads); *total gets the sum.  All threads call it.
+__device__ __forceinline__ int32_t res_block_scan(int32_t x, int32_t *wsum /* [RES_WARPS + 1] */, int32_t *total) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int32_t inc = x;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int32_t y = __shfl_up_sync(0xffffffffu, inc, d);
+        if (lane >= d) inc += y;
+    }
+    if (lane == 31) wsum[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        const int32_t w = wsum[lane];
+        int32_t wi = w;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t y = __shfl_up_sync(0xffffffffu, wi, d);
+            if (lane >= d) wi += y;
+        }
+        wsum[lane] = wi - w;  // exclusive over warps
+        if (lane == 31) wsum[RES_WARPS] = wi;
+    }
+    __syncthreads();
+    *total = wsum[RES_WARPS];
+    return wsum[warp] + inc - x;
+}
+
+// seg_v / seg_r: [2 parities][C CTAs][cap] vertex IDs and out-edge ranges of the claimed vertices.
+__global__ void __launch_bounds__(RES_THREADS, 1) k_bfs_push_resident(
+    const int32_t *__restrict__ rowptr, const int32_t *__restrict__ colidx, uint32_t *visited, int32_t *level,
+    int32_t *q0, int32_t *q1, int32_t *seg_v, int2 *seg_r, int64_t *trace, int32_t lvl0, int32_t n0, double mf0,
+    double mu0, int32_t cap, int32_t max_levels, ResOut *out) {
+    namespace cgs = cooperative_groups;
+    __shared__ int32_t sh_start[RES_THREADS], sh_off[RES_THREADS];
+    __shared__ int32_t wsum[RES_WARPS + 1];
+    __shared__ unsigned long long s_cnt[2][2];  // this CTA's claims by level parity: vertices, out-edges
+    __shared__ int32_t s_pre[RES_MAX_CTAS + 1];  // prefix of the segment counts (the current frontier)
+    __shared__ unsigned long long s_edges;       // out-edges of the current frontier
+    cgs::cluster_group cluster = cgs::this_cluster();
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int32_t C = (int32_t)gridDim.x, c = (int32_t)blockIdx.x;
+    if (tid < 4) s_cnt[tid >> 1][tid & 1] = 0ull;  // ordered before any claim by the scan's barriers
+    int32_t lvl = lvl0, levels = 0, n = n0;
+    double mf = mf0, mu = mu0;
+    bool first = true;  // the frontier is the host's queue (first level), else the segments
+    for (;;) {
+        const int par = lvl & 1;  // claims of this level: counters s_cnt[par], segments of parity par
+        if (!first && tid == 0) {  // read remotely before the previous barrier, by every CTA
+            s_cnt[par][0] = 0ull;
+            s_cnt[par][1] = 0ull;
+        }
+        const int32_t *hq = (lvl & 1) ? q1 : q0;
+        const int2 *in_r = seg_r + (size_t)(par ^ 1) * C * cap;
+        int32_t *out_v = seg_v + ((size_t)par * C + c) * cap;
+        int2 *out_r = seg_r + ((size_t)par * C + c) * cap;
+        const int32_t lo = (int32_t)((int64_t)n * c / C), hi = (int32_t)((int64_t)n * (c + 1) / C);
+        for (int32_t b0 = lo; b0 < hi; b0 += RES_THREADS) {
+            const int32_t i = b0 + tid;
+            int32_t s = 0, e = 0;
+            if (i < hi) {
+                if (first) {
+                    const int32_t u = __ldcg(hq + i);
+                    s = __ldg(rowptr + u);
+                    e = __ldg(rowptr + u + 1);
+                } else {  // entry i of the concatenated segments
+                    int32_t a = 0;
+                    while (a + 1 < C && s_pre[a + 1] <= i) ++a;
+                    const int2 r = __ldcg(in_r + (size_t)a * cap + (i - s_pre[a]));
+                    s = r.x;
+                    e = r.y;
+                }
+            }
+            int32_t total;
+            const int32_t off = res_block_scan(e - s, wsum, &total);
+            sh_start[tid] = s;
+            sh_off[tid] = off;
+            __syncthreads();
+            const int32_t nb = min(RES_THREADS, hi - b0);
+            for (int32_t base = warp * 32; base < total; base += RES_THREADS) {
+                const int32_t k = base + lane;
+                bool claimed = false;
+                int32_t v = 0, vs = 0, ve = 0;
+                if (k < total) {  // the last vertex of the batch whose edges start at or before k
+                    int32_t a = 0, z = nb - 1;
+                    while (a < z) {
+                        const int32_t mid = (a + z + 1) >> 1;
+                        if (sh_off[mid] <= k) a = mid; else z = mid - 1;
+                    }
+                    v = __ldg(colidx + sh_start[a] + (k - sh_off[a]));
+                    const uint32_t bit = 1u << (v & 31);
+                    claimed = !(atomicOr(visited + (v >> 5), bit) & bit);
+                }
+                if (claimed) {
+                    level[v] = lvl + 1;
+                    vs = __ldg(rowptr + v);
+                    ve = __ldg(rowptr + v + 1);
+                }
+                const unsigned cm = __ballot_sync(0xffffffffu, claimed);
+                if (cm) {
+                    const int leader = __ffs(cm) - 1;
+                    unsigned long long dg = (unsigned long long)(ve - vs);
+#pragma unroll
+                    for (int d = 16; d > 0; d >>= 1) dg += __shfl_xor_sync(0xffffffffu, dg, d);
+                    unsigned long long pos0 = 0;
+                    if (lane == leader) {
+                        pos0 = atomicAdd(&s_cnt[par][0], (unsigned long long)__popc(cm));
+                        atomicAdd(&s_cnt[par][1], dg);
+                    }
+                    pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+                    if (claimed) {
+                        const unsigned long long p = pos0 + (unsigned)__popc(cm & ((1u << lane) - 1u));
+                        if (p < (unsigned long long)cap) {  // always: a CTA claims at most the level's edges
+                            out_v[p] = v;
+                            out_r[p] = make_int2(vs, ve);
+                        }
+                    }
+                }
+            }
+            __syncthreads();  // the batch's offsets are read before the next batch overwrites them
+        }
+        ++levels;
+        cluster_barrier();
+        if (warp == 0) {  // every CTA's counters of this level, through distributed shared memory
+            unsigned long long cn = 0, ce = 0;
+            if (lane < C) {
+                const unsigned long long *rc = cluster.map_shared_rank(&s_cnt[par][0], (unsigned)lane);
+                cn = rc[0];
+                ce = rc[1];
+            }
+            unsigned long long inc = cn;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, inc, d);
+                if (lane >= d) inc += y;
+            }
+#pragma unroll
+            for (int d = 16; d > 0; d >>= 1) ce += __shfl_xor_sync(0xffffffffu, ce, d);
+            if (lane < C) s_pre[lane + 1] = (int32_t)inc;
+            if (lane == 0) {
+                s_pre[0] = 0;
+                s_edges = ce;
+            }
+        }
+        __syncthreads();
+        n = s_pre[C];
+        mf = (double)s_edges;
+        mu -= mf;
+        ++lvl;
+        first = false;
+        if (c == 0 && tid == 0 && lvl < TC_BFS_TRACE) trace[lvl] = n;
+        if (n == 0 || mf > mu / 14.0 || n > cap || mf > (double)cap || levels >= max_levels) break;
+    }
+    // the frontier of level lvl into the host's queue for it, segments in CTA order
+    {
+        const int par = (lvl - 1) & 1;
+        const int32_t *src = seg_v + ((size_t)par * C + c) * cap;
+        int32_t *dst = ((lvl & 1) ? q1 : q0) + s_pre[c];
+        const int32_t cnt = s_pre[c + 1] - s_pre[c];
+        for (int32_t i = tid; i < cnt; i += RES_THREADS) dst[i] = __ldcg(src + i);
+    }
+    if (c == 0 && tid == 0) {
+        out->front = (unsigned long long)n;
+        out->m_f = mf;
+        out->m_u = mu;
+        out->lvl = lvl;
+        out->levels = levels;
+    }
+    cluster_barrier();  // no CTA leaves while another may still read its shared memory
+}
+
+// front = the bits of the queue's vertices (the frontier bitmap after resident push levels).
+__global__ void k_queue_bits(const int32_t *__restrict__ queue, int64_t qn, uint32_t *front) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < qn; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = queue[i];
+        atomicOr(front + (v >> 5), 1u << (v & 31));
+    }
+}
+
+// Cluster size for the resident push levels: 16 CTAs when the device schedules such a cluster
+// of RES_THREADS-thread CTAs, else 8, else 0 (resident levels off).
+static int res_cluster_size(cudaStream_t s) {
+    static int chosen = -1;
+    if (chosen >= 0) return chosen;
+    chosen = 0;
+    for (int C : {16, 8}) {
+        if (C > 8 && cudaFuncSetAttribute(k_bfs_push_resident, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                         cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(C);
+        cfg.blockDim = dim3(RES_THREADS);
+        cfg.stream = s;
+        cudaLaunchAttribute at[1];
+        at[0].id = cudaLaunchAttributeClusterDimension;
+        at[0].val.clusterDim.x = C;
+        at[0].val.clusterDim.y = 1;
+        at[0].val.clusterDim.z = 1;
+        cfg.attrs = at;
+        cfg.numAttrs = 1;
+        int nclusters = 0;
+        if (cudaOccupancyMaxActiveClusters(&nclusters, k_bfs_push_resident, &cfg) == cudaSuccess && nclusters >= 1) {
+            chosen = C;
+            break;
+        }
+        cudaGetLastError();
+    }
+    return chosen;
+}
+
 // Queue of the vertices set in a bitmap (for a push level after a pull level): per word a
 // popcount, an exclusive scan (positions), then the write.
 __global__ void k_bitmap_count(const uint32_t *bits, int32_t nwords, int32_t *cnt) {
@@ -336,8 +582,27 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
     }
     bool have_queue = can_push;  // the queue q[lvl & 1] holds the current frontier
     unsigned long long front_count = 1;
-    if (!g->h_counts) TC_CUDA(cudaMallocHost(&g->h_counts, 16));
+    if (!g->h_counts) TC_CUDA(cudaMallocHost(&g->h_counts, 64));
     unsigned long long *h_cnt = g->h_counts;
+    // resident push levels: one cluster runs consecutive push levels whose frontier has at most
+    // res_cap vertices and out-edges (queue segments of res_cap entries per CTA and parity)
+    const int32_t res_cap = bp->resident_edges < 0 ? TC_BFS_RESIDENT_DEFAULT : bp->resident_edges;
+    const int res_C = (can_push && res_cap > 0) ? res_cluster_size(s) : 0;
+    int32_t *res_v = nullptr;  // [2][res_C][res_cap] queue segments
+    int2 *res_r = nullptr;     // their out-edge ranges
+    int64_t *res_trace = nullptr;
+    ResOut *res_out = nullptr;
+    if (res_C > 0) {
+        const size_t nseg = (size_t)2 * res_C * res_cap;
+        TC_TRY(g->ws_res.alloc(nseg * 12 + 64 + TC_BFS_TRACE * 8 + 64));
+        res_r = g->ws_res.as<int2>();
+        res_v = reinterpret_cast<int32_t *>(res_r + nseg);
+        res_out = reinterpret_cast<ResOut *>(reinterpret_cast<unsigned char *>(res_v + nseg) + 64 -
+                                             (reinterpret_cast<uintptr_t>(res_v + nseg) & 63));
+        res_trace = reinterpret_cast<int64_t *>(reinterpret_cast<unsigned char *>(res_out) + 64);
+    }
+    bool bits_valid = true;  // bufs[lvl & 1] holds the frontier (not after resident push levels)
+    int resident_levels = 0;
     // direction switching (Beamer et al.): edges out of the frontier (m_f) against edges out of
     // unvisited vertices (m_u); push -> pull when m_f > m_u / 14, pull -> push when the
     // frontier holds fewer than push_threshold * V vertices
@@ -370,6 +635,60 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
             stats->level_frontier[lvl] = (int64_t)front_count;
         }
         if (lev[0]) cudaEventRecord(lev[0], s);
+        if (use_push && res_C > 0 && have_queue && (int64_t)front_count <= res_cap && m_f <= (double)res_cap) {
+            // consecutive push levels in one cluster launch; the host reads where they stopped
+            cudaLaunchConfig_t cfg = {};
+            cfg.gridDim = dim3(res_C);
+            cfg.blockDim = dim3(RES_THREADS);
+            cfg.stream = s;
+            cudaLaunchAttribute at[1];
+            at[0].id = cudaLaunchAttributeClusterDimension;
+            at[0].val.clusterDim.x = res_C;
+            at[0].val.clusterDim.y = 1;
+            at[0].val.clusterDim.z = 1;
+            cfg.attrs = at;
+            cfg.numAttrs = 1;
+            cudaError_t e = cudaLaunchKernelEx(&cfg, k_bfs_push_resident, (const int32_t *)g->out_rowptr.as<int32_t>(),
+                                               (const int32_t *)g->out_colidx.as<int32_t>(), visited, level, q[0],
+                                               q[1], res_v, res_r, res_trace, (int32_t)lvl, (int32_t)front_count,
+                                               m_f, m_u, res_cap, (int32_t)(V + 1), res_out);
+            if (lev[1] && e == cudaSuccess) e = cudaEventRecord(lev[1], s);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_cnt + 2, res_out, sizeof(ResOut), cudaMemcpyDeviceToHost, s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+            if (e != cudaSuccess) { st = fail(TC_ERR_CUDA, "bfs resident levels from %d: %s", lvl, cudaGetErrorString(e)); break; }
+            ResOut ro;
+            memcpy(&ro, h_cnt + 2, sizeof(ro));
+            if (ro.levels < 1 || ro.lvl != lvl + ro.levels) { st = fail(TC_ERR_CUDA, "bfs resident levels: bad exit state"); break; }
+            if (stats) {
+                float seg_ms = 0.0f;
+                if (lev[1]) cudaEventElapsedTime(&seg_ms, lev[0], lev[1]);
+                const int hi = ro.lvl < TC_BFS_TRACE ? ro.lvl : TC_BFS_TRACE;
+                if (lvl + 1 < hi) {
+                    e = cudaMemcpy(stats->level_frontier + lvl + 1, res_trace + lvl + 1, (size_t)(hi - lvl - 1) * 8,
+                                   cudaMemcpyDeviceToHost);
+                    if (e != cudaSuccess) { st = fail(TC_ERR_CUDA, "bfs trace copy: %s", cudaGetErrorString(e)); break; }
+                }
+                for (int l = lvl; l < hi; ++l) {
+                    stats->level_kind[l] = 3;
+                    stats->level_ms[l] = seg_ms / (float)ro.levels;
+                }
+            }
+            push_levels += ro.levels;
+            resident_levels += ro.levels;
+            front_count = ro.front;
+            m_f = ro.m_f;
+            m_u = ro.m_u;
+            lvl = ro.lvl;
+            have_queue = true;
+            bits_valid = false;
+            continue;
+        }
+        if (!use_push && !bits_valid) {  // pull levels read the frontier bitmap: rebuild it from the queue
+            if (cudaMemsetAsync(front, 0, (size_t)nwords * 4, s) != cudaSuccess) { st = fail(TC_ERR_CUDA, "memset failed"); break; }
+            k_queue_bits<<<grid, BFS_THREADS, 0, s>>>(q[lvl & 1], (int64_t)front_count, front);
+            if (cudaGetLastError() != cudaSuccess) { st = fail(TC_ERR_CUDA, "launch failed"); break; }
+        }
+        bits_valid = true;
         push_levels += use_push ? 1 : 0;
         if (use_push) {
             if (!have_queue) {  // frontier came from a pull level: bitmap -> queue
@@ -444,6 +763,7 @@ static int bfs_impl(const tc_graph *cg, const tc_part *part, int32_t source, con
         stats->levels = lvl;
         stats->tocab_levels = tocab_levels;
         stats->push_levels = push_levels;
+        stats->resident_levels = resident_levels;
         stats->reached = (int64_t)hs[0];
         stats->edges_reached = (int64_t)hs[1];
         stats->ms_total = ms_total;
@@ -466,6 +786,8 @@ extern "C" int tc_bfs_pull(const tc_graph *g, const tc_part *part, int32_t sourc
         return fail(TC_ERR_INVALID_ARG, "tc_bfs_pull: bad out_mem");
     if (part && (part->g != g || part->dir != TC_PULL))
         return fail(TC_ERR_INVALID_ARG, "tc_bfs_pull: partition must be a TC_PULL partition of this graph");
+    if (params->resident_edges > TC_BFS_RESIDENT_MAX)
+        return fail(TC_ERR_INVALID_ARG, "tc_bfs_pull: resident_edges above %d", TC_BFS_RESIDENT_MAX);
     if (part && part->order != TC_ORDER_NATURAL)
         return fail(TC_ERR_UNSUPPORTED, "tc_bfs_pull: renumbered (TC_ORDER_OUTDEGREE) partitions are not supported");
     if (stats) memset(stats, 0, sizeof(*stats));

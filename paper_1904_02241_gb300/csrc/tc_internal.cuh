@@ -170,7 +170,8 @@ struct tc_graph {
     // reusable scratch (grown on demand, freed with the graph)
     tc::DevBuf ws_contrib, ws_scalars, ws_partials, ws_bits, ws_misc;
     tc::DevBuf ws_queue, ws_qcnt, ws_qpos, ws_scan;  // BFS push levels
-    unsigned long long *h_counts = nullptr;          // pinned host words read after each BFS level
+    tc::DevBuf ws_res;  // BFS resident push levels: range queues, counter slots, exit state, trace
+    unsigned long long *h_counts = nullptr;  // pinned host words read after each BFS level (8 words)
     // source of every out-edge (edge-parallel push), built on first use
     bool push_esrc_built = false;
     tc::DevBuf push_esrc;

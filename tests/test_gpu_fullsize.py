@@ -161,6 +161,7 @@ def test_grid4096_bfs_bit_exact(T):
             np.testing.assert_array_equal(lv.cpu().numpy(), want)
             assert st.reached == int((want >= 0).sum())
             assert st.levels == int(want.max()) + 1
+            assert st.resident_levels > st.levels // 2  # the small levels ran inside cluster launches
 
 
 def test_rmat22_spmv_both_forms(T):

@@ -588,6 +588,58 @@ def test_bfs_direction_optimised_bit_exact(T, name, push, tocab):
         assert st.reached == int((want >= 0).sum())
 
 
+@pytest.mark.parametrize("name", list(BFS_GRAPHS))
+@pytest.mark.parametrize("cap", [0, 1, 5, 64, -1])
+def test_bfs_resident_push_levels_bit_exact(T, name, cap):
+    """Consecutive push levels inside one cluster launch: the same levels for every cap on the
+    frontier (0 = host-driven levels only).  Small caps make the launches stop and restart; with
+    push_threshold 0.05 the R-MAT graphs switch to pull levels after resident ones, which rebuild
+    the frontier bitmap from the queue."""
+    g = BFS_GRAPHS[name]
+    G = _load(T, g)
+    P = T.tocab_partition(G, T.TC_PULL, min(4, g.V))
+    rp, ci = g.numpy()
+    for s in gg.sources(g, 3, seed=31) + [0]:
+        want = oracle.bfs(g.V, rp, ci, s)
+        for push, thr in ((1.0, -1.0), (0.05, 0.0), (0.05, -1.0)):
+            lv, st = T.bfs_pull(G, P, s, tocab_threshold=thr, push_threshold=push, resident_edges=cap,
+                                return_stats=True)
+            np.testing.assert_array_equal(lv.cpu().numpy(), want)
+            assert st.reached == int((want >= 0).sum())
+            assert st.levels == int(want.max()) + 1
+            assert 0 <= st.resident_levels <= st.push_levels <= st.levels
+            if cap == 0:
+                assert st.resident_levels == 0
+            if st.levels <= T.TC_BFS_TRACE:
+                kinds = list(st.level_kind)[:st.levels]
+                assert st.resident_levels == sum(k == 3 for k in kinds)
+
+
+def test_bfs_resident_levels_engage(T):
+    """On a grid the levels run resident until the remaining out-edges fall below 14 times the
+    frontier's (the last levels alternate pull and host-driven push), and on the R-MAT graph a
+    pull level follows resident ones (the frontier bitmap rebuilt from the queue)."""
+    g = BFS_GRAPHS["grid"]
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    want = oracle.bfs(g.V, rp, ci, 0)
+    lv, st = T.bfs_pull(G, None, 0, tocab_threshold=-1.0, push_threshold=1.0, return_stats=True)
+    np.testing.assert_array_equal(lv.cpu().numpy(), want)
+    assert st.resident_levels > st.levels // 2
+    g = BFS_GRAPHS["rmat12_sym"]
+    G = _load(T, g)
+    rp, ci = g.numpy()
+    switched = False
+    for s in gg.sources(g, 8, seed=37):
+        lv, st = T.bfs_pull(G, None, s, tocab_threshold=-1.0, push_threshold=0.05, return_stats=True)
+        np.testing.assert_array_equal(lv.cpu().numpy(), oracle.bfs(g.V, rp, ci, s))
+        kinds = list(st.level_kind)[:min(st.levels, T.TC_BFS_TRACE)]
+        switched |= any(a == 3 and b == 0 for a, b in zip(kinds, kinds[1:]))
+    assert switched
+    with pytest.raises(T.TocabError):
+        T.bfs_pull(G, None, 0, push_threshold=0.05, resident_edges=(1 << 20) + 1)
+
+
 @pytest.mark.parametrize("name,n,B", [("rmat12", 256, 3), ("rmat12", 40, 1), ("er", 130, 7), ("plc", 64, 4),
                                       ("grid", 33, 2)])
 def test_ppr_batch_tocab_parity(T, name, n, B):

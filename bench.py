@@ -156,22 +156,26 @@ class ClockSampler:
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch, from one single-pass ncu
 # capture of `bench.py --steps 2 --warmup 1 --quick` on the full workload.  Keyed by kernel, R-MAT
-# scale and block count, and tied to the library sources it was taken on (SHA-256 over
-# csrc/*.cu and *.cuh): after any change to them the figure no longer describes the kernel and
-# the bench reports null.
+# scale and block count, and tied to the sources it was taken on (SHA-256 over the files that
+# define the two kernels, the partition and staged format they read, the graph preprocessing
+# before it and the device helpers they use): after any change to those the figure no longer
+# describes the kernels and the bench reports null.
 NCU_TRAFFIC = {("k_tile_gather", 24, 179): 784808320,  # mean of two launches (786.2 and 783.4 MB)
                ("k_pull_merge_atomic<2>", 24, 179): 349928704}  # (349.7 and 350.1 MB)
-NCU_TRAFFIC_SRC = "fc0df1c7bcfba17c"
+NCU_TRAFFIC_SRC = "78a629374e781bc0"
+
+
+PULL_PATH_SOURCES = ("tc_common_dev.cuh", "tc_graph.cu", "tc_pagerank.cu", "tc_partition.cu", "tc_prims.cu",
+                     "tc_tile.cu")
 
 
 def library_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_1904_02241_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
-        if name.endswith((".cu", ".cuh")):
-            with open(os.path.join(csrc, name), "rb") as f:
-                h.update(name.encode() + b"\0" + f.read())
+    for name in PULL_PATH_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode() + b"\0" + f.read())
     return h.hexdigest()[:16]
 
 

@@ -683,11 +683,22 @@ def spmv_row(stream, scale: int = 22):
         ms_b = statistics.median(time_runs(lambda: T.spmv_tocab(P, x, out=y), 10, stream))
         gc[str(B)] = {"ms": round(ms_b, 4), "local_rows": P.num_rows, "block_width": P.block_width}
         del P
+    # GC-push (row blocks of y, FP32 atomic adds) over the same block counts
+    gp = {}
+    for B in (1, 8, 32, 128):
+        P = T.tocab_partition(A, T.TC_PULL, B, smem_stage=-1)
+        T.part_set_values(P, vals)
+        for _ in range(3):
+            T.spmv_tocab(P, x, out=y)
+        torch.cuda.synchronize()
+        ms_b = statistics.median(time_runs(lambda: T.spmv_tocab(P, x, out=y), 10, stream))
+        gp[str(B)] = {"ms": round(ms_b, 4), "local_rows": P.num_rows, "block_width": P.block_width}
+        del P
     return {"spmv": {"graph": f"rmat{scale}", "V": g.V, "E": g.E, "ms": round(ms, 4),
                      "gflops": round(2 * g.E / (ms * 1e-3) / 1e9, 2),
                      "bytes_frac": round(nbytes / (ms * 1e-3) / 1e9 / peak, 4),
                      "mapping": "lane groups per row (VWC) + CTA per hub row",
-                     "gc_pull_by_blocks": gc}}
+                     "gc_pull_by_blocks": gc, "gc_push_by_blocks": gp}}
 
 
 def bc_rows(stream):

@@ -518,24 +518,30 @@ int tc_bc_tocab(const tc_graph *g, const tc_part *part, const int32_t *sources, 
 int tc_spmv(const tc_graph *g, const float *vals, const float *x, float *y, int mem, void *stream);
 
 /*
- * tc_part_set_values -- give a TC_PUSH partition of the matrix's graph (its blocks are ranges of
- * W columns of A; its local rows are the (column block, row) pieces of Fig. 4) the values of
- * the stored entries, `vals` in the loaded CSR order (float[E], device).  The partition keeps
- * them in its own entry order (the first call also records that order: the partition's stable
- * sort again, carrying entry positions).  For GC-pull SpMV (Sec. 4).  Synchronises.
- * Errors: TC_ERR_INVALID_ARG (NULL, a pull partition), TC_ERR_UNSUPPORTED (host values),
+ * tc_part_set_values -- give a partition of the matrix's graph the values of the stored entries,
+ * `vals` in the loaded CSR order (float[E], device).  A TC_PUSH partition's blocks are ranges of
+ * W columns of A and its local rows the (column block, row) pieces of Fig. 4 (GC-pull SpMV); a
+ * TC_PULL partition's blocks are ranges of W rows of A and its local rows the (row block,
+ * column) pieces (GC-push SpMV).  The partition keeps the values in its own entry order (the
+ * first call also records that order: the partition's stable sorts again, carrying entry
+ * positions).  For the SpMV of Sec. 4.  Synchronises.
+ * Errors: TC_ERR_INVALID_ARG (NULL), TC_ERR_UNSUPPORTED (host values, a renumbered partition),
  * TC_ERR_OOM, TC_ERR_CUDA.
  */
 int tc_part_set_values(tc_part *p, const float *vals, int mem, void *stream);
 
 /*
- * tc_spmv_tocab -- y = A x with TOCAB (the GC-pull SpMV of Sec. 4, a value stream of 4 B per
- * entry): for every local row (column block b, row i), partial = sum of vals * x[col] over the
- * piece's entries (x's block b is the working set, Sec. 3.1), then the merge of Fig. 5 adds row
- * i's pieces in block order.  FP32, in a fixed order (deterministic).  A lane takes a piece below
- * 32 entries, a warp a longer one.
- *   p : a TC_PUSH partition of the graph holding A, with values set by tc_part_set_values;
- *       its merge_range k must be at most 51,200.
+ * tc_spmv_tocab -- y = A x with TOCAB (the SpMV of Sec. 4, a value stream of 4 B per entry).
+ *   TC_PUSH partition: GC-pull.  For every local row (column block b, row i), partial = sum of
+ *       vals * x[col] over the piece's entries (x's block b is the working set, Sec. 3.1), then
+ *       the merge of Fig. 5 adds row i's pieces in block order.  FP32 in a fixed order
+ *       (deterministic).  The merge_range k must be at most 51,200.
+ *   TC_PULL partition (graph's own numbering): GC-push.  y = 0, then for every local row (row
+ *       block b, column j) each entry (i, j) adds vals * x[j] into y[i] with an FP32 atomic add
+ *       (y's block b is the working set).  The order of the additions depends on timing, so the
+ *       last bits of y may differ between calls; each y[i] is within the FP32 summation bound.
+ *   In both, a lane takes a piece below 32 entries, a warp a longer one (Sec. 3.2).
+ *   p : a partition of the graph holding A, with values set by tc_part_set_values.
  *   x : float[V], y : float[V], device.
  * Asynchronous on `stream`.  Errors: TC_ERR_INVALID_ARG, TC_ERR_UNSUPPORTED, TC_ERR_CUDA.
  */

@@ -309,8 +309,8 @@ def spmv(matrix: Graph, vals: torch.Tensor, x: torch.Tensor, out: torch.Tensor |
 
 
 def part_set_values(part: "Partition", vals: torch.Tensor, stream=None):
-    """tc_part_set_values: the matrix values (CSR order, float32 on the device) for GC-pull SpMV
-    on a TC_PUSH partition."""
+    """tc_part_set_values: the matrix values (CSR order, float32 on the device) for SpMV with
+    TOCAB: GC-pull on a TC_PUSH partition, GC-push on a TC_PULL one."""
     if vals.dtype != torch.float32 or not vals.is_cuda or not vals.is_contiguous():
         raise ValueError("vals must be a contiguous float32 CUDA tensor")
     _check(L.load().tc_part_set_values(part.handle, vals.data_ptr() if vals.numel() else None, L.TC_MEM_DEVICE,
@@ -318,7 +318,8 @@ def part_set_values(part: "Partition", vals: torch.Tensor, stream=None):
 
 
 def spmv_tocab(part: "Partition", x: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """tc_spmv_tocab: y = A x through the TC_PUSH partition of A's graph (GC-pull)."""
+    """tc_spmv_tocab: y = A x through a partition of A's graph: GC-pull for a TC_PUSH partition
+    (fixed order), GC-push for a TC_PULL one (FP32 atomic adds)."""
     V = part.graph.V
     if x.dtype != torch.float32 or not x.is_cuda or not x.is_contiguous() or x.numel() < V:
         raise ValueError(f"x must be a contiguous float32 CUDA tensor with {V} elements")

@@ -171,35 +171,86 @@ __global__ void __launch_bounds__(SP_THREADS) k_spmv_merge(const float *__restri
     }
 }
 
+// GC-push (Sec. 4's SpMV in the push direction with TOCAB): the pieces of a TC_PULL partition of
+// the matrix's graph.  Piece r = (row block b, column j = id_map[r]) holds the entries (i, j) of
+// A with i in block b; x[j] is read once per piece and every entry adds vals * x[j] into y[i]
+// with an FP32 atomic add.  The pieces are stored block after block, so while a block's pieces
+// run, the atomics land in its W-entry slice of y, which the L2 holds (Sec. 3.1 with y as the
+// working set).  Load balancing as Sec. 3.2 bins it: a lane per piece below 32 entries, a warp
+// per longer one.  The order of the additions into y[i] depends on timing.
+__global__ void __launch_bounds__(SP_THREADS) k_spmv_push_pieces(const int32_t *__restrict__ rowptr,
+                                                                 const int32_t *__restrict__ colidx,
+                                                                 const float *__restrict__ pvals,
+                                                                 const int32_t *__restrict__ id_map,
+                                                                 const float *__restrict__ x, int64_t R, float *y) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nw = (int64_t)gridDim.x * (SP_THREADS / 32);
+    for (int64_t grp = (blockIdx.x * (int64_t)SP_THREADS + threadIdx.x) >> 5; grp * 32 < R; grp += nw) {
+        const int64_t r = grp * 32 + lane;
+        int32_t s = 0, e = 0;
+        float xj = 0.0f;
+        if (r < R) {
+            s = __ldg(rowptr + r);
+            e = __ldg(rowptr + r + 1);
+            xj = __ldg(x + __ldg(id_map + r));
+        }
+        if (e - s < 32)
+            for (int32_t k = s; k < e; ++k) atomicAdd(y + __ldg(colidx + k), __ldg(pvals + k) * xj);
+        unsigned long_rows = __ballot_sync(0xffffffffu, e - s >= 32);
+        while (long_rows) {
+            const int l = __ffs(long_rows) - 1;
+            long_rows &= long_rows - 1;
+            const int32_t ls = __shfl_sync(0xffffffffu, s, l), le = __shfl_sync(0xffffffffu, e, l);
+            const float xl = __shfl_sync(0xffffffffu, xj, l);
+            for (int32_t k = ls + lane; k < le; k += 32) atomicAdd(y + __ldg(colidx + k), __ldg(pvals + k) * xl);
+        }
+    }
+}
+
 }  // namespace tc
 
 extern "C" int tc_part_set_values(tc_part *p, const float *vals, int mem, void *stream) {
     using namespace tc;
     if (!p || (p->E > 0 && !vals)) return fail(TC_ERR_INVALID_ARG, "tc_part_set_values: null partition or values");
-    if (p->dir != TC_PUSH) return fail(TC_ERR_INVALID_ARG, "tc_part_set_values: needs a TC_PUSH partition");
+    if (p->dir != TC_PUSH && p->dir != TC_PULL) return fail(TC_ERR_INVALID_ARG, "tc_part_set_values: bad partition");
+    if (p->order != TC_ORDER_NATURAL)
+        return fail(TC_ERR_UNSUPPORTED, "tc_part_set_values: renumbered (TC_ORDER_OUTDEGREE) partitions are not supported");
     if (mem != TC_MEM_DEVICE) return fail(TC_ERR_UNSUPPORTED, "tc_part_set_values: vals must be a device pointer");
     cudaStream_t s = (cudaStream_t)stream;
     const int64_t E = p->E;
     DeviceCaps caps;
     TC_TRY(device_caps(&caps));
     const int grid = caps.sms * 8;
-    if (!p->pperm_built) {  // the partition's own sort again, carrying each entry's position
+    if (!p->pperm_built) {  // the partition's own sorts again, carrying each entry's position
         TC_TRY(p->pperm.alloc((size_t)(E > 0 ? E : 1) * 4));
         if (E > 0) {
-            DevBuf iota, keys, kt, vt;
+            DevBuf iota, keys, kt, vt, tpos;
             TC_TRY(iota.alloc((size_t)E * 4));
             k_iota<<<grid, 256, 0, s>>>(E, iota.as<int32_t>());
             TC_LAUNCH_CHECK();
+            TC_TRY(keys.alloc((size_t)E * 4));
+            TC_TRY(kt.alloc((size_t)E * 4));
+            TC_TRY(vt.alloc((size_t)E * 4));
+            // the entries in the order the partition's stream starts from: the CSR itself for a
+            // push partition; for a pull partition G^T, the graph load's stable sort by column
+            const int32_t *ci = p->g->out_colidx.as<int32_t>();
+            const int32_t *pos = iota.as<int32_t>();
+            if (p->dir == TC_PULL) {
+                int vbits = 0;
+                while ((1LL << vbits) < (int64_t)p->V) ++vbits;
+                TC_TRY(tpos.alloc((size_t)E * 4));
+                TC_TRY(stable_bucket_sort(ci, iota.as<int32_t>(), keys.as<int32_t>(), tpos.as<int32_t>(),
+                                          kt.as<int32_t>(), vt.as<int32_t>(), E, 1, vbits, s));
+                ci = p->g->in_colidx.as<int32_t>();
+                pos = tpos.as<int32_t>();
+            }
             if (p->B > 1) {
-                TC_TRY(keys.alloc((size_t)E * 4));
-                TC_TRY(kt.alloc((size_t)E * 4));
-                TC_TRY(vt.alloc((size_t)E * 4));
                 int bits = 0;
                 while ((1LL << bits) < (int64_t)p->B) ++bits;
-                TC_TRY(stable_bucket_sort(p->g->out_colidx.as<int32_t>(), iota.as<int32_t>(), keys.as<int32_t>(),
-                                          p->pperm.as<int32_t>(), kt.as<int32_t>(), vt.as<int32_t>(), E, p->W, bits, s));
+                TC_TRY(stable_bucket_sort(ci, pos, keys.as<int32_t>(), p->pperm.as<int32_t>(), kt.as<int32_t>(),
+                                          vt.as<int32_t>(), E, p->W, bits, s));
             } else {
-                TC_CUDA(cudaMemcpyAsync(p->pperm.p, iota.p, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
+                TC_CUDA(cudaMemcpyAsync(p->pperm.p, pos, (size_t)E * 4, cudaMemcpyDeviceToDevice, s));
             }
             TC_CUDA(cudaStreamSynchronize(s));  // the scratch is freed at the end of this block
         }
@@ -218,11 +269,25 @@ extern "C" int tc_part_set_values(tc_part *p, const float *vals, int mem, void *
 extern "C" int tc_spmv_tocab(const tc_part *p, const float *x, float *y, int mem, void *stream) {
     using namespace tc;
     if (!p || !x || !y) return fail(TC_ERR_INVALID_ARG, "tc_spmv_tocab: null partition or vector");
-    if (p->dir != TC_PUSH || !p->has_vals)
-        return fail(TC_ERR_INVALID_ARG, "tc_spmv_tocab: needs a TC_PUSH partition given values by tc_part_set_values");
+    if (!p->has_vals)
+        return fail(TC_ERR_INVALID_ARG, "tc_spmv_tocab: needs a partition given values by tc_part_set_values");
     if (mem != TC_MEM_DEVICE) return fail(TC_ERR_UNSUPPORTED, "tc_spmv_tocab: x and y must be device pointers");
     const int32_t V = p->V;
     if (V == 0) return TC_OK;
+    if (p->dir == TC_PULL) {  // GC-push: y = 0, then the pieces add into it
+        DeviceCaps caps;
+        TC_TRY(device_caps(&caps));
+        cudaStream_t s = (cudaStream_t)stream;
+        TC_CUDA(cudaMemsetAsync(y, 0, (size_t)V * 4, s));
+        if (p->R > 0) {
+            const int64_t want = (p->R + SP_THREADS - 1) / SP_THREADS;
+            const int grid = (int)(want < (int64_t)caps.sms * 16 ? want : (int64_t)caps.sms * 16);
+            k_spmv_push_pieces<<<grid, SP_THREADS, 0, s>>>(p->rowptr.as<int32_t>(), p->colidx.as<int32_t>(),
+                                                           p->pvals.as<float>(), p->id_map.as<int32_t>(), x, p->R, y);
+            TC_LAUNCH_CHECK();
+        }
+        return TC_OK;
+    }
     if ((size_t)p->k * 4 > 200 * 1024) return fail(TC_ERR_UNSUPPORTED, "tc_spmv_tocab: merge_range above 51,200");
     DeviceCaps caps;
     TC_TRY(device_caps(&caps));

@@ -130,9 +130,80 @@ def test_gc_pull_refusals(T):
     g = gg.rmat(10)
     G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
     x = torch.ones(g.V, dtype=torch.float32, device="cuda")
-    Pp = T.tocab_partition(G, T.TC_PULL, 2)
+    Pr = T.tocab_partition(G, T.TC_PULL, 2, order="outdegree")
     with pytest.raises(T.TocabError):
-        T.part_set_values(Pp, torch.ones(g.E, dtype=torch.float32, device="cuda"))
-    P = T.tocab_partition(G, T.TC_PUSH, 2)
-    with pytest.raises(T.TocabError):
-        T.spmv_tocab(P, x)  # no values yet
+        T.part_set_values(Pr, torch.ones(g.E, dtype=torch.float32, device="cuda"))  # renumbered
+    for d in (T.TC_PUSH, T.TC_PULL):
+        P = T.tocab_partition(G, d, 2)
+        with pytest.raises(T.TocabError):
+            T.spmv_tocab(P, x)  # no values yet
+
+
+# ------------------------------------------------------------------ GC-push SpMV (TOCAB, atomics)
+
+@pytest.mark.parametrize("name", ["rmat", "er", "plc", "grid", "star"])
+@pytest.mark.parametrize("B", [1, 3, 8, 64])
+def test_gc_push_matches_oracle_within_the_fp32_bound(T, name, B):
+    """Row i gets one rounded product per entry added by FP32 atomics in some order: at most
+    d_i + 1 roundings in the longest chain, whatever the order (bound taken with d_i + 6)."""
+    g = {"rmat": gg.rmat(12), "er": gg.random_small(3000, 40000, 2), "plc": gg.powerlaw_config(4000, 8, 2.2, seed=5),
+         "grid": gg.grid2d(60, 70), "star": gg.star(5000)}[name]
+    if B > g.V:
+        pytest.skip("B > V")
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+    P = T.tocab_partition(G, T.TC_PULL, B)
+    vals = gg.edge_values(g, seed=41)
+    x = torch.from_numpy(np.random.default_rng(B + 7).standard_normal(g.V).astype(np.float32))
+    T.part_set_values(P, vals.cuda())
+    rp, ci = g.numpy()
+    v64, x64 = vals.numpy().astype(np.float64), x.numpy().astype(np.float64)
+    want = oracle.spmv(g.V, rp, ci, v64, x64)
+    bound = (np.diff(rp) + 6) * 2.0 ** -24 * oracle.spmv(g.V, rp, ci, np.abs(v64), np.abs(x64))
+    for _ in range(2):  # every call within the bound (the addition order may differ)
+        y = T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64)
+        assert np.all(np.abs(y - want) <= bound + 1e-30)
+    # new values through the same partition
+    vals2 = gg.edge_values(g, seed=42)
+    T.part_set_values(P, vals2.cuda())
+    v2 = vals2.numpy().astype(np.float64)
+    y2 = T.spmv_tocab(P, x.cuda()).cpu().numpy().astype(np.float64)
+    bound2 = (np.diff(rp) + 6) * 2.0 ** -24 * oracle.spmv(g.V, rp, ci, np.abs(v2), np.abs(x64))
+    assert np.all(np.abs(y2 - oracle.spmv(g.V, rp, ci, v2, x64)) <= bound2 + 1e-30)
+
+
+def test_gc_push_permutation_matrix_is_exact(T):
+    """One entry per row: each y[i] is one product with nothing to add, so exact, and it checks
+    the value order of the pull partition (transpose, then blocks)."""
+    n = 3000
+    perm = np.random.default_rng(10).permutation(n)
+    g = gg.from_edge_list(n, np.stack([np.arange(n), perm], 1))
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=n)
+    P = T.tocab_partition(G, T.TC_PULL, 7)
+    vals = torch.from_numpy(np.random.default_rng(2).standard_normal(g.E).astype(np.float32))
+    T.part_set_values(P, vals.cuda())
+    x = torch.from_numpy(np.random.default_rng(3).standard_normal(n).astype(np.float32)).cuda()
+    y = T.spmv_tocab(P, x).cpu().numpy()
+    rp, ci = g.numpy()
+    want = np.zeros(n, np.float32)  # rows whose entry was a self loop were dropped: they are empty
+    want[np.repeat(np.arange(n), np.diff(rp))] = vals.numpy() * x.cpu().numpy()[ci]
+    np.testing.assert_array_equal(y, want)
+
+
+def test_gc_push_agrees_with_gc_pull_and_vwc_on_rmat16(T):
+    """The three SpMV forms on one matrix: each within the FP32 bound of the FP64 product."""
+    g = gg.rmat(16)
+    G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+    vals = gg.edge_values(g, seed=5)
+    x = torch.from_numpy(np.random.default_rng(5).standard_normal(g.V).astype(np.float32))
+    rp, ci = g.numpy()
+    v64, x64 = vals.numpy().astype(np.float64), x.numpy().astype(np.float64)
+    want = oracle.spmv(g.V, rp, ci, v64, x64)
+    mag = oracle.spmv(g.V, rp, ci, np.abs(v64), np.abs(x64))
+    Ppull = T.tocab_partition(G, T.TC_PUSH, 8)
+    Ppush = T.tocab_partition(G, T.TC_PULL, 8)
+    T.part_set_values(Ppull, vals.cuda())
+    T.part_set_values(Ppush, vals.cuda())
+    for y, extra in ((T.spmv(G, vals.cuda(), x.cuda()), 0), (T.spmv_tocab(Ppull, x.cuda()), 8),
+                     (T.spmv_tocab(Ppush, x.cuda()), 0)):
+        err = np.abs(y.cpu().numpy().astype(np.float64) - want)
+        assert np.all(err <= (np.diff(rp) + 6 + extra) * 2.0 ** -24 * mag + 1e-30)

@@ -399,7 +399,14 @@ def variants(args, ctx, world):
     Ps = T.tocab_partition(Gs, T.TC_PULL, args.blocks, block_policy="l2")
     lv = torch.empty(gs.V, dtype=torch.int32, device="cuda")
     srcs = gg.sources(gs, args.bfs_sources, seed=13)
-    for thr, push, key in [(0.05, 0.0, "bfs_tocab"), (-1.0, 0.0, "bfs_unblocked"),
+    # pure pull (the paper's topology-driven BFS): TOCAB with 8 blocks, every level blocked (the
+    # best of the block and threshold sweeps below), against unblocked; then the same with the
+    # L2-rule blocks and tau = 0.05, and direction-optimised levels
+    P8 = T.tocab_partition(Gs, T.TC_PULL, 8, smem_stage=-1)
+    res["bfs_tocab_gteps"] = bfs_rate(T, Gs, P8, srcs, lv, stream, 0.0, 0.0)[0]
+    res["bfs_tocab_config"] = {"blocks": P8.num_blocks, "tocab_threshold": 0.0}
+    del P8
+    for thr, push, key in [(-1.0, 0.0, "bfs_unblocked"), (0.05, 0.0, "bfs_tocab_l2_tau0.05"),
                            (0.05, 1.0 / 24, "bfs_diropt_tocab"), (-1.0, 1.0 / 24, "bfs_diropt_unblocked")]:
         res[key + "_gteps"] = bfs_rate(T, Gs, Ps, srcs, lv, stream, thr, push)[0]
     # the small-frontier push levels host-driven, one launch sequence and round trip per level

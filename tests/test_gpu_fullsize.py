@@ -95,11 +95,13 @@ def test_rmat24_pagerank_renumbered_blocks(T, rmat24):
 
 def test_rmat24_bfs_bit_exact(T, rmat24):
     """Symmetrised R-MAT 24 (~521M directed edges), two seeded sources, direction-optimised with
-    and without TOCAB pull levels, and pure pull."""
+    and without TOCAB pull levels, and pure pull (L2-rule blocks above the threshold, and 8
+    blocks in every level)."""
     g = rmat24[0]
     gs = gg.symmetrize(g)
     Gs = T.graph_load_csr(gs.rowptr, gs.colidx, V=gs.V)
     Ps = T.tocab_partition(Gs, T.TC_PULL, 0, block_policy="l2")
+    P8 = T.tocab_partition(Gs, T.TC_PULL, 8, smem_stage=-1)
     rp, ci = gs.numpy()
     for s in gg.sources(gs, 2, seed=13):
         want = oracle.bfs(gs.V, rp, ci, s)
@@ -107,6 +109,10 @@ def test_rmat24_bfs_bit_exact(T, rmat24):
             lv, st = T.bfs_pull(Gs, Ps, s, tocab_threshold=thr, push_threshold=push, return_stats=True)
             np.testing.assert_array_equal(lv.cpu().numpy(), want)
             assert st.reached == int((want >= 0).sum())
+        # the benchmark's TOCAB configuration: 8 blocks, every pull level blocked
+        lv, st = T.bfs_pull(Gs, P8, s, tocab_threshold=0.0, return_stats=True)
+        np.testing.assert_array_equal(lv.cpu().numpy(), want)
+        assert st.tocab_levels == st.levels
 
 
 def test_rmat22_ppr_batch_sampled_columns(T):

@@ -41,7 +41,7 @@ METRIC = "PageRank/BFS GTEPS on 1 GB300, TOCAB vs unblocked; % of HBM-bound roof
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="tocab", choices=["tocab", "reference"])
     ap.add_argument("--scale", type=int, default=24)

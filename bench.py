@@ -160,9 +160,9 @@ class ClockSampler:
 # define the two kernels, the partition and staged format they read, the graph preprocessing
 # before it and the device helpers they use): after any change to those the figure no longer
 # describes the kernels and the bench reports null.
-NCU_TRAFFIC = {("k_tile_gather", 24, 179): 784808320,  # mean of two launches (786.2 and 783.4 MB)
-               ("k_pull_merge_atomic<2>", 24, 179): 349928704}  # (349.7 and 350.1 MB)
-NCU_TRAFFIC_SRC = "78a629374e781bc0"
+NCU_TRAFFIC = {("k_tile_gather", 24, 179): 784667392,  # mean of two launches (786.0 and 783.3 MB)
+               ("k_pull_merge_atomic<2>", 24, 179): 349975296}  # (349.8 and 350.1 MB)
+NCU_TRAFFIC_SRC = "b4977289e92a6a36"
 
 
 PULL_PATH_SOURCES = ("tc_common_dev.cuh", "tc_graph.cu", "tc_pagerank.cu", "tc_partition.cu", "tc_prims.cu",

@@ -11,9 +11,14 @@ namespace tc {
 
 // ---- device block cache -----------------------------------------------------------------
 namespace {
+struct CachedBlock {
+    void *p;
+    uint64_t seq;  // when it was freed: the cache evicts the least recently freed first
+};
 struct BlockCache {
     std::mutex mu;
-    std::multimap<std::pair<int, size_t>, void *> free_blocks;  // (device, bytes) -> block
+    std::multimap<std::pair<int, size_t>, CachedBlock> free_blocks;  // (device, bytes) -> block
+    uint64_t next_seq = 0;
     size_t cached = 0;
     size_t held = 0;   // bytes obtained from cudaMalloc and not yet returned to the driver
     size_t limit = 0;  // 0: no cap
@@ -22,7 +27,7 @@ struct BlockCache {
         cudaGetDevice(&cur);
         for (auto &kv : free_blocks) {
             cudaSetDevice(kv.first.first);
-            cudaFree(kv.second);
+            cudaFree(kv.second.p);
             held -= kv.first.second;
         }
         if (cur >= 0) cudaSetDevice(cur);
@@ -47,7 +52,7 @@ cudaError_t cache_alloc(size_t n, void **p, size_t *got, int *device) {
         std::lock_guard<std::mutex> lk(c.mu);
         auto it = c.free_blocks.lower_bound({*device, n});
         if (it != c.free_blocks.end() && it->first.first == *device && it->first.second <= 2 * n) {
-            *p = it->second;
+            *p = it->second.p;
             *got = it->first.second;
             c.cached -= *got;
             c.free_blocks.erase(it);
@@ -110,16 +115,20 @@ void cache_free(void *p, size_t bytes, int device) {
         cudaFree(p);
         c.held -= bytes;
     } else {
-        c.free_blocks.insert({{device, bytes}, p});
+        c.free_blocks.insert({{device, bytes}, CachedBlock{p, c.next_seq++}});
         c.cached += bytes;
-        // evict the largest blocks until the cache fits its limit again
+        // evict the least recently freed blocks until the cache fits its limit again: a job that
+        // runs again asks for the sizes it freed last (evicting the largest first dropped
+        // exactly those, the big temporaries of graph load and partition)
         while (c.cached > cache_limit() && !c.free_blocks.empty()) {
-            auto last = std::prev(c.free_blocks.end());
-            cudaSetDevice(last->first.first);
-            cudaFree(last->second);
-            c.cached -= last->first.second;
-            c.held -= last->first.second;
-            c.free_blocks.erase(last);
+            auto old = c.free_blocks.begin();
+            for (auto it = c.free_blocks.begin(); it != c.free_blocks.end(); ++it)
+                if (it->second.seq < old->second.seq) old = it;
+            cudaSetDevice(old->first.first);
+            cudaFree(old->second.p);
+            c.cached -= old->first.second;
+            c.held -= old->first.second;
+            c.free_blocks.erase(old);
         }
     }
     if (cur >= 0) cudaSetDevice(cur);

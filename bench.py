@@ -514,7 +514,8 @@ def bfs_grid_row(stream, nsrc: int = 64):
 def graph_variants(args, stream, E_rmat, run):
     """The other two graph shapes of the PageRank workload: an Erdos-Renyi graph with the R-MAT's
     vertex and edge count, and the 4096 x 4096 grid with 5% of its edges removed.  Pull TOCAB
-    (the default block policy), unblocked pull and unblocked push on each."""
+    (the default block policy, in the graph's own numbering and renumbered), unblocked pull, push
+    TOCAB and unblocked on each, and the pull block-count sweep 1-64."""
     import paper_1904_02241_gb300 as T
     peak, _ = load_peaks()
     res = {}
@@ -528,16 +529,28 @@ def graph_variants(args, stream, E_rmat, run):
         out = torch.empty(g.V, dtype=torch.float32, device="cuda")
         bmin = 4 * g.E + 4 * (g.V + 1) + 12 * g.V
         row = {"V": g.V, "E": g.E, "blocks": P.num_blocks}
+        Pp = T.tocab_partition(G, T.TC_PUSH, 0)
         for key, fn in (("pull_tocab", lambda: T.pagerank_pull(G, P, damping=DAMPING, iters=ITERS, out=out)),
                         ("pull_tocab_renumbered", lambda: T.pagerank_pull(G, Pr, damping=DAMPING, iters=ITERS,
                                                                           out=out)),
                         ("pull_unblocked", lambda: T.pagerank_pull(G, None, damping=DAMPING, iters=ITERS, out=out)),
+                        ("push_tocab", lambda: T.pagerank_push(G, Pp, damping=DAMPING, iters=ITERS, out=out)),
                         ("push_unblocked", lambda: T.pagerank_push(G, None, damping=DAMPING, iters=ITERS, out=out))):
             ms = run(fn)
             row[key + "_gteps"] = round(g.E * ITERS / (ms * 1e-3) / 1e9, 2)
             row[key + "_bmin_frac"] = round(bmin / (ms / ITERS * 1e-3) / 1e9 / peak, 4)
+        row["push_tocab_blocks"] = Pp.num_blocks
+        del Pp, P, Pr
+        # the paper's source-range blocks (unstaged gather) over block counts 1-64
+        sweep = {}
+        for B in (1, 2, 4, 8, 16, 32, 64):
+            Pb = T.tocab_partition(G, T.TC_PULL, B)
+            ms = run(lambda: T.pagerank_pull(G, Pb, damping=DAMPING, iters=ITERS, out=out))
+            sweep[str(B)] = round(g.E * ITERS / (ms * 1e-3) / 1e9, 2)
+            del Pb
+        row["pull_tocab_block_sweep_gteps"] = sweep
         res[name] = row
-        del P, Pr, G, g, out
+        del G, g, out
         torch.cuda.empty_cache()
     return res
 

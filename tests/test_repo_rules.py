@@ -28,10 +28,24 @@ def test_every_entry_point_cites_its_passage():
     assert not missing, missing
 
 
+def _ignored_dirs():
+    """Top-level folders that .gitignore lists (scratch and run output, never committed)."""
+    names = {".git", "__pycache__", "_build", "baseline"}
+    try:
+        for ln in open(os.path.join(ROOT, ".gitignore")):
+            ln = ln.strip()
+            if ln and not ln.startswith("#") and ln.endswith("/") and "*" not in ln:
+                names.add(ln.strip("/").split("/")[0])
+    except OSError:
+        pass
+    return names
+
+
 def _code_files():
     out = []
+    skip = _ignored_dirs()
     for base, dirs, files in os.walk(ROOT):
-        dirs[:] = [d for d in dirs if d not in (".git", "_work", "gpurun_out", "__pycache__", "_build", "baseline")]
+        dirs[:] = [d for d in dirs if d not in skip]
         for f in files:
             if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp", ".sh")) and f != "test_repo_rules.py":
                 out.append(os.path.join(base, f))

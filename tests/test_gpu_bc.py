@@ -95,6 +95,16 @@ def test_closed_forms_on_device(T):
     assert s[0] == 30 * 29 and np.all(s[1:] == 0.0)
 
 
+@pytest.mark.parametrize("n", [64, 65, 2048, 2049])
+def test_star_hub_at_each_degree_class(T, n):
+    """The backward sweep sums a vertex's children in one of three kernels chosen by out-degree
+    (8 lanes up to 64, a warp up to the hub degree 2048, a CTA above): stars whose hub sits on
+    each side of both boundaries give the closed form n (n - 1) for the hub and 0 for the leaves."""
+    G = _load(T, gg.star(n))
+    s = T.bc(G).cpu().numpy()
+    assert s[0] == float(n * (n - 1)) and np.all(s[1:] == 0.0)
+
+
 def test_invalid_source_is_refused(T):
     G = _load(T, gg.path(5))
     with pytest.raises(T.TocabError) as e:

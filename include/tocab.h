@@ -458,11 +458,11 @@ int tc_ppr_set_tuning(tc_graph *g, int32_t hot, int32_t tile);
  * of G: depth_out[v] = hop distance from `source` (-1 when unreachable; the paper's delta) and
  * sigma_out[v] = number of shortest paths from `source` to v (the paper's sigma, FP64, exact
  * below 2^53; 0 when unreachable).  Each level runs in the cheaper direction (Sec. 3.3's
- * push-pull-push): push from the frontier list (compare-and-swap on depth, FP64 atomics on
- * sigma - exact, as every partial sum is an integer below 2^53) while the frontier holds fewer
- * than 1/14 of the vertices not yet reached, else pull over the in-rows of the unreached
- * vertices (a thread per short row, a warp per row of 32 or more in-edges).  Results do not
- * depend on the direction chosen.
+ * push-pull-push): push over the frontier's out-edges, edge-balanced (compare-and-swap on depth,
+ * FP64 atomics on sigma - exact, as every partial sum is an integer below 2^53) while those
+ * edges are fewer than 1/14 of the out-edges of the vertices not yet reached (Beamer's rule),
+ * else pull over the in-rows of the unreached vertices (a thread per short row, a warp per row
+ * of 32 or more in-edges).  Results do not depend on the direction chosen.
  *   out_mem : memory space of depth_out (int32[V]) and sigma_out (double[V]).
  * Synchronises the stream.  Errors: TC_ERR_INVALID_ARG (source outside [0, V), bad out_mem),
  * TC_ERR_OOM, TC_ERR_CUDA.
@@ -479,12 +479,13 @@ int tc_bc_forward(const tc_graph *g, int32_t source, int out_mem, int32_t *depth
  * v itself.  Scores are not normalised and count ordered targets (an undirected graph given
  * with both edge directions counts every pair twice).  FP64 throughout, computed as
  * dep[v] = sigma[v] * sum over w of (1 + dep[w]) / sigma[w] (one division per vertex); every
- * product, quotient and sum is rounded separately; a warp takes each vertex of a level, each
- * lane summing its strided share of the out-row in order and a fixed shuffle tree adding the
- * lanes, so the result is deterministic.
+ * product, quotient and sum is rounded separately.  A vertex's out-row is summed by 8 lanes (up
+ * to 64 edges), a warp (up to the graph's hub degree, 2048) or a CTA (above it), each lane in
+ * strided order and a fixed shuffle or block tree adding the lanes, so the result is
+ * deterministic.
  *   sources : host int32[num_sources], each in [0, V) (repeats allowed; 0 sources gives zeros).
  *   out_mem : memory space of scores_out (double[V]).
- * Scratch: 2 int32[V] + 3 double[V] (+ double[V] for host output), per call.
+ * Scratch: 3 int32[V] + int64[V] + 3 double[V] (+ double[V] for host output), per call.
  * Synchronises the stream.  Errors: TC_ERR_INVALID_ARG, TC_ERR_OOM, TC_ERR_CUDA.
  */
 int tc_bc(const tc_graph *g, const int32_t *sources, int32_t num_sources, int out_mem, double *scores_out,

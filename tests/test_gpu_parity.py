@@ -638,6 +638,8 @@ def test_bfs_resident_levels_engage(T):
     assert switched
     with pytest.raises(T.TocabError):
         T.bfs_pull(G, None, 0, push_threshold=0.05, resident_edges=(1 << 20) + 1)
+    lv = T.bfs_pull(G, None, 0, push_threshold=0.05, resident_edges=1 << 20)  # the largest cap
+    np.testing.assert_array_equal(lv.cpu().numpy(), oracle.bfs(g.V, rp, ci, 0))
 
 
 @pytest.mark.parametrize("name,n,B", [("rmat12", 256, 3), ("rmat12", 40, 1), ("er", 130, 7), ("plc", 64, 4),

@@ -207,3 +207,20 @@ def test_gc_push_agrees_with_gc_pull_and_vwc_on_rmat16(T):
                      (T.spmv_tocab(Ppush, x.cuda()), 0)):
         err = np.abs(y.cpu().numpy().astype(np.float64) - want)
         assert np.all(err <= (np.diff(rp) + 6 + extra) * 2.0 ** -24 * mag + 1e-30)
+
+
+@pytest.mark.parametrize("d", ["push", "pull"])
+def test_tocab_spmv_on_degenerate_matrices(T, d):
+    """No stored entries (y = 0) and a single entry, through both partition directions."""
+    direction = T.TC_PUSH if d == "push" else T.TC_PULL
+    for g in (gg.empty_graph(5), gg.from_edge_list(3, [(2, 0)])):
+        G = T.graph_load_csr(g.rowptr.cuda(), g.colidx.cuda(), V=g.V)
+        P = T.tocab_partition(G, direction, 1)
+        vals = torch.full((g.E,), 1.5, dtype=torch.float32, device="cuda")
+        T.part_set_values(P, vals)
+        x = torch.arange(1, g.V + 1, dtype=torch.float32, device="cuda")
+        y = T.spmv_tocab(P, x).cpu().numpy()
+        want = np.zeros(g.V, np.float32)
+        if g.E:
+            want[2] = 1.5 * 1.0  # row 2 holds one entry in column 0
+        np.testing.assert_array_equal(y, want)
